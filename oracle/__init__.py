@@ -1,0 +1,255 @@
+"""Plain CPU oracle for the sparse hot path (SpMV, format conversions, CG,
+BiCGSTAB, GMRES(m), mixed-precision iterative refinement).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The library product
+(``paper_2103_10116_gb300``) never imports, loads or calls it, and the two share
+no code: the arithmetic lives in ``spx_oracle.c`` (plain sequential C, IEEE
+double, compiled with ``-O2 -ffp-contract=off``), this module only marshals numpy
+arrays into it.
+
+Each function cites the passage of the paper (arXiv 2103.10116) it follows;
+the C source states the algorithm in the paper's order and notation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spx_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIBS: dict[int, C.CDLL] = {}
+
+CONVERGED, MAX_ITER, BREAKDOWN, STAGNATED = 0, 1, 2, 3
+STATUS_NAMES = {CONVERGED: "converged", MAX_ITER: "max_iter", BREAKDOWN: "breakdown",
+                STAGNATED: "stagnated"}
+
+
+class _Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("restarts", C.c_int32), ("iterations", C.c_int64),
+                ("relres_recurrence", C.c_double), ("relres_true", C.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iterations: int
+    restarts: int
+    relres_recurrence: float
+    relres_true: float
+
+
+def build(mutant: int = 0) -> str:
+    """Compile the oracle with gcc; ``mutant`` > 0 plants a known mistake (used
+    only by the mutation tests that show the pins catch it)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, f"liboracle_m{mutant}.so")
+    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           f"-DORC_MUTANT={mutant}", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def _lib(mutant: int = 0) -> C.CDLL:
+    with _LOCK:
+        if mutant not in _LIBS:
+            lib = C.CDLL(build(mutant))
+            i64, dbl, p = C.c_int64, C.c_double, C.c_void_p
+            lib.orc_csr_check.restype = C.c_int
+            lib.orc_csr_check.argtypes = [i64, i64, i64, p, p]
+            for name in ("orc_spmv_csr", "orc_spmv_csr_absbound", "orc_spmv_csr_plain"):
+                getattr(lib, name).restype = None
+                getattr(lib, name).argtypes = [i64, p, p, p, p, p]
+            lib.orc_csr_to_coo_rows.argtypes = [i64, p, p]
+            lib.orc_max_row_len.restype = i64
+            lib.orc_max_row_len.argtypes = [i64, p]
+            lib.orc_csr_to_ell.argtypes = [i64, i64, i64, p, p, p, C.c_int, p, p]
+            lib.orc_hyb_coo_count.restype = i64
+            lib.orc_hyb_coo_count.argtypes = [i64, p, i64]
+            lib.orc_csr_to_hyb.argtypes = [i64, i64, i64, p, p, p, C.c_int, p, p, p, p, p]
+            lib.orc_hyb_auto_width.restype = i64
+            lib.orc_hyb_auto_width.argtypes = [i64, p, C.c_int]
+            for name in ("orc_cg", "orc_bicgstab"):
+                getattr(lib, name).restype = C.c_int
+                getattr(lib, name).argtypes = [i64, p, p, p, p, p, dbl, i64, C.POINTER(_Info), p]
+            lib.orc_gmres.restype = C.c_int
+            lib.orc_gmres.argtypes = [i64, p, p, p, p, p, C.c_int, dbl, i64, C.POINTER(_Info), p]
+            lib.orc_ir.restype = C.c_int
+            lib.orc_ir.argtypes = [i64, p, p, p, C.c_int, p, p, dbl, dbl, C.c_int, i64,
+                                   C.POINTER(_Info)]
+            lib.orc_spmv_repeat.argtypes = [i64, p, p, p, p, p, C.c_int]
+            _LIBS[mutant] = lib
+        return _LIBS[mutant]
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _csr(rp, col, val):
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    return rp, col, val
+
+
+def csr_check(n, ncols, rp, col, mutant=0) -> bool:
+    """CSR well-formedness (Section 5: row pointers index a row-sorted COO)."""
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if rp.shape[0] != n + 1:
+        return False
+    return _lib(mutant).orc_csr_check(n, ncols, int(col.shape[0]), _ptr(rp), _ptr(col)) == 0
+
+
+def spmv_csr(rp, col, val, x, mutant=0) -> np.ndarray:
+    """y = A x for CSR A (Section 5), compensated summation in index order."""
+    rp, col, val = _csr(rp, col, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = rp.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    _lib(mutant).orc_spmv_csr(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y))
+    return y
+
+
+def spmv_csr_plain(rp, col, val, x) -> np.ndarray:
+    """The literal index-order definition of Section 5 without compensation."""
+    rp, col, val = _csr(rp, col, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = rp.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    _lib().orc_spmv_csr_plain(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y))
+    return y
+
+
+def spmv_absbound(rp, col, val, x) -> np.ndarray:
+    """(|A| |x|)_i: the scale against which a row's rounding error is judged."""
+    rp, col, val = _csr(rp, col, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = rp.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    _lib().orc_spmv_csr_absbound(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y))
+    return y
+
+
+def spmv_repeat(rp, col, val, x, reps: int) -> np.ndarray:
+    rp, col, val = _csr(rp, col, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = rp.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    _lib().orc_spmv_repeat(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y), reps)
+    return y
+
+
+def csr_to_coo_rows(rp) -> np.ndarray:
+    """COO row indices of a CSR matrix (Section 5: CSR replaces these by pointers)."""
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    n = rp.shape[0] - 1
+    row = np.empty(int(rp[-1]), dtype=np.int32)
+    _lib().orc_csr_to_coo_rows(n, _ptr(rp), _ptr(row))
+    return row
+
+
+def max_row_len(rp) -> int:
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    return int(_lib().orc_max_row_len(rp.shape[0] - 1, _ptr(rp)))
+
+
+def csr_to_ell(rp, col, val, width: int, ld: int):
+    """Column-major padded ELL: slot (i, j) at j*ld + i, padding col=-1, value +0.0."""
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val)
+    n = rp.shape[0] - 1
+    ecol = np.empty(width * ld, dtype=np.int32)
+    evals = np.empty(width * ld, dtype=val.dtype)
+    _lib().orc_csr_to_ell(n, ld, width, _ptr(rp), _ptr(col), _ptr(val), val.itemsize,
+                          _ptr(ecol), _ptr(evals))
+    return ecol, evals
+
+
+def hyb_coo_count(rp, width: int) -> int:
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    return int(_lib().orc_hyb_coo_count(rp.shape[0] - 1, _ptr(rp), width))
+
+
+def csr_to_hyb(rp, col, val, width: int, ld: int):
+    """HYB = ELL of the given width + COO (CSR order) of what does not fit."""
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val)
+    n = rp.shape[0] - 1
+    nc = hyb_coo_count(rp, width)
+    ecol = np.empty(width * ld, dtype=np.int32)
+    evals = np.empty(width * ld, dtype=val.dtype)
+    crow = np.empty(nc, dtype=np.int32)
+    ccol = np.empty(nc, dtype=np.int32)
+    cval = np.empty(nc, dtype=val.dtype)
+    _lib().orc_csr_to_hyb(n, ld, width, _ptr(rp), _ptr(col), _ptr(val), val.itemsize,
+                          _ptr(ecol), _ptr(evals), _ptr(crow), _ptr(ccol), _ptr(cval))
+    return ecol, evals, crow, ccol, cval
+
+
+def hyb_auto_width(rp, vbytes: int) -> int:
+    """Footprint-optimal ELL width of a HYB matrix."""
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    return int(_lib().orc_hyb_auto_width(rp.shape[0] - 1, _ptr(rp), vbytes))
+
+
+def _solve(fn, args, rp, col, val, b, x0, with_hist, maxit, mutant):
+    rp, col, val = _csr(rp, col, val)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = rp.shape[0] - 1
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    info = _Info()
+    hist = np.full(maxit + 2, np.nan) if with_hist else None
+    getattr(_lib(mutant), fn)(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(b), _ptr(x), *args,
+                              C.byref(info), _ptr(hist) if hist is not None else None)
+    si = SolveInfo(info.status, info.iterations, info.restarts, info.relres_recurrence,
+                   info.relres_true)
+    if with_hist:
+        return x, si, hist[: info.iterations + 1]
+    return x, si
+
+
+def cg(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
+    """Conjugate Gradient for SPD A (Section 5 names CG; textbook form)."""
+    return _solve("orc_cg", [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant)
+
+
+def bicgstab(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
+    """BiCGSTAB for general A (Section 5 names BiCGSTAB; van der Vorst form)."""
+    return _solve("orc_bicgstab", [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit,
+                  mutant)
+
+
+def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
+    """Restarted GMRES(m), MGS Arnoldi + Givens rotations (Section 5 names GMRES)."""
+    return _solve("orc_gmres", [int(m), float(tol), int(maxit)], rp, col, val, b, x0, hist,
+                  maxit, mutant)
+
+
+def ir(rp, col, val, b, solver="cg", tol=1e-10, inner_tol=1e-4, max_outer=20,
+       maxit_inner=10000, x0=None):
+    """FP64 iterative refinement around an FP32 CG / BiCGSTAB inner solve."""
+    rp, col, val = _csr(rp, col, val)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = rp.shape[0] - 1
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    info = _Info()
+    _lib().orc_ir(n, _ptr(rp), _ptr(col), _ptr(val), 0 if solver == "cg" else 1, _ptr(b),
+                  _ptr(x), float(tol), float(inner_tol), int(max_outer), int(maxit_inner),
+                  C.byref(info))
+    return x, SolveInfo(info.status, info.iterations, info.restarts, info.relres_recurrence,
+                        info.relres_true)

@@ -1,0 +1,58 @@
+"""Small test helpers: dense copies and random tiny CSR matrices.  Nothing here
+is used by the library or by the oracle."""
+import numpy as np
+
+
+def to_dense(rp, col, val, ncols=None):
+    n = len(rp) - 1
+    ncols = n if ncols is None else ncols
+    d = np.zeros((n, ncols))
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            d[i, col[k]] += val[k]
+    return d
+
+
+def random_int_csr(rng, n, ncols=None, max_len=6, allow_dup=True, lo=-8, hi=8,
+                   empty_frac=0.2):
+    """Tiny CSR with integer values: empty rows, unsorted and duplicate columns
+    and explicit zeros all occur."""
+    ncols = n if ncols is None else ncols
+    rp = [0]
+    cols, vals = [], []
+    for _ in range(n):
+        L = 0 if rng.random() < empty_frac else int(rng.integers(1, max_len + 1))
+        if not allow_dup:
+            L = min(L, ncols)
+            c = rng.choice(ncols, size=L, replace=False)
+        else:
+            c = rng.integers(0, ncols, size=L)
+        cols.extend(int(v) for v in c)
+        vals.extend(float(v) for v in rng.integers(lo, hi + 1, size=L))
+        rp.append(len(cols))
+    return (np.array(rp, dtype=np.int32), np.array(cols, dtype=np.int32),
+            np.array(vals, dtype=np.float64))
+
+
+def csr_from_dense(d):
+    rp, cols, vals = [0], [], []
+    for i in range(d.shape[0]):
+        for j in range(d.shape[1]):
+            if d[i, j] != 0.0:
+                cols.append(j)
+                vals.append(d[i, j])
+        rp.append(len(cols))
+    return (np.array(rp, dtype=np.int32), np.array(cols, dtype=np.int32),
+            np.array(vals, dtype=np.float64))
+
+
+def laplace1d(m):
+    """tridiag(-1, 2, -1) of size m, assembled here independently of synth."""
+    d = np.zeros((m, m))
+    for i in range(m):
+        d[i, i] = 2.0
+        if i > 0:
+            d[i, i - 1] = -1.0
+        if i + 1 < m:
+            d[i, i + 1] = -1.0
+    return csr_from_dense(d)
