@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark of the SpMV format sweep (and the solves built on it) on GB300.
+
+One step = one SpMV of every (matrix, value type, format) of the sweep:
+  * 27-point 3D stencil on 100^3 (n = 1,000,000, nnz = 26,463,592);
+  * power-law random matrix, n = 2,000,000, row lengths Pareto(tail 1.5) with
+    mean 16 and cap 20,000, uniform columns, N(0,1) values (nnz = 32.0M);
+  x {FP64, FP32} x {CSR (merge-path), ELL, COO, HYB}, int32 indices.  ELL of
+the power-law matrix does not fit (20,000 x 2M padded slots) and is reported
+as rejected, as the library does.
+
+value = algorithmic bytes of all SpMVs of the job / device time (GB/s), the
+byte model being CSR (V+4) nnz + 4 (n+1) + 2 V n, ELL (V+4) k n + 2 V n,
+COO (V+8) nnz + 2 V n, HYB (V+4) k n + (V+8) nnz_coo + 2 V n (x read once,
+y written once).  Every matrix is larger than the 129 MB L2 and the step
+cycles through 14 matrices, so nothing stays cached between timed steps.
+
+--impl reference times the CPU oracle (sequential C, FP64 compensated CSR
+SpMV) on the same workload and metric.  Multi-GPU (torchrun): independent
+replicas, one per GPU, no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GB/s and CG solve time vs HBM roofline; batched solves/s; p50/p99 latency"
+WORKLOAD = ("spmv_format_sweep: 27-point 3D stencil 100^3 (n=1,000,000, nnz=26,463,592) and power-law "
+            "n=2,000,000 (Pareto tail 1.5, mean 16, max 20,000 nnz/row, nnz=32,000,000); "
+            "CSR(merge-path)/ELL/COO/HYB x FP64/FP32 values, int32 indices")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(fmt: str, V: int, n: int, ncols: int, nnz: int, ell_w: int = 0, coo_nnz: int = 0) -> int:
+    """Bytes an SpMV must move at least once: stored entries, row pointers
+    (CSR), x read once and y written once."""
+    vec = V * ncols + V * n
+    if fmt == "csr":
+        return (V + 4) * nnz + 4 * (n + 1) + vec
+    if fmt == "ell":
+        return (V + 4) * ell_w * n + vec
+    if fmt == "coo":
+        return (V + 8) * nnz + vec
+    if fmt == "hyb":
+        return (V + 4) * ell_w * n + (V + 8) * coo_nnz + vec
+    raise ValueError(fmt)
+
+
+def paper_intensity(fmt: str, V: int) -> float:
+    """The paper's simplified arithmetic intensity (Section 6.3): 2 flops per
+    nonzero over 1 value + 1 index (CSR) or 1 value + 2 indices (COO)."""
+    return 2.0 / ((V + 4) if fmt == "csr" else (V + 8))
+
+
+def _src_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = ["paper_2103_10116_gb300/csrc/spmv.cu", "paper_2103_10116_gb300/csrc/dev_common.cuh",
+                  "paper_2103_10116_gb300/csrc/kstate.cuh"]
+
+
+def _traffic(key: str):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel source
+    has not changed since it was taken; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    e = t.get(key)
+    if not e or e.get("source_sha") != _src_hash(KERNEL_SOURCES):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"spx_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() in ("active", "1"):
+                        reasons.add(nm)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def build_workload():
+    from paper_2103_10116_gb300 import synth
+    mats = {"stencil27_100": synth.stencil3d_27pt(100), "powerlaw_2m": synth.powerlaw(2_000_000)}
+    return mats
+
+
+def run_gpu(args):
+    import torch
+    from paper_2103_10116_gb300 import spx
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    spx.load()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = spx.spx_ctx_create(local, stream)
+
+    mats = build_workload()
+    entries = []  # (name, fmt, V, handle, x, y, bytes, launches, x_host, y_host)
+    rejected = []
+    for mname, (rp, col, val) in mats.items():
+        n = rp.shape[0] - 1
+        nnz = col.shape[0]
+        rp_d = torch.from_numpy(rp).to(dev)
+        col_d = torch.from_numpy(col).to(dev)
+        val_d = torch.from_numpy(val).to(dev)
+        xs = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, n)).to(dev)
+        for tdt, V in ((torch.float64, 8), (torch.float32, 4)):
+            vv = val_d.to(tdt)
+            x = xs.to(tdt)
+            for fmt in ("csr", "ell", "coo", "hyb"):
+                try:
+                    with torch.cuda.stream(stream):
+                        A = spx.spx_matrix_create(ctx, fmt, rp_d, col_d, vv)
+                except spx.SpxError as e:
+                    if e.status == spx.SPX_ERR_TOO_LARGE:
+                        rejected.append(f"{mname}/{fmt}/{'f64' if V == 8 else 'f32'}")
+                        continue
+                    raise
+                info = spx.spx_matrix_get_info(A)
+                b = algorithmic_bytes(fmt, V, n, n, nnz, info["ell_width"], info["coo_nnz"])
+                launches = 2 if (fmt == "hyb" and info["coo_nnz"] > 0 and info["ell_width"] > 0) else 1
+                y = torch.empty(n, dtype=tdt, device=dev)
+                xh = x.cpu().pin_memory()
+                yh = torch.empty(n, dtype=tdt).pin_memory()
+                entries.append(dict(name=f"{mname}/{fmt}/{'f64' if V == 8 else 'f32'}", fmt=fmt, V=V, A=A, x=x, y=y,
+                                    bytes=b, launches=launches, xh=xh, yh=yh, n=n, nnz=nnz))
+        del rp_d, col_d, val_d
+    torch.cuda.synchronize()
+
+    def step(evs=None):
+        for i, e in enumerate(entries):
+            if evs is not None:
+                evs[i][0].record(stream)
+            spx.spx_spmv(ctx, e["A"], e["x"], e["y"])
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in entries]
+           for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+        dist.barrier()
+    per_entry_ms = [statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps))
+                    for i in range(len(entries))]
+    bytes_step = sum(e["bytes"] for e in entries)
+    value = bytes_step * args.steps * world / (elapsed_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    for e in entries:
+        spx.spx_spmv_host(ctx, e["A"], e["xh"], e["yh"])
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t = time.perf_counter()
+        for e in entries:
+            spx.spx_spmv_host(ctx, e["A"], e["xh"], e["yh"])
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+    e2e_step_ms = statistics.median(e2e_ms)
+    h2d = sum(e["n"] * e["V"] for e in entries)
+    d2h = sum(e["n"] * e["V"] for e in entries)
+
+    secondary = {}
+    if not args.no_solve:
+        secondary["cg_poisson128"] = cg_secondary(spx, ctx, stream, dev)
+
+    peak, peak_src = _peaks()
+    dom = int(np.argmax(per_entry_ms))
+    de = entries[dom]
+    dom_ms = per_entry_ms[dom] / de["launches"] if de["launches"] == 1 else per_entry_ms[dom]
+    achieved = de["bytes"] / (per_entry_ms[dom] * 1e-3) / 1e9
+    traffic = _traffic(de["name"])
+    result = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64,f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "spmvs_per_step": len(entries),
+            "rejected": rejected,
+            "l2": "inputs larger than L2: every matrix exceeds the 129 MB L2 and a step cycles through all of them",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "per_spmv": {e["name"]: {"us": round(per_entry_ms[i] * 1e3, 1),
+                                     "GB_s": round(e["bytes"] / (per_entry_ms[i] * 1e-3) / 1e9, 1),
+                                     "frac_of_peak": round(e["bytes"] / (per_entry_ms[i] * 1e-3) / 1e9 / peak, 3)}
+                         for i, e in enumerate(entries)},
+        },
+        "roofline": {"bound": "hbm", "kernel": de["name"], "achieved": round(achieved, 1), "peak": peak,
+                     "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback",
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "algorithmic_bytes_per_launch": de["bytes"]},
+        "e2e": {"value": round(bytes_step / (e2e_step_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": sum(e["launches"] for e in entries) * args.steps,
+        "clocks": clk,
+        "secondary": secondary,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_baseline(mats, budget_s=args.cpu_seconds)
+    for e in entries:
+        spx.spx_matrix_destroy(e["A"])
+    spx.spx_ctx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cg_secondary(spx, ctx, stream, dev):
+    """CG on the 128^3 7-point Poisson matrix to relative residual 1e-10 (FP64
+    and FP32-inner / FP64-refinement), b = A x*, x* ~ U[-1,1]: solve time."""
+    import torch
+    from paper_2103_10116_gb300 import synth
+    rp, col, val = synth.laplace3d_7pt(128)
+    n = rp.shape[0] - 1
+    out = {"n": n, "nnz": int(col.shape[0]), "tol": 1e-10}
+    with torch.cuda.stream(stream):
+        A = spx.spx_matrix_create(ctx, "ell", torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                                  torch.from_numpy(val).to(dev), flags=spx.SPX_MIXED_SHADOW)
+        xs = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, n)).to(dev)
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        spx.spx_spmv(ctx, A, xs, b)
+        for prec in ("f64", "mixed"):
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+            spx.spx_solve(ctx, A, b, x, "cg", 1e-10, 5000, precision=prec)  # warm-up (graphs, workspace)
+            x.zero_()
+            torch.cuda.synchronize()
+            info = spx.spx_solve(ctx, A, b, x, "cg", 1e-10, 5000, precision=prec)
+            err = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
+            it = info.iterations
+            # bytes per FP64 CG iteration in the 3-kernel form: ELL matrix + vectors
+            out[prec] = {"solve_ms": round(info.time_ms, 2), "iterations": it, "status": info.status_name,
+                         "relres_true": info.relres_true, "err_vs_xstar": err, "restarts": info.restarts}
+        spx.spx_matrix_destroy(A)
+    return out
+
+
+def cpu_baseline(mats, budget_s=15.0):
+    """The CPU oracle, as it stands (sequential C, compensated FP64 CSR SpMV),
+    on a bounded sample of the same workload: whole-matrix SpMVs of both sweep
+    matrices in FP64, repeated until about budget_s seconds have passed."""
+    import oracle
+    tot_b, tot_t, reps = 0, 0.0, 0
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s or reps == 0:
+        for name, (rp, col, val) in mats.items():
+            n = rp.shape[0] - 1
+            x = np.random.default_rng(1).uniform(-1, 1, n)
+            t = time.perf_counter()
+            oracle.spmv_csr(rp, col, val, x)
+            tot_t += time.perf_counter() - t
+            tot_b += algorithmic_bytes("csr", 8, n, n, col.shape[0])
+        reps += 1
+    return {"value": round(tot_b / tot_t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x (FP64 CSR SpMV of the 27-point 100^3 and power-law 2M matrices), "
+                      f"{tot_t:.1f} s of single-thread CPU time"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    import oracle
+    mats = build_workload()
+    xs = {k: np.random.default_rng(1).uniform(-1, 1, v[0].shape[0] - 1) for k, v in mats.items()}
+
+    def step():
+        b = 0
+        for name, (rp, col, val) in mats.items():
+            oracle.spmv_csr(rp, col, val, xs[name])
+            n = rp.shape[0] - 1
+            b += algorithmic_bytes("csr", 8, n, n, col.shape[0])
+        return b
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    tot = 0
+    for _ in range(args.steps):
+        tot += step()
+    el = time.perf_counter() - t
+    v = tot / el / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (reference step: FP64 CSR SpMV of both matrices by the CPU oracle)"},
+        "cpu_baseline": {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: one FP64 CSR SpMV of each sweep matrix (sequential C oracle)"},
+        "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="spx", choices=["spx", "reference"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the CG solve-time section")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "spx":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

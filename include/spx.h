@@ -1,0 +1,253 @@
+/*
+ * spx.h -- C ABI of libspx, a sparse matrix-vector product (SpMV) and Krylov
+ * solver library for NVIDIA GB300 (sm_103a).
+ *
+ * Operations and where they are defined (arXiv 2103.10116, "Porting a sparse
+ * linear algebra math library to Intel GPUs"):
+ *   - SpMV y = A x and the CSR / COO storage formats: Section 5.
+ *   - CG, BiCGSTAB, GMRES: the Krylov methods of Section 5 (textbook forms of
+ *     the references cited there).
+ *   - ELL and hybrid (ELL + COO) storage, merge-path CSR, FP32 inner / FP64
+ *     outer iterative refinement, batched solves and the request server are
+ *     library extensions; the paper has no counterpart for them.
+ *
+ * Conventions for every entry point:
+ *   - Return value: an spx_status; SPX_OK (0) on success.  No C++ exception
+ *     crosses this boundary.  On failure spx_last_error() returns a message
+ *     for the calling thread.
+ *   - Pointers are DEVICE pointers (cudaMalloc / PyTorch CUDA memory of the
+ *     context's device) unless a parameter says "host".
+ *   - Indices are int32; values are IEEE double (SPX_F64) or float (SPX_F32).
+ *   - Work is enqueued asynchronously on the context's stream unless stated
+ *     otherwise; argument errors are reported synchronously.
+ *   - Vectors passed as input and output of one call must not alias.
+ */
+#ifndef SPX_H
+#define SPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spx_ctx spx_ctx;
+typedef struct spx_matrix spx_matrix;
+typedef struct spx_batch spx_batch;
+typedef struct spx_server spx_server;
+
+typedef enum {
+    SPX_OK = 0,
+    SPX_ERR_INVALID = 1,     /* malformed argument or matrix (e.g. bad row_ptr / column index) */
+    SPX_ERR_TOO_LARGE = 2,   /* a format's padded footprint does not fit (e.g. ELL of a power-law matrix) */
+    SPX_ERR_OOM = 3,         /* device allocation failed */
+    SPX_ERR_CUDA = 4,        /* a CUDA runtime call failed; message in spx_last_error() */
+    SPX_ERR_UNSUPPORTED = 5, /* combination not implemented (e.g. kernel not valid for the format) */
+    SPX_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    SPX_ERR_NOT_FOUND = 7    /* unknown request id or export part */
+} spx_status;
+
+typedef enum { SPX_CSR = 0, SPX_ELL = 1, SPX_COO = 2, SPX_HYB = 3 } spx_format;
+typedef enum { SPX_F64 = 0, SPX_F32 = 1 } spx_dtype;
+typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2 } spx_solver;
+
+/* Arithmetic of a solve: all FP64; all FP32 (values, vectors, dots and
+ * scalars in float); or FP64 iterative refinement around an FP32 inner solve
+ * (outer residual r = b - A x and update x += d in double on the FP64 values;
+ * inner Krylov iterations in float on an FP32 copy of the values). */
+typedef enum { SPX_PREC_F64 = 0, SPX_PREC_F32 = 1, SPX_PREC_MIXED = 2 } spx_precision;
+
+typedef enum {
+    SPX_CONVERGED = 0,  /* true relative residual <= tol */
+    SPX_MAX_ITER = 1,   /* iteration limit reached first */
+    SPX_BREAKDOWN = 2,  /* a Krylov denominator became exactly zero */
+    SPX_STAGNATED = 3,  /* recurrence converged but the true residual stayed above tol after the restarts */
+    SPX_SOLVE_TIMEOUT = 4
+} spx_solve_status;
+
+/* SpMV kernel choice for a matrix (spx_matrix_set_kernel). */
+typedef enum {
+    SPX_KERNEL_AUTO = 0,        /* format default, chosen from row-length statistics */
+    SPX_KERNEL_CSR_VECTOR = 1,  /* CSR: one sub-warp of `param` lanes (1..32, power of 2) per row */
+    SPX_KERNEL_CSR_MERGE = 2,   /* CSR: merge-path split of rows + nonzeros, TMA-staged tiles */
+    SPX_KERNEL_ELL = 3,         /* ELL / HYB ELL part: one thread per `param` rows (1, 2 or 4) */
+    SPX_KERNEL_COO = 4          /* COO / HYB COO part: segmented reduction over nonzero tiles */
+} spx_kernel;
+
+/* spx_matrix_create flags */
+#define SPX_HOST_INPUT 1u     /* row_ptr / col_idx / values are host pointers */
+#define SPX_MIXED_SHADOW 2u   /* also keep an FP32 copy of FP64 values (for SPX_PREC_MIXED) */
+
+/* Device allocator supplied by the caller (for example PyTorch's caching
+ * allocator).  alloc returns NULL on failure.  stream is a cudaStream_t. */
+typedef void *(*spx_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*spx_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context bound to CUDA device `device` and stream `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  With alloc == NULL the
+ * library allocates with cudaMallocAsync / cudaFreeAsync on that stream.
+ * The context owns no user memory.  Errors: SPX_ERR_INVALID (bad device),
+ * SPX_ERR_CUDA. */
+int spx_ctx_create(spx_ctx **out, int device, void *stream, spx_alloc_fn alloc, spx_free_fn free,
+                   void *user);
+/* Destroy a context.  Matrices, batches and servers created from it must be
+ * destroyed first.  NULL is accepted. */
+int spx_ctx_destroy(spx_ctx *ctx);
+/* Rebind the context to another stream of the same device. */
+int spx_ctx_set_stream(spx_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------------ matrices */
+
+/* Create a matrix in `format` (spx_format) with value type `dtype`
+ * (spx_dtype) from CSR arrays (Section 5): row_ptr[nrows+1], col_idx[nnz],
+ * values[nnz] of type `values_dtype`.  The input arrays are borrowed for the
+ * duration of the call only (device pointers, or host pointers with
+ * SPX_HOST_INPUT); the handle owns every array it builds.  The call
+ * validates the CSR structure on the device (row_ptr[0] = 0, non-decreasing,
+ * row_ptr[nrows] = nnz, 0 <= col < ncols); duplicates, unsorted columns and
+ * explicit zeros are accepted and kept in order.  hyb_width: ELL width of the
+ * HYB format, -1 = footprint-optimal.  The call synchronises the stream once.
+ * Errors: SPX_ERR_INVALID, SPX_ERR_TOO_LARGE (ELL width x rows beyond the
+ * device budget), SPX_ERR_OOM. */
+int spx_matrix_create(spx_ctx *ctx, spx_matrix **out, int format, int dtype, int64_t nrows,
+                      int64_t ncols, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                      const void *values, int values_dtype, int64_t hyb_width, unsigned flags);
+/* Free a matrix and all its device arrays (ordered on the creating context's stream). */
+int spx_matrix_destroy(spx_matrix *A);
+
+typedef struct {
+    int32_t format, dtype;
+    int64_t nrows, ncols, nnz;
+    int64_t ell_width;    /* ELL / HYB-ELL width k (0 for CSR / COO) */
+    int64_t ell_ld;       /* leading dimension of the column-major ELL arrays (multiple of 32, >= nrows) */
+    int64_t coo_nnz;      /* entries in the COO (part) */
+    int64_t max_row_len;
+    double mean_row_len;
+    int64_t device_bytes; /* bytes of all arrays the handle owns */
+    int32_t kernel, kernel_param;
+    int32_t has_f32_shadow;
+} spx_matrix_info;
+
+/* Fill `info` (host) for matrix A.  Host-only, no device work. */
+int spx_matrix_get_info(const spx_matrix *A, spx_matrix_info *info);
+
+/* Parts of a matrix that spx_matrix_export can copy out. */
+typedef enum {
+    SPX_PART_ROW_PTR = 0, SPX_PART_COL = 1, SPX_PART_VAL = 2,        /* CSR (CSR format) */
+    SPX_PART_ELL_COL = 3, SPX_PART_ELL_VAL = 4,                      /* ELL / HYB ELL part, [width][ld] */
+    SPX_PART_COO_ROW = 5, SPX_PART_COO_COL = 6, SPX_PART_COO_VAL = 7, /* COO / HYB COO part */
+    SPX_PART_VAL_F32 = 8                                             /* FP32 shadow of the primary values */
+} spx_part;
+
+/* Copy one internal array of A into the caller's device buffer dst of
+ * dst_bytes bytes (synchronous).  *written receives the array size in bytes.
+ * Used to check conversions byte for byte.  Errors: SPX_ERR_NOT_FOUND (the
+ * format has no such part), SPX_ERR_INVALID (dst too small). */
+int spx_matrix_export(spx_ctx *ctx, const spx_matrix *A, int part, void *dst, size_t dst_bytes,
+                      size_t *written);
+
+/* Select the SpMV kernel (spx_kernel) and its parameter for A; host-only.
+ * Errors: SPX_ERR_UNSUPPORTED if the kernel does not apply to A's format. */
+int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param);
+
+/* ------------------------------------------------------------------ SpMV */
+
+/* y = A x (Section 5), x[ncols] and y[nrows] of A's dtype, device pointers,
+ * asynchronous on the context stream.  x and y must not overlap. */
+int spx_spmv(spx_ctx *ctx, const spx_matrix *A, const void *x, void *y);
+
+/* y = alpha A x + beta y (same rules as spx_spmv; alpha, beta given in double
+ * and applied in A's dtype). */
+int spx_spmv_axpby(spx_ctx *ctx, const spx_matrix *A, double alpha, const void *x, double beta,
+                   void *y);
+
+/* End-to-end SpMV from HOST memory: copies x_host (ncols values) to the
+ * device, computes y = A x and copies y back to y_host (nrows values);
+ * returns after the result is in y_host.  Staging buffers are owned by the
+ * handle.  Host buffers should be pinned for full copy bandwidth. */
+int spx_spmv_host(spx_ctx *ctx, const spx_matrix *A, const void *x_host, void *y_host);
+
+/* ------------------------------------------------------------------ BLAS-1 */
+
+/* *result = sum_i x_i y_i with a deterministic two-stage device reduction
+ * (the global synchronisation that Section 6.2 notes for a dot product).
+ * result is a device scalar of the dtype. */
+int spx_dot(spx_ctx *ctx, int dtype, int64_t n, const void *x, const void *y, void *result);
+/* y = alpha x + beta y (device vectors of the dtype). */
+int spx_axpby(spx_ctx *ctx, int dtype, int64_t n, double alpha, const void *x, double beta,
+              void *y);
+
+/* ------------------------------------------------------------------ solvers */
+
+typedef struct {
+    int32_t status;            /* spx_solve_status */
+    int32_t restarts;          /* restarts after a failed true-residual check (IR: outer cycles) */
+    int64_t iterations;        /* Krylov iterations (one SpMV each for CG / GMRES, two for BiCGSTAB) */
+    double relres_recurrence;  /* last recurrence (or estimated) relative residual */
+    double relres_true;        /* ||b - A x|| / ||b|| formed at exit in FP64 */
+    double time_ms;            /* wall time of the call */
+    int64_t inner_iterations;  /* SPX_PREC_MIXED: total FP32 inner iterations */
+} spx_solve_info;
+
+/* Solve A x = b (Section 5's Krylov methods).  b[n] and x[n] are device
+ * vectors of A's dtype (double for SPX_PREC_MIXED, which needs an FP64 matrix
+ * created with SPX_MIXED_SHADOW); x holds the initial guess on entry and the
+ * solution on exit.  solver: spx_solver; restart: GMRES restart length m
+ * (ignored otherwise); precision: spx_precision.  Stopping: recurrence
+ * residual ||r|| / ||b|| <= tol, then the true residual is formed; if it is
+ * above tol the method restarts from x (at most 3 times).  b = 0 gives x = 0.
+ * Synchronous: returns after `info` (host) is filled.  Non-convergence is
+ * reported in info->status, not as an error code.  Workspace is cached in the
+ * matrix handle.  Errors: SPX_ERR_INVALID, SPX_ERR_UNSUPPORTED, SPX_ERR_OOM. */
+int spx_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol,
+              int64_t max_iter, int restart, int precision, spx_solve_info *info);
+
+/* Run exactly `iterations` Krylov iterations without convergence checks
+ * (fixed-work throughput mode, Section 6.4 runs 1,000 iterations).  Same
+ * arguments as spx_solve; info->relres_true is formed at the end. */
+int spx_solve_fixed(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
+                    int64_t iterations, int restart, int precision, spx_solve_info *info);
+
+/* ------------------------------------------------------------------ batched */
+
+/* A batch of nsys independent square CSR systems stored back to back.
+ * row_off[nsys+1] and nnz_off[nsys+1] are HOST int64 prefix offsets;
+ * row_ptr holds, for system s, its LOCAL row pointer (n_s + 1 entries,
+ * starting at 0) at row_ptr[row_off[s] + s]; col_idx (local column indices)
+ * and values (dtype) hold system s at [nnz_off[s], nnz_off[s+1]).
+ * Device pointers, copied into the handle.  Errors: SPX_ERR_INVALID, SPX_ERR_OOM. */
+int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_t nsys, const int64_t *row_off,
+                     const int64_t *nnz_off, const int32_t *row_ptr, const int32_t *col_idx,
+                     const void *values, unsigned flags);
+int spx_batch_destroy(spx_batch *B);
+
+/* Solve all systems of B in one persistent kernel launch (CG or BiCGSTAB),
+ * b and x concatenated by row_off (device, dtype of the batch; x is the
+ * initial guess on entry).  infos: HOST array of nsys entries, or NULL.
+ * precision SPX_PREC_MIXED runs FP32 batched inner solves inside FP64
+ * refinement.  Synchronous. */
+int spx_batch_solve(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int solver, double tol,
+                    int64_t max_iter, int precision, spx_solve_info *infos);
+
+/* Time the candidate tile shapes of the batched kernel on B (threads per
+ * system) and keep the fastest for later spx_batch_solve calls.
+ * *chosen receives the threads per system picked.  Synchronous. */
+int spx_batch_tune(spx_ctx *ctx, spx_batch *B, int solver, int precision, int *chosen);
+
+/* ------------------------------------------------------------------ errors */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *spx_last_error(void);
+/* Static name of a status code. */
+const char *spx_status_str(int status);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int spx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPX_H */

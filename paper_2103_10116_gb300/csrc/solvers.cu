@@ -1,0 +1,989 @@
+// solvers.cu -- Krylov solvers on the device: CG, BiCGSTAB, restarted GMRES(m),
+// and FP64 iterative refinement around an FP32 inner solve.
+//
+// The methods are the ones Section 5 of arXiv 2103.10116 names (CG for SPD
+// systems; BiCGSTAB and GMRES for general ones; GMRES orthogonalises each new
+// direction against all previous ones).  The GPU form differs from a textbook
+// loop only in scheduling:
+//   * every scalar (alpha, beta, omega, rho, norms, Hessenberg column) stays
+//     on the device, updated by the last block of the kernel that reduces it;
+//   * an iteration is a fixed sequence of fused kernels (SpMV with a dot
+//     epilogue, vector update with a dot, direction update), each returning
+//     at once once the solve has stopped, so the host enqueues a chunk of
+//     iterations as one CUDA graph and reads the stop flag once per chunk;
+//   * GMRES orthogonalises with classical Gram-Schmidt applied twice (CGS2),
+//     which reads the Krylov basis in long coalesced streams instead of one
+//     dependent dot product per basis vector (modified Gram-Schmidt).
+// Convergence policy: recurrence residual ||r||/||b|| <= tol, then the true
+// residual b - A x is formed; if it misses tol the solve restarts from x (at
+// most 3 times, then STAGNATED).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dev_common.cuh"
+#include "kstate.cuh"
+#include "spx_internal.cuh"
+
+namespace spx {
+
+constexpr int kVB = 256;        // block of the vector kernels
+constexpr int kGmKmax = 32;     // largest GMRES restart length (basis held in registers per row)
+constexpr int kMaxRestarts = 3;
+
+// ------------------------------------------------------------------ GMRES state
+template <class T> struct GState {
+    T bnorm;     // ||b||
+    T tol;       // relative tolerance
+    T beta;      // ||r|| at the start of the cycle
+    T relres;    // residual estimate |g_{j+1}| / ||b||, or the true one after a restart
+    int done;    // solve finished
+    int skip;    // Arnoldi kernels return at once (done or cycle stopped)
+    int cyc_stop;
+    int est_conv;  // last cycle stopped because the estimate met tol
+    int jdone;     // Arnoldi steps completed in the current cycle
+    int status;
+    int restarts;  // cycles that ended on the estimate but failed the true residual
+    int m;
+    long long iters, maxit;
+};
+
+// small per-solve arrays of GMRES (device): H[(m+1) x m] row-major, cs, sn, g, y, h1, h2
+template <class T> struct GSmall {
+    T *H, *cs, *sn, *g, *y, *h1, *h2;
+};
+
+// ------------------------------------------------------------------ workspace
+struct SolverWork {
+    int dtype = -1, solver = -1, m = 0;
+    int64_t n = 0, ld = 0;
+    int nvec = 0;
+    DBuf vecs, state, dots, red, ticket, small;
+    int red_grid = 0;
+    void *host = nullptr;  // pinned copy of the state
+    // CUDA graph of one chunk of iterations
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey[8] = {0};
+    // mixed precision
+    SolverWork *inner = nullptr;
+    DBuf ir;  // r (FP64), r32, d32
+};
+
+void solver_work_release(spx_ctx *ctx, SolverWork *w)
+{
+    if (!w) return;
+    if (w->gexec) cudaGraphExecDestroy(w->gexec);
+    DBuf *bufs[] = {&w->vecs, &w->state, &w->dots, &w->red, &w->ticket, &w->small, &w->ir};
+    for (DBuf *b : bufs) dbuf_free(ctx, *b);
+    if (w->host) cudaFreeHost(w->host);
+    solver_work_release(ctx, w->inner);
+    delete w;
+}
+
+void solver_work_free(spx_matrix *A)
+{
+    if (A->work) {
+        cudaStreamSynchronize(A->ctx->stream);
+        solver_work_release(A->ctx, A->work);
+    }
+    A->work = nullptr;
+}
+
+static int nvec_for(int solver, int m)
+{
+    if (solver == SPX_CG) return 4;        // r, p, q, scratch
+    if (solver == SPX_BICGSTAB) return 7;  // r, rh, p, v, s, t, scratch
+    return m + 2;                          // V[0..m], scratch
+}
+
+template <class T>
+static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, int m)
+{
+    const int dtype = sizeof(T) == 8 ? SPX_F64 : SPX_F32;
+    if (wk && (wk->dtype != dtype || wk->n != n || wk->solver != solver || wk->m != m)) {
+        SolverWork *inner = wk->inner;
+        wk->inner = nullptr;
+        cudaStreamSynchronize(ctx->stream);
+        solver_work_release(ctx, wk);
+        wk = nullptr;
+        if (inner) {
+            wk = new SolverWork();
+            wk->inner = inner;
+        }
+    }
+    if (!wk) wk = new SolverWork();
+    if (wk->vecs.p) return SPX_OK;
+    wk->dtype = dtype;
+    wk->n = n;
+    wk->solver = solver;
+    wk->m = m;
+    wk->ld = (int64_t)round_up((size_t)(n > 0 ? n : 1), 64);
+    wk->nvec = nvec_for(solver, m);
+    SPX_TRY(dbuf_alloc(ctx, wk->vecs, (size_t)wk->nvec * wk->ld * sizeof(T)));
+    SPX_TRY(dbuf_alloc(ctx, wk->state, 512));
+    SPX_TRY(dbuf_alloc(ctx, wk->dots, 64));
+    wk->red_grid = ctx->sm_count * 4;
+    SPX_TRY(dbuf_alloc(ctx, wk->red, (size_t)wk->red_grid * (kGmKmax + 2) * 8));
+    SPX_TRY(dbuf_alloc(ctx, wk->ticket, 64));
+    SPX_CUDA(cudaMemsetAsync(wk->ticket.p, 0, 64, ctx->stream));
+    SPX_TRY(dbuf_alloc(ctx, wk->small, (size_t)((m + 1) * m + 4 * (m + 2) + 2 * (kGmKmax + 2) + 16) * 8));
+    if (!wk->host) SPX_CUDA(cudaMallocHost(&wk->host, 512));
+    return SPX_OK;
+}
+
+// ------------------------------------------------------------------ fused vector kernels
+// Each returns at once when *skip is set (by an earlier kernel), reduces its
+// dots deterministically and lets the last block update the scalar state.
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_dot_fin(int64_t n, const T *__restrict__ a, const T *__restrict__ b, int fin, KState<T> *st,
+              T *partials, unsigned *ticket)
+{
+    T d0 = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB)
+        d0 = fma(a[i], b[i], d0);
+    grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, fin, st, partials, ticket);
+}
+
+// CG: x += alpha p; r -= alpha q; rho' = r.r
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_cg_xr(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ q,
+            KState<T> *st, T *partials, unsigned *ticket)
+{
+    if (st->done) return;
+    const T alpha = st->alpha;
+    T d0 = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        d0 = fma(ri, ri, d0);
+    }
+    grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, FIN_CG_RHO, st, partials, ticket);
+}
+
+// CG: p = r + beta p
+template <class T>
+__global__ void __launch_bounds__(kVB) k_cg_p(int64_t n, const T *__restrict__ r, T *__restrict__ p, const KState<T> *st)
+{
+    if (st->done) return;
+    const T beta = st->beta;
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+// BiCGSTAB: p = r + beta (p - omega v)
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_bi_p(int64_t n, const T *__restrict__ r, T *__restrict__ p, const T *__restrict__ v, const KState<T> *st)
+{
+    if (st->done) return;
+    const T beta = st->beta, omega = st->omega;
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB)
+        p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+}
+
+// BiCGSTAB: s = r - alpha v; s.s
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_bi_s(int64_t n, const T *__restrict__ r, const T *__restrict__ v, T *__restrict__ s, KState<T> *st,
+           T *partials, unsigned *ticket)
+{
+    if (st->done) return;
+    const T alpha = st->alpha;
+    T d0 = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+        const T si = fma(-alpha, v[i], r[i]);
+        s[i] = si;
+        d0 = fma(si, si, d0);
+    }
+    grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, FIN_BI_S, st, partials, ticket);
+}
+
+// BiCGSTAB: x += alpha p + omega s; r = s - omega t  (or, converged on s:
+// x += alpha p; r = s); dots r.r and r^.r
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_bi_xr(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ rh, const T *__restrict__ p,
+            const T *__restrict__ s, const T *__restrict__ t, KState<T> *st, T *partials, unsigned *ticket)
+{
+    if (st->done) return;
+    const T alpha = st->alpha, omega = st->omega;
+    const bool sconv = st->s_conv != 0;
+    T d0 = T(0), d1 = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+        const T si = s[i];
+        T ri;
+        if (sconv) {
+            x[i] = fma(alpha, p[i], x[i]);
+            ri = si;
+        } else {
+            x[i] = fma(omega, si, fma(alpha, p[i], x[i]));
+            ri = fma(-omega, t[i], si);
+        }
+        r[i] = ri;
+        d0 = fma(ri, ri, d0);
+        d1 = fma(rh[i], ri, d1);
+    }
+    grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, FIN_BI_R, st, partials, ticket);
+}
+
+// ------------------------------------------------------------------ GMRES kernels
+// Basis V[k] = base + k*ld, k = 0..m.  The Arnoldi step j forms w = A v_j in
+// V[j+1], then CGS2: h1 = V_j^T w; w -= V_j h1; h2 = V_j^T w; w -= V_j h2;
+// h = h1 + h2; H(j+1, j) = ||w||; v_{j+1} = w / ||w||.
+
+// Multi-dot h1[k] = v_k . w, k = 0..j (j < kGmKmax); last block finishes.
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_gm_proj(int64_t n, int64_t ld, const T *__restrict__ V, int j, GState<T> *gs, T *hout, T *partials,
+              unsigned *ticket)
+{
+    if (gs->skip) return;
+    const T *w = V + (int64_t)(j + 1) * ld;
+    T acc[kGmKmax];
+#pragma unroll
+    for (int k = 0; k < kGmKmax; ++k) acc[k] = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+        const T wi = w[i];
+#pragma unroll
+        for (int k = 0; k < kGmKmax; ++k)
+            if (k <= j) acc[k] = fma(V[(int64_t)k * ld + i], wi, acc[k]);
+    }
+    __shared__ T sred[kVB / 32][kGmKmax];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kGmKmax; ++k)
+        if (k <= j) {
+            const T s = warp_sum(acc[k]);
+            if (lane == 0) sred[wp][k] = s;
+        }
+    __syncthreads();
+    if (threadIdx.x <= j) {
+        T s = T(0);
+        for (int q = 0; q < kVB / 32; ++q) s += sred[q][threadIdx.x];
+        partials[(int64_t)blockIdx.x * kGmKmax + threadIdx.x] = s;
+    }
+    if (!last_block(ticket, gridDim.x)) return;
+    if (threadIdx.x <= j) {
+        T s = T(0);
+        for (unsigned b = 0; b < gridDim.x; ++b) s += ldcg(partials + (int64_t)b * kGmKmax + threadIdx.x);
+        hout[threadIdx.x] = s;
+    }
+}
+
+// w -= V_j hin; PASS 1 also forms h2 = V_j^T w (new w); PASS 2 forms ||w||^2
+// and the last block updates the Hessenberg column, the Givens rotations and
+// the residual estimate.
+template <class T, int PASS>
+__global__ void __launch_bounds__(kVB)
+    k_gm_orth(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, T *partials,
+              unsigned *ticket)
+{
+    if (gs->skip) return;
+    T *w = V + (int64_t)(j + 1) * ld;
+    const T *hin = PASS == 1 ? sm.h1 : sm.h2;
+    __shared__ T hs[kGmKmax];
+    if (threadIdx.x < kGmKmax) hs[threadIdx.x] = threadIdx.x <= j ? ldcg(hin + threadIdx.x) : T(0);
+    __syncthreads();
+    T acc[kGmKmax];
+#pragma unroll
+    for (int k = 0; k < kGmKmax; ++k) acc[k] = T(0);
+    T ww = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+        T vk[kGmKmax];
+        T wi = w[i];
+#pragma unroll
+        for (int k = 0; k < kGmKmax; ++k)
+            if (k <= j) {
+                vk[k] = V[(int64_t)k * ld + i];
+                wi = fma(-hs[k], vk[k], wi);
+            }
+        w[i] = wi;
+        if (PASS == 1) {
+#pragma unroll
+            for (int k = 0; k < kGmKmax; ++k)
+                if (k <= j) acc[k] = fma(vk[k], wi, acc[k]);
+        } else {
+            ww = fma(wi, wi, ww);
+        }
+    }
+    __shared__ T sred[kVB / 32][kGmKmax];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (PASS == 1) {
+#pragma unroll
+        for (int k = 0; k < kGmKmax; ++k)
+            if (k <= j) {
+                const T s = warp_sum(acc[k]);
+                if (lane == 0) sred[wp][k] = s;
+            }
+        __syncthreads();
+        if (threadIdx.x <= j) {
+            T s = T(0);
+            for (int q = 0; q < kVB / 32; ++q) s += sred[q][threadIdx.x];
+            partials[(int64_t)blockIdx.x * kGmKmax + threadIdx.x] = s;
+        }
+        if (!last_block(ticket, gridDim.x)) return;
+        if (threadIdx.x <= j) {
+            T s = T(0);
+            for (unsigned b = 0; b < gridDim.x; ++b) s += ldcg(partials + (int64_t)b * kGmKmax + threadIdx.x);
+            sm.h2[threadIdx.x] = s;
+        }
+        return;
+    }
+    // PASS 2: ||w||^2, then the scalar work of step j in one thread
+    __shared__ T red[kVB / 32];
+    const T bsum = block_sum<T, kVB>(ww, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bsum;
+    if (!last_block(ticket, gridDim.x)) return;
+    T s = T(0);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVB) s += ldcg(partials + b);
+    s = block_sum<T, kVB>(s, red);
+    if (threadIdx.x != 0) return;
+    const int m = gs->m;
+    T *H = sm.H;
+    const T hn = sqrt(s);
+    for (int k = 0; k <= j; ++k) H[k * m + j] = ldcg(sm.h1 + k) + ldcg(sm.h2 + k);
+    H[(j + 1) * m + j] = hn;
+    for (int k = 0; k < j; ++k) {  // earlier rotations on column j
+        const T a = H[k * m + j], c = H[(k + 1) * m + j];
+        H[k * m + j] = sm.cs[k] * a + sm.sn[k] * c;
+        H[(k + 1) * m + j] = -sm.sn[k] * a + sm.cs[k] * c;
+    }
+    const T a = H[j * m + j], c = H[(j + 1) * m + j];
+    const T d = hypot(a, c);
+    sm.cs[j] = d == T(0) ? T(1) : a / d;
+    sm.sn[j] = d == T(0) ? T(0) : c / d;
+    H[j * m + j] = d;
+    H[(j + 1) * m + j] = T(0);
+    const T gj = sm.g[j];
+    sm.g[j + 1] = -sm.sn[j] * gj;
+    sm.g[j] = sm.cs[j] * gj;
+    gs->iters += 1;
+    gs->jdone = j + 1;
+    gs->relres = fabs(sm.g[j + 1]) / gs->bnorm;
+    sm.h1[kGmKmax] = hn;  // the norm for the normalisation kernel
+    const bool conv = gs->relres <= gs->tol;
+    if (conv || hn == T(0) || gs->iters >= gs->maxit || j + 1 >= m) {
+        gs->cyc_stop = 1;
+        gs->est_conv = conv || hn == T(0);
+        if (conv || hn == T(0) || gs->iters >= gs->maxit) gs->skip = 1;
+    }
+}
+
+// v_{j+1} = w / ||w||
+template <class T>
+__global__ void __launch_bounds__(kVB) k_gm_scale(int64_t n, int64_t ld, T *__restrict__ V, int j, const GState<T> *gs, GSmall<T> sm)
+{
+    // v_{j+1} is needed only while the cycle goes on
+    if (gs->skip || gs->cyc_stop || gs->jdone != j + 1) return;
+    const T inv = T(1) / ldcg(sm.h1 + kGmKmax);
+    T *w = V + (int64_t)(j + 1) * ld;
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) w[i] *= inv;
+}
+
+// End of a cycle: y = H^{-1} g by back substitution (one thread; m <= 32)
+template <class T> __global__ void k_gm_solve(GState<T> *gs, GSmall<T> sm)
+{
+    if (gs->done || threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int jn = gs->jdone, m = gs->m;
+    for (int i = jn - 1; i >= 0; --i) {
+        T s = sm.g[i];
+        for (int k = i + 1; k < jn; ++k) s -= sm.H[i * m + k] * sm.y[k];
+        sm.y[i] = s / sm.H[i * m + i];
+    }
+}
+
+// x += sum_k y_k v_k
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_gm_update(int64_t n, int64_t ld, const T *__restrict__ V, T *__restrict__ x, const GState<T> *gs, GSmall<T> sm)
+{
+    if (gs->done) return;
+    const int jn = gs->jdone;
+    if (jn == 0) return;
+    __shared__ T ys[kGmKmax];
+    if (threadIdx.x < kGmKmax) ys[threadIdx.x] = threadIdx.x < jn ? ldcg(sm.y + threadIdx.x) : T(0);
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+        T xi = x[i];
+#pragma unroll
+        for (int k = 0; k < kGmKmax; ++k)
+            if (k < jn) xi = fma(ys[k], V[(int64_t)k * ld + i], xi);
+        x[i] = xi;
+    }
+}
+
+// Start of a cycle: V[0] holds r = b - A x and dots[1] = r.r (SpMV epilogue).
+// Decide convergence on the TRUE residual, else v_0 = r / ||r||, g = ||r|| e_1.
+template <class T>
+__global__ void __launch_bounds__(kVB) k_gm_start(int64_t n, T *__restrict__ v0, const T *dots, GState<T> *gs, GSmall<T> sm)
+{
+    if (gs->done) return;
+    const T rr = ldcg(dots + 1);
+    const T beta = sqrt(rr);
+    const T rel = beta / gs->bnorm;
+    const bool conv = rel <= gs->tol;
+    const bool stag = !conv && gs->est_conv && gs->restarts >= kMaxRestarts;
+    const bool maxed = gs->iters >= gs->maxit;
+    if (conv || stag || maxed || beta == T(0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            gs->relres = rel;
+            gs->done = 1;
+            gs->skip = 1;
+            gs->status = conv || beta == T(0) ? SPX_CONVERGED : (stag ? SPX_STAGNATED : SPX_MAX_ITER);
+        }
+        return;
+    }
+    const T inv = T(1) / beta;
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) v0[i] *= inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (gs->est_conv) gs->restarts += 1;
+        gs->beta = beta;
+        gs->relres = rel;
+        gs->cyc_stop = 0;
+        gs->est_conv = 0;
+        gs->jdone = 0;
+        gs->skip = 0;
+        sm.g[0] = beta;
+        for (int k = 1; k <= gs->m; ++k) sm.g[k] = T(0);
+    }
+}
+
+// ------------------------------------------------------------------ host drivers
+namespace {
+
+template <class T> T *vec(SolverWork *w, int k) { return w->vecs.as<T>() + (int64_t)k * w->ld; }
+
+int vgrid(spx_ctx *ctx, int64_t n, int cap_per_sm = 4)
+{
+    int64_t g = ceil_div(n, kVB);
+    const int64_t cap = (int64_t)ctx->sm_count * cap_per_sm;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <class T> Epi<T> epi_plain(T *y) { Epi<T> e; e.y = y; return e; }
+
+struct Timer {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double ms() const
+    {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+// Runs `body` either directly on ctx->stream or, for reuse, as a captured CUDA
+// graph keyed by `key` (captured on the private capture stream, launched on
+// ctx->stream).  The first call of a key runs eagerly so that every lazily
+// allocated scratch exists before capture.
+template <class F> int run_chunk(spx_ctx *ctx, SolverWork *w, const uint64_t key[8], bool use_graph, F &&body)
+{
+    bool same = w->gexec != nullptr;
+    for (int i = 0; i < 8 && same; ++i) same = w->gkey[i] == key[i];
+    if (same) {
+        SPX_CUDA(cudaGraphLaunch(w->gexec, ctx->stream));
+        return SPX_OK;
+    }
+    SPX_TRY(body());  // eager run (also the warm-up that allocates scratch)
+    if (!use_graph) return SPX_OK;
+    if (w->gexec) {
+        cudaGraphExecDestroy(w->gexec);
+        w->gexec = nullptr;
+    }
+    // capture the next chunk on the private stream, ordered after ctx->stream
+    cudaEvent_t ev;
+    SPX_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    SPX_CUDA(cudaEventRecord(ev, ctx->stream));
+    SPX_CUDA(cudaStreamWaitEvent(ctx->capture_stream, ev, 0));
+    cudaEventDestroy(ev);
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed);
+    int st = SPX_OK;
+    if (e == cudaSuccess) st = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->capture_stream, &g) : e;
+    ctx->stream = user;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    if (st != SPX_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    w->gexec = ex;
+    std::memcpy(w->gkey, key, sizeof(w->gkey));
+    return SPX_OK;
+}
+
+template <class T> struct KrylovRun {
+    spx_ctx *ctx;
+    spx_matrix *A;
+    SolverWork *w;
+    const T *b;
+    T *x;
+    bool use32;
+    int solver;
+};
+
+// One CG iteration: q = A p (+ p.q -> alpha); x, r update (+ r.r -> beta); p update.
+template <class T> int cg_iter(KrylovRun<T> &R)
+{
+    SolverWork *w = R.w;
+    KState<T> *st = w->state.as<KState<T>>();
+    T *r = vec<T>(w, 0), *p = vec<T>(w, 1), *q = vec<T>(w, 2);
+    const int64_t n = R.A->n;
+    Epi<T> e = epi_plain(q);
+    e.w = p;
+    e.dots = w->dots.as<T>();
+    e.fin = FIN_CG_ALPHA;
+    e.fin_state = st;
+    e.skip = &st->done;
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, p, e, R.use32));
+    const int g = vgrid(R.ctx, n);
+    T *part = w->red.as<T>();
+    unsigned *tk = w->ticket.as<unsigned>();
+    k_cg_xr<T><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, st, part, tk);
+    k_cg_p<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, st);
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T> int bi_iter(KrylovRun<T> &R)
+{
+    SolverWork *w = R.w;
+    KState<T> *st = w->state.as<KState<T>>();
+    T *r = vec<T>(w, 0), *rh = vec<T>(w, 1), *p = vec<T>(w, 2), *v = vec<T>(w, 3), *s = vec<T>(w, 4),
+      *t = vec<T>(w, 5);
+    const int64_t n = R.A->n;
+    const int g = vgrid(R.ctx, n);
+    T *part = w->red.as<T>();
+    unsigned *tk = w->ticket.as<unsigned>();
+    k_bi_p<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, v, st);
+    Epi<T> e = epi_plain(v);
+    e.w = rh;
+    e.dots = w->dots.as<T>();
+    e.fin = FIN_BI_RV;
+    e.fin_state = st;
+    e.skip = &st->done;
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, p, e, R.use32));
+    k_bi_s<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, v, s, st, part, tk);
+    Epi<T> e2 = epi_plain(t);
+    e2.w = s;
+    e2.want_yy = true;
+    e2.dots = w->dots.as<T>();
+    e2.fin = FIN_BI_OMEGA;
+    e2.fin_state = st;
+    e2.skip = &st->skip_t;
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, s, e2, R.use32));
+    k_bi_xr<T><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, rh, p, s, t, st, part, tk);
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+// r = b - A x with r.r; (re)initialise the recurrences.
+template <class T> int krylov_init(KrylovRun<T> &R)
+{
+    SolverWork *w = R.w;
+    KState<T> *st = w->state.as<KState<T>>();
+    const int64_t n = R.A->n;
+    T *r = vec<T>(w, 0);
+    Epi<T> e;
+    e.alpha = T(-1);
+    e.beta = T(1);
+    e.z = R.b;
+    e.y = r;
+    e.want_yy = true;
+    e.dots = w->dots.as<T>();
+    e.fin = R.solver == SPX_CG ? FIN_INIT_CG : FIN_INIT_BI;
+    e.fin_state = st;
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, R.x, e, R.use32));
+    const size_t bytes = (size_t)n * sizeof(T);
+    if (R.solver == SPX_CG) {
+        SPX_CUDA(cudaMemcpyAsync(vec<T>(w, 1), r, bytes, cudaMemcpyDeviceToDevice, R.ctx->stream));
+    } else {
+        SPX_CUDA(cudaMemcpyAsync(vec<T>(w, 1), r, bytes, cudaMemcpyDeviceToDevice, R.ctx->stream));  // r^
+        SPX_CUDA(cudaMemsetAsync(vec<T>(w, 2), 0, bytes, R.ctx->stream));                        // p
+        SPX_CUDA(cudaMemsetAsync(vec<T>(w, 3), 0, bytes, R.ctx->stream));                        // v
+    }
+    return SPX_OK;
+}
+
+// true residual ||b - A x||^2 -> dots[1] (scratch vector)
+template <class T> int true_residual(KrylovRun<T> &R, T *scratch)
+{
+    Epi<T> e;
+    e.alpha = T(-1);
+    e.beta = T(1);
+    e.z = R.b;
+    e.y = scratch;
+    e.want_yy = true;
+    SolverWork *wk = R.w;
+    e.dots = wk->dots.as<T>();
+    return spmv_launch<T>(R.ctx, R.A, R.x, e, R.use32);
+}
+
+template <class T> int read_state(spx_ctx *ctx, SolverWork *w, size_t bytes)
+{
+    SPX_CUDA(cudaMemcpyAsync(w->host, w->state.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SPX_OK;
+}
+
+template <class T> int read_dots(spx_ctx *ctx, SolverWork *w, T out[2])
+{
+    SPX_CUDA(cudaMemcpyAsync(out, w->dots.p, 2 * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SPX_OK;
+}
+
+int check_dev_err(spx_ctx *ctx)
+{
+    unsigned h = 0;
+    SPX_CUDA(cudaMemcpyAsync(&h, ctx->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (h) {
+        cudaMemsetAsync(ctx->dev_err, 0, sizeof(unsigned), ctx->stream);
+        return fail(SPX_ERR_TIMEOUT, "a bounded device-side wait gave up (error word " + std::to_string(h) + ")");
+    }
+    return SPX_OK;
+}
+
+// CG / BiCGSTAB.  inner: FP32 inner solve of refinement (no true-residual
+// check, no restarts; x starts at 0).  fixed > 0: run exactly that many
+// iterations (tol ignored).
+template <class T>
+int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b, T *x, double tol,
+              int64_t maxit, bool use32, bool inner, int64_t fixed, spx_solve_info *info)
+{
+    KrylovRun<T> R{ctx, A, w, b, x, use32, solver};
+    KState<T> hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.rtol2 = fixed > 0 ? T(0) : (T)(tol * tol);
+    hs.maxit = fixed > 0 ? fixed : maxit;
+    hs.status = SPX_MAX_ITER;
+    KState<T> *st = w->state.as<KState<T>>();
+    SPX_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+    const int64_t n = A->n;
+    k_dot_fin<T><<<vgrid(ctx, n), kVB, 0, ctx->stream>>>(n, b, b, FIN_SET_BB, st, w->red.as<T>(),
+                                                         w->ticket.as<unsigned>());
+    SPX_CUDA(cudaGetLastError());
+    if (inner) SPX_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), ctx->stream));
+    KState<T> *h = static_cast<KState<T> *>(w->host);
+    int restarts = 0;
+    const int chunk = fixed > 0 ? 64 : (n < 200000 ? 32 : 16);
+    const bool graphs = true;
+    for (;;) {
+        SPX_TRY(krylov_init(R));
+        SPX_TRY(read_state<T>(ctx, w, sizeof(KState<T>)));
+        if (h->bb == T(0)) {  // b = 0: x = 0
+            SPX_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), ctx->stream));
+            SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+            info->status = SPX_CONVERGED;
+            info->iterations = 0;
+            info->relres_recurrence = info->relres_true = 0.0;
+            return SPX_OK;
+        }
+        int64_t launched = 0;
+        while (!h->done) {
+            const uint64_t key[8] = {(uint64_t)solver, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
+                                     (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T),
+                                     (uint64_t)(uintptr_t)A, 0};
+            SPX_TRY(run_chunk(ctx, w, key, graphs, [&]() -> int {
+                for (int c = 0; c < chunk; ++c) SPX_TRY(solver == SPX_CG ? cg_iter(R) : bi_iter(R));
+                return SPX_OK;
+            }));
+            launched += chunk;
+            SPX_TRY(read_state<T>(ctx, w, sizeof(KState<T>)));
+            if (launched > hs.maxit + 4 * chunk) return fail(SPX_ERR_CUDA, "solver did not stop");
+        }
+        SPX_TRY(check_dev_err(ctx));
+        info->status = h->status;
+        info->iterations = h->iters;
+        info->relres_recurrence = (double)h->relres;
+        if (inner) break;
+        T d[2];
+        SPX_TRY(true_residual(R, vec<T>(w, w->nvec - 1)));
+        SPX_TRY(read_dots<T>(ctx, w, d));
+        info->relres_true = std::sqrt((double)d[1] / (double)h->bb);
+        if (fixed > 0 || h->status != SPX_CONVERGED || info->relres_true <= tol) break;
+        if (restarts == kMaxRestarts) {
+            info->status = SPX_STAGNATED;
+            break;
+        }
+        ++restarts;
+    }
+    info->restarts = restarts;
+    return SPX_OK;
+}
+
+template <class T>
+int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, double tol, int64_t maxit, int m,
+              bool use32, bool inner, int64_t fixed, spx_solve_info *info)
+{
+    const int64_t n = A->n, ld = w->ld;
+    T *V = w->vecs.as<T>();
+    GState<T> *gs = w->state.as<GState<T>>();
+    GSmall<T> sm;
+    T *base = w->small.as<T>();
+    sm.H = base;
+    sm.cs = sm.H + (m + 1) * m;
+    sm.sn = sm.cs + m + 1;
+    sm.g = sm.sn + m + 1;
+    sm.y = sm.g + m + 2;
+    sm.h1 = sm.y + m + 1;
+    sm.h2 = sm.h1 + kGmKmax + 2;
+    T *dots = w->dots.as<T>();
+    T *part = w->red.as<T>();
+    unsigned *tk = w->ticket.as<unsigned>();
+    // ||b||
+    T bb = 0;
+    {
+        SPX_TRY(dot_launch<T>(ctx, n, b, b, dots));
+        T d[2];
+        SPX_CUDA(cudaMemcpyAsync(d, dots, sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+        SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+        bb = d[0];
+    }
+    if (inner) SPX_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), ctx->stream));
+    if (bb == T(0)) {
+        SPX_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), ctx->stream));
+        SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+        info->status = SPX_CONVERGED;
+        return SPX_OK;
+    }
+    GState<T> hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.bnorm = std::sqrt(bb);
+    hs.tol = fixed > 0 ? T(0) : (T)tol;
+    hs.m = m;
+    hs.maxit = fixed > 0 ? fixed : maxit;
+    hs.status = SPX_MAX_ITER;
+    SPX_CUDA(cudaMemcpyAsync(gs, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+    const int g = vgrid(ctx, n, 2);
+    auto cycle = [&]() -> int {
+        // restart: V[0] = b - A x, r.r
+        Epi<T> e;
+        e.alpha = T(-1);
+        e.beta = T(1);
+        e.z = b;
+        e.y = V;
+        e.want_yy = true;
+        e.dots = dots;
+        e.skip = &gs->done;
+        SPX_TRY(spmv_launch<T>(ctx, A, x, e, use32));
+        k_gm_start<T><<<g, kVB, 0, ctx->stream>>>(n, V, dots, gs, sm);
+        for (int j = 0; j < m; ++j) {
+            Epi<T> ea = epi_plain(V + (int64_t)(j + 1) * ld);
+            ea.skip = &gs->skip;
+            SPX_TRY(spmv_launch<T>(ctx, A, V + (int64_t)j * ld, ea, use32));
+            k_gm_proj<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk);
+            k_gm_orth<T, 1><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
+            k_gm_orth<T, 2><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
+            k_gm_scale<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm);
+        }
+        k_gm_solve<T><<<1, 32, 0, ctx->stream>>>(gs, sm);
+        k_gm_update<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, x, gs, sm);
+        SPX_CUDA(cudaGetLastError());
+        return SPX_OK;
+    };
+    GState<T> *h = static_cast<GState<T> *>(w->host);
+    int64_t cycles = 0;
+    for (;;) {
+        const uint64_t key[8] = {(uint64_t)SPX_GMRES, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
+                                 (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T), (uint64_t)(uintptr_t)A, 1};
+        SPX_TRY(run_chunk(ctx, w, key, true, cycle));
+        SPX_TRY(read_state<T>(ctx, w, sizeof(GState<T>)));
+        ++cycles;
+        if (h->done) break;
+        if (inner && h->cyc_stop && (h->est_conv || h->iters >= h->maxit)) break;
+        if (cycles > hs.maxit + 8) return fail(SPX_ERR_CUDA, "GMRES did not stop");
+    }
+    SPX_TRY(check_dev_err(ctx));
+    info->status = h->done ? h->status : (h->est_conv ? SPX_CONVERGED : SPX_MAX_ITER);
+    info->iterations = h->iters;
+    info->restarts = h->restarts;
+    info->relres_recurrence = (double)h->relres;
+    if (!inner) {
+        KrylovRun<T> R{ctx, A, w, b, x, use32, SPX_GMRES};
+        T d[2];
+        SPX_TRY(true_residual(R, V + (int64_t)(m + 1) * ld));
+        SPX_TRY(read_dots<T>(ctx, w, d));
+        info->relres_true = std::sqrt((double)d[1]) / (double)hs.bnorm;
+    }
+    return SPX_OK;
+}
+
+// ------------------------------------------------------------------ mixed precision
+template <class S, class D> __global__ void k_cast_scale(int64_t n, const S *__restrict__ a, S scale, D *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = static_cast<D>(a[i] * scale);
+}
+
+__global__ void k_ir_update(int64_t n, double *__restrict__ x, const float *__restrict__ d, double s)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fma(s, (double)d[i], x[i]);
+}
+
+int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, double tol, int64_t maxit,
+           int m, spx_solve_info *info)
+{
+    const int64_t n = A->n;
+    SolverWork *&w = A->work;
+    SPX_TRY(work_prepare<double>(ctx, w, n, SPX_CG, 0));  // outer: r and scratch only
+    SPX_TRY(work_prepare<float>(ctx, w->inner, n, solver, solver == SPX_GMRES ? m : 0));
+    if (!w->ir.p) SPX_TRY(dbuf_alloc(ctx, w->ir, (size_t)n * 8 + 2 * (size_t)round_up(n, 64) * 4 + 256));
+    double *r = w->ir.as<double>();
+    float *r32 = reinterpret_cast<float *>(w->ir.as<char>() + round_up((size_t)n * 8, 256));
+    float *d32 = r32 + round_up((size_t)n, 64);
+    double bb = 0;
+    {
+        double d[2];
+        SPX_TRY(dot_launch<double>(ctx, n, b, b, w->dots.as<double>()));
+        SPX_CUDA(cudaMemcpyAsync(d, w->dots.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+        bb = d[0];
+    }
+    if (bb == 0.0) {
+        SPX_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 8, ctx->stream));
+        SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+        info->status = SPX_CONVERGED;
+        return SPX_OK;
+    }
+    const double inner_tol = 1e-4;
+    const int max_outer = 20;
+    int64_t inner_total = 0;
+    int outer = 0;
+    double rel = 0.0;
+    int status = SPX_MAX_ITER;
+    const int g = vgrid(ctx, n);
+    for (;; ++outer) {
+        // r = b - A64 x (FP64), ||r||
+        Epi<double> e;
+        e.alpha = -1.0;
+        e.beta = 1.0;
+        e.z = b;
+        e.y = r;
+        e.want_yy = true;
+        e.dots = w->dots.as<double>();
+        SPX_TRY(spmv_launch<double>(ctx, A, x, e, false));
+        double d[2];
+        SPX_TRY(read_dots<double>(ctx, w, d));
+        const double rn = std::sqrt(d[1]);
+        rel = rn / std::sqrt(bb);
+        if (rel <= tol) {
+            status = SPX_CONVERGED;
+            break;
+        }
+        if (outer >= max_outer || inner_total >= maxit) break;
+        k_cast_scale<double, float><<<g, kVB, 0, ctx->stream>>>(n, r, 1.0 / rn, r32);
+        SPX_CUDA(cudaGetLastError());
+        spx_solve_info ii;
+        std::memset(&ii, 0, sizeof(ii));
+        if (solver == SPX_GMRES)
+            SPX_TRY(run_gmres<float>(ctx, A, w->inner, r32, d32, inner_tol, maxit - inner_total, m, true, true, 0, &ii));
+        else
+            SPX_TRY(run_short<float>(ctx, A, w->inner, solver, r32, d32, inner_tol, maxit - inner_total, true, true, 0, &ii));
+        inner_total += ii.iterations;
+        k_ir_update<<<g, kVB, 0, ctx->stream>>>(n, x, d32, rn);
+        SPX_CUDA(cudaGetLastError());
+    }
+    info->status = status;
+    info->iterations = inner_total;
+    info->inner_iterations = inner_total;
+    info->restarts = outer;
+    info->relres_recurrence = rel;
+    info->relres_true = rel;
+    return SPX_OK;
+}
+
+template <class T>
+int solve_typed(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, int solver, double tol, int64_t maxit, int m,
+                bool use32, int64_t fixed, spx_solve_info *info)
+{
+    SPX_TRY(work_prepare<T>(ctx, A->work, A->n, solver, solver == SPX_GMRES ? m : 0));
+    if (solver == SPX_GMRES) return run_gmres<T>(ctx, A, A->work, b, x, tol, maxit, m, use32, false, fixed, info);
+    return run_short<T>(ctx, A, A->work, solver, b, x, tol, maxit, use32, false, fixed, info);
+}
+
+int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol, int64_t maxit,
+                int restart, int precision, int64_t fixed, spx_solve_info *info)
+{
+    if (!ctx || !A || !info || (A->n > 0 && (!b || !x)))
+        return fail(SPX_ERR_INVALID, "spx_solve: NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    if (A->n != A->ncols) return fail(SPX_ERR_INVALID, "spx_solve: the matrix must be square");
+    if (solver < SPX_CG || solver > SPX_GMRES) return fail(SPX_ERR_INVALID, "spx_solve: unknown solver");
+    if (!(tol >= 0.0) || maxit < 0) return fail(SPX_ERR_INVALID, "spx_solve: bad tol or max_iter");
+    if (solver == SPX_GMRES && (restart < 1 || restart > kGmKmax - 1))
+        return fail(SPX_ERR_UNSUPPORTED, "GMRES restart length must be in [1, 31]");
+    if (A->n == 0) {
+        info->status = SPX_CONVERGED;
+        return SPX_OK;
+    }
+    Timer tm;
+    int st;
+    if (precision == SPX_PREC_MIXED) {
+        if (A->dtype != SPX_F64 || !(A->val32.p || A->ell_val32.p || A->coo_val32.p))
+            return fail(SPX_ERR_UNSUPPORTED, "mixed precision needs an FP64 matrix created with SPX_MIXED_SHADOW");
+        if (fixed > 0) return fail(SPX_ERR_UNSUPPORTED, "fixed-iteration mode runs in one precision");
+        st = run_ir(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol, maxit, restart, info);
+    } else if (precision == SPX_PREC_F64 || precision == SPX_PREC_F32) {
+        const int want = precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32;
+        if (A->dtype != want) return fail(SPX_ERR_UNSUPPORTED, "precision must match the matrix dtype (or use MIXED)");
+        st = A->dtype == SPX_F64
+                 ? solve_typed<double>(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol,
+                                       maxit, restart, false, fixed, info)
+                 : solve_typed<float>(ctx, A, static_cast<const float *>(b), static_cast<float *>(x), solver, tol,
+                                      maxit, restart, false, fixed, info);
+    } else {
+        return fail(SPX_ERR_INVALID, "spx_solve: unknown precision");
+    }
+    info->time_ms = tm.ms();
+    return st;
+}
+
+}  // namespace
+}  // namespace spx
+
+using namespace spx;
+
+namespace {
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d);
+        else prev = -1;
+    }
+    ~DevGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
+extern "C" int spx_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol,
+                         int64_t max_iter, int restart, int precision, spx_solve_info *info)
+{
+    if (!ctx) return fail(SPX_ERR_INVALID, "spx_solve: ctx is NULL");
+    DevGuard g(ctx->device);
+    return solve_entry(ctx, A, b, x, solver, tol, max_iter, restart, precision, 0, info);
+}
+
+extern "C" int spx_solve_fixed(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, int64_t iterations,
+                               int restart, int precision, spx_solve_info *info)
+{
+    if (!ctx) return fail(SPX_ERR_INVALID, "spx_solve_fixed: ctx is NULL");
+    if (iterations < 1) return fail(SPX_ERR_INVALID, "spx_solve_fixed: iterations must be >= 1");
+    DevGuard g(ctx->device);
+    return solve_entry(ctx, A, b, x, solver, 0.0, iterations, restart, precision, iterations, info);
+}

@@ -1,0 +1,953 @@
+// spmv.cu -- sparse matrix-vector product kernels for sm_103a.
+//
+// y = A x (Section 5 of arXiv 2103.10116 defines SpMV and the CSR / COO
+// layouts; ELL and HYB are this library's additional storage orders).
+//
+// GB300 shapes the design in one way above all: IEEE double FMA throughput is
+// low (about 2 FMA per SM per clock), so an FP64 SpMV that streams 12 bytes
+// per nonzero from HBM is co-bound by the FP64 pipe.  Every FP64 kernel here
+// therefore spends exactly one FMA per stored entry and as few extra FP64
+// instructions as it can: rows are accumulated sequentially by one thread
+// (merge-path CSR, ELL, segmented COO) and warp-shuffle reductions are kept
+// for the classic vector kernel only.
+//
+// Determinism: no floating-point atomics.  Rows that straddle a thread or tile
+// boundary are completed by a fixed-order carry chain; the per-tile carries
+// and the dot-product partials are finished by the last block to arrive, in
+// index order, so every run gives the same bits.
+#include <climits>
+
+#include "dev_common.cuh"
+#include "kstate.cuh"
+#include "spx_internal.cuh"
+
+namespace spx {
+
+// ------------------------------------------------------------------ epilogue helpers
+template <class T> __device__ __forceinline__ T epi_val(const Epi<T> &e, int64_t r, T t)
+{
+    if (e.alpha != T(1)) t *= e.alpha;
+    if (e.z) t = fma(e.beta, e.z[r], t);
+    return t;
+}
+
+template <class T>
+__device__ __forceinline__ void final_write(const Epi<T> &e, int64_t r, T t, T &d0, T &d1)
+{
+    const T v = epi_val(e, r, t);
+    e.y[r] = v;
+    if (e.w) d0 = fma(e.w[r], v, d0);
+    if (e.want_yy) d1 = fma(v, v, d1);
+}
+
+// Reduce (d0, d1) over the grid; the last block stores dots and runs the
+// scalar update.  Every block must call it.
+template <class T, int BLOCK>
+__device__ __forceinline__ void finish_dots(T d0, T d1, const Epi<T> &e, T *partials,
+                                            unsigned *ticket)
+{
+    grid_dots_finish<T, BLOCK>(d0, d1, e.dots, e.fin, e.fin_state, partials, ticket);
+}
+
+// ------------------------------------------------------------------ cross-tile carries
+// A tile whose end falls inside a row (only rows longer than the tile-map
+// slack) publishes that row's partial sum; the tile where the row ends looks
+// back over the published partials (decoupled look-back).  Waits only point
+// to earlier tiles and the grid is launched cooperatively (all blocks
+// resident), so every wait is satisfied; each wait is still bounded.  The
+// consumer resets the flag it used, so flags are all zero between launches.
+__device__ __forceinline__ void flag_publish(int *flag)
+{
+    __threadfence();
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(flag), "r"(1) : "memory");
+}
+
+__device__ __forceinline__ bool flag_wait(int *flag, unsigned *err, long long limit_cycles = 2000000000LL)
+{
+    int v;
+    const long long t0 = clock64();
+    for (;;) {
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0) return true;
+        if (clock64() - t0 > limit_cycles) {
+            if (err) atomicOr(err, DEVERR_QUEUE_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// ------------------------------------------------------------------ CSR vector
+// One sub-warp of SW lanes per row; lanes stride over the row, then a
+// shuffle reduction inside the sub-warp.  The loop is warp-uniform so every
+// lane reaches every shuffle.
+template <class T, int SW, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_csr_vector(int64_t n, const int *__restrict__ rp, const int *__restrict__ col,
+                 const T *__restrict__ val, const T *__restrict__ x, Epi<T> e, T *partials,
+                 unsigned *ticket)
+{
+    if (e.skip && *e.skip) return;
+    constexpr int RPW = 32 / SW;
+    const int lane = threadIdx.x & 31, sub = lane / SW, sl = lane % SW;
+    const int64_t warp = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * BLOCK) >> 5;
+    T d0 = T(0), d1 = T(0);
+    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
+        const int64_t i = base + sub;
+        T s = T(0);
+        if (i < n) {
+            const int lo = rp[i], hi = rp[i + 1];
+            for (int k = lo + sl; k < hi; k += SW) s = fma(val[k], __ldg(x + col[k]), s);
+        }
+#pragma unroll
+        for (int o = SW / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, SW);
+        if (i < n && sl == 0) final_write(e, i, s, d0, d1);
+    }
+    if (e.dots) finish_dots<T, BLOCK>(d0, d1, e, partials, ticket);
+}
+
+// ------------------------------------------------------------------ merge-path CSR
+// The merge of the row-end list (rp[1..n]) with the nonzero indices 0..nnz-1
+// is cut into tiles of about TILE items (a row end or a nonzero each).  Tile
+// boundaries are precomputed and snapped forward to the next row end when
+// that is at most SLACK items away, so only rows longer than SLACK straddle
+// tiles.  A persistent block loops over its tiles; thread 0 prefetches the
+// next tile's row pointers, column indices and values into the other
+// shared-memory stage with 1-D bulk copies (TMA) while the block works on
+// the current one.  Each thread walks its share of the tile's merge items
+// sequentially: exactly one FMA per nonzero.
+template <class T, int BLOCK, int IPT> struct MergeShape {
+    static constexpr int TILE = BLOCK * IPT;
+    static constexpr int SLACK = TILE / 4;
+    // rp slice (<= rows + 8 ints), cols (<= nnz + 8 ints), vals (<= nnz + 16/V T)
+    // with rows + nnz <= TILE + SLACK, each rounded to 16 B.
+    static constexpr int STAGE = (int)((4 + sizeof(T)) * (TILE + SLACK) + 256);
+    static constexpr int SMEM = 2 * STAGE + BLOCK * (4 + (int)sizeof(T)) + 16;
+    static constexpr int CH = 8;  // nonzeros whose x gathers are issued together
+};
+
+struct TileRanges {
+    int ra, rbytes, ca, cbytes, va, vbytes;
+};
+
+template <class T>
+__device__ __forceinline__ TileRanges merge_ranges(int n, int i0, int j0, int i1, int j1)
+{
+    constexpr int VA = 16 / (int)sizeof(T);
+    TileRanges g;
+    g.ra = i0 & ~3;
+    const int rend = min(i1 + 2, n + 1);  // rp[i0 .. i1+1] (clamped at rp[n])
+    g.rbytes = ((rend - g.ra + 3) & ~3) * 4;
+    g.ca = j0 & ~3;
+    g.cbytes = j1 > j0 ? ((j1 - g.ca + 3) & ~3) * 4 : 0;
+    g.va = j0 & ~(VA - 1);
+    g.vbytes = j1 > j0 ? ((j1 - g.va + VA - 1) & ~(VA - 1)) * (int)sizeof(T) : 0;
+    return g;
+}
+
+// Threads with an empty share of a tile are transparent to carry chains.
+constexpr int kNoCarry = -1, kEmpty = -2;
+
+template <class T, int BLOCK, int IPT>
+__global__ void __launch_bounds__(BLOCK)
+    k_csr_merge(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                const T *__restrict__ val, const T *__restrict__ x, const int2 *__restrict__ tiles,
+                int ntiles, int *carry_row_g, T *carry_val_g, int *flags, T *partials, unsigned *ticket,
+                unsigned *err, Epi<T> e)
+{
+    using S = MergeShape<T, BLOCK, IPT>;
+    constexpr int CH = S::CH;
+    if (e.skip && *e.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *s_crow = reinterpret_cast<int *>(smem + 2 * S::STAGE);
+    T *s_cval = reinterpret_cast<T *>(smem + 2 * S::STAGE + BLOCK * 4);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + BLOCK * (4 + sizeof(T)));
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int t, int stage) {
+        const int2 a = tiles[t], b = tiles[t + 1];
+        const TileRanges g = merge_ranges<T>(n, a.x, a.y, b.x, b.y);
+        unsigned char *base = smem + stage * S::STAGE;
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)(g.rbytes + g.cbytes + g.vbytes));
+        bulk_g2s(base, rp + g.ra, (uint32_t)g.rbytes, &bar[stage]);
+        if (g.cbytes) {
+            bulk_g2s(base + g.rbytes, col + g.ca, (uint32_t)g.cbytes, &bar[stage]);
+            bulk_g2s(base + g.rbytes + g.cbytes, val + g.va, (uint32_t)g.vbytes, &bar[stage]);
+        }
+    };
+
+    T d0 = T(0), d1 = T(0);
+    int it = 0;
+    bool ok = true;
+    bool pending_prefetch = false;
+    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int stage = it & 1;
+        const int tn = t + gridDim.x;
+        pending_prefetch = tn < ntiles;
+        if (tid == 0 && tn < ntiles) {
+            fence_proxy_async();
+            issue(tn, stage ^ 1);
+        }
+        const int2 a = tiles[t], b = tiles[t + 1];
+        const int i0 = a.x, j0 = a.y, i1 = b.x, j1 = b.y;
+        const TileRanges g = merge_ranges<T>(n, i0, j0, i1, j1);
+        const unsigned char *sb = smem + stage * S::STAGE;
+        const int *s_rp = reinterpret_cast<const int *>(sb) + (i0 - g.ra);             // rp[i0 + k]
+        const int *s_col = reinterpret_cast<const int *>(sb + g.rbytes) + (j0 - g.ca);  // col[j0 + k]
+        const T *s_val = reinterpret_cast<const T *>(sb + g.rbytes + g.cbytes) + (j0 - g.va);
+        const int rows_avail = i1 - i0;
+        const int nz_tile = j1 - j0;
+        const int items = rows_avail + nz_tile;
+
+        if (!mbar_wait(&bar[stage], (uint32_t)((it >> 1) & 1), err)) {
+            ok = false;
+            break;
+        }
+
+        // --- this thread's share [dl0, dl1) of the tile's merge items
+        const int dl0 = (int)((int64_t)tid * items / BLOCK), dl1 = (int)((int64_t)(tid + 1) * items / BLOCK);
+        auto search = [&](int dl) {
+            int lo = max(0, dl - nz_tile), hi = min(dl, rows_avail);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (mid + s_rp[mid + 1] - j0 < dl) lo = mid + 1;
+                else hi = mid;
+            }
+            return lo;
+        };
+        const int rl0 = search(dl0), rl1 = search(dl1);
+        const int jstart = j0 + (dl0 - rl0), jend = j0 + (dl1 - rl1);
+        const int rfirst = i0 + rl0, rlast = i0 + rl1;
+        const bool pend_possible = s_rp[rl0] < jstart;  // first row began before this thread
+
+        // --- sequential walk: one FMA per nonzero
+        int r = rfirst;
+        int re = r < n ? s_rp[r - i0 + 1] : INT_MAX;
+        T sum = T(0), pend = T(0);
+        bool first = true, has_pend = false;
+        auto emit = [&](int row, T s) {
+            if (first && pend_possible) {
+                pend = s;
+                has_pend = true;
+            } else {
+                final_write(e, row, s, d0, d1);
+            }
+            first = false;
+        };
+        const int nnz_t = jend - jstart;
+        for (int c = 0; c < nnz_t; c += CH) {
+            T v[CH], xv[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int k = jstart - j0 + c + u;
+                if (c + u < nnz_t) {
+                    v[u] = s_val[k];
+                    xv[u] = __ldg(x + s_col[k]);
+                } else {
+                    v[u] = T(0);
+                    xv[u] = T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                if (c + u < nnz_t) {
+                    const int jj = jstart + c + u;
+                    while (jj >= re) {
+                        emit(r, sum);
+                        sum = T(0);
+                        ++r;
+                        re = r < n ? s_rp[r - i0 + 1] : INT_MAX;
+                    }
+                    sum = fma(v[u], xv[u], sum);
+                }
+            }
+        }
+        while (r < rlast) {
+            emit(r, sum);
+            sum = T(0);
+            ++r;
+        }
+        int crow = kNoCarry;
+        if (dl0 == dl1) crow = kEmpty;
+        else if (r < n && jend > max(jstart, s_rp[r - i0])) crow = r;
+        s_crow[tid] = crow;
+        s_cval[tid] = sum;
+        __syncthreads();
+
+        // --- complete the first row from the carries of the threads (and tiles) before
+        if (has_pend) {
+            T tot = pend;
+            int k = tid - 1;
+            while (k >= 0 && (s_crow[k] == rfirst || s_crow[k] == kEmpty)) {
+                if (s_crow[k] == rfirst) tot += s_cval[k];
+                --k;
+            }
+            if (k < 0 && rfirst == i0 && s_rp[0] < j0) {  // the row began in an earlier tile
+                for (int tp = t - 1; tp >= 0; --tp) {
+                    if (!flag_wait(flags + tp, err)) break;
+                    tot += ldcg(carry_val_g + tp);
+                    flags[tp] = 0;
+                    const int2 pa = tiles[tp];
+                    if (!(pa.x == rfirst && pa.y > s_rp[0])) break;  // tile tp began at or before the row start
+                }
+            }
+            final_write(e, rfirst, tot, d0, d1);
+        }
+        // --- publish the partial of a row that continues into the next tile
+        if (tid == BLOCK - 1 && i1 < n && j1 > s_rp[rows_avail]) {
+            T cv = T(0);
+            for (int k = BLOCK - 1; k >= 0 && (s_crow[k] == i1 || s_crow[k] == kEmpty); --k)
+                if (s_crow[k] == i1) cv += s_cval[k];
+            carry_row_g[t] = i1;
+            carry_val_g[t] = cv;
+            flag_publish(flags + t);
+        }
+        __syncthreads();
+    }
+    if (!ok && pending_prefetch) {
+        // do not leave a bulk copy in flight into this block's shared memory
+        mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), err, 200000000LL);
+    }
+    if (e.dots) finish_dots<T, BLOCK>(d0, d1, e, partials, ticket);
+}
+
+// Tile map: boundary t sits on merge diagonal d = min(t * tile, n + nnz) at
+// (i, j), i = #{r : r + rp[r+1] < d}, j = d - i.  If that splits row i and the
+// end of row i is at most `slack` items further, the boundary moves there.
+// Boundaries that still split a row are counted in *nsplit.
+__global__ void k_merge_tiles(int n, int nnz, const int *__restrict__ rp, int64_t tile, int64_t slack,
+                              int ntiles, int2 *tiles, unsigned *nsplit)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    const int64_t d = min((int64_t)t * tile, (int64_t)n + nnz);
+    int64_t lo = max((int64_t)0, d - nnz), hi = min(d, (int64_t)n);
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (mid + rp[mid + 1] < d) lo = mid + 1;
+        else hi = mid;
+    }
+    int i = (int)lo, j = (int)(d - lo);
+    if (i < n && j > rp[i]) {
+        const int64_t dn = (int64_t)(i + 1) + rp[i + 1];
+        if (dn - d <= slack) {
+            i = i + 1;
+            j = rp[i];
+        } else {
+            atomicAdd(nsplit, 1u);
+        }
+    }
+    tiles[t] = make_int2(i, j);
+}
+
+// ------------------------------------------------------------------ ELL
+// Column-major ELL [width][ld]: thread g handles rows g*R .. g*R+R-1 and
+// reads R consecutive values (16 B for R = 16 / sizeof(T)) per slab, fully
+// coalesced across the warp.  Padding slots (col = -1) are skipped.
+template <class T, int R> struct Vec;
+template <> struct Vec<double, 1> { using V = double; using I = int; };
+template <> struct Vec<double, 2> { using V = double2; using I = int2; };
+template <> struct Vec<float, 1> { using V = float; using I = int; };
+template <> struct Vec<float, 2> { using V = float2; using I = int2; };
+template <> struct Vec<float, 4> { using V = float4; using I = int4; };
+
+template <class T, int R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_ell(int64_t n, int64_t ld, int w, const int *__restrict__ ecol, const T *__restrict__ eval,
+          const T *__restrict__ x, Epi<T> e, T *partials, unsigned *ticket)
+{
+    if (e.skip && *e.skip) return;
+    using VV = typename Vec<T, R>::V;
+    using VI = typename Vec<T, R>::I;
+    T d0 = T(0), d1 = T(0);
+    const int64_t ngroups = (n + R - 1) / R;
+    for (int64_t g = blockIdx.x * (int64_t)BLOCK + threadIdx.x; g < ngroups;
+         g += (int64_t)gridDim.x * BLOCK) {
+        const int64_t i = g * R;
+        T s[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) s[q] = T(0);
+#pragma unroll 4
+        for (int j = 0; j < w; ++j) {
+            const int64_t o = (int64_t)j * ld + i;
+            const VI c = __ldg(reinterpret_cast<const VI *>(ecol + o));
+            const VV v = __ldg(reinterpret_cast<const VV *>(eval + o));
+            const int *cc = reinterpret_cast<const int *>(&c);
+            const T *vv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+                if (cc[q] >= 0) s[q] = fma(vv[q], __ldg(x + cc[q]), s[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (i + q < n) final_write(e, i + q, s[q], d0, d1);
+    }
+    if (e.dots) finish_dots<T, BLOCK>(d0, d1, e, partials, ticket);
+}
+
+// ------------------------------------------------------------------ COO segmented reduction
+// Tiles of about TILE nonzeros (row-sorted COO, boundaries snapped forward to
+// the next row start when it is at most SLACK entries away) are staged by
+// bulk copies; each thread reduces its share of the tile sequentially,
+// emitting a row when the row index changes.  Store mode writes every row
+// (rows without entries get alpha*0 + beta*z); add mode (the COO part of HYB)
+// adds into y.  Rows that straddle tiles use the same look-back as merge CSR.
+template <class T, int BLOCK, int IPT> struct CooShape {
+    static constexpr int TILE = BLOCK * IPT;
+    static constexpr int SLACK = TILE / 4;
+    static constexpr int STAGE = (int)((8 + sizeof(T)) * (TILE + SLACK) + 128);
+    static constexpr int SMEM = 2 * STAGE + BLOCK * (4 + (int)sizeof(T)) + 16;
+    static constexpr int CH = 8;
+};
+
+template <class T>
+__device__ __forceinline__ TileRanges coo_ranges(int64_t k0, int64_t k1)
+{
+    constexpr int VA = 16 / (int)sizeof(T);
+    TileRanges g;
+    g.ra = (int)(k0 & ~3LL);
+    g.rbytes = (int)(((k1 - g.ra + 3) & ~3LL) * 4);
+    g.ca = g.ra;
+    g.cbytes = g.rbytes;
+    g.va = (int)(k0 & ~(int64_t)(VA - 1));
+    g.vbytes = (int)(((k1 - g.va + VA - 1) & ~(int64_t)(VA - 1)) * sizeof(T));
+    return g;
+}
+
+template <class T, int BLOCK, int IPT>
+__global__ void __launch_bounds__(BLOCK)
+    k_coo(int64_t n, int64_t nnz, const int *__restrict__ crow, const int *__restrict__ ccol,
+          const T *__restrict__ cval, const T *__restrict__ x, const int *__restrict__ tiles, int ntiles,
+          int *carry_row_g, T *carry_val_g, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e,
+          int add_mode)
+{
+    using S = CooShape<T, BLOCK, IPT>;
+    constexpr int CH = S::CH;
+    if (e.skip && *e.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *s_crow = reinterpret_cast<int *>(smem + 2 * S::STAGE);
+    T *s_cval = reinterpret_cast<T *>(smem + 2 * S::STAGE + BLOCK * 4);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + BLOCK * (4 + sizeof(T)));
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int t, int stage) {
+        const int64_t k0 = tiles[t], k1 = tiles[t + 1];
+        unsigned char *base = smem + stage * S::STAGE;
+        if (k1 <= k0) {  // empty tile: complete the phase with no bytes
+            mbar_arrive_expect_tx(&bar[stage], 0u);
+            return;
+        }
+        const TileRanges g = coo_ranges<T>(k0, k1);
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)(2 * g.rbytes + g.vbytes));
+        bulk_g2s(base, crow + g.ra, (uint32_t)g.rbytes, &bar[stage]);
+        bulk_g2s(base + g.rbytes, ccol + g.ca, (uint32_t)g.cbytes, &bar[stage]);
+        bulk_g2s(base + 2 * g.rbytes, cval + g.va, (uint32_t)g.vbytes, &bar[stage]);
+    };
+
+    T d0 = T(0), d1 = T(0);
+    int it = 0;
+    bool ok = true, pending_prefetch = false;
+    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int stage = it & 1;
+        const int tn = t + gridDim.x;
+        pending_prefetch = tn < ntiles;
+        if (tid == 0 && tn < ntiles) {
+            fence_proxy_async();
+            issue(tn, stage ^ 1);
+        }
+        const int64_t kt0 = tiles[t], kt1 = tiles[t + 1];
+        const TileRanges g = coo_ranges<T>(kt0, max(kt1, kt0 + 1));
+        const unsigned char *sb = smem + stage * S::STAGE;
+        const int *s_row = reinterpret_cast<const int *>(sb) + (kt0 - g.ra);
+        const int *s_col = reinterpret_cast<const int *>(sb + g.rbytes) + (kt0 - g.ca);
+        const T *s_val = reinterpret_cast<const T *>(sb + 2 * g.rbytes) + (kt0 - g.va);
+        if (!mbar_wait(&bar[stage], (uint32_t)((it >> 1) & 1), err)) {
+            ok = false;
+            break;
+        }
+        const int tile_n = (int)(kt1 - kt0);
+        const int l0 = (int)((int64_t)tid * tile_n / BLOCK), l1 = (int)((int64_t)(tid + 1) * tile_n / BLOCK);
+        auto row_at = [&](int64_t k) -> int {  // row of global entry k (k in [0, nnz))
+            return (k >= kt0 && k < kt1) ? s_row[k - kt0] : __ldg(crow + k);
+        };
+        auto gap = [&](int from, int to) {  // rows [from, to) have no entries
+            if (add_mode) return;
+            for (int q = from; q < to; ++q) final_write(e, q, T(0), d0, d1);
+        };
+        T sum = T(0), pend = T(0);
+        bool has_pend = false;
+        int r = -1, rfirst = -1;
+        int crow_out = kEmpty;
+        if (l0 < l1) {
+            const int64_t k0 = kt0 + l0;
+            r = rfirst = s_row[l0];
+            const bool pend_possible = k0 > 0 && row_at(k0 - 1) == r;
+            if (k0 == 0) gap(0, r);
+            bool first = true;
+            auto emit = [&](int row, T s) {
+                if (first && pend_possible) {
+                    pend = s;
+                    has_pend = true;
+                } else if (add_mode) {
+                    e.y[row] += e.alpha * s;
+                } else {
+                    final_write(e, row, s, d0, d1);
+                }
+                first = false;
+            };
+            const int cnt = l1 - l0;
+            for (int c = 0; c < cnt; c += CH) {
+                T v[CH], xv[CH];
+                int rr[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const int k = l0 + c + u;
+                    if (c + u < cnt) {
+                        v[u] = s_val[k];
+                        xv[u] = __ldg(x + s_col[k]);
+                        rr[u] = s_row[k];
+                    } else {
+                        v[u] = T(0);
+                        xv[u] = T(0);
+                        rr[u] = r;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (c + u < cnt) {
+                        if (rr[u] != r) {
+                            emit(r, sum);
+                            gap(r + 1, rr[u]);
+                            r = rr[u];
+                            sum = T(0);
+                        }
+                        sum = fma(v[u], xv[u], sum);
+                    }
+                }
+            }
+            const int64_t kn = kt0 + l1;
+            const int nr = kn < nnz ? row_at(kn) : (int)n;
+            if (nr == r) {
+                crow_out = r;
+            } else {
+                emit(r, sum);
+                gap(r + 1, nr);
+                sum = T(0);
+                crow_out = kNoCarry;
+            }
+        }
+        s_crow[tid] = crow_out;
+        s_cval[tid] = sum;
+        __syncthreads();
+        if (has_pend) {
+            T tot = pend;
+            int k = tid - 1;
+            while (k >= 0 && (s_crow[k] == rfirst || s_crow[k] == kEmpty)) {
+                if (s_crow[k] == rfirst) tot += s_cval[k];
+                --k;
+            }
+            if (k < 0 && kt0 > 0 && row_at(kt0 - 1) == rfirst) {  // the row began in an earlier tile
+                for (int tp = t - 1; tp >= 0; --tp) {
+                    if (!flag_wait(flags + tp, err)) break;
+                    tot += ldcg(carry_val_g + tp);
+                    flags[tp] = 0;
+                    const int64_t ps = tiles[tp];
+                    if (!(ps > 0 && __ldg(crow + ps) == rfirst && __ldg(crow + ps - 1) == rfirst)) break;
+                }
+            }
+            if (add_mode) e.y[rfirst] += e.alpha * tot;
+            else final_write(e, rfirst, tot, d0, d1);
+        }
+        if (tid == BLOCK - 1 && kt1 < nnz && kt1 > kt0 && s_row[tile_n - 1] == __ldg(crow + kt1)) {
+            const int cr = s_row[tile_n - 1];
+            T cv = T(0);
+            for (int k = BLOCK - 1; k >= 0 && (s_crow[k] == cr || s_crow[k] == kEmpty); --k)
+                if (s_crow[k] == cr) cv += s_cval[k];
+            carry_row_g[t] = cr;
+            carry_val_g[t] = cv;
+            flag_publish(flags + t);
+        }
+        __syncthreads();
+    }
+    if (!ok && pending_prefetch)
+        mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), err, 200000000LL);
+    if (e.dots && !add_mode) finish_dots<T, BLOCK>(d0, d1, e, partials, ticket);
+}
+
+// COO tile map: boundary t at entry k = min(t * tile, nnz), moved forward to
+// the start of the next row when that is at most `slack` entries away.
+__global__ void k_coo_tiles(int64_t nnz, const int *__restrict__ crow, int64_t tile, int64_t slack, int ntiles,
+                            int *tiles, unsigned *nsplit)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    int64_t k = min((int64_t)t * tile, nnz);
+    if (k > 0 && k < nnz && crow[k - 1] == crow[k]) {
+        const int r = crow[k];
+        const int64_t hi = min(k + slack, nnz);
+        if (hi < nnz && crow[hi] == r) {
+            atomicAdd(nsplit, 1u);  // the row runs on past the slack: keep the split
+        } else {  // first q in [k, hi] with q == nnz or crow[q] != r
+            int64_t lo = k, h = hi;
+            while (lo < h) {
+                const int64_t mid = (lo + h) >> 1;
+                if (crow[mid] == r) lo = mid + 1;
+                else h = mid;
+            }
+            k = lo;
+        }
+    }
+    tiles[t] = (int)k;
+}
+
+// ------------------------------------------------------------------ whole-vector epilogue
+// y = beta * z (alpha * A x with no stored entries), used for empty matrices.
+template <class T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_scale_only(int64_t n, Epi<T> e, T *partials, unsigned *ticket)
+{
+    if (e.skip && *e.skip) return;
+    T d0 = T(0), d1 = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK)
+        final_write(e, i, T(0), d0, d1);
+    if (e.dots) finish_dots<T, BLOCK>(d0, d1, e, partials, ticket);
+}
+
+// dots over an already stored y (HYB needs them after both parts are added)
+template <class T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    k_dots_of_y(int64_t n, Epi<T> e, T *partials, unsigned *ticket)
+{
+    if (e.skip && *e.skip) return;
+    T d0 = T(0), d1 = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+        const T v = e.y[i];
+        if (e.w) d0 = fma(e.w[i], v, d0);
+        if (e.want_yy) d1 = fma(v, v, d1);
+    }
+    finish_dots<T, BLOCK>(d0, d1, e, partials, ticket);
+}
+
+// ------------------------------------------------------------------ host side
+namespace {
+
+constexpr int kVecBlock = 256;
+constexpr int kEllBlock = 256;
+constexpr int kMergeBlock = 128;
+constexpr int kCooBlock = 128;
+
+template <class K> int grid_for(spx_ctx *ctx, K kernel, int block, int smem, int64_t work_blocks)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)per_sm * ctx->sm_count;
+    if (g > work_blocks) g = work_blocks;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <class K> int set_smem(K kernel, int bytes)
+{
+    static_assert(sizeof(K) > 0, "");
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e == cudaSuccess ? SPX_OK : cuda_fail(e, "cudaFuncSetAttribute(max dynamic smem)");
+}
+
+// Scratch (carries, look-back flags, partials, ticket) sized for the largest
+// grid / tile count seen.  Flags start at zero and are left at zero by every
+// launch (each consumer resets the flag it used).
+int ensure_scratch(spx_ctx *ctx, spx_matrix *A, int64_t ntiles, int64_t grid, size_t vbytes)
+{
+    const size_t need_c = (size_t)(ntiles + 1);
+    if (A->carry_row.bytes < need_c * 4) {
+        dbuf_free(ctx, A->carry_row);
+        dbuf_free(ctx, A->carry_val);
+        dbuf_free(ctx, A->flags);
+        SPX_TRY(dbuf_alloc(ctx, A->carry_row, need_c * 4));
+        SPX_TRY(dbuf_alloc(ctx, A->carry_val, need_c * 8));
+        SPX_TRY(dbuf_alloc(ctx, A->flags, need_c * 4));
+        SPX_CUDA(cudaMemsetAsync(A->flags.p, 0, need_c * 4, ctx->stream));
+    }
+    const size_t need_p = (size_t)(2 * grid + 2) * 8;
+    if (A->partials.bytes < need_p) {
+        dbuf_free(ctx, A->partials);
+        SPX_TRY(dbuf_alloc(ctx, A->partials, need_p));
+    }
+    if (!A->ticket.p) {
+        SPX_TRY(dbuf_alloc(ctx, A->ticket, 64));
+        SPX_CUDA(cudaMemsetAsync(A->ticket.p, 0, 64, ctx->stream));
+    }
+    (void)vbytes;
+    return SPX_OK;
+}
+
+// Launch, cooperatively when blocks may wait on one another (look-back).
+template <class... KArgs, class... Args>
+int launch_k(void (*kern)(KArgs...), int grid, int block, int smem, cudaStream_t st, bool coop, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = coop ? at : nullptr;
+    cfg.numAttrs = coop ? 1 : 0;
+    SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+    return SPX_OK;
+}
+
+int ensure_coo_tiles(spx_ctx *ctx, spx_matrix *A, int64_t tile_items, int64_t slack)
+{
+    if (A->coo_tiles.p && A->coo_tiles_items == tile_items) return SPX_OK;
+    const int64_t ntiles = ceil_div(A->coo_nnz, tile_items);
+    if (ntiles + 1 > INT_MAX) return fail(SPX_ERR_TOO_LARGE, "too many COO tiles");
+    dbuf_free(ctx, A->coo_tiles);
+    SPX_TRY(dbuf_alloc(ctx, A->coo_tiles, (size_t)(ntiles + 1) * 4 + 16));
+    unsigned *cnt = reinterpret_cast<unsigned *>(A->coo_tiles.as<int>() + ntiles + 1);
+    SPX_CUDA(cudaMemsetAsync(cnt, 0, 4, ctx->stream));
+    k_coo_tiles<<<(int)ceil_div(ntiles + 1, 256), 256, 0, ctx->stream>>>(
+        A->coo_nnz, A->coo_row.as<int>(), tile_items, slack, (int)ntiles, A->coo_tiles.as<int>(), cnt);
+    SPX_CUDA(cudaGetLastError());
+    unsigned h = 0;
+    SPX_CUDA(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    A->coo_tiles_items = tile_items;
+    A->coo_ntiles = ntiles;
+    A->coo_nsplit = h;
+    return SPX_OK;
+}
+
+template <class T, int IPT>
+int launch_merge(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    using S = MergeShape<T, kMergeBlock, IPT>;
+    auto kern = k_csr_merge<T, kMergeBlock, IPT>;
+    SPX_TRY(ensure_merge_tiles(ctx, A, S::TILE, S::SLACK));
+    static bool attr = false;
+    if (!attr) {
+        SPX_TRY(set_smem(kern, S::SMEM));
+        attr = true;
+    }
+    const int grid = grid_for(ctx, kern, kMergeBlock, S::SMEM, A->ntiles);
+    SPX_TRY(ensure_scratch(ctx, A, A->ntiles, grid, sizeof(T)));
+    return launch_k(kern, grid, kMergeBlock, S::SMEM, ctx->stream, A->nsplit > 0, (int)A->n,
+                    (const int *)A->rp.as<int>(), (const int *)A->col.as<int>(), val, x,
+                    (const int2 *)A->tiles.as<int2>(), (int)A->ntiles, A->carry_row.as<int>(), A->carry_val.as<T>(),
+                    A->flags.as<int>(), A->partials.as<T>(), A->ticket.as<unsigned>(), ctx->dev_err, e);
+}
+
+template <class T, int SW>
+int launch_vector(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    auto kern = k_csr_vector<T, SW, kVecBlock>;
+    const int64_t rows_per_block = (kVecBlock / 32) * (32 / SW);
+    const int grid = grid_for(ctx, kern, kVecBlock, 0, ceil_div(A->n, rows_per_block));
+    SPX_TRY(ensure_scratch(ctx, A, 0, grid, sizeof(T)));
+    kern<<<grid, kVecBlock, 0, ctx->stream>>>(A->n, A->rp.as<int>(), A->col.as<int>(), val, x, e,
+                                              A->partials.as<T>(), A->ticket.as<unsigned>());
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T, int R>
+int launch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const Epi<T> &e)
+{
+    auto kern = k_ell<T, R, kEllBlock>;
+    const int grid = grid_for(ctx, kern, kEllBlock, 0, ceil_div(ceil_div(A->n, R), kEllBlock));
+    SPX_TRY(ensure_scratch(ctx, A, 0, grid, sizeof(T)));
+    kern<<<grid, kEllBlock, 0, ctx->stream>>>(A->n, A->ell_ld, (int)A->ell_w, A->ell_col.as<int>(),
+                                              eval, x, e, A->partials.as<T>(),
+                                              A->ticket.as<unsigned>());
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T, int IPT>
+int launch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
+{
+    using S = CooShape<T, kCooBlock, IPT>;
+    auto kern = k_coo<T, kCooBlock, IPT>;
+    static bool attr = false;
+    if (!attr) {
+        SPX_TRY(set_smem(kern, S::SMEM));
+        attr = true;
+    }
+    SPX_TRY(ensure_coo_tiles(ctx, A, S::TILE, S::SLACK));
+    const int64_t ntiles = A->coo_ntiles;
+    const int grid = grid_for(ctx, kern, kCooBlock, S::SMEM, ntiles);
+    SPX_TRY(ensure_scratch(ctx, A, ntiles, grid, sizeof(T)));
+    return launch_k(kern, grid, kCooBlock, S::SMEM, ctx->stream, A->coo_nsplit > 0, A->n, A->coo_nnz,
+                    (const int *)A->coo_row.as<int>(), (const int *)A->coo_col.as<int>(), cval, x,
+                    (const int *)A->coo_tiles.as<int>(), (int)ntiles, A->carry_row.as<int>(),
+                    A->carry_val.as<T>(), A->flags.as<int>(), A->partials.as<T>(), A->ticket.as<unsigned>(),
+                    ctx->dev_err, e, add);
+}
+
+template <class T> int launch_scale_only(spx_ctx *ctx, spx_matrix *A, const Epi<T> &e)
+{
+    auto kern = k_scale_only<T, 256>;
+    const int grid = grid_for(ctx, kern, 256, 0, ceil_div(A->n, 256));
+    SPX_TRY(ensure_scratch(ctx, A, 0, grid, sizeof(T)));
+    kern<<<grid, 256, 0, ctx->stream>>>(A->n, e, A->partials.as<T>(), A->ticket.as<unsigned>());
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T> int launch_dots_of_y(spx_ctx *ctx, spx_matrix *A, const Epi<T> &e)
+{
+    auto kern = k_dots_of_y<T, 256>;
+    const int grid = grid_for(ctx, kern, 256, 0, ceil_div(A->n, 256));
+    SPX_TRY(ensure_scratch(ctx, A, 0, grid, sizeof(T)));
+    kern<<<grid, 256, 0, ctx->stream>>>(A->n, e, A->partials.as<T>(), A->ticket.as<unsigned>());
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T>
+int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    int kern = A->kernel, p = A->kparam;
+    if (kern == SPX_KERNEL_AUTO) kern = SPX_KERNEL_CSR_MERGE;
+    if (kern == SPX_KERNEL_CSR_VECTOR) {
+        if (p <= 0) {  // sub-warp width from the mean row length
+            p = 1;
+            while (p < 32 && p < A->mean_len) p <<= 1;
+        }
+        switch (p) {
+        case 1: return launch_vector<T, 1>(ctx, A, val, x, e);
+        case 2: return launch_vector<T, 2>(ctx, A, val, x, e);
+        case 4: return launch_vector<T, 4>(ctx, A, val, x, e);
+        case 8: return launch_vector<T, 8>(ctx, A, val, x, e);
+        case 16: return launch_vector<T, 16>(ctx, A, val, x, e);
+        case 32: return launch_vector<T, 32>(ctx, A, val, x, e);
+        default: return fail(SPX_ERR_INVALID, "CSR vector sub-warp width must be 1..32, a power of 2");
+        }
+    }
+    if (kern == SPX_KERNEL_CSR_MERGE) {
+        if (p <= 0) p = 16;
+        switch (p) {
+        case 8: return launch_merge<T, 8>(ctx, A, val, x, e);
+        case 16: return launch_merge<T, 16>(ctx, A, val, x, e);
+        case 32: return launch_merge<T, 32>(ctx, A, val, x, e);
+        default: return fail(SPX_ERR_INVALID, "merge items per thread must be 8, 16 or 32");
+        }
+    }
+    return fail(SPX_ERR_UNSUPPORTED, "kernel not valid for a CSR matrix");
+}
+
+template <class T>
+int dispatch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const Epi<T> &e)
+{
+    int p = A->kernel == SPX_KERNEL_ELL ? A->kparam : 0;
+    if (p <= 0) p = (int)(16 / sizeof(T));
+    if constexpr (sizeof(T) == 8) {
+        if (p == 1) return launch_ell<T, 1>(ctx, A, eval, x, e);
+        if (p == 2) return launch_ell<T, 2>(ctx, A, eval, x, e);
+    } else {
+        if (p == 1) return launch_ell<T, 1>(ctx, A, eval, x, e);
+        if (p == 2) return launch_ell<T, 2>(ctx, A, eval, x, e);
+        if (p == 4) return launch_ell<T, 4>(ctx, A, eval, x, e);
+    }
+    return fail(SPX_ERR_INVALID, "ELL rows per thread must be 1, 2 (FP64) or 1, 2, 4 (FP32)");
+}
+
+template <class T>
+int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
+{
+    int p = A->kernel == SPX_KERNEL_COO ? A->kparam : 0;
+    if (p <= 0) p = 16;
+    switch (p) {
+    case 8: return launch_coo<T, 8>(ctx, A, cval, x, e, add);
+    case 16: return launch_coo<T, 16>(ctx, A, cval, x, e, add);
+    case 32: return launch_coo<T, 32>(ctx, A, cval, x, e, add);
+    default: return fail(SPX_ERR_INVALID, "COO items per thread must be 8, 16 or 32");
+    }
+}
+
+}  // namespace
+
+int ensure_merge_tiles(spx_ctx *ctx, spx_matrix *A, int64_t tile_items, int64_t slack)
+{
+    if (A->tiles.p && A->tiles_items == tile_items) return SPX_OK;
+    const int64_t items = A->n + A->nnz;
+    const int64_t ntiles = ceil_div(items, tile_items);
+    if (ntiles + 1 > INT_MAX) return fail(SPX_ERR_TOO_LARGE, "too many merge tiles");
+    dbuf_free(ctx, A->tiles);
+    SPX_TRY(dbuf_alloc(ctx, A->tiles, (size_t)(ntiles + 1) * sizeof(int2) + 16));
+    unsigned *cnt = reinterpret_cast<unsigned *>(A->tiles.as<int2>() + ntiles + 1);
+    SPX_CUDA(cudaMemsetAsync(cnt, 0, 4, ctx->stream));
+    const int threads = 256;
+    k_merge_tiles<<<(int)ceil_div(ntiles + 1, threads), threads, 0, ctx->stream>>>(
+        (int)A->n, (int)A->nnz, A->rp.as<int>(), tile_items, slack, (int)ntiles, A->tiles.as<int2>(), cnt);
+    SPX_CUDA(cudaGetLastError());
+    unsigned h = 0;
+    SPX_CUDA(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    A->tiles_items = tile_items;
+    A->ntiles = ntiles;
+    A->nsplit = h;
+    return SPX_OK;
+}
+
+template <class T>
+int spmv_launch(spx_ctx *ctx, const spx_matrix *Ac, const T *x, const Epi<T> &e, bool use32)
+{
+    spx_matrix *A = const_cast<spx_matrix *>(Ac);
+    if (A->n == 0) return SPX_OK;
+    auto pick = [&](const spx::DBuf &v64, const spx::DBuf &v32) -> const T * {
+        return static_cast<const T *>(use32 ? v32.p : v64.p);
+    };
+    switch (A->format) {
+    case SPX_CSR:
+        if (A->nnz == 0) return launch_scale_only<T>(ctx, A, e);
+        return dispatch_csr<T>(ctx, A, pick(A->val, A->val32), x, e);
+    case SPX_ELL:
+        if (A->ell_w == 0) return launch_scale_only<T>(ctx, A, e);
+        return dispatch_ell<T>(ctx, A, pick(A->ell_val, A->ell_val32), x, e);
+    case SPX_COO:
+        if (A->coo_nnz == 0) return launch_scale_only<T>(ctx, A, e);
+        return dispatch_coo<T>(ctx, A, pick(A->coo_val, A->coo_val32), x, e, 0);
+    case SPX_HYB: {
+        Epi<T> first = e;
+        first.dots = nullptr;
+        first.fin = FIN_NONE;
+        first.w = nullptr;
+        first.want_yy = false;
+        if (A->ell_w > 0) SPX_TRY(dispatch_ell<T>(ctx, A, pick(A->ell_val, A->ell_val32), x, first));
+        else SPX_TRY(launch_scale_only<T>(ctx, A, first));
+        if (A->coo_nnz > 0) {
+            Epi<T> add = first;
+            add.z = nullptr;
+            SPX_TRY(dispatch_coo<T>(ctx, A, pick(A->coo_val, A->coo_val32), x, add, 1));
+        }
+        if (e.dots) SPX_TRY(launch_dots_of_y<T>(ctx, A, e));
+        return SPX_OK;
+    }
+    default: return fail(SPX_ERR_INVALID, "unknown matrix format");
+    }
+}
+
+template int spmv_launch<double>(spx_ctx *, const spx_matrix *, const double *, const Epi<double> &, bool);
+template int spmv_launch<float>(spx_ctx *, const spx_matrix *, const float *, const Epi<float> &, bool);
+
+}  // namespace spx

@@ -1,0 +1,148 @@
+// spx_internal.cuh -- types and helpers shared by the libspx CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/spx.h"
+
+namespace spx {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+int fail(int status, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define SPX_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return ::spx::cuda_fail(e_, #call);       \
+    } while (0)
+
+#define SPX_TRY(call)                                                    \
+    do {                                                                 \
+        int s_ = (call);                                                 \
+        if (s_ != SPX_OK) return s_;                                     \
+    } while (0)
+
+// ------------------------------------------------------------------ device error word
+// Bit flags a kernel may set in ctx->dev_err instead of trapping.
+enum : unsigned { DEVERR_MBAR_TIMEOUT = 1u, DEVERR_BOUNDS = 2u, DEVERR_QUEUE_TIMEOUT = 4u };
+
+}  // namespace spx
+
+// ------------------------------------------------------------------ context
+struct spx_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    spx_alloc_fn alloc = nullptr;
+    spx_free_fn free = nullptr;
+    void *user = nullptr;
+    int sm_count = 0;
+    int max_smem_optin = 0;
+    int64_t l2_bytes = 0;
+    // small always-resident device scratch: reduction tickets, flags
+    unsigned *dev_err = nullptr;      // device error word
+    unsigned *host_err = nullptr;     // pinned mirror
+    // scratch of the stand-alone BLAS-1 reductions (spx_dot): block partials + ticket
+    void *red = nullptr;
+    int red_grid = 0;
+    cudaStream_t capture_stream = nullptr;  // private stream used only to capture CUDA graphs
+};
+
+namespace spx {
+
+void *dalloc(spx_ctx *ctx, size_t bytes);
+void dfree(spx_ctx *ctx, void *p, size_t bytes);
+
+// A device buffer owned by a handle, freed through the allocating context.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+int dbuf_alloc(spx_ctx *ctx, DBuf &b, size_t bytes);
+void dbuf_free(spx_ctx *ctx, DBuf &b);
+
+inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Padding added after every array the library owns, so that 16-byte aligned
+// bulk copies that round a range outwards stay inside the allocation.
+constexpr size_t kArrayPad = 64;
+
+struct SolverWork;  // solvers.cu
+
+}  // namespace spx
+
+// ------------------------------------------------------------------ matrices
+struct spx_matrix {
+    spx_ctx *ctx = nullptr;   // allocating context
+    int format = SPX_CSR;
+    int dtype = SPX_F64;
+    int64_t n = 0, ncols = 0, nnz = 0;
+    int64_t max_len = 0;
+    double mean_len = 0.0;
+    // CSR (CSR format; also kept for the merge tile map)
+    spx::DBuf rp, col, val, val32;
+    // ELL (ELL format or HYB ELL part), column-major [width][ld]
+    int64_t ell_w = 0, ell_ld = 0;
+    spx::DBuf ell_col, ell_val, ell_val32;
+    // COO (COO format or HYB COO part)
+    int64_t coo_nnz = 0;
+    spx::DBuf coo_row, coo_col, coo_val, coo_val32;
+    // SpMV kernel selection
+    int kernel = SPX_KERNEL_AUTO, kparam = 0;
+    // merge-path tile map (CSR), rebuilt when the tile size changes
+    spx::DBuf tiles;          // int2 per tile boundary
+    int64_t tiles_items = 0;  // items per tile the map was built for
+    int64_t ntiles = 0;
+    int64_t nsplit = 0;       // boundaries that split a row (need the look-back)
+    // COO tile map (COO format / HYB COO part)
+    spx::DBuf coo_tiles;      // int per tile boundary
+    int64_t coo_tiles_items = 0, coo_ntiles = 0, coo_nsplit = 0;
+    // per-tile carries, look-back flags, reduction scratch of the SpMV kernels
+    spx::DBuf carry_row, carry_val, flags, partials;
+    spx::DBuf ticket;  // unsigned counters for last-block detection
+    // host staging for spx_spmv_host
+    spx::DBuf stage_x, stage_y;
+    // solver workspace (solvers.cu)
+    spx::SolverWork *work = nullptr;
+};
+
+namespace spx {
+
+// ------------------------------------------------------------------ SpMV epilogue
+// The SpMV kernels compute t_i = (A x)_i and store
+//     y_i = alpha * t_i + beta * z_i          (z may be y itself or null: beta ignored)
+// and, optionally, two dot products over the stored y:
+//     d0 = sum_i w_i * y_i   (w != null)      d1 = sum_i y_i * y_i   (want_yy)
+// reduced deterministically; the last block writes them to dots[0..1] and
+// then runs the scalar update `fin` (solver bookkeeping, see solvers.cu).
+template <class T> struct Epi {
+    T alpha = T(1), beta = T(0);
+    const T *z = nullptr;
+    T *y = nullptr;
+    const T *w = nullptr;
+    bool want_yy = false;
+    T *dots = nullptr;        // device, 2 entries; null = no dots
+    int fin = 0;              // scalar update id (0 = none)
+    void *fin_state = nullptr;
+    const int *skip = nullptr;  // device flag: if *skip != 0 the kernel returns at once
+};
+
+// Launchers (spmv.cu).  All asynchronous on ctx->stream.
+template <class T>
+int spmv_launch(spx_ctx *ctx, const spx_matrix *A, const T *x, const Epi<T> &epi, bool use32 = false);
+
+// Deterministic reductions and vector kernels (blas1.cu).
+template <class T> int dot_launch(spx_ctx *ctx, int64_t n, const T *x, const T *y, T *result);
+template <class T> int axpby_launch(spx_ctx *ctx, int64_t n, T alpha, const T *x, T beta, T *y);
+
+// Tile map for merge-path CSR (spmv.cu).
+int ensure_merge_tiles(spx_ctx *ctx, spx_matrix *A, int64_t tile_items, int64_t slack);
+
+
+}  // namespace spx

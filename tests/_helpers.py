@@ -56,3 +56,22 @@ def laplace1d(m):
         if i + 1 < m:
             d[i, i + 1] = -1.0
     return csr_from_dense(d)
+
+
+# ---------------------------------------------------------------- parity tolerances
+# FP64 SpMV: ||y - y_ref|| <= 1e-12 ||y_ref|| and, per row,
+# |y_i - y_ref,i| <= 1e-12 (|A||x|)_i.  FP32: the same form at 1e-5 against the
+# FP64 oracle applied to the FP32-rounded A and x.  y_ref is the compensated
+# oracle, whose own error is negligible at these scales.
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def assert_spmv_close(y, yref, bound, rel):
+    y = np.asarray(y, dtype=np.float64)
+    err = np.abs(y - yref)
+    bad = err > rel * bound + 1e-300
+    assert not bad.any(), (f"{bad.sum()} rows off; worst row {int(np.argmax(err - rel * bound))}: "
+                           f"err {err.max():.3e} bound {bound[np.argmax(err - rel * bound)]:.3e}")
+    ny = np.linalg.norm(yref)
+    if ny > 0:
+        assert np.linalg.norm(y - yref) <= rel * ny

@@ -1,0 +1,149 @@
+"""GPU batched solves (one persistent launch for all systems) against the CPU
+oracle, system by system: true residual re-formed by the oracle's SpMV,
+error against x*, iteration counts close to the single-system oracle, batch
+order invariance (bit for bit) and the tuner."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_10116_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def spx():
+    from paper_2103_10116_gb300 import spx as s
+    s.load()
+    return s
+
+
+@pytest.fixture(scope="module")
+def ctx(spx):
+    c = spx.spx_ctx_create(0)
+    yield c
+    torch.cuda.synchronize()
+    spx.spx_ctx_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    nsys = 40
+    ro, no, rp, col, val = synth.batch_ragged_laplace(nsys, 100, 3000, seed=4)
+    xs = synth.uniform_vector(int(ro[-1]), seed=5)
+    b = np.empty_like(xs)
+    systems = []
+    for s in range(nsys):
+        r0, r1 = int(ro[s]), int(ro[s + 1])
+        lrp = rp[r0 + s: r1 + s + 1]
+        lcol = col[no[s]: no[s + 1]]
+        lval = val[no[s]: no[s + 1]]
+        b[r0:r1] = oracle.spmv_csr(lrp, lcol, lval, xs[r0:r1])
+        systems.append((lrp, lcol, lval))
+    b[int(ro[7]): int(ro[8])] = 0.0  # one system with b = 0
+    return ro, no, rp, col, val, xs, b, systems
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _check(ro, xs, b, systems, x, tol, err_tol, infos=None, oracle_solver=None):
+    for s, (lrp, lcol, lval) in enumerate(systems):
+        r0, r1 = int(ro[s]), int(ro[s + 1])
+        xb = x[r0:r1]
+        if not b[r0:r1].any():
+            assert not xb.any()
+            continue
+        rr = b[r0:r1] - oracle.spmv_csr(lrp, lcol, lval, xb)
+        assert np.linalg.norm(rr) / np.linalg.norm(b[r0:r1]) <= tol * 1.05, s
+        assert np.linalg.norm(xb - xs[r0:r1]) / np.linalg.norm(xs[r0:r1]) <= err_tol, s
+        if infos is not None and oracle_solver is not None:
+            _, oi = oracle_solver(lrp, lcol, lval, b[r0:r1], tol=tol, maxit=20000)
+            assert abs(infos[s].iterations - oi.iterations) <= max(3, oi.iterations // 10), (s, infos[s], oi)
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+def test_batch_fp64(spx, ctx, batch, solver):
+    ro, no, rp, col, val, xs, b, systems = batch
+    B = spx.spx_batch_create(ctx, ro, no, _t(rp), _t(col), _t(val))
+    try:
+        x = torch.zeros(int(ro[-1]), dtype=torch.float64, device=DEV)
+        infos = spx.spx_batch_solve(ctx, B, _t(b), x, len(systems), solver, 1e-10, 20000)
+        assert all(i.status == spx.SPX_CONVERGED for i in infos), [i.status for i in infos]
+        _check(ro, xs, b, systems, x.cpu().numpy(), 1e-10, 1e-7, infos,
+               oracle.cg if solver == "cg" else oracle.bicgstab)
+        # a second solve replays the captured graph: same bits
+        x2 = torch.zeros_like(x)
+        spx.spx_batch_solve(ctx, B, _t(b), x2, len(systems), solver, 1e-10, 20000)
+        assert torch.equal(x, x2)
+    finally:
+        spx.spx_batch_destroy(B)
+
+
+def test_batch_fp32(spx, ctx, batch):
+    ro, no, rp, col, val, xs, b, systems = batch
+    B = spx.spx_batch_create(ctx, ro, no, _t(rp), _t(col), _t(val).float())
+    try:
+        x = torch.zeros(int(ro[-1]), dtype=torch.float32, device=DEV)
+        infos = spx.spx_batch_solve(ctx, B, _t(b).float(), x, len(systems), "cg", 1e-5, 20000, precision="f32")
+        assert all(i.status == spx.SPX_CONVERGED for i in infos)
+        xh = x.double().cpu().numpy()
+        for s, (lrp, lcol, lval) in enumerate(systems):
+            r0, r1 = int(ro[s]), int(ro[s + 1])
+            bs = b[r0:r1].astype(np.float32).astype(np.float64)
+            if not bs.any():
+                continue
+            rr = bs - oracle.spmv_csr(lrp, lcol, lval.astype(np.float32).astype(np.float64), xh[r0:r1])
+            assert np.linalg.norm(rr) / np.linalg.norm(bs) <= 2e-5
+    finally:
+        spx.spx_batch_destroy(B)
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+def test_batch_mixed(spx, ctx, batch, solver):
+    ro, no, rp, col, val, xs, b, systems = batch
+    B = spx.spx_batch_create(ctx, ro, no, _t(rp), _t(col), _t(val), flags=spx.SPX_MIXED_SHADOW)
+    try:
+        x = torch.zeros(int(ro[-1]), dtype=torch.float64, device=DEV)
+        infos = spx.spx_batch_solve(ctx, B, _t(b), x, len(systems), solver, 1e-10, 20000, precision="mixed")
+        assert all(i.status == spx.SPX_CONVERGED for i in infos), [i.status for i in infos]
+        _check(ro, xs, b, systems, x.cpu().numpy(), 1e-10, 1e-7)
+    finally:
+        spx.spx_batch_destroy(B)
+
+
+def test_batch_order_invariance_and_tune(spx, ctx, batch):
+    ro, no, rp, col, val, xs, b, systems = batch
+    nsys = len(systems)
+    perm = np.random.default_rng(0).permutation(nsys)
+    # rebuild the batch in permuted order
+    sizes = np.diff(ro)[perm]
+    ro2 = np.concatenate([[0], np.cumsum(sizes)])
+    nz = np.diff(no)[perm]
+    no2 = np.concatenate([[0], np.cumsum(nz)])
+    rp2 = np.concatenate([systems[s][0] for s in perm])
+    col2 = np.concatenate([systems[s][1] for s in perm])
+    val2 = np.concatenate([systems[s][2] for s in perm])
+    b2 = np.concatenate([b[int(ro[s]):int(ro[s + 1])] for s in perm])
+    B1 = spx.spx_batch_create(ctx, ro, no, _t(rp), _t(col), _t(val))
+    B2 = spx.spx_batch_create(ctx, ro2, no2, _t(rp2), _t(col2), _t(val2))
+    try:
+        x1 = torch.zeros(int(ro[-1]), dtype=torch.float64, device=DEV)
+        x2 = torch.zeros(int(ro[-1]), dtype=torch.float64, device=DEV)
+        spx.spx_batch_solve(ctx, B1, _t(b), x1, nsys, "cg", 1e-10, 20000)
+        spx.spx_batch_solve(ctx, B2, _t(b2), x2, nsys, "cg", 1e-10, 20000)
+        x1h, x2h = x1.cpu().numpy(), x2.cpu().numpy()
+        for k, s in enumerate(perm):
+            assert np.array_equal(x1h[int(ro[s]):int(ro[s + 1])], x2h[int(ro2[k]):int(ro2[k + 1])])
+        chosen = spx.spx_batch_tune(ctx, B1, "cg")
+        assert chosen in (128, 256, 512, 1024)
+        x1.zero_()
+        infos = spx.spx_batch_solve(ctx, B1, _t(b), x1, nsys, "cg", 1e-10, 20000)
+        assert all(i.status == spx.SPX_CONVERGED for i in infos)
+        _check(ro, xs, b, systems, x1.cpu().numpy(), 1e-10, 1e-7)
+    finally:
+        spx.spx_batch_destroy(B1)
+        spx.spx_batch_destroy(B2)
