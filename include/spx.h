@@ -237,6 +237,48 @@ int spx_batch_solve(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int solv
  * *chosen receives the threads per system picked.  Synchronous. */
 int spx_batch_tune(spx_ctx *ctx, spx_batch *B, int solver, int precision, int *chosen);
 
+/* ------------------------------------------------------------------ serving */
+
+/* A continuous-batching solve server on ctx's device.  budget_bytes caps the
+ * device memory of the requests running at once (<= 0: 90% of the free
+ * memory at creation); max_slots is the number of requests that may run
+ * concurrently, each on its own stream (1..64).  The server owns worker
+ * threads and their contexts (allocating with cudaMallocAsync); ctx is only
+ * used to pick the device.  Errors: SPX_ERR_INVALID, SPX_ERR_CUDA. */
+int spx_server_create(spx_ctx *ctx, spx_server **out, int64_t budget_bytes, int max_slots);
+
+/* Queue one solve A x = b.  row_ptr[n+1], col_idx[nnz], values[nnz] (double),
+ * b[n] and x[n] are HOST buffers that must stay valid (and x untouched) until
+ * the request completes; the operator is uploaded when the request is
+ * admitted (FIFO, as soon as its device footprint fits in the budget) and
+ * freed when it completes.  x receives the solution (initial guess 0).
+ * solver / tol / max_iter / restart / precision as in spx_solve (MIXED keeps
+ * an FP32 copy of the values).  *req_id receives the request id.  Returns at
+ * once.  Errors: SPX_ERR_INVALID, SPX_ERR_TOO_LARGE (footprint > budget). */
+int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                      const double *values, const double *b, double *x, int solver, double tol, int64_t max_iter,
+                      int restart, int precision, int64_t *req_id);
+
+typedef struct {
+    int64_t id;
+    int32_t error;       /* spx_status of the request's own library calls (SPX_OK normally) */
+    int32_t pad;
+    spx_solve_info info; /* as filled by spx_solve */
+    double submit_ms, admit_ms, done_ms;  /* host clock, milliseconds since spx_server_create */
+} spx_server_result;
+
+/* Collect up to max_results completed requests into results (host array),
+ * waiting up to wait_ms milliseconds if none is ready; *count receives how
+ * many were written.  Each completed request is reported once. */
+int spx_server_poll(spx_server *S, spx_server_result *results, int max_results, int wait_ms, int *count);
+
+/* Requests waiting for admission, running, and the device bytes reserved. */
+int spx_server_pending(spx_server *S, int64_t *queued, int64_t *running, int64_t *bytes_in_use);
+
+/* Stop admitting, wait for running requests, join the workers, free all.
+ * Requests still queued are dropped. */
+int spx_server_destroy(spx_server *S);
+
 /* ------------------------------------------------------------------ errors */
 
 /* Message of the last failed call on this thread ("" if none). */

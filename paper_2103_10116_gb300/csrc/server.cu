@@ -1,0 +1,255 @@
+// server.cu -- continuous-batching solve server.
+//
+// Requests (a CSR operator in host memory, a right-hand side, an output
+// buffer, solver settings) enter a FIFO queue.  A request is admitted to a
+// free slot as soon as its device footprint (matrix arrays, FP32 shadow,
+// solver workspace, b and x) fits in what the byte budget has left; while it
+// runs, later requests keep being admitted into the other slots, so solves
+// of different sizes overlap on the GPU.  Each slot is a worker thread with
+// its own context and CUDA stream: the operator is uploaded, solved on the
+// device (the same spx_solve path a single caller uses) and the solution is
+// copied back; then the slot's memory returns to the budget and the next
+// queued request is admitted.  Completion records (status, iterations,
+// residual, submit / admit / finish times) are collected with
+// spx_server_poll.  Results do not depend on what else runs: every kernel of
+// a solve uses only its own matrix's and slot's scratch, with fixed-order
+// reductions.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "spx_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    int64_t id;
+    int64_t n, nnz;
+    const int32_t *rp, *col;
+    const double *val, *b;
+    double *x;
+    int solver, precision, restart;
+    double tol;
+    int64_t max_iter;
+    size_t footprint;
+    Clock::time_point t_submit, t_admit, t_done;
+    spx_solve_info info;
+    int error;
+};
+
+}  // namespace
+
+struct spx_server {
+    int device = 0;
+    size_t budget = 0, in_use = 0;
+    int slots = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::vector<Request *> done;
+    std::vector<std::thread> workers;
+    std::atomic<bool> stop{false};
+    int64_t next_id = 1;
+    int active = 0;
+    Clock::time_point t0 = Clock::now();
+    std::string worker_error;
+};
+
+namespace spx {
+
+// device bytes a request needs while it runs (upper estimate)
+size_t request_footprint(int64_t n, int64_t nnz, int solver, int precision, int restart)
+{
+    const size_t csr = (size_t)nnz * 12 + (size_t)(n + 1) * 4;
+    const size_t shadow = precision == SPX_PREC_MIXED ? (size_t)nnz * 4 : 0;
+    size_t vecs;
+    const size_t V = precision == SPX_PREC_F32 ? 4 : 8;
+    const int nv = solver == SPX_CG ? 4 : (solver == SPX_BICGSTAB ? 7 : restart + 2);
+    if (precision == SPX_PREC_MIXED) vecs = (size_t)n * (8 * 4 + 4 * (nv + 2)) + (size_t)n * 16;
+    else vecs = (size_t)n * V * nv;
+    return csr + shadow + vecs + (size_t)n * 16 /* b, x */ + (1u << 20);
+}
+
+static void worker_main(spx_server *S)
+{
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    spx_ctx *ctx = nullptr;
+    if (spx_ctx_create(&ctx, S->device, st, nullptr, nullptr, nullptr) != SPX_OK) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->worker_error = spx_last_error();
+        return;
+    }
+    for (;;) {
+        Request *R = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // FIFO admission: the head request waits until its footprint fits
+            S->cv_work.wait(lk, [&] {
+                return S->stop.load() ||
+                       (!S->queue.empty() && S->in_use + S->queue.front()->footprint <= S->budget);
+            });
+            if (S->stop.load()) break;
+            if (S->queue.empty() || S->in_use + S->queue.front()->footprint > S->budget) continue;
+            R = S->queue.front();
+            S->queue.pop_front();
+            S->in_use += R->footprint;
+            S->active += 1;
+            R->t_admit = Clock::now();
+        }
+        S->cv_work.notify_all();  // another slot may admit the next request too
+        int err = SPX_OK;
+        spx_matrix *A = nullptr;
+        void *bd = nullptr, *xd = nullptr;
+        std::memset(&R->info, 0, sizeof(R->info));
+        const size_t vb = (size_t)R->n * 8;
+        err = spx_matrix_create(ctx, &A, SPX_CSR, SPX_F64, R->n, R->n, R->nnz, R->rp, R->col, R->val, SPX_F64, -1,
+                                SPX_HOST_INPUT | (R->precision == SPX_PREC_MIXED ? SPX_MIXED_SHADOW : 0u));
+        if (err == SPX_OK && cudaMallocAsync(&bd, vb + 16, st) != cudaSuccess) err = SPX_ERR_OOM;
+        if (err == SPX_OK && cudaMallocAsync(&xd, vb + 16, st) != cudaSuccess) err = SPX_ERR_OOM;
+        if (err == SPX_OK && cudaMemcpyAsync(bd, R->b, vb, cudaMemcpyHostToDevice, st) != cudaSuccess) err = SPX_ERR_CUDA;
+        if (err == SPX_OK && cudaMemsetAsync(xd, 0, vb, st) != cudaSuccess) err = SPX_ERR_CUDA;
+        if (err == SPX_OK)
+            err = spx_solve(ctx, A, bd, xd, R->solver, R->tol, R->max_iter, R->restart, R->precision, &R->info);
+        if (err == SPX_OK && cudaMemcpyAsync(R->x, xd, vb, cudaMemcpyDeviceToHost, st) != cudaSuccess) err = SPX_ERR_CUDA;
+        cudaStreamSynchronize(st);
+        if (A) spx_matrix_destroy(A);
+        if (bd) cudaFreeAsync(bd, st);
+        if (xd) cudaFreeAsync(xd, st);
+        cudaStreamSynchronize(st);
+        R->error = err;
+        R->t_done = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->in_use -= R->footprint;
+            S->active -= 1;
+            S->done.push_back(R);
+        }
+        S->cv_work.notify_all();
+        S->cv_done.notify_all();
+    }
+    spx_ctx_destroy(ctx);
+    cudaStreamDestroy(st);
+}
+
+}  // namespace spx
+
+using namespace spx;
+
+extern "C" int spx_server_create(spx_ctx *ctx, spx_server **out, int64_t budget_bytes, int max_slots)
+{
+    if (!ctx || !out || max_slots < 1 || max_slots > 64) return fail(SPX_ERR_INVALID, "spx_server_create: bad argument");
+    *out = nullptr;
+    size_t freeb = 0, total = 0;
+    {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(ctx->device);
+        cudaError_t e = cudaMemGetInfo(&freeb, &total);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    }
+    spx_server *S = new spx_server();
+    S->device = ctx->device;
+    S->budget = budget_bytes > 0 ? (size_t)budget_bytes : (size_t)(0.9 * (double)freeb);
+    S->slots = max_slots;
+    for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_main, S);
+    *out = S;
+    return SPX_OK;
+}
+
+extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                                 const double *values, const double *b, double *x, int solver, double tol,
+                                 int64_t max_iter, int restart, int precision, int64_t *req_id)
+{
+    if (!S || !row_ptr || !b || !x || !req_id || n <= 0 || nnz < 0 || (nnz > 0 && (!col_idx || !values)))
+        return fail(SPX_ERR_INVALID, "spx_server_submit: bad argument");
+    if (solver < SPX_CG || solver > SPX_GMRES) return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
+    Request *R = new Request();
+    R->n = n;
+    R->nnz = nnz;
+    R->rp = row_ptr;
+    R->col = col_idx;
+    R->val = values;
+    R->b = b;
+    R->x = x;
+    R->solver = solver;
+    R->precision = precision;
+    R->restart = restart;
+    R->tol = tol;
+    R->max_iter = max_iter;
+    R->footprint = request_footprint(n, nnz, solver, precision, restart);
+    R->error = SPX_OK;
+    R->t_submit = Clock::now();
+    if (R->footprint > S->budget) {
+        delete R;
+        return fail(SPX_ERR_TOO_LARGE, "request footprint exceeds the server's byte budget");
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        R->id = S->next_id++;
+        S->queue.push_back(R);
+    }
+    *req_id = R->id;
+    S->cv_work.notify_all();
+    return SPX_OK;
+}
+
+extern "C" int spx_server_poll(spx_server *S, spx_server_result *results, int max_results, int wait_ms, int *count)
+{
+    if (!S || !count || (max_results > 0 && !results)) return fail(SPX_ERR_INVALID, "spx_server_poll: bad argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->done.empty() && wait_ms > 0)
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });
+    const int k = std::min<int>(max_results, (int)S->done.size());
+    spx_server_result *out = results;
+    auto ms = [&](Clock::time_point t) { return std::chrono::duration<double, std::milli>(t - S->t0).count(); };
+    for (int i = 0; i < k; ++i) {
+        Request *R = S->done[(size_t)i];
+        out[i].id = R->id;
+        out[i].error = R->error;
+        out[i].pad = 0;
+        out[i].info = R->info;
+        out[i].submit_ms = ms(R->t_submit);
+        out[i].admit_ms = ms(R->t_admit);
+        out[i].done_ms = ms(R->t_done);
+        delete R;
+    }
+    S->done.erase(S->done.begin(), S->done.begin() + k);
+    *count = k;
+    return SPX_OK;
+}
+
+extern "C" int spx_server_pending(spx_server *S, int64_t *queued, int64_t *running, int64_t *bytes_in_use)
+{
+    if (!S) return fail(SPX_ERR_INVALID, "spx_server_pending: NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (queued) *queued = (int64_t)S->queue.size();
+    if (running) *running = S->active;
+    if (bytes_in_use) *bytes_in_use = (int64_t)S->in_use;
+    return SPX_OK;
+}
+
+extern "C" int spx_server_destroy(spx_server *S)
+{
+    if (!S) return SPX_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop.store(true);
+    }
+    S->cv_work.notify_all();
+    for (auto &t : S->workers) t.join();
+    for (Request *R : S->queue) delete R;
+    for (Request *R : S->done) delete R;
+    delete S;
+    return SPX_OK;
+}

@@ -16,6 +16,7 @@
 // and the dot-product partials are finished by the last block to arrive, in
 // index order, so every run gives the same bits.
 #include <climits>
+#include <mutex>
 
 #include "dev_common.cuh"
 #include "kstate.cuh"
@@ -743,11 +744,10 @@ int launch_merge(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
     using S = MergeShape<T, kMergeBlock, IPT>;
     auto kern = k_csr_merge<T, kMergeBlock, IPT>;
     SPX_TRY(ensure_merge_tiles(ctx, A, S::TILE, S::SLACK));
-    static bool attr = false;
-    if (!attr) {
-        SPX_TRY(set_smem(kern, S::SMEM));
-        attr = true;
-    }
+    static std::once_flag once;
+    static int attr_st = SPX_OK;
+    std::call_once(once, [&] { attr_st = set_smem(kern, S::SMEM); });
+    SPX_TRY(attr_st);
     const int grid = grid_for(ctx, kern, kMergeBlock, S::SMEM, A->ntiles);
     SPX_TRY(ensure_scratch(ctx, A, A->ntiles, grid, sizeof(T)));
     return launch_k(kern, grid, kMergeBlock, S::SMEM, ctx->stream, A->nsplit > 0, (int)A->n,
@@ -787,11 +787,10 @@ int launch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi
 {
     using S = CooShape<T, kCooBlock, IPT>;
     auto kern = k_coo<T, kCooBlock, IPT>;
-    static bool attr = false;
-    if (!attr) {
-        SPX_TRY(set_smem(kern, S::SMEM));
-        attr = true;
-    }
+    static std::once_flag once;
+    static int attr_st = SPX_OK;
+    std::call_once(once, [&] { attr_st = set_smem(kern, S::SMEM); });
+    SPX_TRY(attr_st);
     SPX_TRY(ensure_coo_tiles(ctx, A, S::TILE, S::SLACK));
     const int64_t ntiles = A->coo_ntiles;
     const int grid = grid_for(ctx, kern, kCooBlock, S::SMEM, ntiles);

@@ -1,0 +1,81 @@
+"""Serving orchestration on top of the native request server (spx_server_*):
+keeps request buffers alive, replays an arrival trace, and summarises
+latency and throughput.  Scheduling, admission and the solves themselves run
+in the C++/CUDA library."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import spx
+
+
+class Server:
+    def __init__(self, ctx: int, budget_bytes: int = 0, max_slots: int = 8):
+        self.h = spx.spx_server_create(ctx, budget_bytes, max_slots)
+        self.live = {}      # id -> (arrays kept alive, x)
+        self.results = {}   # id -> result dict
+
+    def submit(self, rp, col, val, b, solver="cg", tol=1e-8, max_iter=100000, precision="mixed") -> int:
+        x = np.zeros(b.shape[0])
+        rid = spx.spx_server_submit(self.h, rp, col, val, b, x, solver, tol, max_iter, 30, precision)
+        self.live[rid] = (rp, col, val, b, x)
+        return rid
+
+    def poll(self, wait_ms: int = 0) -> int:
+        got = spx.spx_server_poll(self.h, 1024, wait_ms)
+        for r in got:
+            r["x"] = self.live.pop(r["id"])[4]
+            self.results[r["id"]] = r
+        return len(got)
+
+    def drain(self, timeout_s: float = 600.0):
+        t = time.time()
+        while self.live and time.time() - t < timeout_s:
+            self.poll(wait_ms=50)
+        if self.live:
+            raise TimeoutError(f"{len(self.live)} requests did not complete")
+
+    def close(self):
+        if self.h:
+            spx.spx_server_destroy(self.h)
+            self.h = None
+
+
+def poisson_trace(rate_per_s: float, duration_s: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate_per_s)
+        if t >= duration_s:
+            return np.array(out)
+        out.append(t)
+
+
+def replay(server: Server, trace_s: np.ndarray, requests: list, solver_of, tol=1e-8, precision="mixed"):
+    """Submit requests[i] at wall time trace_s[i] (relative to the start) while
+    collecting completions; returns the wall time of the run."""
+    t0 = time.perf_counter()
+    ids = []
+    for i, ta in enumerate(trace_s):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= ta:
+                break
+            server.poll(wait_ms=0)
+            time.sleep(min(0.0005, ta - now))
+        rp, col, val, b = requests[i]
+        ids.append(server.submit(rp, col, val, b, solver=solver_of(i), tol=tol, precision=precision))
+        server.poll(wait_ms=0)
+    server.drain()
+    return time.perf_counter() - t0, ids
+
+
+def latency_stats(results: list[dict]) -> dict:
+    lat = np.array([r["done_ms"] - r["submit_ms"] for r in results])
+    wait = np.array([r["admit_ms"] - r["submit_ms"] for r in results])
+    return {"count": int(lat.size), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "queue_wait_p50_ms": float(np.percentile(wait, 50)),
+            "queue_wait_p99_ms": float(np.percentile(wait, 99))}

@@ -61,6 +61,11 @@ class spx_solve_info(C.Structure):
                 ("inner_iterations", C.c_int64)]
 
 
+class spx_server_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("error", C.c_int32), ("pad", C.c_int32), ("info", spx_solve_info),
+                ("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -87,6 +92,11 @@ SIGNATURES = {
     "spx_batch_destroy": (_I, [_P]),
     "spx_batch_solve": (_I, [_P, _P, _P, _P, _I, _D, _I64, _I, _P]),
     "spx_batch_tune": (_I, [_P, _P, _I, _I, C.POINTER(C.c_int)]),
+    "spx_server_create": (_I, [_P, _PP, _I64, _I]),
+    "spx_server_submit": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(C.c_int64)]),
+    "spx_server_poll": (_I, [_P, C.POINTER(spx_server_result), _I, _I, C.POINTER(C.c_int)]),
+    "spx_server_pending": (_I, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "spx_server_destroy": (_I, [_P]),
     "spx_last_error": (C.c_char_p, []),
     "spx_status_str": (C.c_char_p, [_I]),
     "spx_version": (_I, []),
@@ -330,6 +340,52 @@ def spx_batch_tune(ctx: int, B: int, solver="cg", precision="f64") -> int:
     _check(load().spx_batch_tune(ctx, B, SOLVERS.get(solver, solver), PRECISIONS.get(precision, precision),
                                  C.byref(chosen)))
     return chosen.value
+
+
+# ------------------------------------------------------------------ serving
+def spx_server_create(ctx: int, budget_bytes: int = 0, max_slots: int = 8) -> int:
+    out = C.c_void_p()
+    _check(load().spx_server_create(ctx, C.byref(out), int(budget_bytes), int(max_slots)))
+    return out.value
+
+
+def spx_server_submit(S: int, row_ptr, col_idx, values, b, x, solver="cg", tol: float = 1e-8,
+                      max_iter: int = 100000, restart: int = 30, precision="mixed") -> int:
+    """Queue a solve on HOST numpy arrays (int32 row_ptr / col_idx, float64 values / b / x).
+    The caller keeps every array alive and x untouched until the request completes."""
+    import numpy as np
+    for a, dt in ((row_ptr, np.int32), (col_idx, np.int32), (values, np.float64), (b, np.float64),
+                  (x, np.float64)):
+        if not (isinstance(a, np.ndarray) and a.dtype == dt and a.flags.c_contiguous):
+            raise TypeError("spx_server_submit takes contiguous numpy arrays (int32 indices, float64 values)")
+    rid = C.c_int64()
+    _check(load().spx_server_submit(S, row_ptr.shape[0] - 1, col_idx.shape[0], row_ptr.ctypes.data,
+                                    col_idx.ctypes.data, values.ctypes.data, b.ctypes.data, x.ctypes.data,
+                                    SOLVERS.get(solver, solver), float(tol), int(max_iter), int(restart),
+                                    PRECISIONS.get(precision, precision), C.byref(rid)))
+    return rid.value
+
+
+def spx_server_poll(S: int, max_results: int = 256, wait_ms: int = 0) -> list[dict]:
+    buf = (spx_server_result * max(1, max_results))()
+    cnt = C.c_int()
+    _check(load().spx_server_poll(S, buf, max_results, int(wait_ms), C.byref(cnt)))
+    out = []
+    for i in range(cnt.value):
+        r = buf[i]
+        out.append({"id": r.id, "error": r.error, "info": _info(r.info), "submit_ms": r.submit_ms,
+                    "admit_ms": r.admit_ms, "done_ms": r.done_ms})
+    return out
+
+
+def spx_server_pending(S: int) -> tuple[int, int, int]:
+    q, r, b = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().spx_server_pending(S, C.byref(q), C.byref(r), C.byref(b)))
+    return q.value, r.value, b.value
+
+
+def spx_server_destroy(S: int):
+    _check(load().spx_server_destroy(S))
 
 
 # ------------------------------------------------------------------ errors

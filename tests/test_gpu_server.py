@@ -1,0 +1,101 @@
+"""The request server: results alone equal results in a mix of concurrent
+requests (bit for bit: every solve uses only its own scratch and fixed-order
+reductions), every result meets tol on the true residual (re-formed by the
+CPU oracle), and admission never exceeds the byte budget."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_10116_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spx():
+    from paper_2103_10116_gb300 import spx as s
+    s.load()
+    return s
+
+
+@pytest.fixture(scope="module")
+def ctx(spx):
+    c = spx.spx_ctx_create(0)
+    yield c
+    spx.spx_ctx_destroy(c)
+
+
+def _requests():
+    reqs = []
+    for k, m in enumerate((10, 14, 18, 22, 26)):
+        rp, col, val = synth.laplace3d_7pt(m)
+        b = synth.uniform_vector(m**3, seed=100 + k)
+        reqs.append((rp, col, val, b, "cg"))
+    for k, n in enumerate((1000, 4000, 9000, 20000)):
+        rp, col, val = synth.diagdom_random(n, seed=200 + k)
+        b = synth.uniform_vector(n, seed=300 + k)
+        reqs.append((rp, col, val, b, "bicgstab"))
+    return reqs
+
+
+def test_alone_equals_mix(spx, ctx):
+    from paper_2103_10116_gb300.serving import Server
+    reqs = _requests()
+    srv = Server(ctx, 0, max_slots=4)
+    try:
+        alone = {}
+        for i, (rp, col, val, b, solver) in enumerate(reqs):
+            rid = srv.submit(rp, col, val, b, solver=solver, tol=1e-8)
+            srv.drain()
+            alone[i] = srv.results[rid]
+        mix_ids = {}
+        order = list(range(len(reqs))) * 3
+        np.random.default_rng(1).shuffle(order)
+        for i in order:
+            rp, col, val, b, solver = reqs[i]
+            mix_ids.setdefault(i, []).append(srv.submit(rp, col, val, b, solver=solver, tol=1e-8))
+        srv.drain()
+        for i, (rp, col, val, b, solver) in enumerate(reqs):
+            ra = alone[i]
+            assert ra["error"] == 0 and ra["info"].status == spx.SPX_CONVERGED, ra
+            r = b - oracle.spmv_csr(rp, col, val, ra["x"])
+            assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.05e-8
+            for rid in mix_ids[i]:
+                rm = srv.results[rid]
+                assert rm["error"] == 0 and rm["info"].status == spx.SPX_CONVERGED
+                assert np.array_equal(rm["x"], ra["x"]), i
+                assert rm["info"].iterations == ra["info"].iterations
+        # the mix really overlapped: some request was admitted before another finished
+        res = [srv.results[r] for ids in mix_ids.values() for r in ids]
+        res.sort(key=lambda r: r["admit_ms"])
+        assert any(res[k + 1]["admit_ms"] < res[k]["done_ms"] for k in range(len(res) - 1))
+    finally:
+        srv.close()
+
+
+def test_admission_respects_budget(spx, ctx):
+    from paper_2103_10116_gb300.serving import Server
+    reqs = _requests()
+    budget = 12 * 2**20  # ~12 MB: only a few of the small requests fit at once
+    srv = Server(ctx, budget, max_slots=8)
+    try:
+        big = synth.laplace3d_7pt(60)
+        with pytest.raises(spx.SpxError) as ei:
+            srv.submit(big[0], big[1], big[2], np.ones(60**3))
+        assert ei.value.status == spx.SPX_ERR_TOO_LARGE
+        srv.live.clear()
+        ids = []
+        for i in range(3):
+            for rp, col, val, b, solver in reqs[:4]:
+                ids.append(srv.submit(rp, col, val, b, solver=solver))
+        peak = 0
+        while srv.live:
+            q, running, used = spx.spx_server_pending(srv.h)
+            peak = max(peak, used)
+            assert used <= budget
+            srv.poll(wait_ms=5)
+        assert peak > 0
+        assert all(srv.results[i]["info"].status == spx.SPX_CONVERGED for i in ids)
+    finally:
+        srv.close()
