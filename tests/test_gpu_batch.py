@@ -62,7 +62,9 @@ def _check(ro, xs, b, systems, x, tol, err_tol, infos=None, oracle_solver=None):
         assert np.linalg.norm(xb - xs[r0:r1]) / np.linalg.norm(xs[r0:r1]) <= err_tol, s
         if infos is not None and oracle_solver is not None:
             _, oi = oracle_solver(lrp, lcol, lval, b[r0:r1], tol=tol, maxit=20000)
-            assert abs(infos[s].iterations - oi.iterations) <= max(3, oi.iterations // 10), (s, infos[s], oi)
+            # BiCGSTAB convergence is irregular: rounding moves the stop by a few steps
+            slack = max(3, oi.iterations // 10) if oracle_solver is oracle.cg else max(6, oi.iterations // 5)
+            assert abs(infos[s].iterations - oi.iterations) <= slack, (s, infos[s], oi)
 
 
 @pytest.mark.parametrize("solver", ["cg", "bicgstab"])
