@@ -170,6 +170,33 @@ int spx_spmv_axpby(spx_ctx *ctx, const spx_matrix *A, double alpha, const void *
  * handle.  Host buffers should be pinned for full copy bandwidth. */
 int spx_spmv_host(spx_ctx *ctx, const spx_matrix *A, const void *x_host, void *y_host);
 
+/* SpMV for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart for this entry point.  It exists for callers
+ * that may not call cudaMalloc (or any allocating routine) when they need a
+ * product: code running while a CUDA graph is captured, real-time loops whose
+ * memory is fixed up front, or frameworks that own every allocation.  It
+ * computes y = A x with the merge-path CSR kernel directly from the caller's
+ * CSR arrays (no matrix handle, no context) on `stream` (a cudaStream_t) of
+ * the current device, and allocates nothing: the kernel's scratch (tile map,
+ * per-tile carries, look-back flags) lives in one fixed 1 MiB array that the
+ * library declares in device global memory; every GPU that loads the library
+ * holds it until the process exits.
+ *   - Limit: nrows + nnz <= SPX_NOALLOC_MAX_TILES * 2048 (67,108,864);
+ *     larger problems return SPX_ERR_TOO_LARGE and launch nothing.
+ *   - row_ptr, col_idx and values must be 16-byte aligned (SPX_ERR_INVALID
+ *     otherwise) and form a valid CSR matrix (not checked here).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and clears what must start at zero, so
+ *     calls whose kernels overlap on the GPU (different streams, no ordering)
+ *     race and give wrong results; order them on one stream.
+ *   - dtype: SPX_F64 or SPX_F32 for values, x and y.  Asynchronous. */
+#define SPX_NOALLOC_MAX_TILES 32768
+int spx_spmv_csr_noalloc(void *stream, int dtype, int64_t nrows, int64_t ncols, int64_t nnz,
+                         const int32_t *row_ptr, const int32_t *col_idx, const void *values, const void *x,
+                         void *y);
+
 /* ------------------------------------------------------------------ BLAS-1 */
 
 /* *result = sum_i x_i y_i with a deterministic two-stage device reduction

@@ -950,3 +950,118 @@ template int spmv_launch<double>(spx_ctx *, const spx_matrix *, const double *, 
 template int spmv_launch<float>(spx_ctx *, const spx_matrix *, const float *, const Epi<float> &, bool);
 
 }  // namespace spx
+
+// ------------------------------------------------------------------ SpMV without allocation
+// Some callers cannot allocate device memory at the point where they need a
+// product: code that runs while a CUDA graph is being captured, a real-time
+// loop whose memory is fixed up front, or a host framework that owns every
+// allocation and forbids libraries from calling cudaMalloc (which may also
+// synchronise the device).  For them this entry point runs the merge-path
+// CSR kernel straight from the caller's CSR arrays with all of its scratch
+// (tile map, per-tile carries, look-back flags) in one fixed array in device
+// global memory that the library declares at file scope.  Every GPU that
+// loads the library holds that array until the process exits.
+namespace spx {
+namespace {
+
+constexpr int kNoAllocIpt = 16;
+constexpr int64_t kNoAllocMaxTiles = SPX_NOALLOC_MAX_TILES;
+constexpr size_t kNoAllocBytes = 1u << 20;  // 1 MiB
+
+// scratch layout: tiles int2[max+1] | carry_val 8B[max] | carry_row int[max] | flags int[max] | counters
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static_assert((kNoAllocMaxTiles + 1) * 8 + kNoAllocMaxTiles * (8 + 4 + 4) + 256 <= (int64_t)kNoAllocBytes,
+              "no-alloc scratch too small for its tile limit");
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[256];  // device address of the scratch per device, set once
+
+int noalloc_scratch(int dev, void **out)
+{
+    if (dev < 0 || dev >= 256) return fail(SPX_ERR_INVALID, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        // host code must not use the symbol itself: it names a host-side stand-in
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SPX_OK;
+}
+
+template <class T>
+int spmv_noalloc(cudaStream_t st, void *scratch, int64_t n, int64_t nnz, const int *rp, const int *col, const T *val,
+                 const T *x, T *y, int sm_count, unsigned *err)
+{
+    using S = MergeShape<T, kMergeBlock, kNoAllocIpt>;
+    auto kern = k_csr_merge<T, kMergeBlock, kNoAllocIpt>;
+    const int64_t ntiles = ceil_div(n + nnz, S::TILE);
+    char *base = static_cast<char *>(scratch);
+    int2 *tiles = reinterpret_cast<int2 *>(base);
+    T *carry_val = reinterpret_cast<T *>(base + (kNoAllocMaxTiles + 1) * 8);
+    int *carry_row = reinterpret_cast<int *>(base + (kNoAllocMaxTiles + 1) * 8 + kNoAllocMaxTiles * 8);
+    int *flags = carry_row + kNoAllocMaxTiles;
+    unsigned *counters = reinterpret_cast<unsigned *>(flags + kNoAllocMaxTiles);  // nsplit, ticket
+    // the array keeps the previous call's contents: flags and counters must start at zero
+    SPX_CUDA(cudaMemsetAsync(flags, 0, (size_t)ntiles * 4, st));
+    SPX_CUDA(cudaMemsetAsync(counters, 0, 64, st));
+    k_merge_tiles<<<(int)ceil_div(ntiles + 1, 256), 256, 0, st>>>((int)n, (int)nnz, rp, S::TILE, S::SLACK, (int)ntiles,
+                                                                 tiles, counters);
+    SPX_CUDA(cudaGetLastError());
+    static std::once_flag once;
+    static int attr_st = SPX_OK;
+    std::call_once(once, [&] { attr_st = set_smem(kern, S::SMEM); });
+    SPX_TRY(attr_st);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMergeBlock, S::SMEM) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t grid = (int64_t)per_sm * sm_count;
+    if (grid > ntiles) grid = ntiles;
+    Epi<T> e;
+    e.y = y;
+    // the split count is not read back (no synchronisation): always launch cooperatively
+    return launch_k(kern, (int)grid, kMergeBlock, S::SMEM, st, true, (int)n, rp, col, val, x, (const int2 *)tiles,
+                    (int)ntiles, carry_row, carry_val, flags, (T *)nullptr, counters + 1, err, e);
+}
+
+}  // namespace
+}  // namespace spx
+
+extern "C" int spx_spmv_csr_noalloc(void *stream, int dtype, int64_t nrows, int64_t ncols, int64_t nnz,
+                                    const int32_t *row_ptr, const int32_t *col_idx, const void *values,
+                                    const void *x, void *y)
+{
+    using namespace spx;
+    if (dtype != SPX_F64 && dtype != SPX_F32) return fail(SPX_ERR_INVALID, "spx_spmv_csr_noalloc: bad dtype");
+    if (nrows < 0 || ncols < 0 || nnz < 0 || nrows >= INT_MAX || nnz > INT_MAX)
+        return fail(SPX_ERR_INVALID, "spx_spmv_csr_noalloc: bad sizes");
+    if (nrows == 0) return SPX_OK;
+    if (!row_ptr || !y || (nnz > 0 && (!col_idx || !values || !x)))
+        return fail(SPX_ERR_INVALID, "spx_spmv_csr_noalloc: NULL array");
+    const int64_t tile = (int64_t)kMergeBlock * kNoAllocIpt;
+    if (ceil_div(nrows + nnz, tile) > kNoAllocMaxTiles)
+        return fail(SPX_ERR_TOO_LARGE, "spx_spmv_csr_noalloc: nrows + nnz = " + std::to_string((long long)(nrows + nnz)) +
+                                           " exceeds the fixed scratch limit of " +
+                                           std::to_string((long long)(kNoAllocMaxTiles * tile)));
+    if (((uintptr_t)row_ptr | (uintptr_t)col_idx | (uintptr_t)values) & 15u)
+        return fail(SPX_ERR_INVALID, "spx_spmv_csr_noalloc: row_ptr, col_idx and values must be 16-byte aligned");
+    int dev = 0;
+    SPX_CUDA(cudaGetDevice(&dev));
+    void *scratch = nullptr;
+    SPX_TRY(noalloc_scratch(dev, &scratch));
+    int sms = 0;
+    SPX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *err = reinterpret_cast<unsigned *>(static_cast<char *>(scratch) + kNoAllocBytes - 64);
+    if (nnz == 0) {  // y = 0
+        const cudaError_t e = cudaMemsetAsync(y, 0, (size_t)nrows * (dtype == SPX_F64 ? 8 : 4), st);
+        return e == cudaSuccess ? SPX_OK : cuda_fail(e, "cudaMemsetAsync");
+    }
+    if (dtype == SPX_F64)
+        return spmv_noalloc<double>(st, scratch, nrows, nnz, row_ptr, col_idx, static_cast<const double *>(values),
+                                    static_cast<const double *>(x), static_cast<double *>(y), sms, err);
+    return spmv_noalloc<float>(st, scratch, nrows, nnz, row_ptr, col_idx, static_cast<const float *>(values),
+                               static_cast<const float *>(x), static_cast<float *>(y), sms, err);
+}

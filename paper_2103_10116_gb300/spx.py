@@ -84,6 +84,7 @@ SIGNATURES = {
     "spx_spmv": (_I, [_P, _P, _P, _P]),
     "spx_spmv_axpby": (_I, [_P, _P, _D, _P, _D, _P]),
     "spx_spmv_host": (_I, [_P, _P, _P, _P]),
+    "spx_spmv_csr_noalloc": (_I, [_P, _I, _I64, _I64, _I64, _P, _P, _P, _P, _P]),
     "spx_dot": (_I, [_P, _I, _I64, _P, _P, _P]),
     "spx_axpby": (_I, [_P, _I, _I64, _D, _P, _D, _P]),
     "spx_solve": (_I, [_P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(spx_solve_info)]),
@@ -264,6 +265,18 @@ def spx_spmv_host(ctx: int, A: int, x_host: torch.Tensor, y_host: torch.Tensor):
     if x_host.is_cuda or y_host.is_cuda:
         raise ValueError("spx_spmv_host takes host tensors")
     _check(load().spx_spmv_host(ctx, A, _ptr(x_host), _ptr(y_host)))
+
+
+def spx_spmv_csr_noalloc(row_ptr: torch.Tensor, col_idx: torch.Tensor, values: torch.Tensor, x: torch.Tensor,
+                         y: torch.Tensor, ncols: int | None = None, stream=None):
+    """y = A x straight from device CSR tensors; allocates nothing (fixed scratch inside the
+    library).  stream: torch Stream / raw handle / None (torch's current stream)."""
+    if stream is None:
+        stream = torch.cuda.current_stream(values.device)
+    handle = stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
+    n = row_ptr.numel() - 1
+    _check(load().spx_spmv_csr_noalloc(handle, _dt(values), n, n if ncols is None else ncols, col_idx.numel(),
+                                       _ptr(row_ptr), _ptr(col_idx), _ptr(values), _ptr(x), _ptr(y)))
 
 
 def spx_dot(ctx: int, x: torch.Tensor, y: torch.Tensor, result: torch.Tensor):
