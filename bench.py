@@ -254,14 +254,16 @@ def run_gpu(args):
     h2d = sum(e["n"] * e["V"] for e in entries)
     d2h = sum(e["n"] * e["V"] for e in entries)
 
+    peak, peak_src = _peaks()
     secondary = {}
     if not args.no_solve:
-        secondary["cg_poisson128"] = cg_secondary(spx, ctx, stream, dev)
-
-    peak, peak_src = _peaks()
+        secondary["solves"] = solve_secondary(spx, ctx, stream, dev, peak)
+    if args.batched:
+        secondary["batched"] = batched_secondary(spx, ctx, stream, dev)
+    if args.serve_seconds > 0:
+        secondary["serving"] = serving_secondary(spx, ctx, seconds=args.serve_seconds)
     dom = int(np.argmax(per_entry_ms))
     de = entries[dom]
-    dom_ms = per_entry_ms[dom] / de["launches"] if de["launches"] == 1 else per_entry_ms[dom]
     achieved = de["bytes"] / (per_entry_ms[dom] * 1e-3) / 1e9
     traffic = _traffic(de["name"])
     result = {
@@ -309,33 +311,166 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def cg_secondary(spx, ctx, stream, dev):
-    """CG on the 128^3 7-point Poisson matrix to relative residual 1e-10 (FP64
-    and FP32-inner / FP64-refinement), b = A x*, x* ~ U[-1,1]: solve time."""
+def solve_bytes_per_iter(solver: str, fmt_bytes: int, n: int, m: int = 30) -> int:
+    """Algorithmic bytes of one FP64 iteration in this library's fused form:
+    SpMV stream (fmt_bytes: matrix + gathered vector + result) plus the vector
+    kernels.  CG: SpMV (+p re-read for p.q), x/r update (4 reads, 2 writes),
+    p update (2 reads, 1 write).  BiCGSTAB: two SpMVs (+ dot operands), p, s,
+    x/r updates.  GMRES(m), averaged over a cycle: SpMV + CGS2 (three passes
+    over the j+1 basis vectors) + normalisation."""
+    V = 8
+    if solver == "cg":
+        return fmt_bytes + V * n + 6 * V * n + 3 * V * n
+    if solver == "bicgstab":
+        return 2 * fmt_bytes + 2 * V * n + 4 * V * n + 3 * V * n + 8 * V * n
+    jbar = (m + 1) / 2.0
+    return int(fmt_bytes + 3 * (jbar + 1) * V * n + 2 * V * n + 2 * V * n)
+
+
+def solve_secondary(spx, ctx, stream, dev, peak):
+    """Krylov solves to relative residual 1e-10 with b = A x*, x* ~ U[-1,1]:
+    CG on the 128^3 7-point Poisson matrix; BiCGSTAB and GMRES(30) on the
+    128^3 upwind convection-diffusion matrix (Peclet 10).  FP64 and FP32
+    inner iterations inside FP64 refinement ("mixed").  ELL storage."""
     import torch
     from paper_2103_10116_gb300 import synth
-    rp, col, val = synth.laplace3d_7pt(128)
-    n = rp.shape[0] - 1
-    out = {"n": n, "nnz": int(col.shape[0]), "tol": 1e-10}
+    out = {}
+    cases = [("cg_poisson128", synth.laplace3d_7pt(128), "cg"),
+             ("bicgstab_convdiff128", synth.convdiff3d_upwind(128), "bicgstab"),
+             ("gmres30_convdiff128", synth.convdiff3d_upwind(128), "gmres")]
+    for name, (rp, col, val), solver in cases:
+        n = rp.shape[0] - 1
+        res = {"n": n, "nnz": int(col.shape[0]), "tol": 1e-10, "format": "ell"}
+        with torch.cuda.stream(stream):
+            A = spx.spx_matrix_create(ctx, "ell", torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                                      torch.from_numpy(val).to(dev), flags=spx.SPX_MIXED_SHADOW)
+            info = spx.spx_matrix_get_info(A)
+            xs = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, n)).to(dev)
+            b = torch.empty(n, dtype=torch.float64, device=dev)
+            spx.spx_spmv(ctx, A, xs, b)
+            fmt_bytes = algorithmic_bytes("ell", 8, n, n, col.shape[0], info["ell_width"], 0)
+            for prec in ("f64", "mixed"):
+                x = torch.zeros(n, dtype=torch.float64, device=dev)
+                spx.spx_solve(ctx, A, b, x, solver, 1e-10, 20000, restart=30, precision=prec)  # warm-up
+                x.zero_()
+                torch.cuda.synchronize()
+                si = spx.spx_solve(ctx, A, b, x, solver, 1e-10, 20000, restart=30, precision=prec)
+                err = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
+                r = {"solve_ms": round(si.time_ms, 2), "iterations": si.iterations, "status": si.status_name,
+                     "relres_true": si.relres_true, "err_vs_xstar": err, "restarts": si.restarts}
+                if prec == "f64" and si.iterations > 0:
+                    bpi = solve_bytes_per_iter(solver, fmt_bytes, n)
+                    gbs = bpi * si.iterations / (si.time_ms * 1e-3) / 1e9
+                    r.update({"bytes_per_iter": bpi, "achieved_GB_s": round(gbs, 1),
+                              "frac_of_hbm_peak": round(gbs / peak, 3),
+                              "roofline_ms": round(bpi * si.iterations / (peak * 1e9) * 1e3, 2)})
+                res[prec] = r
+            spx.spx_matrix_destroy(A)
+        out[name] = res
+    return out
+
+
+def batched_secondary(spx, ctx, stream, dev, plain_sample=32):
+    """4096 SPD systems, n_i ~ U{100..10000}, 2D 5-point Laplacian of the
+    ragged n_i-row grid plus a diagonal shift ~ U[0.01, 1], b_i = A_i x*_i:
+    one persistent batched CG launch (FP64, and FP32 inner + FP64 refinement)
+    to 1e-10, against the plain per-system FP64 path (spx_solve per system,
+    timed on the first `plain_sample` systems and scaled to the batch)."""
+    import scipy.sparse as sp
+    import torch
+    from paper_2103_10116_gb300 import synth
+    nsys = 4096
+    ro, no, rp, col, val = synth.batch_ragged_laplace(nsys, 100, 10000, seed=4)
+    xs = np.random.default_rng(5).uniform(-1, 1, int(ro[-1]))
+    b = np.empty_like(xs)
+    for s in range(nsys):
+        r0, r1 = int(ro[s]), int(ro[s + 1])
+        A = sp.csr_matrix((val[no[s]:no[s + 1]], col[no[s]:no[s + 1]], rp[r0 + s:r1 + s + 1]), shape=(r1 - r0,) * 2)
+        b[r0:r1] = A @ xs[r0:r1]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    out = {"systems": nsys, "rows": int(ro[-1]), "nnz": int(no[-1]), "tol": 1e-10}
     with torch.cuda.stream(stream):
-        A = spx.spx_matrix_create(ctx, "ell", torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
-                                  torch.from_numpy(val).to(dev), flags=spx.SPX_MIXED_SHADOW)
-        xs = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, n)).to(dev)
-        b = torch.empty(n, dtype=torch.float64, device=dev)
-        spx.spx_spmv(ctx, A, xs, b)
+        B = spx.spx_batch_create(ctx, ro, no, t(rp), t(col), t(val), flags=spx.SPX_MIXED_SHADOW)
+        bd, xsd = t(b), t(xs)
         for prec in ("f64", "mixed"):
-            x = torch.zeros(n, dtype=torch.float64, device=dev)
-            spx.spx_solve(ctx, A, b, x, "cg", 1e-10, 5000, precision=prec)  # warm-up (graphs, workspace)
+            chosen = spx.spx_batch_tune(ctx, B, "cg", prec)
+            x = torch.zeros_like(bd)
+            spx.spx_batch_solve(ctx, B, bd, x, nsys, "cg", 1e-10, 20000, precision=prec)  # warm-up + graph
             x.zero_()
             torch.cuda.synchronize()
-            info = spx.spx_solve(ctx, A, b, x, "cg", 1e-10, 5000, precision=prec)
-            err = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
-            it = info.iterations
-            # bytes per FP64 CG iteration in the 3-kernel form: ELL matrix + vectors
-            out[prec] = {"solve_ms": round(info.time_ms, 2), "iterations": it, "status": info.status_name,
-                         "relres_true": info.relres_true, "err_vs_xstar": err, "restarts": info.restarts}
-        spx.spx_matrix_destroy(A)
+            t0 = time.perf_counter()
+            infos = spx.spx_batch_solve(ctx, B, bd, x, nsys, "cg", 1e-10, 20000, precision=prec)
+            el = time.perf_counter() - t0
+            conv = sum(1 for i in infos if i.status == spx.SPX_CONVERGED)
+            err = float(torch.linalg.norm(x - xsd) / torch.linalg.norm(xsd))
+            out[prec] = {"solve_ms": round(el * 1e3, 2), "solves_per_s": round(nsys / el, 1), "converged": conv,
+                         "threads_per_system": chosen, "err_vs_xstar": err,
+                         "max_relres": max(i.relres_true for i in infos)}
+        spx.spx_batch_destroy(B)
+        # plain per-system FP64 path on a sample
+        el = 0.0
+        for s in range(plain_sample):
+            r0, r1 = int(ro[s]), int(ro[s + 1])
+            A = spx.spx_matrix_create(ctx, "csr", t(rp[r0 + s:r1 + s + 1]), t(col[no[s]:no[s + 1]]),
+                                      t(val[no[s]:no[s + 1]]))
+            x = torch.zeros(r1 - r0, dtype=torch.float64, device=dev)
+            spx.spx_solve(ctx, A, t(b[r0:r1]), x, "cg", 1e-10, 20000)  # warm-up
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            spx.spx_solve(ctx, A, t(b[r0:r1]), x, "cg", 1e-10, 20000)
+            el += time.perf_counter() - t0
+            spx.spx_matrix_destroy(A)
+        rows_sample = int(ro[plain_sample])
+        est = el * (int(ro[-1]) / rows_sample)
+        out["plain_per_system_f64"] = {"sample_systems": plain_sample, "sample_ms": round(el * 1e3, 2),
+                                       "est_batch_ms": round(est * 1e3, 1), "solves_per_s": round(nsys / est, 1)}
+        out["speedup_f64_vs_plain"] = round(est * 1e3 / out["f64"]["solve_ms"], 1)
+        out["speedup_mixed_vs_plain"] = round(est * 1e3 / out["mixed"]["solve_ms"], 1)
     return out
+
+
+def serving_secondary(spx, ctx, seconds: float = 10.0, rate: float = 2000.0, slots: int = 16, pool: int = 12):
+    """Poisson arrivals (rate req/s for `seconds`), sizes log-uniform in
+    [1e3, 1e6] rows drawn from a pool of `pool` log-spaced sizes per family,
+    50/50 3D 7-point stencils (CG) and diagonally dominant random rows with
+    8-32 nonzeros (BiCGSTAB), tolerance 1e-8, FP32 inner + FP64 refinement,
+    admission by device footprint (90% of free memory)."""
+    from paper_2103_10116_gb300 import synth
+    from paper_2103_10116_gb300.serving import Server, latency_stats, poisson_trace, replay
+    rng = np.random.default_rng(5)
+    ks = np.unique(np.round(np.geomspace(10, 100, pool)).astype(int))       # stencil k, n = k^3
+    rs = np.unique(np.round(np.geomspace(1e3, 1e6, pool)).astype(int))     # random rows
+    stencils = {int(k): synth.laplace3d_7pt(int(k)) for k in ks}
+    randoms = {int(n): synth.diagdom_random(int(n), seed=int(n) % 1000 + 7) for n in rs}
+    trace = poisson_trace(rate, seconds, seed=5)
+    reqs, kinds = [], []
+    logn = rng.uniform(np.log(1e3), np.log(1e6), size=trace.shape[0])
+    fam = rng.random(trace.shape[0]) < 0.5
+    for i in range(trace.shape[0]):
+        if fam[i]:
+            k = int(ks[np.argmin(np.abs(np.log(ks.astype(float) ** 3) - logn[i]))])
+            rp, col, val = stencils[k]
+            kinds.append("cg")
+        else:
+            n = int(rs[np.argmin(np.abs(np.log(rs.astype(float)) - logn[i]))])
+            rp, col, val = randoms[n]
+            kinds.append("bicgstab")
+        b = np.random.default_rng(i).uniform(-1, 1, rp.shape[0] - 1)
+        reqs.append((rp, col, val, b))
+    srv = Server(ctx, 0, max_slots=slots)
+    try:
+        wall, ids = replay(srv, trace, reqs, lambda i: kinds[i], tol=1e-8, precision="mixed")
+        res = [srv.results[i] for i in ids]
+    finally:
+        srv.close()
+    st = latency_stats(res)
+    conv = sum(1 for r in res if r["info"].status == spx.SPX_CONVERGED and r["error"] == 0)
+    busy = sum(r["done_ms"] - r["admit_ms"] for r in res) / 1e3
+    st.update({"requests": len(res), "converged": conv, "arrival_rate_per_s": rate, "window_s": seconds,
+               "wall_s": round(wall, 2), "solves_per_s": round(len(res) / wall, 1), "slots": slots,
+               "slot_busy_s": round(busy, 2), "pool_sizes_per_family": int(len(ks))})
+    return st
 
 
 def cpu_baseline(mats, budget_s=15.0):
@@ -404,6 +539,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the CG solve-time section")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="0 disables the serving run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "spx":
         args.warmup = 3

@@ -635,8 +635,8 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
         !(param == 1 || param == 2 || param == 4 || param == 8 || param == 16 || param == 32))
         return fail(SPX_ERR_INVALID, "CSR vector width must be 0 (auto) or 1..32, a power of 2");
     if ((kernel == SPX_KERNEL_CSR_MERGE || kernel == SPX_KERNEL_COO) && param != 0 &&
-        !(param == 8 || param == 16 || param == 32))
-        return fail(SPX_ERR_INVALID, "items per thread must be 0 (auto), 8, 16 or 32");
+        !(param == 4 || param == 8 || param == 16))
+        return fail(SPX_ERR_INVALID, "items per thread must be 0 (auto), 4, 8 or 16");
     if (kernel == SPX_KERNEL_ELL && param != 0 && !(param == 1 || param == 2 || (param == 4 && A->dtype == SPX_F32)))
         return fail(SPX_ERR_INVALID, "ELL rows per thread must be 0 (auto), 1, 2 (or 4 for FP32)");
     A->kernel = kernel;

@@ -25,9 +25,15 @@
 namespace spx {
 
 // ------------------------------------------------------------------ epilogue helpers
+template <class T> __device__ __forceinline__ bool is_one(T a)
+{
+    if constexpr (sizeof(T) == 8) return __double_as_longlong(a) == 0x3FF0000000000000LL;
+    else return __float_as_int(a) == 0x3F800000;
+}
+
 template <class T> __device__ __forceinline__ T epi_val(const Epi<T> &e, int64_t r, T t)
 {
-    if (e.alpha != T(1)) t *= e.alpha;
+    if (!is_one(e.alpha)) t *= e.alpha;
     if (e.z) t = fma(e.beta, e.z[r], t);
     return t;
 }
@@ -116,16 +122,30 @@ __global__ void __launch_bounds__(BLOCK)
 // tiles.  A persistent block loops over its tiles; thread 0 prefetches the
 // next tile's row pointers, column indices and values into the other
 // shared-memory stage with 1-D bulk copies (TMA) while the block works on
-// the current one.  Each thread walks its share of the tile's merge items
-// sequentially: exactly one FMA per nonzero.
+// the current one, and keeps the tile coordinates one tile ahead so that
+// issuing a copy never waits on a global load.
+//   walk:     each thread takes an equal share of the tile's merge items and
+//             accumulates sequentially (one FMA per nonzero, all x gathers of
+//             the share issued together); a row end costs one shared-memory
+//             store of the running sum, so divergent row ends stay cheap;
+//   finalise: one thread per row adds the partial sums of the threads before
+//             the row's owner that carried the same row (fixed order), applies
+//             the epilogue and stores y coalesced.
+// The row sums live in the stage buffer after the copied data: a tile with
+// R row ends and Z nonzeros copies 4R + (4+V)Z bytes, and R + Z <= TILE +
+// SLACK leaves V*R bytes free.
 template <class T, int BLOCK, int IPT> struct MergeShape {
     static constexpr int TILE = BLOCK * IPT;
     static constexpr int SLACK = TILE / 4;
-    // rp slice (<= rows + 8 ints), cols (<= nnz + 8 ints), vals (<= nnz + 16/V T)
-    // with rows + nnz <= TILE + SLACK, each rounded to 16 B.
     static constexpr int STAGE = (int)((4 + sizeof(T)) * (TILE + SLACK) + 256);
-    static constexpr int SMEM = 2 * STAGE + BLOCK * (4 + (int)sizeof(T)) + 16;
-    static constexpr int CH = 8;  // nonzeros whose x gathers are issued together
+    // stages | carry rows | carry values | search results | tile coords (2 stages) | mbarriers
+    static constexpr int OFF_CROW = 2 * STAGE;
+    static constexpr int OFF_CVAL = OFF_CROW + BLOCK * 4;
+    static constexpr int OFF_RL = OFF_CVAL + BLOCK * (int)sizeof(T);
+    static constexpr int OFF_COORD = OFF_RL + (BLOCK + 1) * 4 + 12;
+    static constexpr int OFF_BAR = OFF_COORD + 32;
+    static constexpr int SMEM = OFF_BAR + 16;
+    static constexpr int CH = IPT < 8 ? IPT : 8;  // nonzeros whose x gathers are issued together
 };
 
 struct TileRanges {
@@ -150,6 +170,15 @@ __device__ __forceinline__ TileRanges merge_ranges(int n, int i0, int j0, int i1
 // Threads with an empty share of a tile are transparent to carry chains.
 constexpr int kNoCarry = -1, kEmpty = -2;
 
+// the thread whose share [t*items/B, (t+1)*items/B) contains item p (32-bit: items*B < 2^31)
+template <int BLOCK> __device__ __forceinline__ int owner_of(int p, int items)
+{
+    int t = (p * BLOCK) / items;
+    while (t > 0 && (t * items) / BLOCK > p) --t;
+    while (t + 1 < BLOCK && ((t + 1) * items) / BLOCK <= p) ++t;
+    return t;
+}
+
 template <class T, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK)
     k_csr_merge(int n, const int *__restrict__ rp, const int *__restrict__ col,
@@ -161,9 +190,11 @@ __global__ void __launch_bounds__(BLOCK)
     constexpr int CH = S::CH;
     if (e.skip && *e.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    int *s_crow = reinterpret_cast<int *>(smem + 2 * S::STAGE);
-    T *s_cval = reinterpret_cast<T *>(smem + 2 * S::STAGE + BLOCK * 4);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + BLOCK * (4 + sizeof(T)));
+    int *s_crow = reinterpret_cast<int *>(smem + S::OFF_CROW);
+    T *s_cval = reinterpret_cast<T *>(smem + S::OFF_CVAL);
+    int *s_rl = reinterpret_cast<int *>(smem + S::OFF_RL);
+    int4 *s_coord = reinterpret_cast<int4 *>(smem + S::OFF_COORD);  // per stage (i0, j0, i1, j1)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S::OFF_BAR);
     const int tid = threadIdx.x;
 
     if (tid == 0) {
@@ -173,8 +204,9 @@ __global__ void __launch_bounds__(BLOCK)
     }
     __syncthreads();
 
-    auto issue = [&](int t, int stage) {
-        const int2 a = tiles[t], b = tiles[t + 1];
+    // thread 0 only: copy tile t (coordinates a, b) into `stage`
+    auto issue = [&](int2 a, int2 b, int stage) {
+        s_coord[stage] = make_int4(a.x, a.y, b.x, b.y);
         const TileRanges g = merge_ranges<T>(n, a.x, a.y, b.x, b.y);
         unsigned char *base = smem + stage * S::STAGE;
         mbar_arrive_expect_tx(&bar[stage], (uint32_t)(g.rbytes + g.cbytes + g.vbytes));
@@ -189,61 +221,66 @@ __global__ void __launch_bounds__(BLOCK)
     int it = 0;
     bool ok = true;
     bool pending_prefetch = false;
-    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    int2 na = make_int2(0, 0), nb = make_int2(0, 0);  // thread 0: coordinates of the tile after next
+    if (tid == 0 && (int)blockIdx.x < ntiles) {
+        issue(tiles[blockIdx.x], tiles[blockIdx.x + 1], 0);
+        const int t2 = blockIdx.x + gridDim.x;
+        if (t2 < ntiles) {
+            na = tiles[t2];
+            nb = tiles[t2 + 1];
+        }
+    }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int stage = it & 1;
         const int tn = t + gridDim.x;
         pending_prefetch = tn < ntiles;
         if (tid == 0 && tn < ntiles) {
             fence_proxy_async();
-            issue(tn, stage ^ 1);
+            issue(na, nb, stage ^ 1);
+            const int t3 = tn + gridDim.x;
+            if (t3 < ntiles) {  // load the coordinates one tile ahead
+                na = tiles[t3];
+                nb = tiles[t3 + 1];
+            }
         }
-        const int2 a = tiles[t], b = tiles[t + 1];
-        const int i0 = a.x, j0 = a.y, i1 = b.x, j1 = b.y;
-        const TileRanges g = merge_ranges<T>(n, i0, j0, i1, j1);
-        const unsigned char *sb = smem + stage * S::STAGE;
-        const int *s_rp = reinterpret_cast<const int *>(sb) + (i0 - g.ra);             // rp[i0 + k]
-        const int *s_col = reinterpret_cast<const int *>(sb + g.rbytes) + (j0 - g.ca);  // col[j0 + k]
-        const T *s_val = reinterpret_cast<const T *>(sb + g.rbytes + g.cbytes) + (j0 - g.va);
-        const int rows_avail = i1 - i0;
-        const int nz_tile = j1 - j0;
-        const int items = rows_avail + nz_tile;
-
         if (!mbar_wait(&bar[stage], (uint32_t)((it >> 1) & 1), err)) {
             ok = false;
             break;
         }
+        const int4 co = s_coord[stage];
+        const int i0 = co.x, j0 = co.y, i1 = co.z, j1 = co.w;
+        const TileRanges g = merge_ranges<T>(n, i0, j0, i1, j1);
+        unsigned char *sb = smem + stage * S::STAGE;
+        const int *s_rp = reinterpret_cast<const int *>(sb) + (i0 - g.ra);             // rp[i0 + k]
+        const int *s_col = reinterpret_cast<const int *>(sb + g.rbytes) + (j0 - g.ca);  // col[j0 + k]
+        const T *s_val = reinterpret_cast<const T *>(sb + g.rbytes + g.cbytes) + (j0 - g.va);
+        T *s_res = reinterpret_cast<T *>(sb + g.rbytes + g.cbytes + g.vbytes);          // row sums
+        const int rows_avail = i1 - i0;
+        const int nz_tile = j1 - j0;
+        const int items = rows_avail + nz_tile;
 
-        // --- this thread's share [dl0, dl1) of the tile's merge items
-        const int dl0 = (int)((int64_t)tid * items / BLOCK), dl1 = (int)((int64_t)(tid + 1) * items / BLOCK);
-        auto search = [&](int dl) {
-            int lo = max(0, dl - nz_tile), hi = min(dl, rows_avail);
+        // --- this thread's share [dl0, dl1): one search, the end comes from the next thread
+        const int dl0 = (tid * items) / BLOCK, dl1 = ((tid + 1) * items) / BLOCK;
+        int rl0;
+        {
+            int lo = max(0, dl0 - nz_tile), hi = min(dl0, rows_avail);
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (mid + s_rp[mid + 1] - j0 < dl) lo = mid + 1;
+                if (mid + s_rp[mid + 1] - j0 < dl0) lo = mid + 1;
                 else hi = mid;
             }
-            return lo;
-        };
-        const int rl0 = search(dl0), rl1 = search(dl1);
+            rl0 = lo;
+        }
+        s_rl[tid] = rl0;
+        if (tid == 0) s_rl[BLOCK] = rows_avail;
+        __syncthreads();
+        const int rl1 = s_rl[tid + 1];
         const int jstart = j0 + (dl0 - rl0), jend = j0 + (dl1 - rl1);
-        const int rfirst = i0 + rl0, rlast = i0 + rl1;
-        const bool pend_possible = s_rp[rl0] < jstart;  // first row began before this thread
 
-        // --- sequential walk: one FMA per nonzero
-        int r = rfirst;
-        int re = r < n ? s_rp[r - i0 + 1] : INT_MAX;
-        T sum = T(0), pend = T(0);
-        bool first = true, has_pend = false;
-        auto emit = [&](int row, T s) {
-            if (first && pend_possible) {
-                pend = s;
-                has_pend = true;
-            } else {
-                final_write(e, row, s, d0, d1);
-            }
-            first = false;
-        };
+        // --- walk: one FMA per nonzero; a row end stores the running sum
+        int lr = rl0;  // local row
+        int re = i0 + lr < n ? s_rp[lr + 1] : INT_MAX;
+        T sum = T(0);
         const int nnz_t = jend - jstart;
         for (int c = 0; c < nnz_t; c += CH) {
             T v[CH], xv[CH];
@@ -263,45 +300,47 @@ __global__ void __launch_bounds__(BLOCK)
                 if (c + u < nnz_t) {
                     const int jj = jstart + c + u;
                     while (jj >= re) {
-                        emit(r, sum);
+                        s_res[lr] = sum;
                         sum = T(0);
-                        ++r;
-                        re = r < n ? s_rp[r - i0 + 1] : INT_MAX;
+                        ++lr;
+                        re = i0 + lr < n ? s_rp[lr + 1] : INT_MAX;
                     }
                     sum = fma(v[u], xv[u], sum);
                 }
             }
         }
-        while (r < rlast) {
-            emit(r, sum);
+        while (lr < rl1) {
+            s_res[lr] = sum;
             sum = T(0);
-            ++r;
+            ++lr;
         }
         int crow = kNoCarry;
+        const int r = i0 + lr;
         if (dl0 == dl1) crow = kEmpty;
-        else if (r < n && jend > max(jstart, s_rp[r - i0])) crow = r;
+        else if (r < n && jend > max(jstart, s_rp[lr])) crow = r;
         s_crow[tid] = crow;
         s_cval[tid] = sum;
         __syncthreads();
 
-        // --- complete the first row from the carries of the threads (and tiles) before
-        if (has_pend) {
-            T tot = pend;
-            int k = tid - 1;
-            while (k >= 0 && (s_crow[k] == rfirst || s_crow[k] == kEmpty)) {
-                if (s_crow[k] == rfirst) tot += s_cval[k];
+        // --- finalise the rows that end in this tile, one thread per row
+        for (int q = tid; q < rows_avail; q += BLOCK) {
+            const int row = i0 + q;
+            T v = s_res[q];
+            int k = owner_of<BLOCK>(q + s_rp[q + 1] - j0, items) - 1;
+            while (k >= 0 && (s_crow[k] == row || s_crow[k] == kEmpty)) {
+                if (s_crow[k] == row) v += s_cval[k];
                 --k;
             }
-            if (k < 0 && rfirst == i0 && s_rp[0] < j0) {  // the row began in an earlier tile
+            if (q == 0 && k < 0 && s_rp[0] < j0) {  // the row began in an earlier tile
                 for (int tp = t - 1; tp >= 0; --tp) {
                     if (!flag_wait(flags + tp, err)) break;
-                    tot += ldcg(carry_val_g + tp);
+                    v += ldcg(carry_val_g + tp);
                     flags[tp] = 0;
                     const int2 pa = tiles[tp];
-                    if (!(pa.x == rfirst && pa.y > s_rp[0])) break;  // tile tp began at or before the row start
+                    if (!(pa.x == row && pa.y > s_rp[0])) break;  // tile tp began at or before the row start
                 }
             }
-            final_write(e, rfirst, tot, d0, d1);
+            final_write(e, row, v, d0, d1);
         }
         // --- publish the partial of a row that continues into the next tile
         if (tid == BLOCK - 1 && i1 < n && j1 > s_rp[rows_avail]) {
@@ -398,16 +437,24 @@ __global__ void __launch_bounds__(BLOCK)
 // ------------------------------------------------------------------ COO segmented reduction
 // Tiles of about TILE nonzeros (row-sorted COO, boundaries snapped forward to
 // the next row start when it is at most SLACK entries away) are staged by
-// bulk copies; each thread reduces its share of the tile sequentially,
-// emitting a row when the row index changes.  Store mode writes every row
-// (rows without entries get alpha*0 + beta*z); add mode (the COO part of HYB)
-// adds into y.  Rows that straddle tiles use the same look-back as merge CSR.
+// bulk copies.  walk: each thread reduces an equal share of the tile's
+// entries sequentially; when the row index changes, the finished sum goes
+// into the shared-memory value slot of the row's last entry (a slot only
+// this thread reads, already consumed).  finalise: one thread per row end
+// adds the carries of the threads before the owner (fixed order) and stores
+// y; rows without entries get alpha*0 + beta*z.  Add mode (the COO part of
+// HYB) adds into y instead.  Rows that straddle tiles use the look-back.
 template <class T, int BLOCK, int IPT> struct CooShape {
     static constexpr int TILE = BLOCK * IPT;
     static constexpr int SLACK = TILE / 4;
     static constexpr int STAGE = (int)((8 + sizeof(T)) * (TILE + SLACK) + 128);
-    static constexpr int SMEM = 2 * STAGE + BLOCK * (4 + (int)sizeof(T)) + 16;
-    static constexpr int CH = 8;
+    // stages | carry rows | carry values | tile coords (2 stages) | mbarriers
+    static constexpr int OFF_CROW = 2 * STAGE;
+    static constexpr int OFF_CVAL = OFF_CROW + BLOCK * 4;
+    static constexpr int OFF_COORD = OFF_CVAL + BLOCK * (int)sizeof(T);
+    static constexpr int OFF_BAR = OFF_COORD + 32;
+    static constexpr int SMEM = OFF_BAR + 16;
+    static constexpr int CH = IPT < 8 ? IPT : 8;
 };
 
 template <class T>
@@ -435,9 +482,10 @@ __global__ void __launch_bounds__(BLOCK)
     constexpr int CH = S::CH;
     if (e.skip && *e.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    int *s_crow = reinterpret_cast<int *>(smem + 2 * S::STAGE);
-    T *s_cval = reinterpret_cast<T *>(smem + 2 * S::STAGE + BLOCK * 4);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + BLOCK * (4 + sizeof(T)));
+    int *s_crow = reinterpret_cast<int *>(smem + S::OFF_CROW);
+    T *s_cval = reinterpret_cast<T *>(smem + S::OFF_CVAL);
+    int4 *s_coord = reinterpret_cast<int4 *>(smem + S::OFF_COORD);  // (k0, k1, row before, row after)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S::OFF_BAR);
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -446,8 +494,13 @@ __global__ void __launch_bounds__(BLOCK)
     }
     __syncthreads();
 
-    auto issue = [&](int t, int stage) {
-        const int64_t k0 = tiles[t], k1 = tiles[t + 1];
+    auto coords = [&](int t) -> int4 {  // thread 0, one tile ahead of its use
+        const int k0 = tiles[t], k1 = tiles[t + 1];
+        return make_int4(k0, k1, k0 > 0 ? __ldg(crow + k0 - 1) : -1, k1 < nnz ? __ldg(crow + k1) : (int)n);
+    };
+    auto issue = [&](int4 c, int stage) {
+        s_coord[stage] = c;
+        const int64_t k0 = c.x, k1 = c.y;
         unsigned char *base = smem + stage * S::STAGE;
         if (k1 <= k0) {  // empty tile: complete the phase with no bytes
             mbar_arrive_expect_tx(&bar[stage], 0u);
@@ -463,55 +516,42 @@ __global__ void __launch_bounds__(BLOCK)
     T d0 = T(0), d1 = T(0);
     int it = 0;
     bool ok = true, pending_prefetch = false;
-    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    int4 nc = make_int4(0, 0, 0, 0);  // thread 0: coordinates of the tile after next
+    if (tid == 0 && (int)blockIdx.x < ntiles) {
+        issue(coords(blockIdx.x), 0);
+        if ((int)(blockIdx.x + gridDim.x) < ntiles) nc = coords(blockIdx.x + gridDim.x);
+    }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int stage = it & 1;
         const int tn = t + gridDim.x;
         pending_prefetch = tn < ntiles;
         if (tid == 0 && tn < ntiles) {
             fence_proxy_async();
-            issue(tn, stage ^ 1);
+            issue(nc, stage ^ 1);
+            if (tn + (int)gridDim.x < ntiles) nc = coords(tn + gridDim.x);
         }
-        const int64_t kt0 = tiles[t], kt1 = tiles[t + 1];
-        const TileRanges g = coo_ranges<T>(kt0, max(kt1, kt0 + 1));
-        const unsigned char *sb = smem + stage * S::STAGE;
-        const int *s_row = reinterpret_cast<const int *>(sb) + (kt0 - g.ra);
-        const int *s_col = reinterpret_cast<const int *>(sb + g.rbytes) + (kt0 - g.ca);
-        const T *s_val = reinterpret_cast<const T *>(sb + 2 * g.rbytes) + (kt0 - g.va);
         if (!mbar_wait(&bar[stage], (uint32_t)((it >> 1) & 1), err)) {
             ok = false;
             break;
         }
+        const int4 co = s_coord[stage];
+        const int64_t kt0 = co.x, kt1 = co.y;
+        const int row_before = co.z, row_after = co.w;
+        const TileRanges g = coo_ranges<T>(kt0, max(kt1, kt0 + 1));
+        unsigned char *sb = smem + stage * S::STAGE;
+        const int *s_row = reinterpret_cast<const int *>(sb) + (kt0 - g.ra);
+        const int *s_col = reinterpret_cast<const int *>(sb + g.rbytes) + (kt0 - g.ca);
+        T *s_val = reinterpret_cast<T *>(sb + 2 * g.rbytes) + (kt0 - g.va);
         const int tile_n = (int)(kt1 - kt0);
-        const int l0 = (int)((int64_t)tid * tile_n / BLOCK), l1 = (int)((int64_t)(tid + 1) * tile_n / BLOCK);
-        auto row_at = [&](int64_t k) -> int {  // row of global entry k (k in [0, nnz))
-            return (k >= kt0 && k < kt1) ? s_row[k - kt0] : __ldg(crow + k);
+        const int l0 = (tid * tile_n) / BLOCK, l1 = ((tid + 1) * tile_n) / BLOCK;
+        auto row_at = [&](int64_t k) -> int {  // row of entry k in [kt0, kt1]
+            return k < kt1 ? s_row[k - kt0] : row_after;
         };
-        auto gap = [&](int from, int to) {  // rows [from, to) have no entries
-            if (add_mode) return;
-            for (int q = from; q < to; ++q) final_write(e, q, T(0), d0, d1);
-        };
-        T sum = T(0), pend = T(0);
-        bool has_pend = false;
-        int r = -1, rfirst = -1;
+        // --- walk
+        T sum = T(0);
         int crow_out = kEmpty;
         if (l0 < l1) {
-            const int64_t k0 = kt0 + l0;
-            r = rfirst = s_row[l0];
-            const bool pend_possible = k0 > 0 && row_at(k0 - 1) == r;
-            if (k0 == 0) gap(0, r);
-            bool first = true;
-            auto emit = [&](int row, T s) {
-                if (first && pend_possible) {
-                    pend = s;
-                    has_pend = true;
-                } else if (add_mode) {
-                    e.y[row] += e.alpha * s;
-                } else {
-                    final_write(e, row, s, d0, d1);
-                }
-                first = false;
-            };
+            int r = s_row[l0];
             const int cnt = l1 - l0;
             for (int c = 0; c < cnt; c += CH) {
                 T v[CH], xv[CH];
@@ -532,9 +572,8 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
                     if (c + u < cnt) {
-                        if (rr[u] != r) {
-                            emit(r, sum);
-                            gap(r + 1, rr[u]);
+                        if (rr[u] != r) {  // entry l0+c+u-1 ended row r
+                            s_val[l0 + c + u - 1] = sum;
                             r = rr[u];
                             sum = T(0);
                         }
@@ -542,13 +581,10 @@ __global__ void __launch_bounds__(BLOCK)
                     }
                 }
             }
-            const int64_t kn = kt0 + l1;
-            const int nr = kn < nnz ? row_at(kn) : (int)n;
-            if (nr == r) {
+            if (row_at(kt0 + l1) == r) {
                 crow_out = r;
             } else {
-                emit(r, sum);
-                gap(r + 1, nr);
+                s_val[l1 - 1] = sum;
                 sum = T(0);
                 crow_out = kNoCarry;
             }
@@ -556,26 +592,36 @@ __global__ void __launch_bounds__(BLOCK)
         s_crow[tid] = crow_out;
         s_cval[tid] = sum;
         __syncthreads();
-        if (has_pend) {
-            T tot = pend;
-            int k = tid - 1;
-            while (k >= 0 && (s_crow[k] == rfirst || s_crow[k] == kEmpty)) {
-                if (s_crow[k] == rfirst) tot += s_cval[k];
+        // --- finalise: one thread per entry that ends a row in this tile
+        if (tid == 0 && kt0 == 0 && tile_n > 0 && !add_mode)
+            for (int q = 0; q < s_row[0]; ++q) final_write(e, q, T(0), d0, d1);  // rows before the first entry
+        for (int q = tid; q < tile_n; q += BLOCK) {
+            const int row = s_row[q];
+            const int next = q + 1 < tile_n ? s_row[q + 1] : row_after;
+            if (next == row) continue;  // not the row's last entry
+            T v = s_val[q];
+            int k = owner_of<BLOCK>(q, tile_n) - 1;
+            while (k >= 0 && (s_crow[k] == row || s_crow[k] == kEmpty)) {
+                if (s_crow[k] == row) v += s_cval[k];
                 --k;
             }
-            if (k < 0 && kt0 > 0 && row_at(kt0 - 1) == rfirst) {  // the row began in an earlier tile
+            if (k < 0 && row_before == row) {  // the row began in an earlier tile
                 for (int tp = t - 1; tp >= 0; --tp) {
                     if (!flag_wait(flags + tp, err)) break;
-                    tot += ldcg(carry_val_g + tp);
+                    v += ldcg(carry_val_g + tp);
                     flags[tp] = 0;
                     const int64_t ps = tiles[tp];
-                    if (!(ps > 0 && __ldg(crow + ps) == rfirst && __ldg(crow + ps - 1) == rfirst)) break;
+                    if (!(ps > 0 && __ldg(crow + ps) == row && __ldg(crow + ps - 1) == row)) break;
                 }
             }
-            if (add_mode) e.y[rfirst] += e.alpha * tot;
-            else final_write(e, rfirst, tot, d0, d1);
+            if (add_mode) {
+                e.y[row] += e.alpha * v;
+            } else {
+                final_write(e, row, v, d0, d1);
+                for (int gq = row + 1; gq < next; ++gq) final_write(e, gq, T(0), d0, d1);  // rows without entries
+            }
         }
-        if (tid == BLOCK - 1 && kt1 < nnz && kt1 > kt0 && s_row[tile_n - 1] == __ldg(crow + kt1)) {
+        if (tid == BLOCK - 1 && kt1 < nnz && kt1 > kt0 && s_row[tile_n - 1] == row_after) {
             const int cr = s_row[tile_n - 1];
             T cv = T(0);
             for (int k = BLOCK - 1; k >= 0 && (s_crow[k] == cr || s_crow[k] == kEmpty); --k)
@@ -650,8 +696,8 @@ namespace {
 
 constexpr int kVecBlock = 256;
 constexpr int kEllBlock = 256;
-constexpr int kMergeBlock = 128;
-constexpr int kCooBlock = 128;
+constexpr int kMergeBlock = 256;
+constexpr int kCooBlock = 256;
 
 template <class K> int grid_for(spx_ctx *ctx, K kernel, int block, int smem, int64_t work_blocks)
 {
@@ -843,12 +889,12 @@ int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
         }
     }
     if (kern == SPX_KERNEL_CSR_MERGE) {
-        if (p <= 0) p = 16;
+        if (p <= 0) p = 8;
         switch (p) {
+        case 4: return launch_merge<T, 4>(ctx, A, val, x, e);
         case 8: return launch_merge<T, 8>(ctx, A, val, x, e);
         case 16: return launch_merge<T, 16>(ctx, A, val, x, e);
-        case 32: return launch_merge<T, 32>(ctx, A, val, x, e);
-        default: return fail(SPX_ERR_INVALID, "merge items per thread must be 8, 16 or 32");
+        default: return fail(SPX_ERR_INVALID, "merge items per thread must be 4, 8 or 16");
         }
     }
     return fail(SPX_ERR_UNSUPPORTED, "kernel not valid for a CSR matrix");
@@ -874,12 +920,12 @@ template <class T>
 int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
 {
     int p = A->kernel == SPX_KERNEL_COO ? A->kparam : 0;
-    if (p <= 0) p = 16;
+    if (p <= 0) p = 8;
     switch (p) {
+    case 4: return launch_coo<T, 4>(ctx, A, cval, x, e, add);
     case 8: return launch_coo<T, 8>(ctx, A, cval, x, e, add);
     case 16: return launch_coo<T, 16>(ctx, A, cval, x, e, add);
-    case 32: return launch_coo<T, 32>(ctx, A, cval, x, e, add);
-    default: return fail(SPX_ERR_INVALID, "COO items per thread must be 8, 16 or 32");
+    default: return fail(SPX_ERR_INVALID, "COO items per thread must be 4, 8 or 16");
     }
 }
 
@@ -964,7 +1010,7 @@ template int spmv_launch<float>(spx_ctx *, const spx_matrix *, const float *, co
 namespace spx {
 namespace {
 
-constexpr int kNoAllocIpt = 16;
+constexpr int kNoAllocIpt = 8;
 constexpr int64_t kNoAllocMaxTiles = SPX_NOALLOC_MAX_TILES;
 constexpr size_t kNoAllocBytes = 1u << 20;  // 1 MiB
 

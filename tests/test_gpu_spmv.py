@@ -66,9 +66,9 @@ MATRICES = {
 VARIANTS = [
     ("csr", None, 0),
     ("csr", "vector", 1), ("csr", "vector", 4), ("csr", "vector", 32),
-    ("csr", "merge", 8), ("csr", "merge", 16), ("csr", "merge", 32),
+    ("csr", "merge", 4), ("csr", "merge", 8), ("csr", "merge", 16),
     ("ell", None, 0), ("ell", "ell", 1),
-    ("coo", None, 0), ("coo", "coo", 8), ("coo", "coo", 32),
+    ("coo", None, 0), ("coo", "coo", 4), ("coo", "coo", 16),
     ("hyb", None, 0), ("hyb0", None, 0), ("hyb3", None, 0),
 ]
 

@@ -35,7 +35,7 @@ def test_no_alloc_matches_spmv(spx, which, dtype):
     rp_d, col_d, val_d = t(rp), t(col), t(val).to(dtype)
     ctx = spx.spx_ctx_create(0)
     A = spx.spx_matrix_create(ctx, "csr", rp_d, col_d, val_d)
-    spx.spx_matrix_set_kernel(A, spx.SPX_KERNEL_CSR_MERGE, 16)
+    spx.spx_matrix_set_kernel(A, spx.SPX_KERNEL_CSR_MERGE, 8)
     try:
         for seed in (1, 2):  # two calls in a row
             xh = synth.uniform_vector(n, seed)
