@@ -291,7 +291,8 @@ void free_matrix_arrays(spx_matrix *A)
     DBuf *bufs[] = {&A->rp,       &A->col,       &A->val,      &A->val32,     &A->ell_col,
                     &A->ell_val,  &A->ell_val32, &A->coo_row,  &A->coo_col,   &A->coo_val,
                     &A->coo_val32, &A->tiles,    &A->carry_row, &A->carry_val, &A->partials,
-                    &A->ticket,   &A->stage_x,   &A->stage_y,   &A->coo_tiles, &A->flags};
+                    &A->ticket,   &A->stage_x,   &A->stage_y,   &A->coo_tiles, &A->flags,
+                    &A->hint};
     for (DBuf *b : bufs) dbuf_free(c, *b);
 }
 
@@ -625,7 +626,10 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     if (!A) return fail(SPX_ERR_INVALID, "spx_matrix_set_kernel: A is NULL");
     bool okk = false;
     switch (A->format) {
-    case SPX_CSR: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_CSR_VECTOR || kernel == SPX_KERNEL_CSR_MERGE; break;
+    case SPX_CSR:
+        okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_CSR_VECTOR || kernel == SPX_KERNEL_CSR_MERGE ||
+              kernel == SPX_KERNEL_CSR_SPLIT;
+        break;
     case SPX_ELL: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_ELL; break;
     case SPX_COO: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_COO; break;
     case SPX_HYB: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_ELL || kernel == SPX_KERNEL_COO; break;
@@ -634,9 +638,13 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     if (kernel == SPX_KERNEL_CSR_VECTOR && param != 0 &&
         !(param == 1 || param == 2 || param == 4 || param == 8 || param == 16 || param == 32))
         return fail(SPX_ERR_INVALID, "CSR vector width must be 0 (auto) or 1..32, a power of 2");
-    if ((kernel == SPX_KERNEL_CSR_MERGE || kernel == SPX_KERNEL_COO) && param != 0 &&
-        !(param == 4 || param == 8 || param == 16))
-        return fail(SPX_ERR_INVALID, "items per thread must be 0 (auto), 4, 8 or 16");
+    if (kernel == SPX_KERNEL_CSR_MERGE && param != 0 && !(param == 4 || param == 8 || param == 16))
+        return fail(SPX_ERR_INVALID, "merge items per thread must be 0 (auto), 4, 8 or 16");
+    if (kernel == SPX_KERNEL_COO && param != 0 &&
+        !(param == 8 || param == 16 || param == 104 || param == 108 || param == 116))
+        return fail(SPX_ERR_INVALID, "COO parameter must be 0 (auto), 8, 16 (split) or 104, 108, 116 (tiled)");
+    if (kernel == SPX_KERNEL_CSR_SPLIT && param != 0 && !(param == 8 || param == 16))
+        return fail(SPX_ERR_INVALID, "split nonzeros per lane must be 0 (auto), 8 or 16");
     if (kernel == SPX_KERNEL_ELL && param != 0 && !(param == 1 || param == 2 || (param == 4 && A->dtype == SPX_F32)))
         return fail(SPX_ERR_INVALID, "ELL rows per thread must be 0 (auto), 1, 2 (or 4 for FP32)");
     A->kernel = kernel;

@@ -389,6 +389,365 @@ __global__ void k_merge_tiles(int n, int nnz, const int *__restrict__ rp, int64_
     tiles[t] = make_int2(i, j);
 }
 
+// ------------------------------------------------------------------ nnz-split CSR (warp-independent)
+// Every lane of a persistent warp takes a granule of IPT consecutive nonzeros
+// (loads fully independent of any search: coalesced across the warp) and
+// finds its first row through a row hint (hint[g] = row holding nonzero
+// g*IPT).  It accumulates sequentially, one FMA per nonzero, and writes y for
+// every row that ends inside its granule.  A row that began in an earlier
+// lane of the same chunk is completed from those lanes' partial sums (a short
+// chain in shared memory); a row running past the chunk is carried to the
+// warp's next chunk in registers.  Each warp owns one contiguous range of
+// chunks, so only the row straddling a range boundary crosses warps: the
+// warp publishes that partial when it finishes and completes its own first
+// row last, looking back at the previous warps (cooperative launch).  No
+// block-wide barrier is needed until the final dot reduction.
+//   Row ownership: row r ends in the lane whose granule [a, b) has
+//   a < rp[r+1] <= b (rows with rp[r+1] == 0 belong to granule 0).
+template <class T, int IPT>
+__global__ void __launch_bounds__(256)
+    k_csr_split(int n, int nnz, const int *__restrict__ rp, const int *__restrict__ col,
+                const T *__restrict__ val, const T *__restrict__ x, const int *__restrict__ hint, int nchunks,
+                int *carry_row_w, T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err,
+                Epi<T> e)
+{
+    constexpr int CH = 8;
+    constexpr int NW = 256 / 32;
+    if (e.skip && *e.skip) return;
+    __shared__ int s_cr[NW][32];
+    __shared__ T s_cv[NW][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int W = gridDim.x * NW;
+    const int w = blockIdx.x * NW + wib;
+    const int c_begin = (int)(((int64_t)nchunks * w) / W), c_end = (int)(((int64_t)nchunks * (w + 1)) / W);
+    T d0 = T(0), d1 = T(0);
+
+    // the range's first row, if it began before the range, is completed last
+    const int64_t range_a = (int64_t)c_begin * 32 * IPT;
+    int first_row = -1;
+    bool range_inside = false;
+    if (c_begin < c_end && range_a < nnz) {
+        first_row = hint[(int64_t)c_begin * 32];
+        range_inside = rp[first_row] < range_a;
+    }
+    T first_val = T(0);
+    bool first_ready = false;   // the first row ended in this range (value in first_val, lane 0)
+    int run_row = -1;           // row carried from the previous chunk (warp-uniform)
+    T run_val = T(0);
+
+    for (int c = c_begin; c < c_end; ++c) {
+        const int64_t g = (int64_t)c * 32 + lane;
+        const int64_t a = g * IPT;
+        const int b = (int)min(a + IPT, (int64_t)nnz);
+        const bool active = a < nnz;
+        int r = active ? hint[g] : n;
+        int re = r < n ? rp[r + 1] : INT_MAX;
+        const bool pend_possible = active && rp[r] < a;
+        T sum = T(0), pend = T(0);
+        bool first = true, has_pend = false;
+        const int rstart = r;
+#define SPX_SPLIT_EMIT(row_, s_)                       \
+    do {                                               \
+        if (first && pend_possible) {                  \
+            pend = (s_);                               \
+            has_pend = true;                           \
+        } else {                                       \
+            final_write(e, (row_), (s_), d0, d1);      \
+        }                                              \
+        first = false;                                 \
+    } while (0)
+        if (a == 0 && active)  // rows before the first nonzero have no entries
+            for (int q = 0; q < r; ++q) final_write(e, q, T(0), d0, d1);
+        if (active) {
+            const int cnt = b - (int)a;
+#pragma unroll
+            for (int kk = 0; kk < IPT; kk += CH) {
+                T v[CH], xv[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const int j = (int)a + kk + u;
+                    if (kk + u < cnt) {
+                        v[u] = val[j];
+                        xv[u] = __ldg(x + col[j]);
+                    } else {
+                        v[u] = T(0);
+                        xv[u] = T(0);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (kk + u < cnt) {
+                        const int j = (int)a + kk + u;
+                        while (j >= re) {
+                            SPX_SPLIT_EMIT(r, sum);
+                            sum = T(0);
+                            ++r;
+                            re = r < n ? rp[r + 1] : INT_MAX;
+                        }
+                        sum = fma(v[u], xv[u], sum);
+                    }
+                }
+            }
+            while (r < n && re <= b) {  // rows ending exactly at b (and empty rows there)
+                SPX_SPLIT_EMIT(r, sum);
+                sum = T(0);
+                ++r;
+                re = r < n ? rp[r + 1] : INT_MAX;
+            }
+        }
+        int cr = kEmpty;
+        if (active) cr = (r < n && b > max((int)a, rp[r])) ? r : kNoCarry;
+        s_cr[wib][lane] = cr;
+        s_cv[wib][lane] = sum;
+        __syncwarp();
+        // complete a row that began in earlier lanes (and maybe earlier chunks)
+        if (has_pend) {
+            T tot = pend;
+            int k = lane - 1;
+            while (k >= 0 && (s_cr[wib][k] == rstart || s_cr[wib][k] == kEmpty)) {
+                if (s_cr[wib][k] == rstart) tot += s_cv[wib][k];
+                --k;
+            }
+            if (k < 0 && rstart == run_row) tot += run_val;
+            if (range_inside && rstart == first_row) {
+                first_val = tot;  // finished last, after the look-back
+                first_ready = true;
+            } else {
+                final_write(e, rstart, tot, d0, d1);
+            }
+        }
+        // carry to the next chunk: the row still open at the end of lane 31
+        int nrow = -1;
+        T nval = T(0);
+        if (lane == 31 && s_cr[wib][31] >= 0) {
+            nrow = s_cr[wib][31];
+            int k = 31;
+            while (k >= 0 && (s_cr[wib][k] == nrow || s_cr[wib][k] == kEmpty)) {
+                if (s_cr[wib][k] == nrow) nval += s_cv[wib][k];
+                --k;
+            }
+            if (k < 0 && nrow == run_row) nval += run_val;
+        }
+        run_row = __shfl_sync(0xffffffffu, nrow, 31);
+        run_val = __shfl_sync(0xffffffffu, nval, 31);
+        // the lane that finished the deferred first row passes it to lane 0
+        const unsigned fm = __ballot_sync(0xffffffffu, first_ready);
+        if (fm) {
+            const int src = __ffs(fm) - 1;
+            first_val = __shfl_sync(0xffffffffu, first_val, src);
+            first_ready = true;
+        }
+        __syncwarp();
+    }
+    // publish the partial of the row that continues into the next warp's range
+    if (lane == 0 && run_row >= 0) {
+        carry_row_w[w] = run_row;
+        carry_val_w[w] = run_val;
+        flag_publish(flags + w);
+    }
+    // then complete the range's first row from the previous ranges' partials
+    if (lane == 0 && range_inside && first_ready) {
+        T tot = first_val;
+        const int rs = rp[first_row];
+        for (int wp = w - 1; wp >= 0; --wp) {
+            const int pb = (int)(((int64_t)nchunks * wp) / W), pe = (int)(((int64_t)nchunks * (wp + 1)) / W);
+            if (pb >= pe) continue;  // empty range
+            if (!flag_wait(flags + wp, err)) break;
+            tot += ldcg(carry_val_w + wp);
+            flags[wp] = 0;
+            if (!(rs < (int64_t)pb * 32 * IPT)) break;  // range wp began at or before the row start
+        }
+        final_write(e, first_row, tot, d0, d1);
+    }
+    if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
+#undef SPX_SPLIT_EMIT
+}
+
+// ------------------------------------------------------------------ nnz-split COO (warp-independent)
+// The COO counterpart of k_csr_split: lane granules of IPT consecutive
+// entries, the row of every entry read from the row array.  A lane ends row r
+// at its last entry when the next entry's row differs; rows without entries
+// between two entries are written (store mode) by the lane that sees the
+// jump.  Carries between lanes, chunks and warp ranges as in k_csr_split.
+// Add mode (the COO part of HYB) adds alpha * sum into y and writes no gaps.
+template <class T, int IPT>
+__global__ void __launch_bounds__(256)
+    k_coo_split(int n, int nnz, const int *__restrict__ crow, const int *__restrict__ ccol,
+                const T *__restrict__ cval, const T *__restrict__ x, int nchunks, int *carry_row_w,
+                T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e, int add_mode)
+{
+    constexpr int CH = 8;
+    constexpr int NW = 256 / 32;
+    if (e.skip && *e.skip) return;
+    __shared__ int s_cr[NW][32];
+    __shared__ T s_cv[NW][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int W = gridDim.x * NW;
+    const int w = blockIdx.x * NW + wib;
+    const int c_begin = (int)(((int64_t)nchunks * w) / W), c_end = (int)(((int64_t)nchunks * (w + 1)) / W);
+    T d0 = T(0), d1 = T(0);
+#define SPX_COO_OUT(row_, s_)                                                      \
+    do {                                                                           \
+        if (add_mode) e.y[(row_)] += e.alpha * (s_);                               \
+        else final_write(e, (row_), (s_), d0, d1);                                 \
+    } while (0)
+
+    const int64_t range_a = (int64_t)c_begin * 32 * IPT;
+    int first_row = -1;
+    bool range_inside = false;
+    if (c_begin < c_end && range_a < nnz) {
+        first_row = crow[range_a];
+        range_inside = range_a > 0 && crow[range_a - 1] == first_row;
+    }
+    T first_val = T(0);
+    bool first_ready = false;
+    int run_row = -1;
+    T run_val = T(0);
+
+    for (int c = c_begin; c < c_end; ++c) {
+        const int64_t g = (int64_t)c * 32 + lane;
+        const int64_t a = g * IPT;
+        const int b = (int)min(a + IPT, (int64_t)nnz);
+        const bool active = a < nnz;
+        int r = active ? crow[a] : n;
+        const bool pend_possible = active && a > 0 && crow[a - 1] == r;
+        const int rstart = r;
+        T sum = T(0), pend = T(0);
+        bool first = true, has_pend = false;
+#define SPX_COO_EMIT(row_, s_)                                                     \
+    do {                                                                           \
+        if (first && pend_possible) {                                              \
+            pend = (s_);                                                           \
+            has_pend = true;                                                       \
+        } else {                                                                   \
+            SPX_COO_OUT(row_, s_);                                                 \
+        }                                                                          \
+        first = false;                                                             \
+    } while (0)
+        if (a == 0 && active && !add_mode)
+            for (int q = 0; q < r; ++q) final_write(e, q, T(0), d0, d1);  // rows before the first entry
+        int cr = kEmpty;
+        if (active) {
+            const int cnt = b - (int)a;
+#pragma unroll
+            for (int kk = 0; kk < IPT; kk += CH) {
+                T v[CH], xv[CH];
+                int rr[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    const int j = (int)a + kk + u;
+                    if (kk + u < cnt) {
+                        v[u] = cval[j];
+                        xv[u] = __ldg(x + ccol[j]);
+                        rr[u] = crow[j];
+                    } else {
+                        v[u] = T(0);
+                        xv[u] = T(0);
+                        rr[u] = r;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (kk + u < cnt) {
+                        if (rr[u] != r) {
+                            SPX_COO_EMIT(r, sum);
+                            if (!add_mode)
+                                for (int q = r + 1; q < rr[u]; ++q) final_write(e, q, T(0), d0, d1);
+                            r = rr[u];
+                            sum = T(0);
+                        }
+                        sum = fma(v[u], xv[u], sum);
+                    }
+                }
+            }
+            const int nr = b < nnz ? crow[b] : n;
+            if (nr == r) {
+                cr = r;
+            } else {
+                SPX_COO_EMIT(r, sum);
+                if (!add_mode)
+                    for (int q = r + 1; q < nr; ++q) final_write(e, q, T(0), d0, d1);
+                sum = T(0);
+                cr = kNoCarry;
+            }
+        }
+        s_cr[wib][lane] = cr;
+        s_cv[wib][lane] = sum;
+        __syncwarp();
+        if (has_pend) {
+            T tot = pend;
+            int k = lane - 1;
+            while (k >= 0 && (s_cr[wib][k] == rstart || s_cr[wib][k] == kEmpty)) {
+                if (s_cr[wib][k] == rstart) tot += s_cv[wib][k];
+                --k;
+            }
+            if (k < 0 && rstart == run_row) tot += run_val;
+            if (range_inside && rstart == first_row) {
+                first_val = tot;
+                first_ready = true;
+            } else {
+                SPX_COO_OUT(rstart, tot);
+            }
+        }
+        int nrow = -1;
+        T nval = T(0);
+        if (lane == 31 && s_cr[wib][31] >= 0) {
+            nrow = s_cr[wib][31];
+            int k = 31;
+            while (k >= 0 && (s_cr[wib][k] == nrow || s_cr[wib][k] == kEmpty)) {
+                if (s_cr[wib][k] == nrow) nval += s_cv[wib][k];
+                --k;
+            }
+            if (k < 0 && nrow == run_row) nval += run_val;
+        }
+        run_row = __shfl_sync(0xffffffffu, nrow, 31);
+        run_val = __shfl_sync(0xffffffffu, nval, 31);
+        const unsigned fm = __ballot_sync(0xffffffffu, first_ready);
+        if (fm) {
+            const int src = __ffs(fm) - 1;
+            first_val = __shfl_sync(0xffffffffu, first_val, src);
+            first_ready = true;
+        }
+        __syncwarp();
+#undef SPX_COO_EMIT
+    }
+    if (lane == 0 && run_row >= 0) {
+        carry_row_w[w] = run_row;
+        carry_val_w[w] = run_val;
+        flag_publish(flags + w);
+    }
+    if (lane == 0 && range_inside && first_ready) {
+        T tot = first_val;
+        for (int wp = w - 1; wp >= 0; --wp) {
+            const int pb = (int)(((int64_t)nchunks * wp) / W), pe = (int)(((int64_t)nchunks * (wp + 1)) / W);
+            if (pb >= pe) continue;
+            if (!flag_wait(flags + wp, err)) break;
+            tot += ldcg(carry_val_w + wp);
+            flags[wp] = 0;
+            const int64_t ps = (int64_t)pb * 32 * IPT;
+            if (!(ps > 0 && crow[ps - 1] == first_row)) break;  // range wp began at the row start
+        }
+        SPX_COO_OUT(first_row, tot);
+    }
+    if (e.dots && !add_mode) finish_dots<T, 256>(d0, d1, e, partials, ticket);
+#undef SPX_COO_OUT
+}
+
+// hint[g] = the row holding nonzero g*ipt: first r with rp[r+1] > g*ipt
+__global__ void k_row_hint(int n, int nnz, const int *__restrict__ rp, int ipt, int ng, int *hint)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    const int64_t j = (int64_t)g * ipt;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rp[mid + 1] > j) hi = mid;
+        else lo = mid + 1;
+    }
+    hint[g] = lo;
+}
+
 // ------------------------------------------------------------------ ELL
 // Column-major ELL [width][ld]: thread g handles rows g*R .. g*R+R-1 and
 // reads R consecutive values (16 B for R = 16 / sizeof(T)) per slab, fully
@@ -802,6 +1161,58 @@ int launch_merge(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
                     A->flags.as<int>(), A->partials.as<T>(), A->ticket.as<unsigned>(), ctx->dev_err, e);
 }
 
+int ensure_hint(spx_ctx *ctx, spx_matrix *A, int ipt)
+{
+    if (A->hint.p && A->hint_ipt == ipt) return SPX_OK;
+    const int64_t ng = ceil_div(A->nnz, ipt);
+    dbuf_free(ctx, A->hint);
+    SPX_TRY(dbuf_alloc(ctx, A->hint, (size_t)(ng > 0 ? ng : 1) * 4));
+    if (ng > 0) {
+        k_row_hint<<<(int)ceil_div(ng, 256), 256, 0, ctx->stream>>>((int)A->n, (int)A->nnz, A->rp.as<int>(), ipt,
+                                                                  (int)ng, A->hint.as<int>());
+        SPX_CUDA(cudaGetLastError());
+    }
+    A->hint_ipt = ipt;
+    return SPX_OK;
+}
+
+template <class T, int IPT>
+int launch_split(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    auto kern = k_csr_split<T, IPT>;
+    SPX_TRY(ensure_hint(ctx, A, IPT));
+    const int64_t nchunks = ceil_div(ceil_div(A->nnz, IPT), 32);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    const int64_t need = ceil_div(nchunks, 8);  // at least one chunk per warp
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    SPX_TRY(ensure_scratch(ctx, A, grid * 8, grid, sizeof(T)));
+    return launch_k(kern, (int)grid, 256, 0, ctx->stream, true, (int)A->n, (int)A->nnz, (const int *)A->rp.as<int>(),
+                    (const int *)A->col.as<int>(), val, x, (const int *)A->hint.as<int>(), (int)nchunks,
+                    A->carry_row.as<int>(), A->carry_val.as<T>(), A->flags.as<int>(), A->partials.as<T>(),
+                    A->ticket.as<unsigned>(), ctx->dev_err, e);
+}
+
+template <class T, int IPT>
+int launch_coo_split(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
+{
+    auto kern = k_coo_split<T, IPT>;
+    const int64_t nchunks = ceil_div(ceil_div(A->coo_nnz, IPT), 32);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    const int64_t need = ceil_div(nchunks, 8);
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    SPX_TRY(ensure_scratch(ctx, A, grid * 8, grid, sizeof(T)));
+    return launch_k(kern, (int)grid, 256, 0, ctx->stream, true, (int)A->n, (int)A->coo_nnz,
+                    (const int *)A->coo_row.as<int>(), (const int *)A->coo_col.as<int>(), cval, x, (int)nchunks,
+                    A->carry_row.as<int>(), A->carry_val.as<T>(), A->flags.as<int>(), A->partials.as<T>(),
+                    A->ticket.as<unsigned>(), ctx->dev_err, e, add);
+}
+
 template <class T, int SW>
 int launch_vector(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
 {
@@ -872,7 +1283,11 @@ template <class T>
 int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
 {
     int kern = A->kernel, p = A->kparam;
-    if (kern == SPX_KERNEL_AUTO) kern = SPX_KERNEL_CSR_MERGE;
+    if (kern == SPX_KERNEL_AUTO) {
+        // regular rows: merge-path tiles; heavy-tailed rows: the warp-independent split kernel
+        kern = (double)A->max_len <= 4.0 * A->mean_len + 8.0 ? SPX_KERNEL_CSR_MERGE : SPX_KERNEL_CSR_SPLIT;
+        p = kern == SPX_KERNEL_CSR_SPLIT ? 8 : 0;
+    }
     if (kern == SPX_KERNEL_CSR_VECTOR) {
         if (p <= 0) {  // sub-warp width from the mean row length
             p = 1;
@@ -886,6 +1301,14 @@ int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
         case 16: return launch_vector<T, 16>(ctx, A, val, x, e);
         case 32: return launch_vector<T, 32>(ctx, A, val, x, e);
         default: return fail(SPX_ERR_INVALID, "CSR vector sub-warp width must be 1..32, a power of 2");
+        }
+    }
+    if (kern == SPX_KERNEL_CSR_SPLIT) {
+        if (p <= 0) p = 16;
+        switch (p) {
+        case 8: return launch_split<T, 8>(ctx, A, val, x, e);
+        case 16: return launch_split<T, 16>(ctx, A, val, x, e);
+        default: return fail(SPX_ERR_INVALID, "split nonzeros per lane must be 8 or 16");
         }
     }
     if (kern == SPX_KERNEL_CSR_MERGE) {
@@ -919,13 +1342,17 @@ int dispatch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const E
 template <class T>
 int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
 {
+    // param: 8 / 16 = nonzeros per lane of the warp-independent split kernel (default 8);
+    // 104 / 108 / 116 = tiled segmented reduction with 4 / 8 / 16 items per thread
     int p = A->kernel == SPX_KERNEL_COO ? A->kparam : 0;
     if (p <= 0) p = 8;
     switch (p) {
-    case 4: return launch_coo<T, 4>(ctx, A, cval, x, e, add);
-    case 8: return launch_coo<T, 8>(ctx, A, cval, x, e, add);
-    case 16: return launch_coo<T, 16>(ctx, A, cval, x, e, add);
-    default: return fail(SPX_ERR_INVALID, "COO items per thread must be 4, 8 or 16");
+    case 8: return launch_coo_split<T, 8>(ctx, A, cval, x, e, add);
+    case 16: return launch_coo_split<T, 16>(ctx, A, cval, x, e, add);
+    case 104: return launch_coo<T, 4>(ctx, A, cval, x, e, add);
+    case 108: return launch_coo<T, 8>(ctx, A, cval, x, e, add);
+    case 116: return launch_coo<T, 16>(ctx, A, cval, x, e, add);
+    default: return fail(SPX_ERR_INVALID, "COO kernel parameter must be 8, 16 (split) or 104, 108, 116 (tiled)");
     }
 }
 

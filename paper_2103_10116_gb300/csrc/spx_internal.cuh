@@ -100,6 +100,9 @@ struct spx_matrix {
     int64_t tiles_items = 0;  // items per tile the map was built for
     int64_t ntiles = 0;
     int64_t nsplit = 0;       // boundaries that split a row (need the look-back)
+    // row hints of the nnz-split CSR kernel (row holding nonzero g * hint_ipt)
+    spx::DBuf hint;
+    int hint_ipt = 0;
     // COO tile map (COO format / HYB COO part)
     spx::DBuf coo_tiles;      // int per tile boundary
     int64_t coo_tiles_items = 0, coo_ntiles = 0, coo_nsplit = 0;

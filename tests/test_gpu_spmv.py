@@ -67,8 +67,9 @@ VARIANTS = [
     ("csr", None, 0),
     ("csr", "vector", 1), ("csr", "vector", 4), ("csr", "vector", 32),
     ("csr", "merge", 4), ("csr", "merge", 8), ("csr", "merge", 16),
+    ("csr", "split", 8), ("csr", "split", 16),
     ("ell", None, 0), ("ell", "ell", 1),
-    ("coo", None, 0), ("coo", "coo", 4), ("coo", "coo", 16),
+    ("coo", None, 0), ("coo", "coo", 16), ("coo", "coo", 104), ("coo", "coo", 116),
     ("hyb", None, 0), ("hyb0", None, 0), ("hyb3", None, 0),
 ]
 
@@ -99,6 +100,7 @@ def _make(spx, ctx, fmt, rp, col, val, ncols, dtype, flags=0):
 
 def _kernel_code(spx, kname):
     return {None: spx.SPX_KERNEL_AUTO, "vector": spx.SPX_KERNEL_CSR_VECTOR, "merge": spx.SPX_KERNEL_CSR_MERGE,
+            "split": spx.SPX_KERNEL_CSR_SPLIT,
             "ell": spx.SPX_KERNEL_ELL, "coo": spx.SPX_KERNEL_COO}[kname]
 
 
