@@ -31,6 +31,7 @@ namespace spx {
 constexpr int kVB = 256;        // block of the vector kernels
 constexpr int kGmKmax = 32;     // largest GMRES restart length (basis held in registers per row)
 constexpr int kMaxRestarts = 3;
+constexpr int64_t kGraphMinRows = 50000;  // smaller solves launch directly (no graph capture)
 
 // ------------------------------------------------------------------ GMRES state
 template <class T> struct GState {
@@ -235,52 +236,61 @@ __global__ void __launch_bounds__(kVB)
 // V[j+1], then CGS2: h1 = V_j^T w; w -= V_j h1; h2 = V_j^T w; w -= V_j h2;
 // h = h1 + h2; H(j+1, j) = ||w||; v_{j+1} = w / ||w||.
 
-// Multi-dot h1[k] = v_k . w, k = 0..j (j < kGmKmax); last block finishes.
+// Multi-dot hout[k] = v_k . w, k = 0..j (j < kGmKmax).  Blocks take chunks of
+// kGmRows rows (grid-stride, fixed grid); w's chunk is staged in shared
+// memory; warp wp owns vectors k = wp, wp+8, wp+16, wp+24 (four independent
+// FMA chains, rows coalesced).  Block partials [k][block] are summed by the
+// last block in block order (deterministic).
+constexpr int kGmRows = 1024;
+
 template <class T>
 __global__ void __launch_bounds__(kVB)
-    k_gm_proj(int64_t n, int64_t ld, const T *__restrict__ V, int j, GState<T> *gs, T *hout, T *partials,
+    k_gm_dots(int64_t n, int64_t ld, const T *__restrict__ V, int j, const GState<T> *gs, T *hout, T *partials,
               unsigned *ticket)
 {
     if (gs->skip) return;
     const T *w = V + (int64_t)(j + 1) * ld;
-    T acc[kGmKmax];
-#pragma unroll
-    for (int k = 0; k < kGmKmax; ++k) acc[k] = T(0);
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        const T wi = w[i];
-#pragma unroll
-        for (int k = 0; k < kGmKmax; ++k)
-            if (k <= j) acc[k] = fma(V[(int64_t)k * ld + i], wi, acc[k]);
-    }
-    __shared__ T sred[kVB / 32][kGmKmax];
+    __shared__ T ws[kGmRows];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int64_t r0 = (int64_t)blockIdx.x * kGmRows; r0 < n; r0 += (int64_t)gridDim.x * kGmRows) {
+        const int nr = (int)min((int64_t)kGmRows, n - r0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nr; i += kVB) ws[i] = w[r0 + i];
+        __syncthreads();
+        for (int i = lane; i < nr; i += 32) {
+            const T wi = ws[i];
 #pragma unroll
-    for (int k = 0; k < kGmKmax; ++k)
-        if (k <= j) {
-            const T s = warp_sum(acc[k]);
-            if (lane == 0) sred[wp][k] = s;
+            for (int q = 0; q < 4; ++q) {
+                const int k = wp + 8 * q;
+                if (k <= j) acc[q] = fma(V[(int64_t)k * ld + r0 + i], wi, acc[q]);
+            }
         }
-    __syncthreads();
-    if (threadIdx.x <= j) {
-        T s = T(0);
-        for (int q = 0; q < kVB / 32; ++q) s += sred[q][threadIdx.x];
-        partials[(int64_t)blockIdx.x * kGmKmax + threadIdx.x] = s;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = wp + 8 * q;
+        const T s = warp_sum(acc[q]);
+        if (lane == 0 && k <= j) partials[(int64_t)k * gridDim.x + blockIdx.x] = s;
     }
     if (!last_block(ticket, gridDim.x)) return;
-    if (threadIdx.x <= j) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = wp + 8 * q;
+        if (k > j) continue;
         T s = T(0);
-        for (unsigned b = 0; b < gridDim.x; ++b) s += ldcg(partials + (int64_t)b * kGmKmax + threadIdx.x);
-        hout[threadIdx.x] = s;
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += ldcg(partials + (int64_t)k * gridDim.x + b);
+        s = warp_sum(s);
+        if (lane == 0) hout[k] = s;
     }
 }
 
-// w -= V_j hin; PASS 1 also forms h2 = V_j^T w (new w); PASS 2 forms ||w||^2
-// and the last block updates the Hessenberg column, the Givens rotations and
-// the residual estimate.
+// w -= V_j hin (thread per row).  PASS 2 also forms ||w||^2; its last block
+// updates the Hessenberg column, the Givens rotations and the estimate.
 template <class T, int PASS>
 __global__ void __launch_bounds__(kVB)
-    k_gm_orth(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, T *partials,
-              unsigned *ticket)
+    k_gm_upd(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, T *partials,
+             unsigned *ticket)
 {
     if (gs->skip) return;
     T *w = V + (int64_t)(j + 1) * ld;
@@ -288,52 +298,14 @@ __global__ void __launch_bounds__(kVB)
     __shared__ T hs[kGmKmax];
     if (threadIdx.x < kGmKmax) hs[threadIdx.x] = threadIdx.x <= j ? ldcg(hin + threadIdx.x) : T(0);
     __syncthreads();
-    T acc[kGmKmax];
-#pragma unroll
-    for (int k = 0; k < kGmKmax; ++k) acc[k] = T(0);
     T ww = T(0);
     for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        T vk[kGmKmax];
         T wi = w[i];
-#pragma unroll
-        for (int k = 0; k < kGmKmax; ++k)
-            if (k <= j) {
-                vk[k] = V[(int64_t)k * ld + i];
-                wi = fma(-hs[k], vk[k], wi);
-            }
+        for (int k = 0; k <= j; ++k) wi = fma(-hs[k], V[(int64_t)k * ld + i], wi);
         w[i] = wi;
-        if (PASS == 1) {
-#pragma unroll
-            for (int k = 0; k < kGmKmax; ++k)
-                if (k <= j) acc[k] = fma(vk[k], wi, acc[k]);
-        } else {
-            ww = fma(wi, wi, ww);
-        }
+        if (PASS == 2) ww = fma(wi, wi, ww);
     }
-    __shared__ T sred[kVB / 32][kGmKmax];
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    if (PASS == 1) {
-#pragma unroll
-        for (int k = 0; k < kGmKmax; ++k)
-            if (k <= j) {
-                const T s = warp_sum(acc[k]);
-                if (lane == 0) sred[wp][k] = s;
-            }
-        __syncthreads();
-        if (threadIdx.x <= j) {
-            T s = T(0);
-            for (int q = 0; q < kVB / 32; ++q) s += sred[q][threadIdx.x];
-            partials[(int64_t)blockIdx.x * kGmKmax + threadIdx.x] = s;
-        }
-        if (!last_block(ticket, gridDim.x)) return;
-        if (threadIdx.x <= j) {
-            T s = T(0);
-            for (unsigned b = 0; b < gridDim.x; ++b) s += ldcg(partials + (int64_t)b * kGmKmax + threadIdx.x);
-            sm.h2[threadIdx.x] = s;
-        }
-        return;
-    }
-    // PASS 2: ||w||^2, then the scalar work of step j in one thread
+    if (PASS == 1) return;
     __shared__ T red[kVB / 32];
     const T bsum = block_sum<T, kVB>(ww, red);
     if (threadIdx.x == 0) partials[blockIdx.x] = bsum;
@@ -678,7 +650,9 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
     KState<T> *h = static_cast<KState<T> *>(w->host);
     int restarts = 0;
     const int chunk = fixed > 0 ? 64 : (n < 200000 ? 32 : 16);
-    const bool graphs = true;
+    // capturing a graph costs about a millisecond: worth it when a large system
+    // replays the chunk many times, not for small one-off solves
+    const bool graphs = n >= kGraphMinRows;
     for (;;) {
         SPX_TRY(krylov_init(R));
         SPX_TRY(read_state<T>(ctx, w, sizeof(KState<T>)));
@@ -767,6 +741,10 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
     hs.status = SPX_MAX_ITER;
     SPX_CUDA(cudaMemcpyAsync(gs, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
     const int g = vgrid(ctx, n, 2);
+    int gd = (int)ceil_div(n, kGmRows);  // multi-dot: persistent grid, at most 2 blocks per SM
+    if (gd > 2 * ctx->sm_count) gd = 2 * ctx->sm_count;
+    if (gd < 1) gd = 1;
+    const int gu = vgrid(ctx, n, 8);
     auto cycle = [&]() -> int {
         // restart: V[0] = b - A x, r.r
         Epi<T> e;
@@ -783,9 +761,10 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
             Epi<T> ea = epi_plain(V + (int64_t)(j + 1) * ld);
             ea.skip = &gs->skip;
             SPX_TRY(spmv_launch<T>(ctx, A, V + (int64_t)j * ld, ea, use32));
-            k_gm_proj<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk);
-            k_gm_orth<T, 1><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
-            k_gm_orth<T, 2><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
+            k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk);
+            k_gm_upd<T, 1><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
+            k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h2, part, tk);
+            k_gm_upd<T, 2><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
             k_gm_scale<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm);
         }
         k_gm_solve<T><<<1, 32, 0, ctx->stream>>>(gs, sm);
@@ -798,7 +777,7 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
     for (;;) {
         const uint64_t key[8] = {(uint64_t)SPX_GMRES, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
                                  (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T), (uint64_t)(uintptr_t)A, 1};
-        SPX_TRY(run_chunk(ctx, w, key, true, cycle));
+        SPX_TRY(run_chunk(ctx, w, key, n >= kGraphMinRows, cycle));
         SPX_TRY(read_state<T>(ctx, w, sizeof(GState<T>)));
         ++cycles;
         if (h->done) break;
