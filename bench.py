@@ -148,10 +148,11 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def build_workload():
+def build_workload(only: str = ""):
+    """The two sweep matrices (only those an --only filter can match)."""
     from paper_2103_10116_gb300 import synth
-    mats = {"stencil27_100": synth.stencil3d_27pt(100), "powerlaw_2m": synth.powerlaw(2_000_000)}
-    return mats
+    gens = {"stencil27_100": lambda: synth.stencil3d_27pt(100), "powerlaw_2m": lambda: synth.powerlaw(2_000_000)}
+    return {k: f() for k, f in gens.items() if not only or k in only or "/" not in only and only in k}
 
 
 def run_gpu(args):
@@ -171,7 +172,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     ctx = spx.spx_ctx_create(local, stream)
 
-    mats = build_workload()
+    mats = build_workload(args.only)
     entries = []  # (name, fmt, V, handle, x, y, bytes, launches, x_host, y_host)
     rejected = []
     for mname, (rp, col, val) in mats.items():
@@ -185,6 +186,8 @@ def run_gpu(args):
             vv = val_d.to(tdt)
             x = xs.to(tdt)
             for fmt in ("csr", "ell", "coo", "hyb"):
+                if args.only and args.only not in f"{mname}/{fmt}/{'f64' if V == 8 else 'f32'}":
+                    continue
                 try:
                     with torch.cuda.stream(stream):
                         A = spx.spx_matrix_create(ctx, fmt, rp_d, col_d, vv)
@@ -540,6 +543,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--only", default="", help="run only sweep entries whose name contains this, "
+                                                 "e.g. stencil27_100/ell/f64 (for profiling)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="0 disables the serving run")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "spx":

@@ -389,6 +389,55 @@ __global__ void k_merge_tiles(int n, int nnz, const int *__restrict__ rp, int64_
     tiles[t] = make_int2(i, j);
 }
 
+// Partial sums of the lanes before a lane that completes a row (the lanes that
+// carried the same row), plus the chunk carry when that run reaches lane 0.
+// Called by all 32 lanes.  Short chains are walked by the lanes that need
+// them; if any chain in the warp is long (a row over many lanes), all lanes
+// run one segmented scan in lockstep instead, so the FP64 adds stay full-warp.
+template <class T>
+__device__ __forceinline__ T chain_total(bool has_pend, int rstart, T pend, const int *cr, const T *cv, int lane,
+                                         int run_row, T run_val)
+{
+    const bool longchain = has_pend && lane >= 4 && cr[lane - 1] == rstart && cr[lane - 2] == rstart &&
+                           cr[lane - 3] == rstart && cr[lane - 4] == rstart;
+    if (!__any_sync(0xffffffffu, longchain)) {
+        if (!has_pend) return T(0);
+        T tot = pend;
+        int k = lane - 1;
+        while (k >= 0 && (cr[k] == rstart || cr[k] == kEmpty)) {
+            if (cr[k] == rstart) tot += cv[k];
+            --k;
+        }
+        if (k < 0 && rstart == run_row) tot += run_val;
+        return tot;
+    }
+    const int key = cr[lane];
+    T sv = key >= 0 ? cv[lane] : T(0);
+    int hd = (lane == 0 || cr[lane - 1] != key) ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {  // segmented inclusive scan by key
+        const T vu = __shfl_up_sync(0xffffffffu, sv, d);
+        const int hu = __shfl_up_sync(0xffffffffu, hd, d);
+        if (lane >= d) {
+            if (!hd) sv += vu;
+            hd |= hu;
+        }
+    }
+    const T prev = __shfl_up_sync(0xffffffffu, sv, 1);
+    const unsigned meq = __match_any_sync(0xffffffffu, key);
+    const unsigned prevmask = __shfl_up_sync(0xffffffffu, meq, 1);
+    if (!has_pend) return T(0);
+    T tot = pend;
+    if (lane > 0 && cr[lane - 1] == rstart) {
+        tot += prev;
+        const unsigned below = (1u << lane) - 1u;
+        if ((prevmask & below) == below && rstart == run_row) tot += run_val;
+    } else if (lane == 0 && rstart == run_row) {
+        tot += run_val;
+    }
+    return tot;
+}
+
 // ------------------------------------------------------------------ nnz-split CSR (warp-independent)
 // Every lane of a persistent warp takes a granule of IPT consecutive nonzeros
 // (loads fully independent of any search: coalesced across the warp) and
@@ -476,16 +525,16 @@ __global__ void __launch_bounds__(256)
                 }
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
-                    if (kk + u < cnt) {
-                        const int j = (int)a + kk + u;
-                        while (j >= re) {
+                    const int j = (int)a + kk + u;
+                    if (kk + u < cnt && j >= re) {  // divergent, but free of FP64 work
+                        do {
                             SPX_SPLIT_EMIT(r, sum);
                             sum = T(0);
                             ++r;
                             re = r < n ? rp[r + 1] : INT_MAX;
-                        }
-                        sum = fma(v[u], xv[u], sum);
+                        } while (j >= re);
                     }
+                    sum = fma(v[u], xv[u], sum);  // unused slots hold zeros: uniform across the warp
                 }
             }
             while (r < n && re <= b) {  // rows ending exactly at b (and empty rows there)
@@ -501,14 +550,8 @@ __global__ void __launch_bounds__(256)
         s_cv[wib][lane] = sum;
         __syncwarp();
         // complete a row that began in earlier lanes (and maybe earlier chunks)
+        const T tot = chain_total<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val);
         if (has_pend) {
-            T tot = pend;
-            int k = lane - 1;
-            while (k >= 0 && (s_cr[wib][k] == rstart || s_cr[wib][k] == kEmpty)) {
-                if (s_cr[wib][k] == rstart) tot += s_cv[wib][k];
-                --k;
-            }
-            if (k < 0 && rstart == run_row) tot += run_val;
             if (range_inside && rstart == first_row) {
                 first_val = tot;  // finished last, after the look-back
                 first_ready = true;
@@ -517,19 +560,20 @@ __global__ void __launch_bounds__(256)
             }
         }
         // carry to the next chunk: the row still open at the end of lane 31
-        int nrow = -1;
+        // carry to the next chunk: the row still open at lane 31.  Its lanes form
+        // the suffix of the warp; sum them in lockstep (fixed shuffle tree).
+        const int nrow = s_cr[wib][31] >= 0 ? s_cr[wib][31] : -1;
         T nval = T(0);
-        if (lane == 31 && s_cr[wib][31] >= 0) {
-            nrow = s_cr[wib][31];
-            int k = 31;
-            while (k >= 0 && (s_cr[wib][k] == nrow || s_cr[wib][k] == kEmpty)) {
-                if (s_cr[wib][k] == nrow) nval += s_cv[wib][k];
-                --k;
-            }
-            if (k < 0 && nrow == run_row) nval += run_val;
+        if (nrow >= 0) {
+            const int mine = s_cr[wib][lane];
+            const unsigned in_row = __ballot_sync(0xffffffffu, mine == nrow || mine == kEmpty);
+            const int len = __clz(~in_row);  // leading ones: lanes 31 .. 32-len
+            const bool take = lane >= 32 - len && mine == nrow;
+            nval = warp_sum(take ? s_cv[wib][lane] : T(0));
+            if (len == 32 && nrow == run_row) nval += run_val;
         }
-        run_row = __shfl_sync(0xffffffffu, nrow, 31);
-        run_val = __shfl_sync(0xffffffffu, nval, 31);
+        run_row = nrow;
+        run_val = nval;
         // the lane that finished the deferred first row passes it to lane 0
         const unsigned fm = __ballot_sync(0xffffffffu, first_ready);
         if (fm) {
@@ -648,16 +692,14 @@ __global__ void __launch_bounds__(256)
                 }
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
-                    if (kk + u < cnt) {
-                        if (rr[u] != r) {
-                            SPX_COO_EMIT(r, sum);
-                            if (!add_mode)
-                                for (int q = r + 1; q < rr[u]; ++q) final_write(e, q, T(0), d0, d1);
-                            r = rr[u];
-                            sum = T(0);
-                        }
-                        sum = fma(v[u], xv[u], sum);
+                    if (kk + u < cnt && rr[u] != r) {  // divergent, but free of FP64 work
+                        SPX_COO_EMIT(r, sum);
+                        if (!add_mode)
+                            for (int q = r + 1; q < rr[u]; ++q) final_write(e, q, T(0), d0, d1);
+                        r = rr[u];
+                        sum = T(0);
                     }
+                    sum = fma(v[u], xv[u], sum);  // unused slots hold zeros: uniform across the warp
                 }
             }
             const int nr = b < nnz ? crow[b] : n;
@@ -674,14 +716,8 @@ __global__ void __launch_bounds__(256)
         s_cr[wib][lane] = cr;
         s_cv[wib][lane] = sum;
         __syncwarp();
+        const T tot = chain_total<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val);
         if (has_pend) {
-            T tot = pend;
-            int k = lane - 1;
-            while (k >= 0 && (s_cr[wib][k] == rstart || s_cr[wib][k] == kEmpty)) {
-                if (s_cr[wib][k] == rstart) tot += s_cv[wib][k];
-                --k;
-            }
-            if (k < 0 && rstart == run_row) tot += run_val;
             if (range_inside && rstart == first_row) {
                 first_val = tot;
                 first_ready = true;
@@ -689,19 +725,20 @@ __global__ void __launch_bounds__(256)
                 SPX_COO_OUT(rstart, tot);
             }
         }
-        int nrow = -1;
+        // carry to the next chunk: the row still open at lane 31.  Its lanes form
+        // the suffix of the warp; sum them in lockstep (fixed shuffle tree).
+        const int nrow = s_cr[wib][31] >= 0 ? s_cr[wib][31] : -1;
         T nval = T(0);
-        if (lane == 31 && s_cr[wib][31] >= 0) {
-            nrow = s_cr[wib][31];
-            int k = 31;
-            while (k >= 0 && (s_cr[wib][k] == nrow || s_cr[wib][k] == kEmpty)) {
-                if (s_cr[wib][k] == nrow) nval += s_cv[wib][k];
-                --k;
-            }
-            if (k < 0 && nrow == run_row) nval += run_val;
+        if (nrow >= 0) {
+            const int mine = s_cr[wib][lane];
+            const unsigned in_row = __ballot_sync(0xffffffffu, mine == nrow || mine == kEmpty);
+            const int len = __clz(~in_row);  // leading ones: lanes 31 .. 32-len
+            const bool take = lane >= 32 - len && mine == nrow;
+            nval = warp_sum(take ? s_cv[wib][lane] : T(0));
+            if (len == 32 && nrow == run_row) nval += run_val;
         }
-        run_row = __shfl_sync(0xffffffffu, nrow, 31);
-        run_val = __shfl_sync(0xffffffffu, nval, 31);
+        run_row = nrow;
+        run_val = nval;
         const unsigned fm = __ballot_sync(0xffffffffu, first_ready);
         if (fm) {
             const int src = __ffs(fm) - 1;
@@ -767,6 +804,7 @@ __global__ void __launch_bounds__(BLOCK)
     if (e.skip && *e.skip) return;
     using VV = typename Vec<T, R>::V;
     using VI = typename Vec<T, R>::I;
+    constexpr int U = 4;  // slabs whose loads are issued together
     T d0 = T(0), d1 = T(0);
     const int64_t ngroups = (n + R - 1) / R;
     for (int64_t g = blockIdx.x * (int64_t)BLOCK + threadIdx.x; g < ngroups;
@@ -775,8 +813,37 @@ __global__ void __launch_bounds__(BLOCK)
         T s[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) s[q] = T(0);
-#pragma unroll 4
-        for (int j = 0; j < w; ++j) {
+        int j = 0;
+        for (; j + U <= w; j += U) {
+            VI c[U];
+            VV v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t o = (int64_t)(j + u) * ld + i;
+                c[u] = __ldg(reinterpret_cast<const VI *>(ecol + o));
+                v[u] = __ldg(reinterpret_cast<const VV *>(eval + o));
+            }
+            T xg[U][R];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int *cc = reinterpret_cast<const int *>(&c[u]);
+#pragma unroll
+                for (int q = 0; q < R; ++q) xg[u][q] = cc[q] >= 0 ? __ldg(x + cc[q]) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const T *vv = reinterpret_cast<const T *>(&v[u]);
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    if constexpr (sizeof(T) == 8) {  // FP64 pipe is scarce: skip padding slots
+                        if (reinterpret_cast<const int *>(&c[u])[q] >= 0) s[q] = fma(vv[q], xg[u][q], s[q]);
+                    } else {
+                        s[q] = fma(vv[q], xg[u][q], s[q]);  // padding multiplies 0 * 0
+                    }
+                }
+            }
+        }
+        for (; j < w; ++j) {
             const int64_t o = (int64_t)j * ld + i;
             const VI c = __ldg(reinterpret_cast<const VI *>(ecol + o));
             const VV v = __ldg(reinterpret_cast<const VV *>(eval + o));
