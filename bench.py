@@ -155,6 +155,24 @@ def build_workload(only: str = ""):
     return {k: f() for k, f in gens.items() if not only or k in only or "/" not in only and only in k}
 
 
+def max_over_ranks(elapsed_ms: float, dist=None, device=None) -> float:
+    """The job's time is the slowest replica's: all-reduce MAX, then a barrier.
+    Replicas share no data; this is the only collective and it sits outside the
+    timed region."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(elapsed_ms)
+    import torch
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(bytes_per_step: int, steps: int, world: int, elapsed_ms: float) -> float:
+    """Whole-job GB/s: every replica moves bytes_per_step per step."""
+    return bytes_per_step * steps * world / (elapsed_ms * 1e-3) / 1e9
+
+
 def run_gpu(args):
     import torch
     from paper_2103_10116_gb300 import spx
@@ -233,16 +251,11 @@ def run_gpu(args):
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    elapsed_ms = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-        dist.barrier()
+    elapsed_ms = max_over_ranks(t0.elapsed_time(t1), dist, dev)
     per_entry_ms = [statistics.mean(evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps))
                     for i in range(len(entries))]
     bytes_step = sum(e["bytes"] for e in entries)
-    value = bytes_step * args.steps * world / (elapsed_ms * 1e-3) / 1e9
+    value = job_value(bytes_step, args.steps, world, elapsed_ms)
 
     # end to end through the public API with host buffers (copies inside the timed region)
     for e in entries:
