@@ -84,17 +84,23 @@ KERNEL_SOURCES = ["paper_2103_10116_gb300/csrc/spmv.cu", "paper_2103_10116_gb300
 
 
 def _traffic(key: str):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel source
-    has not changed since it was taken; else None."""
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+    the committed ncu summary table profiles/dram_traffic.md, if the kernel
+    source has not changed since the capture; else None."""
     try:
-        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
-            t = json.load(f)
-    except Exception:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.md")) as f:
+            lines = f.read().splitlines()
+    except OSError:
         return None
-    e = t.get(key)
-    if not e or e.get("source_sha") != _src_hash(KERNEL_SOURCES):
-        return None
-    return e.get("dram_bytes_per_launch")
+    for ln in lines:
+        cells = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == key:
+            try:
+                nbytes = int(cells[1].replace(",", ""))
+            except ValueError:
+                return None
+            return nbytes if cells[2] == _src_hash(KERNEL_SOURCES) else None
+    return None
 
 
 class Clocks:
@@ -446,12 +452,37 @@ def batched_secondary(spx, ctx, stream, dev, plain_sample=32):
     return out
 
 
-def serving_secondary(spx, ctx, seconds: float = 10.0, rate: float = 2000.0, slots: int = 16, pool: int = 12):
+def plain_serial_f64(spx, ctx, reqs, kinds, tol, budget_s=8.0, max_count=400):
+    """The plain per-system FP64 path on the first requests of the trace, one
+    at a time: upload the operator (host CSR), solve in FP64, read x back."""
+    import torch
+    t0 = time.perf_counter()
+    done = 0
+    for i, (rp, col, val, b) in enumerate(reqs[:max_count]):
+        A = spx.spx_matrix_create(ctx, "csr", torch.from_numpy(rp), torch.from_numpy(col), torch.from_numpy(val))
+        try:
+            bd = torch.from_numpy(b).cuda()
+            xd = torch.zeros_like(bd)
+            spx.spx_solve(ctx, A, bd, xd, solver=kinds[i], tol=tol, max_iter=100000, precision="f64")
+            xd.cpu()
+        finally:
+            spx.spx_matrix_destroy(A)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"sample_requests": done, "sample_s": round(el, 2), "solves_per_s": round(done / el, 1)}
+
+
+def serving_secondary(spx, ctx, seconds: float = 10.0, rate: float = 2000.0, slots: int = 16, pool: int = 12,
+                      batch_rows=None, plain=True):
     """Poisson arrivals (rate req/s for `seconds`), sizes log-uniform in
     [1e3, 1e6] rows drawn from a pool of `pool` log-spaced sizes per family,
     50/50 3D 7-point stencils (CG) and diagonally dominant random rows with
     8-32 nonzeros (BiCGSTAB), tolerance 1e-8, FP32 inner + FP64 refinement,
-    admission by device footprint (90% of free memory)."""
+    admission by device footprint (90% of free memory).  Small requests are
+    batched by the server's batch lanes (batch_rows: their size limit, None =
+    the server default, 0 = every request on its own slot)."""
     from paper_2103_10116_gb300 import synth
     from paper_2103_10116_gb300.serving import Server, latency_stats, poisson_trace, replay
     rng = np.random.default_rng(5)
@@ -474,8 +505,9 @@ def serving_secondary(spx, ctx, seconds: float = 10.0, rate: float = 2000.0, slo
             kinds.append("bicgstab")
         b = np.random.default_rng(i).uniform(-1, 1, rp.shape[0] - 1)
         reqs.append((rp, col, val, b))
-    srv = Server(ctx, 0, max_slots=slots)
+    srv = Server(ctx, 0, max_slots=slots, batch_rows=batch_rows)
     try:
+        eff_rows = spx.spx_server_set_batching(srv.h, -1)
         wall, ids = replay(srv, trace, reqs, lambda i: kinds[i], tol=1e-8, precision="mixed")
         res = [srv.results[i] for i in ids]
     finally:
@@ -485,7 +517,12 @@ def serving_secondary(spx, ctx, seconds: float = 10.0, rate: float = 2000.0, slo
     busy = sum(r["done_ms"] - r["admit_ms"] for r in res) / 1e3
     st.update({"requests": len(res), "converged": conv, "arrival_rate_per_s": rate, "window_s": seconds,
                "wall_s": round(wall, 2), "solves_per_s": round(len(res) / wall, 1), "slots": slots,
-               "slot_busy_s": round(busy, 2), "pool_sizes_per_family": int(len(ks))})
+               "slot_busy_s": round(busy, 2), "pool_sizes_per_family": int(len(ks)), "batch_rows": int(eff_rows),
+               "batched_requests": int(sum(1 for i in range(len(reqs)) if reqs[i][0].shape[0] - 1 <= eff_rows
+                                           and kinds[i] in ("cg", "bicgstab")))})
+    if plain:
+        st["plain_per_system_f64"] = plain_serial_f64(spx, ctx, reqs, kinds, 1e-8)
+        st["speedup_vs_plain_f64"] = round(st["solves_per_s"] / st["plain_per_system_f64"]["solves_per_s"], 2)
     return st
 
 

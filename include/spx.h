@@ -72,7 +72,7 @@ typedef enum {
     SPX_KERNEL_CSR_VECTOR = 1,  /* CSR: one sub-warp of `param` lanes (1..32, power of 2) per row */
     SPX_KERNEL_CSR_MERGE = 2,   /* CSR: merge-path split of rows + nonzeros, TMA-staged tiles */
     SPX_KERNEL_ELL = 3,         /* ELL / HYB ELL part: one thread per `param` rows (1, 2 or 4) */
-    SPX_KERNEL_COO = 4,         /* COO / HYB COO part: 8/16 = warp-independent split (default 8),
+    SPX_KERNEL_COO = 4,         /* COO / HYB COO part: 8/16 = warp-independent split (default 16 FP64, 8 FP32),
                                    104/108/116 = tiled segmented reduction with 4/8/16 items per thread */
     SPX_KERNEL_CSR_SPLIT = 5    /* CSR: each lane takes `param` (8 or 16) consecutive nonzeros, warps independent */
 } spx_kernel;
@@ -247,7 +247,12 @@ int spx_solve_fixed(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int sol
  * row_ptr holds, for system s, its LOCAL row pointer (n_s + 1 entries,
  * starting at 0) at row_ptr[row_off[s] + s]; col_idx (local column indices)
  * and values (dtype) hold system s at [nnz_off[s], nnz_off[s+1]).
- * Device pointers, copied into the handle.  Errors: SPX_ERR_INVALID, SPX_ERR_OOM. */
+ * Device pointers (host pointers with flags SPX_HOST_INPUT), copied into the
+ * handle; SPX_MIXED_SHADOW also keeps FP32 values for SPX_PREC_MIXED.  A
+ * system's vector is held in shared memory by the kernel, so the largest
+ * system may have about 28 000 rows (227 KB / 8 B); larger ones fail in
+ * spx_batch_solve with SPX_ERR_TOO_LARGE.
+ * Errors: SPX_ERR_INVALID, SPX_ERR_TOO_LARGE, SPX_ERR_OOM. */
 int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_t nsys, const int64_t *row_off,
                      const int64_t *nnz_off, const int32_t *row_ptr, const int32_t *col_idx,
                      const void *values, unsigned flags);
@@ -270,10 +275,16 @@ int spx_batch_tune(spx_ctx *ctx, spx_batch *B, int solver, int precision, int *c
 
 /* A continuous-batching solve server on ctx's device.  budget_bytes caps the
  * device memory of the requests running at once (<= 0: 90% of the free
- * memory at creation); max_slots is the number of requests that may run
- * concurrently, each on its own stream (1..64).  The server owns worker
- * threads and their contexts (allocating with cudaMallocAsync); ctx is only
- * used to pick the device.  Errors: SPX_ERR_INVALID, SPX_ERR_CUDA. */
+ * memory at creation); max_slots is the number of large requests that may
+ * run concurrently, each on its own stream (1..64).  Small CG / BiCGSTAB
+ * requests (FP64 or MIXED, at most 24 576 rows by default, see
+ * spx_server_set_batching) are instead gathered by four batch lanes: each
+ * lane solves every queued small request of one kind (same solver, tol,
+ * max_iter, precision and size class) in one launch of the batched kernel,
+ * and the lanes run concurrently with each other and with the slots.  The
+ * server owns worker threads and their contexts (allocating with
+ * cudaMallocAsync); ctx is only used to pick the device.
+ * Errors: SPX_ERR_INVALID, SPX_ERR_CUDA. */
 int spx_server_create(spx_ctx *ctx, spx_server **out, int64_t budget_bytes, int max_slots);
 
 /* Queue one solve A x = b.  row_ptr[n+1], col_idx[nnz], values[nnz] (double),
@@ -300,6 +311,14 @@ typedef struct {
  * waiting up to wait_ms milliseconds if none is ready; *count receives how
  * many were written.  Each completed request is reported once. */
 int spx_server_poll(spx_server *S, spx_server_result *results, int max_results, int wait_ms, int *count);
+
+/* Route requests of at most max_rows rows to the batch lanes from now on
+ * (0: none; capped at what the batched kernel holds, about 28 000 rows;
+ * negative: leave the limit unchanged, only report it).
+ * *effective (may be NULL) receives the limit in force.  A request's result
+ * does not depend on the route of others, but the same request may differ in
+ * the last bits between the two routes (different reduction trees). */
+int spx_server_set_batching(spx_server *S, int64_t max_rows, int64_t *effective);
 
 /* Requests waiting for admission, running, and the device bytes reserved. */
 int spx_server_pending(spx_server *S, int64_t *queued, int64_t *running, int64_t *bytes_in_use);

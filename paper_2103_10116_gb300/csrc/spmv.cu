@@ -47,6 +47,20 @@ __device__ __forceinline__ void final_write(const Epi<T> &e, int64_t r, T t, T &
     if (e.want_yy) d1 = fma(v, v, d1);
 }
 
+// Row output of the nnz-split kernels.  MODE 0: the general epilogue; 1: plain
+// store y = t; 2: y += alpha t (the COO part of HYB); 3: y += t.  Fixing the
+// mode at compile time keeps the unused epilogue terms out of the row-emission
+// code: predicated-off FP64 instructions still take FP64 issue slots, and the
+// FP64 pipe is what bounds these kernels.
+template <int MODE, class T>
+__device__ __forceinline__ void out_row(const Epi<T> &e, int64_t r, T t, T &d0, T &d1)
+{
+    if constexpr (MODE == 0) final_write(e, r, t, d0, d1);
+    else if constexpr (MODE == 1) e.y[r] = t;
+    else if constexpr (MODE == 2) e.y[r] += e.alpha * t;
+    else e.y[r] += t;
+}
+
 // Reduce (d0, d1) over the grid; the last block stores dots and runs the
 // scalar update.  Every block must call it.
 template <class T, int BLOCK>
@@ -389,18 +403,30 @@ __global__ void k_merge_tiles(int n, int nnz, const int *__restrict__ rp, int64_
     tiles[t] = make_int2(i, j);
 }
 
-// Partial sums of the lanes before a lane that completes a row (the lanes that
-// carried the same row), plus the chunk carry when that run reaches lane 0.
-// Called by all 32 lanes.  Short chains are walked by the lanes that need
-// them; if any chain in the warp is long (a row over many lanes), all lanes
-// run one segmented scan in lockstep instead, so the FP64 adds stay full-warp.
+// Cross-lane completion of one warp chunk.  cr[l] / cv[l]: the row lane l
+// left open at its granule end and that partial sum (kNoCarry / kEmpty if
+// none).  Returns, for a lane that ends a row begun in earlier lanes
+// (has_pend, row rstart, own part pend), the row's total: its own part, the
+// parts of the earlier lanes of the same row, and the chunk carry (run_row,
+// run_val) if the row reaches back to lane 0.  Also forms the new chunk carry:
+// the row still open at lane 31 (nrow, -1 if none) and its partial (nval).
+// Called by all 32 lanes.  When some chain is long, or the carried row spans
+// more than one lane, one segmented scan in lockstep (5 steps, full-warp FP64
+// adds) gives both; otherwise the short chains are walked directly and the
+// carry is lane 31's own partial.
 template <class T>
-__device__ __forceinline__ T chain_total(bool has_pend, int rstart, T pend, const int *cr, const T *cv, int lane,
-                                         int run_row, T run_val)
+__device__ __forceinline__ T chunk_combine(bool has_pend, int rstart, T pend, const int *cr, const T *cv, int lane,
+                                           int run_row, T run_val, int &nrow, T &nval)
 {
+    const int key = cr[lane];
+    nrow = cr[31] >= 0 ? cr[31] : -1;
+    const unsigned in_row = __ballot_sync(0xffffffffu, nrow >= 0 && key == nrow);
+    const int len = __clz(~in_row);  // lanes 31 .. 32-len carry row nrow
     const bool longchain = has_pend && lane >= 4 && cr[lane - 1] == rstart && cr[lane - 2] == rstart &&
                            cr[lane - 3] == rstart && cr[lane - 4] == rstart;
-    if (!__any_sync(0xffffffffu, longchain)) {
+    if (!__any_sync(0xffffffffu, longchain) && len <= 1) {
+        nval = T(0);
+        if (nrow >= 0) nval = cv[31];
         if (!has_pend) return T(0);
         T tot = pend;
         int k = lane - 1;
@@ -411,7 +437,6 @@ __device__ __forceinline__ T chain_total(bool has_pend, int rstart, T pend, cons
         if (k < 0 && rstart == run_row) tot += run_val;
         return tot;
     }
-    const int key = cr[lane];
     T sv = key >= 0 ? cv[lane] : T(0);
     int hd = (lane == 0 || cr[lane - 1] != key) ? 1 : 0;
 #pragma unroll
@@ -426,6 +451,9 @@ __device__ __forceinline__ T chain_total(bool has_pend, int rstart, T pend, cons
     const T prev = __shfl_up_sync(0xffffffffu, sv, 1);
     const unsigned meq = __match_any_sync(0xffffffffu, key);
     const unsigned prevmask = __shfl_up_sync(0xffffffffu, meq, 1);
+    nval = __shfl_sync(0xffffffffu, sv, 31);
+    if (nrow < 0) nval = T(0);
+    else if (len == 32 && nrow == run_row) nval += run_val;
     if (!has_pend) return T(0);
     T tot = pend;
     if (lane > 0 && cr[lane - 1] == rstart) {
@@ -453,7 +481,7 @@ __device__ __forceinline__ T chain_total(bool has_pend, int rstart, T pend, cons
 // block-wide barrier is needed until the final dot reduction.
 //   Row ownership: row r ends in the lane whose granule [a, b) has
 //   a < rp[r+1] <= b (rows with rp[r+1] == 0 belong to granule 0).
-template <class T, int IPT>
+template <class T, int IPT, int MODE>
 __global__ void __launch_bounds__(256)
     k_csr_split(int n, int nnz, const int *__restrict__ rp, const int *__restrict__ col,
                 const T *__restrict__ val, const T *__restrict__ x, const int *__restrict__ hint, int nchunks,
@@ -462,10 +490,14 @@ __global__ void __launch_bounds__(256)
 {
     constexpr int CH = 8;
     constexpr int NW = 256 / 32;
+    constexpr int CHUNK = 32 * IPT, PADDED = CHUNK + 32;  // element k sits at k + k / IPT
     if (e.skip && *e.skip) return;
     __shared__ int s_cr[NW][32];
     __shared__ T s_cv[NW][32];
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *sc = reinterpret_cast<int *>(smem_dyn) + wib * PADDED;
+    T *sv = reinterpret_cast<T *>(smem_dyn + (size_t)NW * PADDED * 4) + wib * PADDED;
     const int W = gridDim.x * NW;
     const int w = blockIdx.x * NW + wib;
     const int c_begin = (int)(((int64_t)nchunks * w) / W), c_end = (int)(((int64_t)nchunks * (w + 1)) / W);
@@ -489,6 +521,19 @@ __global__ void __launch_bounds__(256)
         const int64_t a = g * IPT;
         const int b = (int)min(a + IPT, (int64_t)nnz);
         const bool active = a < nnz;
+        {  // coalesced copy of the chunk's columns and values into padded shared memory
+            const int64_t a0 = (int64_t)c * CHUNK;
+            const int cc = (int)min((int64_t)CHUNK, (int64_t)nnz - a0);
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int kq = lane + 32 * q;
+                if (kq < cc) {
+                    sc[kq + kq / IPT] = col[a0 + kq];
+                    sv[kq + kq / IPT] = val[a0 + kq];
+                }
+            }
+            __syncwarp();
+        }
         int r = active ? hint[g] : n;
         int re = r < n ? rp[r + 1] : INT_MAX;
         const bool pend_possible = active && rp[r] < a;
@@ -501,12 +546,12 @@ __global__ void __launch_bounds__(256)
             pend = (s_);                               \
             has_pend = true;                           \
         } else {                                       \
-            final_write(e, (row_), (s_), d0, d1);      \
+            out_row<MODE>(e, (row_), (s_), d0, d1);    \
         }                                              \
         first = false;                                 \
     } while (0)
         if (a == 0 && active)  // rows before the first nonzero have no entries
-            for (int q = 0; q < r; ++q) final_write(e, q, T(0), d0, d1);
+            for (int q = 0; q < r; ++q) out_row<MODE>(e, q, T(0), d0, d1);
         if (active) {
             const int cnt = b - (int)a;
 #pragma unroll
@@ -514,10 +559,9 @@ __global__ void __launch_bounds__(256)
                 T v[CH], xv[CH];
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
-                    const int j = (int)a + kk + u;
                     if (kk + u < cnt) {
-                        v[u] = val[j];
-                        xv[u] = __ldg(x + col[j]);
+                        v[u] = sv[lane * (IPT + 1) + kk + u];
+                        xv[u] = __ldg(x + sc[lane * (IPT + 1) + kk + u]);
                     } else {
                         v[u] = T(0);
                         xv[u] = T(0);
@@ -549,28 +593,19 @@ __global__ void __launch_bounds__(256)
         s_cr[wib][lane] = cr;
         s_cv[wib][lane] = sum;
         __syncwarp();
-        // complete a row that began in earlier lanes (and maybe earlier chunks)
-        const T tot = chain_total<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val);
+        // complete a row that began in earlier lanes (and maybe earlier chunks);
+        // carry the row still open at lane 31 to the next chunk
+        int nrow;
+        T nval;
+        const T tot = chunk_combine<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val, nrow,
+                                       nval);
         if (has_pend) {
             if (range_inside && rstart == first_row) {
                 first_val = tot;  // finished last, after the look-back
                 first_ready = true;
             } else {
-                final_write(e, rstart, tot, d0, d1);
+                out_row<MODE>(e, rstart, tot, d0, d1);
             }
-        }
-        // carry to the next chunk: the row still open at the end of lane 31
-        // carry to the next chunk: the row still open at lane 31.  Its lanes form
-        // the suffix of the warp; sum them in lockstep (fixed shuffle tree).
-        const int nrow = s_cr[wib][31] >= 0 ? s_cr[wib][31] : -1;
-        T nval = T(0);
-        if (nrow >= 0) {
-            const int mine = s_cr[wib][lane];
-            const unsigned in_row = __ballot_sync(0xffffffffu, mine == nrow || mine == kEmpty);
-            const int len = __clz(~in_row);  // leading ones: lanes 31 .. 32-len
-            const bool take = lane >= 32 - len && mine == nrow;
-            nval = warp_sum(take ? s_cv[wib][lane] : T(0));
-            if (len == 32 && nrow == run_row) nval += run_val;
         }
         run_row = nrow;
         run_val = nval;
@@ -601,9 +636,10 @@ __global__ void __launch_bounds__(256)
             flags[wp] = 0;
             if (!(rs < (int64_t)pb * 32 * IPT)) break;  // range wp began at or before the row start
         }
-        final_write(e, first_row, tot, d0, d1);
+        out_row<MODE>(e, first_row, tot, d0, d1);
     }
-    if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
+    if constexpr (MODE == 0)
+        if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
 #undef SPX_SPLIT_EMIT
 }
 
@@ -614,27 +650,29 @@ __global__ void __launch_bounds__(256)
 // between two entries are written (store mode) by the lane that sees the
 // jump.  Carries between lanes, chunks and warp ranges as in k_csr_split.
 // Add mode (the COO part of HYB) adds alpha * sum into y and writes no gaps.
-template <class T, int IPT>
+template <class T, int IPT, int MODE>
 __global__ void __launch_bounds__(256)
     k_coo_split(int n, int nnz, const int *__restrict__ crow, const int *__restrict__ ccol,
                 const T *__restrict__ cval, const T *__restrict__ x, int nchunks, int *carry_row_w,
-                T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e, int add_mode)
+                T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e)
 {
+    constexpr bool add_mode = MODE >= 2;  // y += ..., no rows without entries written
     constexpr int CH = 8;
     constexpr int NW = 256 / 32;
+    constexpr int CHUNK = 32 * IPT, PADDED = CHUNK + 32;  // element k sits at k + k / IPT
     if (e.skip && *e.skip) return;
     __shared__ int s_cr[NW][32];
     __shared__ T s_cv[NW][32];
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *sc = reinterpret_cast<int *>(smem_dyn) + wib * PADDED;
+    int *sr = reinterpret_cast<int *>(smem_dyn) + (NW + wib) * PADDED;
+    T *sv = reinterpret_cast<T *>(smem_dyn + (size_t)2 * NW * PADDED * 4) + wib * PADDED;
     const int W = gridDim.x * NW;
     const int w = blockIdx.x * NW + wib;
     const int c_begin = (int)(((int64_t)nchunks * w) / W), c_end = (int)(((int64_t)nchunks * (w + 1)) / W);
     T d0 = T(0), d1 = T(0);
-#define SPX_COO_OUT(row_, s_)                                                      \
-    do {                                                                           \
-        if (add_mode) e.y[(row_)] += e.alpha * (s_);                               \
-        else final_write(e, (row_), (s_), d0, d1);                                 \
-    } while (0)
+#define SPX_COO_OUT(row_, s_) out_row<MODE>(e, (row_), (s_), d0, d1)
 
     const int64_t range_a = (int64_t)c_begin * 32 * IPT;
     int first_row = -1;
@@ -653,7 +691,21 @@ __global__ void __launch_bounds__(256)
         const int64_t a = g * IPT;
         const int b = (int)min(a + IPT, (int64_t)nnz);
         const bool active = a < nnz;
-        int r = active ? crow[a] : n;
+        {  // coalesced copy of the chunk's rows, columns and values into padded shared memory
+            const int64_t a0 = (int64_t)c * CHUNK;
+            const int cc = (int)min((int64_t)CHUNK, (int64_t)nnz - a0);
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const int kq = lane + 32 * q;
+                if (kq < cc) {
+                    sr[kq + kq / IPT] = crow[a0 + kq];
+                    sc[kq + kq / IPT] = ccol[a0 + kq];
+                    sv[kq + kq / IPT] = cval[a0 + kq];
+                }
+            }
+            __syncwarp();
+        }
+        int r = active ? sr[lane * (IPT + 1)] : n;
         const bool pend_possible = active && a > 0 && crow[a - 1] == r;
         const int rstart = r;
         T sum = T(0), pend = T(0);
@@ -669,7 +721,7 @@ __global__ void __launch_bounds__(256)
         first = false;                                                             \
     } while (0)
         if (a == 0 && active && !add_mode)
-            for (int q = 0; q < r; ++q) final_write(e, q, T(0), d0, d1);  // rows before the first entry
+            for (int q = 0; q < r; ++q) out_row<MODE>(e, q, T(0), d0, d1);  // rows before the first entry
         int cr = kEmpty;
         if (active) {
             const int cnt = b - (int)a;
@@ -679,11 +731,10 @@ __global__ void __launch_bounds__(256)
                 int rr[CH];
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
-                    const int j = (int)a + kk + u;
                     if (kk + u < cnt) {
-                        v[u] = cval[j];
-                        xv[u] = __ldg(x + ccol[j]);
-                        rr[u] = crow[j];
+                        v[u] = sv[lane * (IPT + 1) + kk + u];
+                        xv[u] = __ldg(x + sc[lane * (IPT + 1) + kk + u]);
+                        rr[u] = sr[lane * (IPT + 1) + kk + u];
                     } else {
                         v[u] = T(0);
                         xv[u] = T(0);
@@ -695,7 +746,7 @@ __global__ void __launch_bounds__(256)
                     if (kk + u < cnt && rr[u] != r) {  // divergent, but free of FP64 work
                         SPX_COO_EMIT(r, sum);
                         if (!add_mode)
-                            for (int q = r + 1; q < rr[u]; ++q) final_write(e, q, T(0), d0, d1);
+                            for (int q = r + 1; q < rr[u]; ++q) out_row<MODE>(e, q, T(0), d0, d1);
                         r = rr[u];
                         sum = T(0);
                     }
@@ -708,7 +759,7 @@ __global__ void __launch_bounds__(256)
             } else {
                 SPX_COO_EMIT(r, sum);
                 if (!add_mode)
-                    for (int q = r + 1; q < nr; ++q) final_write(e, q, T(0), d0, d1);
+                    for (int q = r + 1; q < nr; ++q) out_row<MODE>(e, q, T(0), d0, d1);
                 sum = T(0);
                 cr = kNoCarry;
             }
@@ -716,7 +767,10 @@ __global__ void __launch_bounds__(256)
         s_cr[wib][lane] = cr;
         s_cv[wib][lane] = sum;
         __syncwarp();
-        const T tot = chain_total<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val);
+        int nrow;
+        T nval;
+        const T tot = chunk_combine<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val, nrow,
+                                       nval);
         if (has_pend) {
             if (range_inside && rstart == first_row) {
                 first_val = tot;
@@ -724,18 +778,6 @@ __global__ void __launch_bounds__(256)
             } else {
                 SPX_COO_OUT(rstart, tot);
             }
-        }
-        // carry to the next chunk: the row still open at lane 31.  Its lanes form
-        // the suffix of the warp; sum them in lockstep (fixed shuffle tree).
-        const int nrow = s_cr[wib][31] >= 0 ? s_cr[wib][31] : -1;
-        T nval = T(0);
-        if (nrow >= 0) {
-            const int mine = s_cr[wib][lane];
-            const unsigned in_row = __ballot_sync(0xffffffffu, mine == nrow || mine == kEmpty);
-            const int len = __clz(~in_row);  // leading ones: lanes 31 .. 32-len
-            const bool take = lane >= 32 - len && mine == nrow;
-            nval = warp_sum(take ? s_cv[wib][lane] : T(0));
-            if (len == 32 && nrow == run_row) nval += run_val;
         }
         run_row = nrow;
         run_val = nval;
@@ -766,7 +808,8 @@ __global__ void __launch_bounds__(256)
         }
         SPX_COO_OUT(first_row, tot);
     }
-    if (e.dots && !add_mode) finish_dots<T, 256>(d0, d1, e, partials, ticket);
+    if constexpr (MODE == 0)
+        if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
 #undef SPX_COO_OUT
 }
 
@@ -1243,41 +1286,74 @@ int ensure_hint(spx_ctx *ctx, spx_matrix *A, int ipt)
     return SPX_OK;
 }
 
-template <class T, int IPT>
-int launch_split(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+// y = A x with nothing else: no scaling, no z, no dots
+template <class T> bool epi_is_plain(const Epi<T> &e)
 {
-    auto kern = k_csr_split<T, IPT>;
+    return e.alpha == T(1) && !e.z && !e.w && !e.want_yy && !e.dots;
+}
+
+template <class T, int IPT, int MODE>
+int launch_split_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    auto kern = k_csr_split<T, IPT, MODE>;
+    const int smem = 8 * (32 * IPT + 32) * (4 + (int)sizeof(T));
+    static std::once_flag once;
+    static int attr_st = SPX_OK;
+    std::call_once(once, [&] { attr_st = set_smem(kern, smem); });
+    SPX_TRY(attr_st);
     SPX_TRY(ensure_hint(ctx, A, IPT));
     const int64_t nchunks = ceil_div(ceil_div(A->nnz, IPT), 32);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * ctx->sm_count;
     const int64_t need = ceil_div(nchunks, 8);  // at least one chunk per warp
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     SPX_TRY(ensure_scratch(ctx, A, grid * 8, grid, sizeof(T)));
-    return launch_k(kern, (int)grid, 256, 0, ctx->stream, true, (int)A->n, (int)A->nnz, (const int *)A->rp.as<int>(),
+    return launch_k(kern, (int)grid, 256, smem, ctx->stream, true, (int)A->n, (int)A->nnz, (const int *)A->rp.as<int>(),
                     (const int *)A->col.as<int>(), val, x, (const int *)A->hint.as<int>(), (int)nchunks,
                     A->carry_row.as<int>(), A->carry_val.as<T>(), A->flags.as<int>(), A->partials.as<T>(),
                     A->ticket.as<unsigned>(), ctx->dev_err, e);
 }
 
 template <class T, int IPT>
-int launch_coo_split(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
+int launch_split(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
 {
-    auto kern = k_coo_split<T, IPT>;
+    return epi_is_plain(e) ? launch_split_m<T, IPT, 1>(ctx, A, val, x, e)
+                           : launch_split_m<T, IPT, 0>(ctx, A, val, x, e);
+}
+
+template <class T, int IPT, int MODE>
+int launch_coo_split_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e)
+{
+    auto kern = k_coo_split<T, IPT, MODE>;
+    const int smem = 8 * (32 * IPT + 32) * (8 + (int)sizeof(T));
+    static std::once_flag once;
+    static int attr_st = SPX_OK;
+    std::call_once(once, [&] { attr_st = set_smem(kern, smem); });
+    SPX_TRY(attr_st);
     const int64_t nchunks = ceil_div(ceil_div(A->coo_nnz, IPT), 32);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)per_sm * ctx->sm_count;
     const int64_t need = ceil_div(nchunks, 8);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     SPX_TRY(ensure_scratch(ctx, A, grid * 8, grid, sizeof(T)));
-    return launch_k(kern, (int)grid, 256, 0, ctx->stream, true, (int)A->n, (int)A->coo_nnz,
+    return launch_k(kern, (int)grid, 256, smem, ctx->stream, true, (int)A->n, (int)A->coo_nnz,
                     (const int *)A->coo_row.as<int>(), (const int *)A->coo_col.as<int>(), cval, x, (int)nchunks,
                     A->carry_row.as<int>(), A->carry_val.as<T>(), A->flags.as<int>(), A->partials.as<T>(),
-                    A->ticket.as<unsigned>(), ctx->dev_err, e, add);
+                    A->ticket.as<unsigned>(), ctx->dev_err, e);
+}
+
+// add: y += alpha A x (the COO part of HYB), else y = epilogue(A x)
+template <class T, int IPT>
+int launch_coo_split(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
+{
+    if (add) return e.alpha == T(1) ? launch_coo_split_m<T, IPT, 3>(ctx, A, cval, x, e)
+                                    : launch_coo_split_m<T, IPT, 2>(ctx, A, cval, x, e);
+    return epi_is_plain(e) ? launch_coo_split_m<T, IPT, 1>(ctx, A, cval, x, e)
+                           : launch_coo_split_m<T, IPT, 0>(ctx, A, cval, x, e);
 }
 
 template <class T, int SW>
@@ -1409,10 +1485,11 @@ int dispatch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const E
 template <class T>
 int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
 {
-    // param: 8 / 16 = nonzeros per lane of the warp-independent split kernel (default 8);
+    // param: 8 / 16 = nonzeros per lane of the warp-independent split kernel (default 16
+    // for FP64, where longer granules amortise the FP64 carry adds; 8 for FP32);
     // 104 / 108 / 116 = tiled segmented reduction with 4 / 8 / 16 items per thread
     int p = A->kernel == SPX_KERNEL_COO ? A->kparam : 0;
-    if (p <= 0) p = 8;
+    if (p <= 0) p = sizeof(T) == 8 ? 16 : 8;
     switch (p) {
     case 8: return launch_coo_split<T, 8>(ctx, A, cval, x, e, add);
     case 16: return launch_coo_split<T, 16>(ctx, A, cval, x, e, add);
