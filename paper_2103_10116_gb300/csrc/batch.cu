@@ -549,10 +549,11 @@ extern "C" int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_
     if (st == SPX_OK) {
         cudaError_t e = cudaMemcpyAsync(B->d_row_off.p, row_off, (size_t)(nsys + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_nnz_off.p, nnz_off, (size_t)(nsys + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
+        const cudaMemcpyKind kind = (flags & SPX_HOST_INPUT) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
         if (e == cudaSuccess && nrows + nsys > 0)
-            e = cudaMemcpyAsync(B->rp.p, row_ptr, (size_t)(nrows + nsys) * 4, cudaMemcpyDeviceToDevice, ctx->stream);
-        if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(B->col.p, col_idx, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, ctx->stream);
-        if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(B->val.p, values, (size_t)nnz * V, cudaMemcpyDeviceToDevice, ctx->stream);
+            e = cudaMemcpyAsync(B->rp.p, row_ptr, (size_t)(nrows + nsys) * 4, kind, ctx->stream);
+        if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(B->col.p, col_idx, (size_t)nnz * 4, kind, ctx->stream);
+        if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(B->val.p, values, (size_t)nnz * V, kind, ctx->stream);
         if (e == cudaSuccess && nsys > 0) e = cudaMemcpyAsync(B->order.p, order.data(), (size_t)nsys * 4, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess && B->val32.p && nnz > 0) {
             k_cast_f32<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(nnz, B->val.as<double>(), B->val32.as<float>());
@@ -655,6 +656,19 @@ int batch_solve_impl(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int sol
     return SPX_OK;
 }
 }  // namespace
+
+namespace spx {
+// One-shot batches (the request server builds a new batch per launch): no
+// graph capture, block size given by the caller.
+int batch_solve_direct(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int solver, double tol, int64_t max_iter,
+                       int precision, int block, spx_solve_info *infos)
+{
+    if (B->nsys == 0) return SPX_OK;
+    return batch_solve_impl(ctx, B, b, x, solver, tol, max_iter, precision, infos, block, false);
+}
+
+int batch_max_rows(const spx_ctx *ctx) { return (ctx->max_smem_optin - 1024) / 8; }
+}  // namespace spx
 
 extern "C" int spx_batch_solve(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int solver, double tol,
                                int64_t max_iter, int precision, spx_solve_info *infos)

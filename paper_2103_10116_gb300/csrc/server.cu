@@ -11,9 +11,21 @@
 // copied back; then the slot's memory returns to the budget and the next
 // queued request is admitted.  Completion records (status, iterations,
 // residual, submit / admit / finish times) are collected with
-// spx_server_poll.  Results do not depend on what else runs: every kernel of
-// a solve uses only its own matrix's and slot's scratch, with fixed-order
-// reductions.
+// spx_server_poll.
+//
+// Small CG / BiCGSTAB requests (up to batch_rows rows, a size the batched
+// kernel holds in shared memory) do not take a slot of their own: batch
+// lanes (further worker threads, each with its own context and stream) take
+// every queued small request with the same solver settings and size class
+// that fits the budget, stage them back to back in pinned host memory, and
+// solve them all with one launch of the persistent batched kernel.  A request
+// arriving while such a batch runs is picked up by the next free lane, so
+// batches overlap each other and the large solves.
+//
+// Results do not depend on what else runs: every kernel of a solve uses only
+// its own matrix's and slot's scratch, with fixed-order reductions; a
+// batched request always runs at the block size of its size class, with
+// block-local reductions, whatever it is batched with.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -30,8 +42,15 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+constexpr int kBatchLanes = 4;
+constexpr int64_t kServeBatchRows = 24576;     // default size limit of batched requests
+constexpr size_t kMaxBatchSystems = 4096;
+constexpr int64_t kMaxBatchRows = 16 << 20;
+
 struct Request {
     int64_t id;
+    bool batched;
+    int block;  // threads per system when batched
     int64_t n, nnz;
     const int32_t *rp, *col;
     const double *val, *b;
@@ -53,7 +72,9 @@ struct spx_server {
     int slots = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue;
+    std::deque<Request *> queue;   // requests that take a slot of their own
+    std::deque<Request *> bqueue;  // requests for the batch lanes
+    int64_t batch_rows = 0, batch_rows_limit = 0;
     std::vector<Request *> done;
     std::vector<std::thread> workers;
     std::atomic<bool> stop{false};
@@ -141,6 +162,181 @@ static void worker_main(spx_server *S)
     cudaStreamDestroy(st);
 }
 
+// threads per system of a batched request: a function of its own size only
+static int batch_block_for(int64_t n) { return n <= 1024 ? 128 : n <= 4096 ? 256 : n <= 8192 ? 512 : 1024; }
+
+static bool same_batch_key(const Request *a, const Request *b)
+{
+    return a->solver == b->solver && a->precision == b->precision && a->tol == b->tol &&
+           a->max_iter == b->max_iter && a->block == b->block;
+}
+
+// row_ptr monotone from 0 to nnz, columns in [0, n)
+static bool csr_ok(const Request *R)
+{
+    if (R->rp[0] != 0 || R->rp[R->n] != R->nnz) return false;
+    for (int64_t i = 0; i < R->n; ++i)
+        if (R->rp[i + 1] < R->rp[i]) return false;
+    for (int64_t k = 0; k < R->nnz; ++k)
+        if (R->col[k] < 0 || R->col[k] >= R->n) return false;
+    return true;
+}
+
+struct Pinned {
+    void *p = nullptr;
+    size_t cap = 0;
+    bool reserve(size_t bytes)
+    {
+        if (bytes <= cap) return true;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = std::max(bytes, cap + cap / 2);
+        if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) return false;
+        cap = want;
+        return true;
+    }
+    ~Pinned()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+// Solve the requests rs (same solver settings) as one batch; per-request
+// errors (an invalid operator) are set in R->error, the batch's own error is
+// returned.
+static int run_batch(spx_ctx *ctx, cudaStream_t st, Pinned &stage, std::vector<Request *> &rs)
+{
+    std::vector<Request *> ok;
+    for (Request *R : rs) {
+        std::memset(&R->info, 0, sizeof(R->info));
+        R->error = csr_ok(R) ? SPX_OK : SPX_ERR_INVALID;
+        if (R->error == SPX_OK) ok.push_back(R);
+    }
+    if (ok.empty()) return SPX_OK;
+    const int64_t ns = (int64_t)ok.size();
+    int64_t rows = 0, nnz = 0;
+    for (Request *R : ok) {
+        rows += R->n;
+        nnz += R->nnz;
+    }
+    const size_t o_row = 0, o_nnz = round_up((size_t)(ns + 1) * 8, 256);
+    const size_t o_rp = o_nnz + round_up((size_t)(ns + 1) * 8, 256);
+    const size_t o_col = o_rp + round_up((size_t)(rows + ns) * 4, 256);
+    const size_t o_val = o_col + round_up((size_t)nnz * 4, 256);
+    const size_t o_b = o_val + round_up((size_t)nnz * 8, 256);
+    const size_t total = o_b + round_up((size_t)rows * 8, 256);
+    if (!stage.reserve(total)) return fail(SPX_ERR_OOM, "pinned staging for a batch");
+    char *h = static_cast<char *>(stage.p);
+    int64_t *row_off = reinterpret_cast<int64_t *>(h + o_row), *nnz_off = reinterpret_cast<int64_t *>(h + o_nnz);
+    int32_t *rp = reinterpret_cast<int32_t *>(h + o_rp), *col = reinterpret_cast<int32_t *>(h + o_col);
+    double *val = reinterpret_cast<double *>(h + o_val), *b = reinterpret_cast<double *>(h + o_b);
+    row_off[0] = nnz_off[0] = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        const Request *R = ok[(size_t)s];
+        std::memcpy(rp + row_off[s] + s, R->rp, (size_t)(R->n + 1) * 4);
+        std::memcpy(col + nnz_off[s], R->col, (size_t)R->nnz * 4);
+        std::memcpy(val + nnz_off[s], R->val, (size_t)R->nnz * 8);
+        std::memcpy(b + row_off[s], R->b, (size_t)R->n * 8);
+        row_off[s + 1] = row_off[s] + R->n;
+        nnz_off[s + 1] = nnz_off[s] + R->nnz;
+    }
+    const Request *h0 = ok[0];
+    spx_batch *B = nullptr;
+    int err = spx_batch_create(ctx, &B, SPX_F64, ns, row_off, nnz_off, rp, col, val,
+                               SPX_HOST_INPUT | (h0->precision == SPX_PREC_MIXED ? SPX_MIXED_SHADOW : 0u));
+    void *bd = nullptr, *xd = nullptr;
+    const size_t vb = (size_t)rows * 8;
+    if (err == SPX_OK && cudaMallocAsync(&bd, vb + 16, st) != cudaSuccess) err = fail(SPX_ERR_OOM, "batch b");
+    if (err == SPX_OK && cudaMallocAsync(&xd, vb + 16, st) != cudaSuccess) err = fail(SPX_ERR_OOM, "batch x");
+    if (err == SPX_OK && cudaMemcpyAsync(bd, b, vb, cudaMemcpyHostToDevice, st) != cudaSuccess) err = SPX_ERR_CUDA;
+    if (err == SPX_OK && cudaMemsetAsync(xd, 0, vb, st) != cudaSuccess) err = SPX_ERR_CUDA;
+    std::vector<spx_solve_info> infos((size_t)ns);
+    if (err == SPX_OK)
+        err = batch_solve_direct(ctx, B, bd, xd, h0->solver, h0->tol, h0->max_iter, h0->precision, h0->block,
+                                 infos.data());
+    // the solve has synchronised the stream: b's staging is free for x
+    if (err == SPX_OK && cudaMemcpyAsync(b, xd, vb, cudaMemcpyDeviceToHost, st) != cudaSuccess) err = SPX_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess && err == SPX_OK) err = SPX_ERR_CUDA;
+    if (err == SPX_OK) {
+        for (int64_t s = 0; s < ns; ++s) {
+            Request *R = ok[(size_t)s];
+            std::memcpy(R->x, b + row_off[s], (size_t)R->n * 8);
+            R->info = infos[(size_t)s];
+        }
+    }
+    if (B) spx_batch_destroy(B);
+    if (bd) cudaFreeAsync(bd, st);
+    if (xd) cudaFreeAsync(xd, st);
+    cudaStreamSynchronize(st);
+    return err;
+}
+
+static void lane_main(spx_server *S)
+{
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    spx_ctx *ctx = nullptr;
+    if (spx_ctx_create(&ctx, S->device, st, nullptr, nullptr, nullptr) != SPX_OK) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->worker_error = spx_last_error();
+        return;
+    }
+    Pinned stage;
+    for (;;) {
+        std::vector<Request *> take;
+        size_t bytes = 0;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] {
+                return S->stop.load() ||
+                       (!S->bqueue.empty() && S->in_use + S->bqueue.front()->footprint <= S->budget);
+            });
+            if (S->stop.load()) break;
+            if (S->bqueue.empty() || S->in_use + S->bqueue.front()->footprint > S->budget) continue;
+            // the head request and every later one of its kind that still fits, in arrival order
+            const Request *head = S->bqueue.front();
+            int64_t rows = 0;
+            for (auto it = S->bqueue.begin(); it != S->bqueue.end();) {
+                Request *R = *it;
+                if (!same_batch_key(R, head)) {
+                    ++it;
+                    continue;
+                }
+                if (take.size() >= kMaxBatchSystems || rows + R->n > kMaxBatchRows ||
+                    S->in_use + bytes + R->footprint > S->budget)
+                    break;
+                take.push_back(R);
+                bytes += R->footprint;
+                rows += R->n;
+                it = S->bqueue.erase(it);
+            }
+            S->in_use += bytes;
+            S->active += (int)take.size();
+            const auto now = Clock::now();
+            for (Request *R : take) R->t_admit = now;
+        }
+        S->cv_work.notify_all();
+        const int err = run_batch(ctx, st, stage, take);
+        const auto now = Clock::now();
+        for (Request *R : take) {
+            if (err != SPX_OK && R->error == SPX_OK) R->error = err;
+            R->t_done = now;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->in_use -= bytes;
+            S->active -= (int)take.size();
+            for (Request *R : take) S->done.push_back(R);
+        }
+        S->cv_work.notify_all();
+        S->cv_done.notify_all();
+    }
+    spx_ctx_destroy(ctx);
+    cudaStreamDestroy(st);
+}
+
 }  // namespace spx
 
 using namespace spx;
@@ -162,7 +358,10 @@ extern "C" int spx_server_create(spx_ctx *ctx, spx_server **out, int64_t budget_
     S->device = ctx->device;
     S->budget = budget_bytes > 0 ? (size_t)budget_bytes : (size_t)(0.9 * (double)freeb);
     S->slots = max_slots;
+    S->batch_rows_limit = batch_max_rows(ctx);
+    S->batch_rows = std::min<int64_t>(kServeBatchRows, S->batch_rows_limit);
     for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_main, S);
+    for (int i = 0; i < kBatchLanes; ++i) S->workers.emplace_back(lane_main, S);
     *out = S;
     return SPX_OK;
 }
@@ -190,6 +389,7 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     R->footprint = request_footprint(n, nnz, solver, precision, restart);
     R->error = SPX_OK;
     R->t_submit = Clock::now();
+    R->block = batch_block_for(n);
     if (R->footprint > S->budget) {
         delete R;
         return fail(SPX_ERR_TOO_LARGE, "request footprint exceeds the server's byte budget");
@@ -197,7 +397,9 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     {
         std::lock_guard<std::mutex> lk(S->mu);
         R->id = S->next_id++;
-        S->queue.push_back(R);
+        R->batched = (solver == SPX_CG || solver == SPX_BICGSTAB) &&
+                     (precision == SPX_PREC_F64 || precision == SPX_PREC_MIXED) && n <= S->batch_rows;
+        (R->batched ? S->bqueue : S->queue).push_back(R);
     }
     *req_id = R->id;
     S->cv_work.notify_all();
@@ -233,7 +435,7 @@ extern "C" int spx_server_pending(spx_server *S, int64_t *queued, int64_t *runni
 {
     if (!S) return fail(SPX_ERR_INVALID, "spx_server_pending: NULL server");
     std::lock_guard<std::mutex> lk(S->mu);
-    if (queued) *queued = (int64_t)S->queue.size();
+    if (queued) *queued = (int64_t)(S->queue.size() + S->bqueue.size());
     if (running) *running = S->active;
     if (bytes_in_use) *bytes_in_use = (int64_t)S->in_use;
     return SPX_OK;
@@ -249,7 +451,17 @@ extern "C" int spx_server_destroy(spx_server *S)
     S->cv_work.notify_all();
     for (auto &t : S->workers) t.join();
     for (Request *R : S->queue) delete R;
+    for (Request *R : S->bqueue) delete R;
     for (Request *R : S->done) delete R;
     delete S;
+    return SPX_OK;
+}
+
+extern "C" int spx_server_set_batching(spx_server *S, int64_t max_rows, int64_t *effective)
+{
+    if (!S) return fail(SPX_ERR_INVALID, "spx_server_set_batching: NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (max_rows >= 0) S->batch_rows = std::min<int64_t>(max_rows, S->batch_rows_limit);
+    if (effective) *effective = S->batch_rows;
     return SPX_OK;
 }

@@ -12,8 +12,9 @@ from . import spx
 
 
 class Server:
-    def __init__(self, ctx: int, budget_bytes: int = 0, max_slots: int = 8):
+    def __init__(self, ctx: int, budget_bytes: int = 0, max_slots: int = 8, batch_rows: int | None = None):
         self.h = spx.spx_server_create(ctx, budget_bytes, max_slots)
+        self.batch_rows = spx.spx_server_set_batching(self.h, batch_rows) if batch_rows is not None else None
         self.live = {}      # id -> (arrays kept alive, x)
         self.results = {}   # id -> result dict
 

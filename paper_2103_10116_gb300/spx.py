@@ -97,6 +97,7 @@ SIGNATURES = {
     "spx_server_create": (_I, [_P, _PP, _I64, _I]),
     "spx_server_submit": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(C.c_int64)]),
     "spx_server_poll": (_I, [_P, C.POINTER(spx_server_result), _I, _I, C.POINTER(C.c_int)]),
+    "spx_server_set_batching": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
     "spx_server_pending": (_I, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spx_server_destroy": (_I, [_P]),
     "spx_last_error": (C.c_char_p, []),
@@ -390,6 +391,12 @@ def spx_server_poll(S: int, max_results: int = 256, wait_ms: int = 0) -> list[di
         out.append({"id": r.id, "error": r.error, "info": _info(r.info), "submit_ms": r.submit_ms,
                     "admit_ms": r.admit_ms, "done_ms": r.done_ms})
     return out
+
+
+def spx_server_set_batching(S: int, max_rows: int) -> int:
+    eff = C.c_int64(0)
+    _check(load().spx_server_set_batching(S, int(max_rows), C.byref(eff)))
+    return eff.value
 
 
 def spx_server_pending(S: int) -> tuple[int, int, int]:

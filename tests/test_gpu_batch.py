@@ -149,3 +149,21 @@ def test_batch_order_invariance_and_tune(spx, ctx, batch):
     finally:
         spx.spx_batch_destroy(B1)
         spx.spx_batch_destroy(B2)
+
+
+def test_batch_host_input_same_bits(spx, ctx, batch):
+    """A batch built from host arrays (SPX_HOST_INPUT) solves to the same bits
+    as one built from device arrays."""
+    ro, no, rp, col, val, xs, b, systems = batch
+    out = []
+    for host in (False, True):
+        conv = (lambda a: torch.from_numpy(np.ascontiguousarray(a))) if host else _t
+        B = spx.spx_batch_create(ctx, ro, no, conv(rp), conv(col), conv(val),
+                                 flags=spx.SPX_HOST_INPUT if host else 0)
+        try:
+            x = torch.zeros(int(ro[-1]), dtype=torch.float64, device=DEV)
+            spx.spx_batch_solve(ctx, B, _t(b), x, len(systems), "cg", 1e-10, 20000)
+            out.append(x.cpu().numpy())
+        finally:
+            spx.spx_batch_destroy(B)
+    assert np.array_equal(out[0], out[1])

@@ -26,8 +26,11 @@ def ctx(spx):
     spx.spx_ctx_destroy(c)
 
 
-def _requests():
+def _requests(large=False):
     reqs = []
+    if large:  # above the batch lanes' size limit: solved on a slot of its own
+        rp, col, val = synth.laplace3d_7pt(32)
+        reqs.append((rp, col, val, synth.uniform_vector(32**3, seed=99), "cg"))
     for k, m in enumerate((10, 14, 18, 22, 26)):
         rp, col, val = synth.laplace3d_7pt(m)
         b = synth.uniform_vector(m**3, seed=100 + k)
@@ -39,10 +42,16 @@ def _requests():
     return reqs
 
 
-def test_alone_equals_mix(spx, ctx):
+@pytest.mark.parametrize("batch_rows", [None, 0])
+def test_alone_equals_mix(spx, ctx, batch_rows):
+    """batch_rows None: small requests go through the batch lanes, the large
+    one through a slot; 0: every request on a slot of its own."""
     from paper_2103_10116_gb300.serving import Server
-    reqs = _requests()
-    srv = Server(ctx, 0, max_slots=4)
+    reqs = _requests(large=True)
+    srv = Server(ctx, 0, max_slots=4, batch_rows=batch_rows)
+    assert (srv.batch_rows is None) or srv.batch_rows == 0
+    if batch_rows is None:
+        assert 20000 <= spx.spx_server_set_batching(srv.h, -1) < 32**3
     try:
         alone = {}
         for i, (rp, col, val, b, solver) in enumerate(reqs):
@@ -97,5 +106,25 @@ def test_admission_respects_budget(spx, ctx):
             srv.poll(wait_ms=5)
         assert peak > 0
         assert all(srv.results[i]["info"].status == spx.SPX_CONVERGED for i in ids)
+    finally:
+        srv.close()
+
+
+def test_invalid_operator_in_batch_is_rejected_alone(spx, ctx):
+    """A batched request with a column out of range fails with SPX_ERR_INVALID
+    and does not disturb the requests batched with it."""
+    from paper_2103_10116_gb300.serving import Server
+    reqs = _requests()[:3]
+    rp, col, val = synth.laplace3d_7pt(8)
+    bad = col.copy()
+    bad[5] = 8**3 + 3
+    srv = Server(ctx, 0, max_slots=2)
+    try:
+        ids = [srv.submit(rp_, col_, val_, b_, solver=s_) for rp_, col_, val_, b_, s_ in reqs]
+        bad_id = srv.submit(rp, bad, val, np.ones(8**3), solver="cg")
+        srv.drain()
+        assert srv.results[bad_id]["error"] == spx.SPX_ERR_INVALID
+        for i in ids:
+            assert srv.results[i]["error"] == 0 and srv.results[i]["info"].status == spx.SPX_CONVERGED
     finally:
         srv.close()
