@@ -74,7 +74,11 @@ typedef enum {
     SPX_KERNEL_ELL = 3,         /* ELL / HYB ELL part: one thread per `param` rows (1, 2 or 4) */
     SPX_KERNEL_COO = 4,         /* COO / HYB COO part: 8/16 = warp-independent split (default 16 FP64, 8 FP32),
                                    104/108/116 = tiled segmented reduction with 4/8/16 items per thread */
-    SPX_KERNEL_CSR_SPLIT = 5    /* CSR: each lane takes `param` (8 or 16) consecutive nonzeros, warps independent */
+    SPX_KERNEL_CSR_SPLIT = 5,   /* CSR: each lane takes `param` (8 or 16) consecutive nonzeros, warps independent */
+    SPX_KERNEL_CSR_ROWS = 6     /* CSR: tiles of 128 rows bulk-copied to shared memory, one thread per row
+                                   (rows of similar length; SPX_ERR_TOO_LARGE if a tile's nonzeros do not
+                                   fit in shared memory); param = shared-memory stages per block:
+                                   2 (default, the next tile copied while this one is reduced) or 1 */
 } spx_kernel;
 
 /* spx_matrix_create flags */

@@ -628,7 +628,7 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     switch (A->format) {
     case SPX_CSR:
         okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_CSR_VECTOR || kernel == SPX_KERNEL_CSR_MERGE ||
-              kernel == SPX_KERNEL_CSR_SPLIT;
+              kernel == SPX_KERNEL_CSR_SPLIT || kernel == SPX_KERNEL_CSR_ROWS;
         break;
     case SPX_ELL: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_ELL; break;
     case SPX_COO: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_COO; break;
@@ -643,6 +643,8 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     if (kernel == SPX_KERNEL_COO && param != 0 &&
         !(param == 8 || param == 16 || param == 104 || param == 108 || param == 116))
         return fail(SPX_ERR_INVALID, "COO parameter must be 0 (auto), 8, 16 (split) or 104, 108, 116 (tiled)");
+    if (kernel == SPX_KERNEL_CSR_ROWS && param != 0 && !(param == 1 || param == 2))
+        return fail(SPX_ERR_INVALID, "row-block stages must be 0 (auto), 1 or 2");
     if (kernel == SPX_KERNEL_CSR_SPLIT && param != 0 && !(param == 8 || param == 16))
         return fail(SPX_ERR_INVALID, "split nonzeros per lane must be 0 (auto), 8 or 16");
     if (kernel == SPX_KERNEL_ELL && param != 0 && !(param == 1 || param == 2 || (param == 4 && A->dtype == SPX_F32)))

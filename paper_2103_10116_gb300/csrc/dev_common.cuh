@@ -20,6 +20,13 @@ template <class T> __device__ __forceinline__ T warp_sum(T v)
 
 // Block sum of v; the result is valid in every thread.  red must hold
 // BLOCK/32 elements; the call ends with the buffer free for reuse.
+__device__ __forceinline__ int warp_max(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 template <class T, int BLOCK> __device__ __forceinline__ T block_sum(T v, T *red)
 {
     static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block size");

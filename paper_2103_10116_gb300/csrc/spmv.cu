@@ -466,6 +466,169 @@ __device__ __forceinline__ T chunk_combine(bool has_pend, int rstart, T pend, co
     return tot;
 }
 
+// ------------------------------------------------------------------ row-block CSR (regular rows)
+// For matrices whose rows have similar lengths: a persistent block takes
+// tiles of ROWS consecutive rows; one thread copies the tile's row pointers,
+// column indices and values into shared memory with three 1-D bulk copies
+// (double-buffered: the next tile is in flight while this one is reduced),
+// and each thread then reduces one row sequentially from shared memory, one
+// FMA per stored entry — ELL's arithmetic without ELL's padding.  `cap` is
+// the largest number of nonzeros in any tile (measured on the host), so the
+// copies always fit; a tile above it (never, for an unmodified matrix) sets
+// DEVERR_BOUNDS and is skipped.
+template <class T, int ROWS> struct RowsShape {
+    static constexpr int RP_BYTES = (ROWS + 8) * 4;  // rp[r0 - 3 .. r1 + 3], 16-byte rounded
+    static __host__ __device__ int col_bytes(int cap) { return ((cap + 8) * 4 + 15) & ~15; }
+    static __host__ __device__ int val_bytes(int cap) { return ((cap + 8) * (int)sizeof(T) + 15) & ~15; }
+    static __host__ __device__ int stage(int cap) { return RP_BYTES + col_bytes(cap) + val_bytes(cap); }
+    // stages | tile coordinates (2 x int4) | mbarriers (2)
+    static __host__ __device__ int smem(int cap, int stages) { return stages * stage(cap) + 32 + 16; }
+};
+
+template <class T, int ROWS, int STAGES, int MODE>
+__global__ void __launch_bounds__(ROWS)
+    k_csr_rows(int n, const int *__restrict__ rp, const int *__restrict__ col, const T *__restrict__ val,
+               const T *__restrict__ x, int ntiles, int cap, T *partials, unsigned *ticket, unsigned *err, Epi<T> e)
+{
+    using S = RowsShape<T, ROWS>;
+    constexpr int VA = 16 / (int)sizeof(T);
+    constexpr int CH = 8;
+    static_assert(STAGES == 1 || STAGES == 2, "one or two stages");
+    if (e.skip && *e.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int stage_bytes = S::stage(cap);
+    int4 *s_coord = reinterpret_cast<int4 *>(smem + STAGES * stage_bytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + STAGES * stage_bytes + 32);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < STAGES; ++k) mbar_init(&bar[k], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    // thread 0 only: copy the tile with rows [r0, r1) and nonzeros [j0, j1) into `stage`
+    auto issue = [&](int r0, int r1, int j0, int j1, int stage) {
+        unsigned char *base = smem + stage * stage_bytes;
+        const int ra = r0 & ~3;
+        const int rbytes = ((r1 + 1 - ra + 3) & ~3) * 4;
+        int ca = j0 & ~3, cbytes = ((j1 - ca + 3) & ~3) * 4;
+        int va = j0 & ~(VA - 1), vbytes = ((j1 - va + VA - 1) & ~(VA - 1)) * (int)sizeof(T);
+        if (j1 - j0 > cap) {  // cannot happen for the matrix the cap was measured on
+            atomicOr(err, DEVERR_BOUNDS);
+            j1 = j0;
+        }
+        if (j1 == j0) cbytes = vbytes = 0;
+        s_coord[stage] = make_int4(r0, j0, r1, j1);
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)(rbytes + cbytes + vbytes));
+        bulk_g2s(base, rp + ra, (uint32_t)rbytes, &bar[stage]);
+        if (cbytes) {
+            bulk_g2s(base + S::RP_BYTES, col + ca, (uint32_t)cbytes, &bar[stage]);
+            bulk_g2s(base + S::RP_BYTES + S::col_bytes(cap), val + va, (uint32_t)vbytes, &bar[stage]);
+        }
+    };
+
+    T d0 = T(0), d1 = T(0);
+    int it = 0;
+    bool ok = true, pending_prefetch = false;
+    // thread 0: the next tile to copy (tile index, nonzero range), loaded one copy ahead
+    int nt = blockIdx.x, nj0 = 0, nj1 = 0;
+    auto load_next = [&]() {
+        if (nt < ntiles) {
+            nj0 = rp[nt * ROWS];
+            nj1 = rp[min(n, nt * ROWS + ROWS)];
+        }
+    };
+    auto issue_next = [&](int stage) {
+        if (nt < ntiles) issue(nt * ROWS, min(n, nt * ROWS + ROWS), nj0, nj1, stage);
+        nt += gridDim.x;
+        load_next();
+    };
+    if (tid == 0) {
+        load_next();
+        if (STAGES == 2) issue_next(0);
+    }
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int stage = STAGES == 2 ? (it & 1) : 0;
+        if (STAGES == 2) {
+            pending_prefetch = t + (int)gridDim.x < ntiles;
+            if (tid == 0) {
+                fence_proxy_async();
+                issue_next(stage ^ 1);  // the tile after this one
+            }
+        } else if (tid == 0) {
+            fence_proxy_async();
+            issue_next(0);  // this tile
+        }
+        const uint32_t parity = STAGES == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
+        if (!mbar_wait(&bar[stage], parity, err)) {
+            ok = false;
+            break;
+        }
+        const int4 co = s_coord[stage];
+        const int r0 = co.x, j0 = co.y, r1 = co.z, j1 = co.w;
+        const unsigned char *sb = smem + stage * stage_bytes;
+        const int *s_rp = reinterpret_cast<const int *>(sb) + (r0 - (r0 & ~3));
+        const int *s_col = reinterpret_cast<const int *>(sb + S::RP_BYTES) + (j0 - (j0 & ~3));
+        const T *s_val = reinterpret_cast<const T *>(sb + S::RP_BYTES + S::col_bytes(cap)) + (j0 - (j0 & ~(VA - 1)));
+        const int q = tid;
+        if (r0 + q < r1) {
+            int a = s_rp[q] - j0;
+            const int b = j1 > j0 ? s_rp[q + 1] - j0 : a;
+            T sum = T(0);
+            for (; a + CH <= b; a += CH) {  // full chunks: CH gathers in flight, then CH FMAs
+                T v[CH], xv[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    v[u] = s_val[a + u];
+                    xv[u] = __ldg(x + s_col[a + u]);
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) sum = fma(v[u], xv[u], sum);
+            }
+            const int rem = b - a;  // 0 .. CH-1: gathers issued together, FMAs only for real entries
+            if (rem > 0) {
+                T v[CH - 1], xv[CH - 1];
+#pragma unroll
+                for (int u = 0; u < CH - 1; ++u) {
+                    v[u] = u < rem ? s_val[a + u] : T(0);
+                    xv[u] = u < rem ? __ldg(x + s_col[a + u]) : T(0);
+                }
+                if (rem & 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) sum = fma(v[u], xv[u], sum);
+                    v[0] = v[4]; v[1] = v[5]; v[2] = v[6];
+                    xv[0] = xv[4]; xv[1] = xv[5]; xv[2] = xv[6];
+                }
+                if (rem & 2) {
+                    sum = fma(v[0], xv[0], sum);
+                    sum = fma(v[1], xv[1], sum);
+                    v[0] = v[2];
+                    xv[0] = xv[2];
+                }
+                if (rem & 1) sum = fma(v[0], xv[0], sum);
+            }
+            out_row<MODE>(e, r0 + q, sum, d0, d1);
+        }
+        __syncthreads();  // the stage is refilled by a later copy
+    }
+    if (!ok && pending_prefetch) {
+        // do not leave a bulk copy in flight into this block's shared memory
+        mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), err, 200000000LL);
+    }
+    if constexpr (MODE == 0)
+        if (e.dots) finish_dots<T, ROWS>(d0, d1, e, partials, ticket);
+}
+
+// the largest number of nonzeros in a tile of `rows` consecutive rows
+__global__ void k_tile_max_nnz(int n, const int *__restrict__ rp, int rows, int ntiles, int *out)
+{
+    int m = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+        m = max(m, rp[min(n, (t + 1) * rows)] - rp[t * rows]);
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 // ------------------------------------------------------------------ nnz-split CSR (warp-independent)
 // Every lane of a persistent warp takes a granule of IPT consecutive nonzeros
 // (loads fully independent of any search: coalesced across the warp) and
@@ -1292,6 +1455,76 @@ template <class T> bool epi_is_plain(const Epi<T> &e)
     return e.alpha == T(1) && !e.z && !e.w && !e.want_yy && !e.dots;
 }
 
+constexpr int kRowsTile = 128;
+constexpr int kRowsStages = 2;  // default shared-memory stages per block of the row-block kernel
+
+int ensure_rows_cap(spx_ctx *ctx, spx_matrix *A)
+{
+    if (A->rows_cap >= 0) return SPX_OK;
+    const int64_t ntiles = ceil_div(A->n, kRowsTile);
+    DBuf m;
+    SPX_TRY(dbuf_alloc(ctx, m, 16));
+    int cap = 0;
+    cudaError_t e = cudaMemsetAsync(m.p, 0, 4, ctx->stream);
+    if (e == cudaSuccess && ntiles > 0) {
+        const int g = (int)std::min<int64_t>(ceil_div(ntiles, 256), (int64_t)ctx->sm_count * 8);
+        k_tile_max_nnz<<<g, 256, 0, ctx->stream>>>((int)A->n, A->rp.as<int>(), kRowsTile, (int)ntiles, m.as<int>());
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cap, m.p, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dbuf_free(ctx, m);
+    if (e != cudaSuccess) return cuda_fail(e, "row-block tile sizes");
+    A->rows_cap = cap;
+    return SPX_OK;
+}
+
+// shared memory the row-block kernel needs for A (bytes)
+template <class T> int64_t rows_smem(const spx_matrix *A, int stages)
+{
+    return RowsShape<T, kRowsTile>::smem((int)std::min<int64_t>(A->rows_cap, 1 << 24), stages);
+}
+
+template <class T, int STAGES, int MODE>
+int launch_rows_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    auto kern = k_csr_rows<T, kRowsTile, STAGES, MODE>;
+    SPX_TRY(ensure_rows_cap(ctx, A));
+    // the dynamic shared memory may reach the opt-in limit less the static part
+    static std::once_flag once;
+    static int attr_st = SPX_OK, dyn_max = 0;
+    std::call_once(once, [&] {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        if (e == cudaSuccess) {
+            dyn_max = ctx->max_smem_optin - (int)fa.sharedSizeBytes;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+        }
+        attr_st = e == cudaSuccess ? SPX_OK : cuda_fail(e, "row-block CSR shared-memory limit");
+    });
+    SPX_TRY(attr_st);
+    const int64_t smem = rows_smem<T>(A, STAGES);
+    if (smem > dyn_max)
+        return fail(SPX_ERR_TOO_LARGE, "row-block CSR: a tile of 128 rows does not fit in shared memory");
+    const int64_t ntiles = ceil_div(A->n, kRowsTile);
+    const int grid = grid_for(ctx, kern, kRowsTile, (int)smem, ntiles);
+    SPX_TRY(ensure_scratch(ctx, A, 0, grid, sizeof(T)));
+    kern<<<grid, kRowsTile, (int)smem, ctx->stream>>>((int)A->n, A->rp.as<int>(), A->col.as<int>(), val, x,
+                                                      (int)ntiles, (int)A->rows_cap, A->partials.as<T>(),
+                                                      A->ticket.as<unsigned>(), ctx->dev_err, e);
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+// stages: 1 or 2 (param of SPX_KERNEL_CSR_ROWS; 0 = 2)
+template <class T>
+int launch_rows(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e, int stages)
+{
+    const bool plain = epi_is_plain(e);
+    if (stages == 1) return plain ? launch_rows_m<T, 1, 1>(ctx, A, val, x, e) : launch_rows_m<T, 1, 0>(ctx, A, val, x, e);
+    return plain ? launch_rows_m<T, 2, 1>(ctx, A, val, x, e) : launch_rows_m<T, 2, 0>(ctx, A, val, x, e);
+}
+
 template <class T, int IPT, int MODE>
 int launch_split_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
 {
@@ -1427,9 +1660,20 @@ int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
 {
     int kern = A->kernel, p = A->kparam;
     if (kern == SPX_KERNEL_AUTO) {
-        // regular rows: merge-path tiles; heavy-tailed rows: the warp-independent split kernel
-        kern = (double)A->max_len <= 4.0 * A->mean_len + 8.0 ? SPX_KERNEL_CSR_MERGE : SPX_KERNEL_CSR_SPLIT;
+        // rows of nearly equal length: row blocks (one thread per row); moderately
+        // uneven rows: merge-path tiles; heavy-tailed rows: the warp-independent split kernel
+        const double mx = (double)A->max_len, mean = A->mean_len;
+        if (mx <= 2.0 * mean + 8.0) {
+            SPX_TRY(ensure_rows_cap(ctx, A));
+            if (rows_smem<T>(A, kRowsStages) <= std::min<int64_t>(ctx->max_smem_optin, 120 * 1024))
+                return launch_rows<T>(ctx, A, val, x, e, kRowsStages);
+        }
+        kern = mx <= 4.0 * mean + 8.0 ? SPX_KERNEL_CSR_MERGE : SPX_KERNEL_CSR_SPLIT;
         p = kern == SPX_KERNEL_CSR_SPLIT ? 8 : 0;
+    }
+    if (kern == SPX_KERNEL_CSR_ROWS) {
+        if (p != 0 && p != 1 && p != 2) return fail(SPX_ERR_INVALID, "row-block stages must be 1 or 2");
+        return launch_rows<T>(ctx, A, val, x, e, p == 0 ? kRowsStages : p);
     }
     if (kern == SPX_KERNEL_CSR_VECTOR) {
         if (p <= 0) {  // sub-warp width from the mean row length

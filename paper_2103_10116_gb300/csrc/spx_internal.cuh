@@ -100,6 +100,8 @@ struct spx_matrix {
     int64_t tiles_items = 0;  // items per tile the map was built for
     int64_t ntiles = 0;
     int64_t nsplit = 0;       // boundaries that split a row (need the look-back)
+    // row-block CSR: the most nonzeros in a tile of 128 rows (-1: not measured yet)
+    int64_t rows_cap = -1;
     // row hints of the nnz-split CSR kernel (row holding nonzero g * hint_ipt)
     spx::DBuf hint;
     int hint_ipt = 0;

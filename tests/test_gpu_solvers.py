@@ -62,7 +62,8 @@ def _make(spx, ctx, fmt, rp, col, val, flags=0, kernel=None, param=0, dtype=torc
     return A
 
 
-FMTS = [("csr", None, 0), ("csr", 1, 4), ("csr", 2, 16), ("csr", 5, 16), ("ell", None, 0), ("coo", None, 0), ("hyb", None, 0)]
+FMTS = [("csr", None, 0), ("csr", 1, 4), ("csr", 2, 16), ("csr", 5, 16), ("csr", 6, 0), ("ell", None, 0),
+        ("coo", None, 0), ("hyb", None, 0)]
 
 
 @pytest.mark.parametrize("fmt", FMTS, ids=lambda f: f"{f[0]}-{f[1]}-{f[2]}")

@@ -67,7 +67,7 @@ VARIANTS = [
     ("csr", None, 0),
     ("csr", "vector", 1), ("csr", "vector", 4), ("csr", "vector", 32),
     ("csr", "merge", 4), ("csr", "merge", 8), ("csr", "merge", 16),
-    ("csr", "split", 8), ("csr", "split", 16),
+    ("csr", "split", 8), ("csr", "split", 16), ("csr", "rows", 0), ("csr", "rows", 1),
     ("ell", None, 0), ("ell", "ell", 1),
     ("coo", None, 0), ("coo", "coo", 16), ("coo", "coo", 104), ("coo", "coo", 116),
     ("hyb", None, 0), ("hyb0", None, 0), ("hyb3", None, 0),
@@ -100,7 +100,7 @@ def _make(spx, ctx, fmt, rp, col, val, ncols, dtype, flags=0):
 
 def _kernel_code(spx, kname):
     return {None: spx.SPX_KERNEL_AUTO, "vector": spx.SPX_KERNEL_CSR_VECTOR, "merge": spx.SPX_KERNEL_CSR_MERGE,
-            "split": spx.SPX_KERNEL_CSR_SPLIT,
+            "split": spx.SPX_KERNEL_CSR_SPLIT, "rows": spx.SPX_KERNEL_CSR_ROWS,
             "ell": spx.SPX_KERNEL_ELL, "coo": spx.SPX_KERNEL_COO}[kname]
 
 
@@ -286,3 +286,33 @@ def test_dot_and_axpby(spx, ctx, dtype):
     torch.cuda.synchronize()
     ref = 2.0 * a.double() - 0.5 * b.double()
     assert torch.allclose(y.double(), ref, rtol=tol, atol=tol)
+
+
+def test_rows_kernel_tile_too_large(spx, ctx):
+    """The row-block kernel holds a tile of 128 rows in shared memory: a matrix
+    with a 60,000-entry row cannot use it (SPX_ERR_TOO_LARGE, nothing
+    launched), and the automatic choice falls back to another kernel."""
+    n = 300
+    lens = np.full(n, 3, np.int64)
+    lens[7] = 60000
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum(lens)
+    rng = np.random.default_rng(3)
+    col = rng.integers(0, n, size=int(rp[-1])).astype(np.int32)
+    val = rng.standard_normal(int(rp[-1]))
+    x = synth.uniform_vector(n, seed=2)
+    A = _make(spx, ctx, "csr", rp, col, val, n, torch.float64)
+    try:
+        xd = torch.from_numpy(x).to(DEV)
+        y = torch.empty(n, dtype=torch.float64, device=DEV)
+        spx.spx_matrix_set_kernel(A, spx.SPX_KERNEL_CSR_ROWS, 0)
+        with pytest.raises(spx.SpxError) as ei:
+            spx.spx_spmv(ctx, A, xd, y)
+        assert ei.value.status == spx.SPX_ERR_TOO_LARGE
+        spx.spx_matrix_set_kernel(A, spx.SPX_KERNEL_AUTO, 0)
+        spx.spx_spmv(ctx, A, xd, y)
+        torch.cuda.synchronize()
+        yref = oracle.spmv_csr(rp, col, val, x)
+        assert_spmv_close(y.cpu().numpy(), yref, oracle.spmv_absbound(rp, col, val, x), TOL["f64"])
+    finally:
+        spx.spx_matrix_destroy(A)
