@@ -338,22 +338,24 @@ def solve_bytes_per_iter(solver: str, fmt_bytes: int, n: int, m: int = 30) -> in
     SpMV stream (fmt_bytes: matrix + gathered vector + result) plus the vector
     kernels.  CG: SpMV (+p re-read for p.q), x/r update (4 reads, 2 writes),
     p update (2 reads, 1 write).  BiCGSTAB: two SpMVs (+ dot operands), p, s,
-    x/r updates.  GMRES(m), averaged over a cycle: SpMV + CGS2 (three passes
-    over the j+1 basis vectors) + normalisation."""
+    x/r updates.  GMRES(m), averaged over a cycle: SpMV + one Gram-Schmidt
+    pass (the j+1 basis vectors read for the dots and again for the update, w
+    read and written) + normalisation; a reorthogonalisation pass is extra
+    work, not counted."""
     V = 8
     if solver == "cg":
         return fmt_bytes + V * n + 6 * V * n + 3 * V * n
     if solver == "bicgstab":
         return 2 * fmt_bytes + 2 * V * n + 4 * V * n + 3 * V * n + 8 * V * n
     jbar = (m + 1) / 2.0
-    return int(fmt_bytes + 3 * (jbar + 1) * V * n + 2 * V * n + 2 * V * n)
+    return int(fmt_bytes + 2 * (jbar + 1) * V * n + 2 * V * n + 2 * V * n)
 
 
-def solve_secondary(spx, ctx, stream, dev, peak):
+def solve_secondary(spx, ctx, stream, dev, peak, fmt="csr"):
     """Krylov solves to relative residual 1e-10 with b = A x*, x* ~ U[-1,1]:
     CG on the 128^3 7-point Poisson matrix; BiCGSTAB and GMRES(30) on the
     128^3 upwind convection-diffusion matrix (Peclet 10).  FP64 and FP32
-    inner iterations inside FP64 refinement ("mixed").  ELL storage."""
+    inner iterations inside FP64 refinement ("mixed").  Storage `fmt`."""
     import torch
     from paper_2103_10116_gb300 import synth
     out = {}
@@ -362,15 +364,15 @@ def solve_secondary(spx, ctx, stream, dev, peak):
              ("gmres30_convdiff128", synth.convdiff3d_upwind(128), "gmres")]
     for name, (rp, col, val), solver in cases:
         n = rp.shape[0] - 1
-        res = {"n": n, "nnz": int(col.shape[0]), "tol": 1e-10, "format": "ell"}
+        res = {"n": n, "nnz": int(col.shape[0]), "tol": 1e-10, "format": fmt}
         with torch.cuda.stream(stream):
-            A = spx.spx_matrix_create(ctx, "ell", torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+            A = spx.spx_matrix_create(ctx, fmt, torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
                                       torch.from_numpy(val).to(dev), flags=spx.SPX_MIXED_SHADOW)
             info = spx.spx_matrix_get_info(A)
             xs = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, n)).to(dev)
             b = torch.empty(n, dtype=torch.float64, device=dev)
             spx.spx_spmv(ctx, A, xs, b)
-            fmt_bytes = algorithmic_bytes("ell", 8, n, n, col.shape[0], info["ell_width"], 0)
+            fmt_bytes = algorithmic_bytes(fmt, 8, n, n, col.shape[0], info["ell_width"], info["coo_nnz"])
             for prec in ("f64", "mixed"):
                 x = torch.zeros(n, dtype=torch.float64, device=dev)
                 spx.spx_solve(ctx, A, b, x, solver, 1e-10, 20000, restart=30, precision=prec)  # warm-up

@@ -11,7 +11,8 @@
 //     epilogue, vector update with a dot, direction update), each returning
 //     at once once the solve has stopped, so the host enqueues a chunk of
 //     iterations as one CUDA graph and reads the stop flag once per chunk;
-//   * GMRES orthogonalises with classical Gram-Schmidt applied twice (CGS2),
+//   * GMRES orthogonalises with classical Gram-Schmidt, repeated once when the
+//     first pass cancels most of the vector (selective reorthogonalisation),
 //     which reads the Krylov basis in long coalesced streams instead of one
 //     dependent dot product per basis vector (modified Gram-Schmidt).
 // Convergence policy: recurrence residual ||r||/||b|| <= tol, then the true
@@ -47,6 +48,7 @@ template <class T> struct GState {
     int status;
     int restarts;  // cycles that ended on the estimate but failed the true residual
     int m;
+    int reorth;    // the current Arnoldi step needs the second Gram-Schmidt pass
     long long iters, maxit;
 };
 
@@ -233,16 +235,100 @@ __global__ void __launch_bounds__(kVB)
 
 // ------------------------------------------------------------------ GMRES kernels
 // Basis V[k] = base + k*ld, k = 0..m.  The Arnoldi step j forms w = A v_j in
-// V[j+1], then CGS2: h1 = V_j^T w; w -= V_j h1; h2 = V_j^T w; w -= V_j h2;
-// h = h1 + h2; H(j+1, j) = ||w||; v_{j+1} = w / ||w||.
+// V[j+1] (with ||w||^2 from the SpMV epilogue), then classical Gram-Schmidt
+// with selective reorthogonalisation (the criterion of Daniel, Gragg, Kaufman
+// and Stewart, 1976): h1 = V_j^T w; w -= V_j h1; and only if that pass
+// cancelled most of w (||w_new|| < ||w_old|| / sqrt 2) a second pass
+// h2 = V_j^T w; w -= V_j h2.  h = h1 + h2; H(j+1, j) = ||w||; v_{j+1} = w / ||w||.
 
-// Multi-dot hout[k] = v_k . w, k = 0..j (j < kGmKmax).  Blocks take chunks of
-// kGmRows rows (grid-stride, fixed grid); w's chunk is staged in shared
-// memory; warp wp owns vectors k = wp, wp+8, wp+16, wp+24 (four independent
-// FMA chains, rows coalesced).  Block partials [k][block] are summed by the
-// last block in block order (deterministic).
+// Gram-Schmidt kernels.  Rows are processed in chunks of kGmRows (grid-stride
+// over a fixed grid).  Dots: the chunk of w sits in shared memory; warp wp
+// owns basis vectors k = wp, wp+8, wp+16, wp+24 and each lane takes four
+// rows at a time, so up to 16 independent loads per lane are in flight.
+// Block partials [k][block] are summed by the last block in block order
+// (deterministic).  Updates: a thread owns rows, two basis vectors per step.
 constexpr int kGmRows = 1024;
 
+// acc[q] += sum over the chunk's rows of V[wp + 8q][r0 + i] * ws[i]
+template <class T>
+__device__ __forceinline__ void gm_chunk_dots(const T *__restrict__ V, int64_t ld, int64_t r0, int nr, const T *ws,
+                                              int j, int lane, int wp, T acc[4])
+{
+    for (int i0 = lane; i0 < nr; i0 += 128) {
+        T wi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wi[u] = i0 + 32 * u < nr ? ws[i0 + 32 * u] : T(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = wp + 8 * q;
+            if (k > j) break;  // warp-uniform
+            const T *vk = V + (int64_t)k * ld + r0;
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = i0 + 32 * u < nr ? vk[i0 + 32 * u] : T(0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[q] = fma(v[u], wi[u], acc[q]);
+        }
+    }
+}
+
+// The last block of a dots pass: hout[k] = sum of the block partials of k.
+template <class T>
+__device__ __forceinline__ void gm_store_dots(const T acc[4], int j, int lane, int wp, T *partials, T *hout,
+                                              unsigned *ticket, bool &last)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = wp + 8 * q;
+        const T s = warp_sum(acc[q]);
+        if (lane == 0 && k <= j) partials[(int64_t)k * gridDim.x + blockIdx.x] = s;
+    }
+    last = last_block(ticket, gridDim.x);
+    if (!last) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = wp + 8 * q;
+        if (k > j) continue;
+        T s = T(0);
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += ldcg(partials + (int64_t)k * gridDim.x + b);
+        s = warp_sum(s);
+        if (lane == 0) hout[k] = s;
+    }
+}
+
+// w_i -= sum_{k<=j} hs[k] V[k][i] for R rows i = i0 + stride * u (those with
+// ok[u]); two basis vectors per step, so 2R loads are in flight together.
+template <class T, int R>
+__device__ __forceinline__ void gm_rows_update(const T *__restrict__ V, int64_t ld, int64_t i0, int64_t stride,
+                                               const bool ok[R], int jn, const T *hs, T wr[R])
+{
+    int k = 0;
+    for (; k + 2 <= jn; k += 2) {
+        const T *v0 = V + (int64_t)k * ld + i0, *v1 = v0 + ld;
+        T a[R], c[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            a[u] = ok[u] ? v0[stride * u] : T(0);
+            c[u] = ok[u] ? v1[stride * u] : T(0);
+        }
+        const T h0 = hs[k], h1 = hs[k + 1];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            wr[u] = fma(-h0, a[u], wr[u]);
+            wr[u] = fma(-h1, c[u], wr[u]);
+        }
+    }
+    if (k < jn) {
+        const T *v0 = V + (int64_t)k * ld + i0;
+        T a[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) a[u] = ok[u] ? v0[stride * u] : T(0);
+#pragma unroll
+        for (int u = 0; u < R; ++u) wr[u] = fma(-hs[k], a[u], wr[u]);
+    }
+}
+
+// First pass: h1 = V_j^T w.
 template <class T>
 __global__ void __launch_bounds__(kVB)
     k_gm_dots(int64_t n, int64_t ld, const T *__restrict__ V, int j, const GState<T> *gs, T *hout, T *partials,
@@ -258,65 +344,20 @@ __global__ void __launch_bounds__(kVB)
         __syncthreads();
         for (int i = threadIdx.x; i < nr; i += kVB) ws[i] = w[r0 + i];
         __syncthreads();
-        for (int i = lane; i < nr; i += 32) {
-            const T wi = ws[i];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k = wp + 8 * q;
-                if (k <= j) acc[q] = fma(V[(int64_t)k * ld + r0 + i], wi, acc[q]);
-            }
-        }
+        gm_chunk_dots<T>(V, ld, r0, nr, ws, j, lane, wp, acc);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int k = wp + 8 * q;
-        const T s = warp_sum(acc[q]);
-        if (lane == 0 && k <= j) partials[(int64_t)k * gridDim.x + blockIdx.x] = s;
-    }
-    if (!last_block(ticket, gridDim.x)) return;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int k = wp + 8 * q;
-        if (k > j) continue;
-        T s = T(0);
-        for (unsigned b = lane; b < gridDim.x; b += 32) s += ldcg(partials + (int64_t)k * gridDim.x + b);
-        s = warp_sum(s);
-        if (lane == 0) hout[k] = s;
-    }
+    bool last;
+    gm_store_dots<T>(acc, j, lane, wp, partials, hout, ticket, last);
 }
 
-// w -= V_j hin (thread per row).  PASS 2 also forms ||w||^2; its last block
-// updates the Hessenberg column, the Givens rotations and the estimate.
-template <class T, int PASS>
-__global__ void __launch_bounds__(kVB)
-    k_gm_upd(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, T *partials,
-             unsigned *ticket)
+// Column j of the Hessenberg matrix from h1 + h2 and ||w|| = sqrt(ww): the
+// earlier Givens rotations, a new rotation, the residual estimate and the
+// stopping decision (one thread).
+template <class T> __device__ void gm_finish_column(GState<T> *gs, GSmall<T> sm, int j, T ww)
 {
-    if (gs->skip) return;
-    T *w = V + (int64_t)(j + 1) * ld;
-    const T *hin = PASS == 1 ? sm.h1 : sm.h2;
-    __shared__ T hs[kGmKmax];
-    if (threadIdx.x < kGmKmax) hs[threadIdx.x] = threadIdx.x <= j ? ldcg(hin + threadIdx.x) : T(0);
-    __syncthreads();
-    T ww = T(0);
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        T wi = w[i];
-        for (int k = 0; k <= j; ++k) wi = fma(-hs[k], V[(int64_t)k * ld + i], wi);
-        w[i] = wi;
-        if (PASS == 2) ww = fma(wi, wi, ww);
-    }
-    if (PASS == 1) return;
-    __shared__ T red[kVB / 32];
-    const T bsum = block_sum<T, kVB>(ww, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = bsum;
-    if (!last_block(ticket, gridDim.x)) return;
-    T s = T(0);
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVB) s += ldcg(partials + b);
-    s = block_sum<T, kVB>(s, red);
-    if (threadIdx.x != 0) return;
     const int m = gs->m;
     T *H = sm.H;
-    const T hn = sqrt(s);
+    const T hn = sqrt(ww);
     for (int k = 0; k <= j; ++k) H[k * m + j] = ldcg(sm.h1 + k) + ldcg(sm.h2 + k);
     H[(j + 1) * m + j] = hn;
     for (int k = 0; k < j; ++k) {  // earlier rotations on column j
@@ -343,6 +384,105 @@ __global__ void __launch_bounds__(kVB)
         gs->est_conv = conv || hn == T(0);
         if (conv || hn == T(0) || gs->iters >= gs->maxit) gs->skip = 1;
     }
+}
+
+// First update and second dots, fused over each chunk of rows:
+// w -= V_j h1 (written back and kept in shared memory), ||w||^2, and
+// h2 = V_j^T w from the chunk just updated (its basis rows are still in
+// L1/L2).  The last block compares ||w||^2 with ||A v_j||^2 (wa[1], from
+// the SpMV): if the first pass kept more than half of it (squared), the
+// column is finished with h2 = 0; otherwise the second update runs.
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_gm_upd_dots(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, const T *wa,
+                  T *partials, unsigned *ticket)
+{
+    if (gs->skip) return;
+    T *w = V + (int64_t)(j + 1) * ld;
+    __shared__ T hs[kGmKmax];
+    __shared__ T ws[kGmRows];
+    __shared__ T red[kVB / 32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int jn = j + 1;
+    if (threadIdx.x < kGmKmax) hs[threadIdx.x] = threadIdx.x < jn ? ldcg(sm.h1 + threadIdx.x) : T(0);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    T ww = T(0);
+    for (int64_t r0 = (int64_t)blockIdx.x * kGmRows; r0 < n; r0 += (int64_t)gridDim.x * kGmRows) {
+        const int nr = (int)min((int64_t)kGmRows, n - r0);
+        __syncthreads();  // hs loaded / ws free
+        constexpr int R = kGmRows / kVB;
+        bool ok[R];
+        T wr[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int il = threadIdx.x + kVB * u;
+            ok[u] = il < nr;
+            wr[u] = ok[u] ? w[r0 + il] : T(0);
+        }
+        gm_rows_update<T, R>(V, ld, r0 + threadIdx.x, kVB, ok, jn, hs, wr);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int il = threadIdx.x + kVB * u;
+            if (ok[u]) {
+                w[r0 + il] = wr[u];
+                ws[il] = wr[u];
+            }
+            ww = fma(wr[u], wr[u], ww);  // zero for rows past the end
+        }
+        __syncthreads();
+        gm_chunk_dots<T>(V, ld, r0, nr, ws, j, lane, wp, acc);
+    }
+    // ||w||^2 partial at slot [kGmKmax + 1][block]
+    const T bsum = block_sum<T, kVB>(ww, red);
+    if (threadIdx.x == 0) partials[(int64_t)(kGmKmax + 1) * gridDim.x + blockIdx.x] = bsum;
+    bool last;
+    gm_store_dots<T>(acc, j, lane, wp, partials, sm.h2, ticket, last);
+    if (!last) return;
+    T s = T(0);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVB)
+        s += ldcg(partials + (int64_t)(kGmKmax + 1) * gridDim.x + b);
+    s = block_sum<T, kVB>(s, red);
+    const bool again = s < T(0.5) * ldcg(wa + 1);  // ||w_new||^2 < ||w_old||^2 / 2
+    __syncthreads();  // h2 stores of this block done
+    if (!again && threadIdx.x < jn) sm.h2[threadIdx.x] = T(0);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    gs->reorth = again ? 1 : 0;
+    if (!again) gm_finish_column<T>(gs, sm, j, s);
+}
+
+// Second update (only when asked for): w -= V_j h2, ||w||^2; the last block
+// finishes the column.
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_gm_upd2(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, T *partials,
+              unsigned *ticket)
+{
+    if (gs->skip || !gs->reorth) return;
+    T *w = V + (int64_t)(j + 1) * ld;
+    __shared__ T hs[kGmKmax];
+    __shared__ T red[kVB / 32];
+    const int jn = j + 1;
+    if (threadIdx.x < kGmKmax) hs[threadIdx.x] = threadIdx.x < jn ? ldcg(sm.h2 + threadIdx.x) : T(0);
+    __syncthreads();
+    T ww = T(0);
+    const int64_t stride = (int64_t)gridDim.x * kVB;
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += 2 * stride) {
+        const bool ok[2] = {true, i + stride < n};
+        T wr[2] = {w[i], ok[1] ? w[i + stride] : T(0)};
+        gm_rows_update<T, 2>(V, ld, i, stride, ok, jn, hs, wr);
+        w[i] = wr[0];
+        if (ok[1]) w[i + stride] = wr[1];
+        ww = fma(wr[0], wr[0], ww);
+        ww = fma(wr[1], wr[1], ww);
+    }
+    const T bsum = block_sum<T, kVB>(ww, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bsum;
+    if (!last_block(ticket, gridDim.x)) return;
+    T s = T(0);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVB) s += ldcg(partials + b);
+    s = block_sum<T, kVB>(s, red);
+    if (threadIdx.x == 0) gm_finish_column<T>(gs, sm, j, s);
 }
 
 // v_{j+1} = w / ||w||
@@ -741,8 +881,8 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
     hs.status = SPX_MAX_ITER;
     SPX_CUDA(cudaMemcpyAsync(gs, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
     const int g = vgrid(ctx, n, 2);
-    int gd = (int)ceil_div(n, kGmRows);  // multi-dot: persistent grid, at most 2 blocks per SM
-    if (gd > 2 * ctx->sm_count) gd = 2 * ctx->sm_count;
+    int gd = (int)ceil_div(n, kGmRows);  // dots passes: persistent grid, at most 4 blocks per SM
+    if (gd > 4 * ctx->sm_count) gd = 4 * ctx->sm_count;
     if (gd < 1) gd = 1;
     const int gu = vgrid(ctx, n, 8);
     auto cycle = [&]() -> int {
@@ -760,11 +900,12 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
         for (int j = 0; j < m; ++j) {
             Epi<T> ea = epi_plain(V + (int64_t)(j + 1) * ld);
             ea.skip = &gs->skip;
+            ea.want_yy = true;  // ||A v_j||^2 -> dots[1], for the reorthogonalisation test
+            ea.dots = dots;
             SPX_TRY(spmv_launch<T>(ctx, A, V + (int64_t)j * ld, ea, use32));
             k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk);
-            k_gm_upd<T, 1><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
-            k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h2, part, tk);
-            k_gm_upd<T, 2><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
+            k_gm_upd_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dots, part, tk);
+            k_gm_upd2<T><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
             k_gm_scale<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm);
         }
         k_gm_solve<T><<<1, 32, 0, ctx->stream>>>(gs, sm);
