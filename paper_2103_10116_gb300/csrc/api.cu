@@ -109,11 +109,27 @@ __global__ void k_validate_cols(int64_t nnz, int64_t ncols, const int *__restric
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, 2u);
 }
 
-__global__ void k_len_hist(int64_t n, const int *__restrict__ rp, unsigned long long *hist)
+// Row-length histogram.  Lengths below kHistShared are counted in a block-local
+// shared histogram first (one global atomic per bin per block instead of one
+// per row: most rows fall in a handful of bins); longer rows go straight to
+// the global bins.
+constexpr int kHistShared = 2048;
+
+__global__ void k_len_hist(int64_t n, const int *__restrict__ rp, unsigned long long *hist, int64_t bins)
 {
+    __shared__ unsigned sh[kHistShared];
+    const int nb = bins < kHistShared ? (int)bins : kHistShared;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
+    __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(hist + (rp[i + 1] - rp[i]), 1ull);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int len = rp[i + 1] - rp[i];
+        if (len < nb) atomicAdd(sh + len, 1u);
+        else atomicAdd(hist + len, 1ull);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
 }
 
 // ------------------------------------------------------------------ conversions
@@ -417,7 +433,8 @@ int matrix_build(spx_ctx *ctx, spx_matrix *A, const int32_t *rp_in, const int32_
             const int64_t bins = A->max_len + 1;
             SPX_TRY(dbuf_alloc(ctx, hist, (size_t)bins * 8));
             SPX_CUDA(cudaMemsetAsync(hist.p, 0, (size_t)bins * 8, ctx->stream));
-            k_len_hist<<<grid1d(ctx, n), 256, 0, ctx->stream>>>(n, A->rp.as<int>(), hist.as<unsigned long long>());
+            k_len_hist<<<grid1d(ctx, n), 256, 0, ctx->stream>>>(n, A->rp.as<int>(), hist.as<unsigned long long>(),
+                                                                bins);
             SPX_CUDA(cudaGetLastError());
             std::vector<unsigned long long> h((size_t)bins);
             SPX_CUDA(cudaMemcpyAsync(h.data(), hist.p, (size_t)bins * 8, cudaMemcpyDeviceToHost, ctx->stream));

@@ -57,8 +57,11 @@ __device__ __forceinline__ void out_row(const Epi<T> &e, int64_t r, T t, T &d0, 
 {
     if constexpr (MODE == 0) final_write(e, r, t, d0, d1);
     else if constexpr (MODE == 1) e.y[r] = t;
-    else if constexpr (MODE == 2) e.y[r] += e.alpha * t;
-    else e.y[r] += t;
+    // add modes: one add per row into a y no other thread touches in this launch,
+    // so a fire-and-forget atomic gives the same bits as load + store without
+    // stalling the emitting lane on the load
+    else if constexpr (MODE == 2) atomicAdd(e.y + r, e.alpha * t);
+    else atomicAdd(e.y + r, t);
 }
 
 // Reduce (d0, d1) over the grid; the last block stores dots and runs the
