@@ -138,14 +138,42 @@ static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, in
 // ------------------------------------------------------------------ fused vector kernels
 // Each returns at once when *skip is set (by an earlier kernel), reduces its
 // dots deterministically and lets the last block update the scalar state.
+// Grid-stride loops over a fixed grid take kU elements per thread per step,
+// all their loads issued before the arithmetic (kU * operands loads in
+// flight), then a scalar tail.
+constexpr int kU = 4;
+
+#define SPX_ROWS_LOOP(LOAD, STORE)                                                   \
+    {                                                                                \
+        const int64_t stride_ = (int64_t)gridDim.x * kVB;                            \
+        int64_t i0_ = blockIdx.x * (int64_t)kVB + threadIdx.x;                       \
+        for (; i0_ + (kU - 1) * stride_ < n; i0_ += kU * stride_) {                  \
+            _Pragma("unroll") for (int u = 0; u < kU; ++u) {                         \
+                const int64_t i = i0_ + u * stride_;                                 \
+                LOAD                                                                 \
+            }                                                                        \
+            _Pragma("unroll") for (int u = 0; u < kU; ++u) {                         \
+                const int64_t i = i0_ + u * stride_;                                 \
+                (void)i;                                                             \
+                STORE                                                                \
+            }                                                                        \
+        }                                                                            \
+        for (; i0_ < n; i0_ += stride_) {                                            \
+            constexpr int u = 0;                                                     \
+            const int64_t i = i0_;                                                   \
+            LOAD                                                                     \
+            STORE                                                                    \
+        }                                                                            \
+    }
+
 template <class T>
 __global__ void __launch_bounds__(kVB)
     k_dot_fin(int64_t n, const T *__restrict__ a, const T *__restrict__ b, int fin, KState<T> *st,
               T *partials, unsigned *ticket)
 {
     T d0 = T(0);
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB)
-        d0 = fma(a[i], b[i], d0);
+    T av[kU], bv[kU];
+    SPX_ROWS_LOOP(av[u] = a[i]; bv[u] = b[i];, d0 = fma(av[u], bv[u], d0);)
     grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, fin, st, partials, ticket);
 }
 
@@ -158,12 +186,10 @@ __global__ void __launch_bounds__(kVB)
     if (st->done) return;
     const T alpha = st->alpha;
     T d0 = T(0);
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const T ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        d0 = fma(ri, ri, d0);
-    }
+    T xv[kU], rv[kU], pv[kU], qv[kU];
+    SPX_ROWS_LOOP(xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i];,
+                  x[i] = fma(alpha, pv[u], xv[u]); const T ri = fma(-alpha, qv[u], rv[u]); r[i] = ri;
+                  d0 = fma(ri, ri, d0);)
     grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, FIN_CG_RHO, st, partials, ticket);
 }
 
@@ -173,8 +199,8 @@ __global__ void __launch_bounds__(kVB) k_cg_p(int64_t n, const T *__restrict__ r
 {
     if (st->done) return;
     const T beta = st->beta;
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB)
-        p[i] = fma(beta, p[i], r[i]);
+    T rv[kU], pv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; pv[u] = p[i];, p[i] = fma(beta, pv[u], rv[u]);)
 }
 
 // BiCGSTAB: p = r + beta (p - omega v)
@@ -184,8 +210,8 @@ __global__ void __launch_bounds__(kVB)
 {
     if (st->done) return;
     const T beta = st->beta, omega = st->omega;
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB)
-        p[i] = fma(beta, fma(-omega, v[i], p[i]), r[i]);
+    T rv[kU], pv[kU], vv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; pv[u] = p[i]; vv[u] = v[i];, p[i] = fma(beta, fma(-omega, vv[u], pv[u]), rv[u]);)
 }
 
 // BiCGSTAB: s = r - alpha v; s.s
@@ -197,11 +223,9 @@ __global__ void __launch_bounds__(kVB)
     if (st->done) return;
     const T alpha = st->alpha;
     T d0 = T(0);
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        const T si = fma(-alpha, v[i], r[i]);
-        s[i] = si;
-        d0 = fma(si, si, d0);
-    }
+    T rv[kU], vv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; vv[u] = v[i];, const T si = fma(-alpha, vv[u], rv[u]); s[i] = si;
+                  d0 = fma(si, si, d0);)
     grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, FIN_BI_S, st, partials, ticket);
 }
 
@@ -216,19 +240,15 @@ __global__ void __launch_bounds__(kVB)
     const T alpha = st->alpha, omega = st->omega;
     const bool sconv = st->s_conv != 0;
     T d0 = T(0), d1 = T(0);
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        const T si = s[i];
-        T ri;
-        if (sconv) {
-            x[i] = fma(alpha, p[i], x[i]);
-            ri = si;
-        } else {
-            x[i] = fma(omega, si, fma(alpha, p[i], x[i]));
-            ri = fma(-omega, t[i], si);
-        }
-        r[i] = ri;
-        d0 = fma(ri, ri, d0);
-        d1 = fma(rh[i], ri, d1);
+    T xv[kU], pv[kU], sv[kU], tv[kU], hv[kU];
+    if (sconv) {
+        SPX_ROWS_LOOP(xv[u] = x[i]; pv[u] = p[i]; sv[u] = s[i]; hv[u] = rh[i];,
+                      x[i] = fma(alpha, pv[u], xv[u]); const T ri = sv[u]; r[i] = ri; d0 = fma(ri, ri, d0);
+                      d1 = fma(hv[u], ri, d1);)
+    } else {
+        SPX_ROWS_LOOP(xv[u] = x[i]; pv[u] = p[i]; sv[u] = s[i]; tv[u] = t[i]; hv[u] = rh[i];,
+                      x[i] = fma(omega, sv[u], fma(alpha, pv[u], xv[u])); const T ri = fma(-omega, tv[u], sv[u]);
+                      r[i] = ri; d0 = fma(ri, ri, d0); d1 = fma(hv[u], ri, d1);)
     }
     grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, FIN_BI_R, st, partials, ticket);
 }
