@@ -80,7 +80,7 @@ def _lib(mutant: int = 0) -> C.CDLL:
             lib.orc_csr_to_hyb.argtypes = [i64, i64, i64, p, p, p, C.c_int, p, p, p, p, p]
             lib.orc_hyb_auto_width.restype = i64
             lib.orc_hyb_auto_width.argtypes = [i64, p, C.c_int]
-            for name in ("orc_cg", "orc_bicgstab"):
+            for name in ("orc_cg", "orc_bicgstab", "orc_cgs"):
                 getattr(lib, name).restype = C.c_int
                 getattr(lib, name).argtypes = [i64, p, p, p, p, p, dbl, i64, C.POINTER(_Info), p]
             lib.orc_gmres.restype = C.c_int
@@ -234,6 +234,11 @@ def bicgstab(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutan
                   mutant)
 
 
+def cgs(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
+    """Conjugate Gradient Squared (Sonneveld) for general A (Section 5 names CGS)."""
+    return _solve("orc_cgs", [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant)
+
+
 def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
     """Restarted GMRES(m), MGS Arnoldi + Givens rotations (Section 5 names GMRES)."""
     return _solve("orc_gmres", [int(m), float(tol), int(maxit)], rp, col, val, b, x0, hist,
@@ -242,13 +247,13 @@ def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mu
 
 def ir(rp, col, val, b, solver="cg", tol=1e-10, inner_tol=1e-4, max_outer=20,
        maxit_inner=10000, x0=None):
-    """FP64 iterative refinement around an FP32 CG / BiCGSTAB inner solve."""
+    """FP64 iterative refinement around an FP32 CG / BiCGSTAB / CGS inner solve."""
     rp, col, val = _csr(rp, col, val)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = rp.shape[0] - 1
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     info = _Info()
-    _lib().orc_ir(n, _ptr(rp), _ptr(col), _ptr(val), 0 if solver == "cg" else 1, _ptr(b),
+    _lib().orc_ir(n, _ptr(rp), _ptr(col), _ptr(val), {"cg": 0, "bicgstab": 1, "cgs": 3}[solver], _ptr(b),
                   _ptr(x), float(tol), float(inner_tol), int(max_outer), int(maxit_inner),
                   C.byref(info))
     return x, SolveInfo(info.status, info.iterations, info.restarts, info.relres_recurrence,

@@ -10,9 +10,9 @@
  *   - sparse matrix-vector product y = A x for a CSR matrix, summed in index
  *     order (Section 5 defines SpMV and the CSR / COO layouts);
  *   - the storage conversions CSR -> COO, ELL, HYB as plain byte copies;
- *   - textbook CG, BiCGSTAB and restarted GMRES(m) with modified Gram-Schmidt
- *     and Givens rotations (the Krylov methods Section 5 names, in the form of
- *     the textbooks it cites);
+ *   - textbook CG, BiCGSTAB, CGS and restarted GMRES(m) with modified
+ *     Gram-Schmidt and Givens rotations (the Krylov methods Section 5 names, in
+ *     the form of the textbooks it cites);
  *   - iterative refinement with an FP32 inner Krylov solve and FP64 outer
  *     residual and update.
  *
@@ -388,6 +388,75 @@ int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double 
 }
 
 /* ------------------------------------------------------------------------- */
+/* CGS, Sonneveld's conjugate gradient squared method (the fourth Krylov     */
+/* solver Section 5 lists), in the textbook form (Saad, Iterative Methods,   */
+/* section 7.4.1): shadow residual r^ = r0, p = u = r0; each iteration       */
+/*   alpha = (r, r^) / (A p, r^);  q = u - alpha A p;                         */
+/*   x += alpha (u + q);  r -= alpha A (u + q);                               */
+/*   beta = (r_new, r^) / (r, r^);  u = r + beta q;  p = u + beta (q + beta p). */
+/* Two SpMVs per iteration.  Breakdown when (A p, r^) or (r, r^) is exactly 0. */
+/* ------------------------------------------------------------------------- */
+int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+            const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+{
+    memset(info, 0, sizeof(*info));
+    double bnorm = nrm2(n, b);
+    if (bnorm == 0.0) {
+        memset(x, 0, (size_t)n * sizeof(double));
+        return 0;
+    }
+    size_t bytes = (size_t)n * sizeof(double);
+    double *r = malloc(bytes), *rh = malloc(bytes), *p = malloc(bytes), *u = malloc(bytes);
+    double *q = malloc(bytes), *v = malloc(bytes), *w = malloc(bytes);
+    int64_t it = 0;
+    int status = ORC_MAX_ITER;
+    double rel = 0.0, reltrue = 0.0;
+    for (int restart = 0;; ++restart) {
+        orc_spmv_csr(n, rp, col, val, x, v);
+        for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - v[i]; rh[i] = r[i]; p[i] = r[i]; u[i] = r[i]; }
+        double rho = dot(n, rh, r);
+        rel = nrm2(n, r) / bnorm;
+        if (hist && it == 0) hist[0] = rel;
+        status = rel <= tol ? ORC_CONVERGED : ORC_MAX_ITER;
+        while (status == ORC_MAX_ITER && it < maxit) {
+            if (rho == 0.0) { status = ORC_BREAKDOWN; break; }
+            orc_spmv_csr(n, rp, col, val, p, v);                       /* v = A p */
+            double vr = dot(n, rh, v);
+            if (vr == 0.0) { status = ORC_BREAKDOWN; break; }
+            double alpha = rho / vr;
+            for (int64_t i = 0; i < n; ++i) q[i] = u[i] - alpha * v[i];
+            for (int64_t i = 0; i < n; ++i) w[i] = u[i] + q[i];      /* u + q */
+            for (int64_t i = 0; i < n; ++i) x[i] += alpha * w[i];
+            orc_spmv_csr(n, rp, col, val, w, v);                       /* A (u + q) */
+#if ORC_MUTANT == 6
+            for (int64_t i = 0; i < n; ++i) r[i] += alpha * v[i];     /* planted: wrong sign */
+#else
+            for (int64_t i = 0; i < n; ++i) r[i] -= alpha * v[i];
+#endif
+            ++it;
+            rel = nrm2(n, r) / bnorm;
+            if (hist) hist[it] = rel;
+            if (rel <= tol) { status = ORC_CONVERGED; break; }
+            double rho1 = dot(n, rh, r);
+            double beta = rho1 / rho;
+            for (int64_t i = 0; i < n; ++i) u[i] = r[i] + beta * q[i];
+            for (int64_t i = 0; i < n; ++i) p[i] = u[i] + beta * (q[i] + beta * p[i]);
+            rho = rho1;
+        }
+        reltrue = true_relres(n, rp, col, val, b, x, bnorm, v);
+        info->restarts = restart;
+        if (status != ORC_CONVERGED || reltrue <= tol) break;
+        if (restart == ORC_MAX_RESTARTS) { status = ORC_STAGNATED; break; }
+    }
+    info->status = status;
+    info->iterations = it;
+    info->relres_recurrence = rel;
+    info->relres_true = reltrue;
+    free(r); free(rh); free(p); free(u); free(q); free(v); free(w);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Restarted GMRES(m) (Saad & Schultz): Arnoldi with modified Gram-Schmidt,  */
 /* Givens rotations applied to the Hessenberg column as it is formed, the    */
 /* residual estimate |g_{j+1}|, and at the end of each cycle x += V_j y_j    */
@@ -589,11 +658,40 @@ static int64_t bicgstab_f32(int64_t n, const int32_t *rp, const int32_t *col, co
     return it;
 }
 
+static int64_t cgs_f32(int64_t n, const int32_t *rp, const int32_t *col, const float *val,
+                       const float *b, float *x, float tol, int64_t maxit)
+{
+    size_t bytes = (size_t)n * sizeof(float);
+    float *r = malloc(bytes), *rh = malloc(bytes), *p = malloc(bytes), *u = malloc(bytes);
+    float *q = malloc(bytes), *v = malloc(bytes), *w = malloc(bytes);
+    float bn = sqrtf(dot_f32(n, b, b));
+    for (int64_t i = 0; i < n; ++i) { x[i] = 0.0f; r[i] = b[i]; rh[i] = b[i]; p[i] = b[i]; u[i] = b[i]; }
+    float rho = dot_f32(n, rh, r);
+    int64_t it = 0;
+    while (it < maxit && bn > 0.0f && rho != 0.0f) {
+        spmv_f32(n, rp, col, val, p, v);
+        float vr = dot_f32(n, rh, v);
+        if (vr == 0.0f) break;
+        float alpha = rho / vr;
+        for (int64_t i = 0; i < n; ++i) { q[i] = u[i] - alpha * v[i]; w[i] = u[i] + q[i]; x[i] += alpha * w[i]; }
+        spmv_f32(n, rp, col, val, w, v);
+        for (int64_t i = 0; i < n; ++i) r[i] -= alpha * v[i];
+        ++it;
+        if (sqrtf(dot_f32(n, r, r)) / bn <= tol) break;
+        float rho1 = dot_f32(n, rh, r);
+        float beta = rho1 / rho;
+        for (int64_t i = 0; i < n; ++i) { u[i] = r[i] + beta * q[i]; p[i] = u[i] + beta * (q[i] + beta * p[i]); }
+        rho = rho1;
+    }
+    free(r); free(rh); free(p); free(u); free(q); free(v); free(w);
+    return it;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Mixed-precision iterative refinement.                                     */
 /*   x = x0; loop: r = b - A64 x (double); stop if ||r||/||b|| <= tol;       */
-/*   d32 solves A32 d = fl32(r / ||r||) to inner_tol by CG (solver 0) or     */
-/*   BiCGSTAB (solver 1) in float; x += ||r|| * fl64(d)  (double).           */
+/*   d32 solves A32 d = fl32(r / ||r||) to inner_tol by CG (solver 0),       */
+/*   BiCGSTAB (solver 1) or CGS (solver 3) in float; x += ||r|| * fl64(d).   */
 /* A32 is the FP32 rounding of A64's values on the same index arrays.        */
 /* iterations counts inner Krylov iterations; restarts counts outer cycles.  */
 /* ------------------------------------------------------------------------- */
@@ -624,8 +722,9 @@ int orc_ir(int64_t n, const int32_t *rp, const int32_t *col, const double *val, 
         if (rel <= tol) { status = ORC_CONVERGED; break; }
         if (outer >= max_outer) { status = ORC_MAX_ITER; break; }
         for (int64_t i = 0; i < n; ++i) r32[i] = (float)(r[i] / rn);
-        inner += solver == 0 ? cg_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner)
-                             : bicgstab_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner);
+        inner += solver == 0   ? cg_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner)
+                 : solver == 3 ? cgs_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner)
+                               : bicgstab_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner);
         for (int64_t i = 0; i < n; ++i) x[i] += rn * (double)d32[i];
     }
     info->status = status;

@@ -3,10 +3,12 @@
 Facts used (none comes from the oracle itself): CG terminates in at most n
 steps on SPD systems and in at most d steps when b lies in a d-dimensional
 invariant subspace with d distinct eigenvalues; CG on an eigenvector converges
-in one step to v / lambda; BiCGSTAB on c*I converges in one step; GMRES on a
-matrix whose minimal polynomial has degree d terminates in at most d steps and
-its residual never increases; manufactured solutions b = A x* with the error
-bounded by kappa * tol; numpy's dense LU as an independent solve.
+in one step to v / lambda; BiCGSTAB and CGS on c*I converge in one step; CGS's
+residual polynomial is the square of CG's on an SPD matrix with r^ = r0 (by
+its construction), so it also terminates in d steps; GMRES on a matrix whose
+minimal polynomial has degree d terminates in at most d steps and its residual
+never increases; manufactured solutions b = A x* with the error bounded by
+kappa * tol; numpy's dense LU as an independent solve.
 """
 import numpy as np
 import pytest
@@ -134,6 +136,76 @@ def test_bicgstab_planted_mistake_is_caught():
     assert bad.status != oracle.CONVERGED or bad.relres_true > 1e-10
 
 
+# ---------------------------------------------------------------- CGS
+def _diag(vals):
+    n = len(vals)
+    return np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.asarray(vals, dtype=np.float64)
+
+
+@pytest.mark.parametrize("c", [1.0, 3.5, -2.0])
+def test_cgs_scaled_identity_one_step(c):
+    rp, col, val = _diag(np.full(17, c))
+    b = np.random.default_rng(1).standard_normal(17)
+    x, info = oracle.cgs(rp, col, val, b, tol=1e-12)
+    assert info.iterations == 1 and info.status == oracle.CONVERGED
+    assert np.allclose(x, b / c, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("j", [1, 2, 3, 4])
+def test_cgs_residual_is_cg_residual_polynomial_squared(j):
+    # A = diag(lam), r^ = r0 = b: CG's residual is phi_j(A) b, CGS's is
+    # phi_j(A)^2 b, so componentwise r_cgs[i] * b[i] = r_cg[i]^2.
+    rng = np.random.default_rng(7)
+    lam = rng.uniform(1.0, 10.0, size=30)
+    rp, col, val = _diag(lam)
+    b = rng.uniform(0.5, 1.5, size=30) * rng.choice([-1.0, 1.0], size=30)
+    x_cg, _ = oracle.cg(rp, col, val, b, tol=0.0, maxit=j)
+    x_cgs, info = oracle.cgs(rp, col, val, b, tol=0.0, maxit=j)
+    assert info.iterations == j
+    r_cg = b - lam * x_cg
+    r_cgs = b - lam * x_cgs
+    scale = np.abs(b).max() ** 2
+    assert np.max(np.abs(r_cgs * b - r_cg**2)) <= 1e-12 * scale
+    assert np.linalg.norm(r_cgs) > 1e-8  # not converged yet: the identity is not trivially 0 = 0
+
+
+@pytest.mark.parametrize("d", [2, 3, 5])
+def test_cgs_terminates_in_d_steps_for_d_distinct_eigenvalues(d):
+    rng = np.random.default_rng(d)
+    ev = np.linspace(1.0, 4.0, d)
+    lam = ev[rng.integers(0, d, size=40)]
+    lam[:d] = ev  # every eigenvalue present
+    rp, col, val = _diag(lam)
+    b = rng.uniform(0.5, 1.5, size=40)
+    _, info = oracle.cgs(rp, col, val, b, tol=1e-10, maxit=d)
+    assert info.status == oracle.CONVERGED and info.iterations <= d
+    _, short = oracle.cgs(rp, col, val, b, tol=0.0, maxit=d - 1)
+    assert short.relres_true > 1e-6  # a degree d-1 polynomial cannot vanish on d eigenvalues
+
+
+def test_cgs_convdiff_manufactured():
+    m = 8
+    rp, col, val = synth.convdiff3d_upwind(m, peclet=10.0)
+    n = m**3
+    xs = synth.uniform_vector(n, seed=3)
+    b = oracle.spmv_csr(rp, col, val, xs)
+    x, info = oracle.cgs(rp, col, val, b, tol=1e-10, maxit=1000)
+    assert info.status == oracle.CONVERGED and info.relres_true <= 1e-10
+    ref = np.linalg.solve(to_dense(rp, col, val), b)
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-8
+
+
+def test_cgs_planted_mistake_is_caught():
+    rng = np.random.default_rng(7)
+    lam = rng.uniform(1.0, 10.0, size=30)
+    rp, col, val = _diag(lam)
+    b = rng.uniform(0.5, 1.5, size=30)
+    x_cg, _ = oracle.cg(rp, col, val, b, tol=0.0, maxit=2)
+    x_bad, _ = oracle.cgs(rp, col, val, b, tol=0.0, maxit=2, mutant=6)
+    r_cg, r_bad = b - lam * x_cg, b - lam * x_bad
+    assert np.max(np.abs(r_bad * b - r_cg**2)) > 1e-6
+
+
 # ---------------------------------------------------------------- GMRES
 @pytest.mark.parametrize("d", [1, 2, 4, 7])
 def test_gmres_terminates_at_minimal_polynomial_degree(d):
@@ -206,5 +278,14 @@ def test_ir_reaches_fp64_tolerance_bicgstab():
     xs = synth.uniform_vector(512, 3)
     b = oracle.spmv_csr(rp, col, val, xs)
     x, info = oracle.ir(rp, col, val, b, solver="bicgstab", tol=1e-10)
+    assert info.status == oracle.CONVERGED and info.relres_true <= 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8
+
+
+def test_ir_reaches_fp64_tolerance_cgs():
+    rp, col, val = synth.convdiff3d_upwind(8)
+    xs = synth.uniform_vector(512, 3)
+    b = oracle.spmv_csr(rp, col, val, xs)
+    x, info = oracle.ir(rp, col, val, b, solver="cgs", tol=1e-10)
     assert info.status == oracle.CONVERGED and info.relres_true <= 1e-10
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8
