@@ -280,6 +280,9 @@ def run_gpu(args):
     secondary = {}
     if not args.no_solve:
         secondary["solves"] = solve_secondary(spx, ctx, stream, dev, peak)
+    if not args.no_solve:
+        secondary["fixed_iterations"] = fixed_iter_secondary(spx, ctx, stream, dev)
+        secondary["vendor_csr_context"] = vendor_secondary(mats, dev)
     if args.batched:
         secondary["batched"] = batched_secondary(spx, ctx, stream, dev)
     if args.serve_seconds > 0:
@@ -351,6 +354,8 @@ def solve_bytes_per_iter(solver: str, fmt_bytes: int, n: int, m: int = 30) -> in
         return fmt_bytes + V * n + 6 * V * n + 3 * V * n
     if solver == "bicgstab":
         return 2 * fmt_bytes + 2 * V * n + 4 * V * n + 3 * V * n + 8 * V * n
+    if solver == "cgs":  # v = A p (+r^), q/w/x (3 reads, 3 writes), A w, r (3 reads, 1 write), u/p (3 reads, 2 writes)
+        return 2 * fmt_bytes + V * n + 6 * V * n + 4 * V * n + 5 * V * n
     jbar = (m + 1) / 2.0
     return int(fmt_bytes + 2 * (jbar + 1) * V * n + 2 * V * n + 2 * V * n)
 
@@ -363,9 +368,11 @@ def solve_secondary(spx, ctx, stream, dev, peak, fmt="csr"):
     import torch
     from paper_2103_10116_gb300 import synth
     out = {}
+    cd = synth.convdiff3d_upwind(128)
     cases = [("cg_poisson128", synth.laplace3d_7pt(128), "cg"),
-             ("bicgstab_convdiff128", synth.convdiff3d_upwind(128), "bicgstab"),
-             ("gmres30_convdiff128", synth.convdiff3d_upwind(128), "gmres")]
+             ("bicgstab_convdiff128", cd, "bicgstab"),
+             ("cgs_convdiff128", cd, "cgs"),
+             ("gmres30_convdiff128", cd, "gmres")]
     for name, (rp, col, val), solver in cases:
         n = rp.shape[0] - 1
         res = {"n": n, "nnz": int(col.shape[0]), "tol": 1e-10, "format": fmt}
@@ -395,6 +402,87 @@ def solve_secondary(spx, ctx, stream, dev, peak, fmt="csr"):
                 res[prec] = r
             spx.spx_matrix_destroy(A)
         out[name] = res
+    return out
+
+
+def solver_flops_per_iter(solver: str, n: int, nnz: int, m: int = 30) -> float:
+    """Floating-point operations of one iteration (an FMA counts 2): SpMVs
+    2 nnz each, dot products and vector updates 2n per FMA each.  GMRES(m):
+    one Gram-Schmidt pass (dots and update over the j+1 basis vectors),
+    the norm and the scaling, averaged over a cycle."""
+    if solver == "cg":       # A p; p.q, r.r; x, r, p updates
+        return 2 * nnz + 10 * n
+    if solver == "bicgstab":  # A p, A s; r^.v, s.s, t.s, t.t, r.r, r^.r; p (2 FMA), s, x (2), r
+        return 4 * nnz + 24 * n
+    if solver == "cgs":       # A p, A w; r^.v, r.r, r^.r; q, w (add), x, r, u, p (2 FMA)
+        return 4 * nnz + 19 * n
+    jbar = (m - 1) / 2.0
+    return 2 * nnz + 4 * (jbar + 1) * n + 3 * n
+
+
+def fixed_iter_secondary(spx, ctx, stream, dev, iters: int = 1000):
+    """The solver throughput protocol of Section 6.4: each Krylov solver runs
+    exactly `iters` iterations after a warm-up, with COO SpMV, reported in
+    GFLOP/s (solver_flops_per_iter).  Matrix: the 128^3 7-point Poisson
+    matrix (SPD, so every solver is defined on it), FP64 and FP32."""
+    import torch
+    from paper_2103_10116_gb300 import synth
+    rp, col, val = synth.laplace3d_7pt(128)
+    n, nnz = rp.shape[0] - 1, int(col.shape[0])
+    out = {"matrix": "7-point Poisson 128^3", "n": n, "nnz": nnz, "format": "coo", "iterations": iters}
+    for tdt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        with torch.cuda.stream(stream):
+            A = spx.spx_matrix_create(ctx, "coo", torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                                      torch.from_numpy(val).to(dev).to(tdt))
+            b = torch.from_numpy(np.random.default_rng(6).uniform(-1, 1, n)).to(dev).to(tdt)
+            res = {}
+            for solver in ("cg", "bicgstab", "cgs", "gmres"):
+                x = torch.zeros(n, dtype=tdt, device=dev)
+                spx.spx_solve_fixed(ctx, A, b, x, solver, 30, restart=30, precision=name)  # warm-up
+                x.zero_()
+                torch.cuda.synchronize()
+                si = spx.spx_solve_fixed(ctx, A, b, x, solver, iters, restart=30, precision=name)
+                fl = solver_flops_per_iter(solver, n, nnz) * si.iterations
+                res[solver] = {"ms": round(si.time_ms, 2), "iterations": si.iterations,
+                               "gflops": round(fl / (si.time_ms * 1e-3) / 1e9, 1)}
+            spx.spx_matrix_destroy(A)
+        out[name] = res
+    return out
+
+
+def vendor_secondary(mats, dev, steps: int = 10):
+    """Context only (never on the library's path): PyTorch's CSR
+    matrix-vector product, which calls the vendor sparse library, on the
+    sweep's CSR matrices, timed with CUDA events like the sweep (median over
+    `steps` after 3 warm-ups, a 256 MB buffer written between launches so that
+    L2 starts cold)."""
+    import torch
+    out = {"library": "torch.sparse CSR matvec (cuSPARSE)", "torch": torch.__version__}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for mname, (rp, col, val) in mats.items():
+        n, nnz = rp.shape[0] - 1, int(col.shape[0])
+        for tdt, V, tag in ((torch.float64, 8, "f64"), (torch.float32, 4, "f32")):
+            try:
+                A = torch.sparse_csr_tensor(torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                                            torch.from_numpy(val).to(dev).to(tdt), size=(n, n))
+                x = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, n)).to(dev).to(tdt)
+                for _ in range(3):
+                    torch.mv(A, x)
+                ts = []
+                for _ in range(steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    torch.mv(A, x)
+                    e1.record()
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                b = algorithmic_bytes("csr", V, n, n, nnz)
+                out[f"{mname}/csr/{tag}"] = {"us": round(ms * 1e3, 1), "GB_s": round(b / (ms * 1e-3) / 1e9, 1)}
+                del A
+            except Exception as e:  # a torch build without the sparse path: report, do not fail the bench
+                out[f"{mname}/csr/{tag}"] = {"unavailable": str(e).splitlines()[0][:120]}
     return out
 
 

@@ -50,7 +50,7 @@ typedef enum {
 
 typedef enum { SPX_CSR = 0, SPX_ELL = 1, SPX_COO = 2, SPX_HYB = 3 } spx_format;
 typedef enum { SPX_F64 = 0, SPX_F32 = 1 } spx_dtype;
-typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2 } spx_solver;
+typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2, SPX_CGS = 3 } spx_solver;
 
 /* Arithmetic of a solve: all FP64; all FP32 (values, vectors, dots and
  * scalars in float); or FP64 iterative refinement around an FP32 inner solve
@@ -218,14 +218,16 @@ int spx_axpby(spx_ctx *ctx, int dtype, int64_t n, double alpha, const void *x, d
 typedef struct {
     int32_t status;            /* spx_solve_status */
     int32_t restarts;          /* restarts after a failed true-residual check (IR: outer cycles) */
-    int64_t iterations;        /* Krylov iterations (one SpMV each for CG / GMRES, two for BiCGSTAB) */
+    int64_t iterations;        /* Krylov iterations (one SpMV each for CG / GMRES, two for BiCGSTAB / CGS) */
     double relres_recurrence;  /* last recurrence (or estimated) relative residual */
     double relres_true;        /* ||b - A x|| / ||b|| formed at exit in FP64 */
     double time_ms;            /* wall time of the call */
     int64_t inner_iterations;  /* SPX_PREC_MIXED: total FP32 inner iterations */
 } spx_solve_info;
 
-/* Solve A x = b (Section 5's Krylov methods).  b[n] and x[n] are device
+/* Solve A x = b (Section 5's Krylov methods: CG, BiCGSTAB, CGS, GMRES(m);
+ * CGS is Sonneveld's conjugate gradient squared with shadow residual r0).
+ * b[n] and x[n] are device
  * vectors of A's dtype (double for SPX_PREC_MIXED, which needs an FP64 matrix
  * created with SPX_MIXED_SHADOW); x holds the initial guess on entry and the
  * solution on exit.  solver: spx_solver; restart: GMRES restart length m

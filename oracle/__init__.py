@@ -246,8 +246,9 @@ def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mu
 
 
 def ir(rp, col, val, b, solver="cg", tol=1e-10, inner_tol=1e-4, max_outer=20,
-       maxit_inner=10000, x0=None):
-    """FP64 iterative refinement around an FP32 CG / BiCGSTAB / CGS inner solve."""
+       maxit_inner=500, x0=None):
+    """FP64 iterative refinement around an FP32 CG / BiCGSTAB / CGS inner solve
+    (at most maxit_inner inner iterations per refinement cycle)."""
     rp, col, val = _csr(rp, col, val)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = rp.shape[0] - 1

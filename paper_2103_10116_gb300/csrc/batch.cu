@@ -371,11 +371,13 @@ __global__ void __launch_bounds__(BLOCK)
                 __syncthreads();
                 float rel32 = 0.f;
                 float *ps32 = reinterpret_cast<float *>(smem);
+                // at most kIrInnerCap inner iterations per refinement cycle
+                const long long cyc_max = min(maxit, iters + (long long)kIrInnerCap);
                 if (SOLVER == SPX_CG)
                     cg_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv[0], fv[1], ps32, redf, 1e-4f,
-                                                   maxit, true, false, iters, rel32);
+                                                   cyc_max, true, false, iters, rel32);
                 else
-                    bicgstab_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, maxit,
+                    bicgstab_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, cyc_max,
                                                          true, false, iters, rel32);
                 for (int i = threadIdx.x; i < n; i += BLOCK) xd[i] = fma(rn, (double)d32[i], xd[i]);
                 __syncthreads();

@@ -41,6 +41,7 @@ enum : int {
     FIN_INIT_CG = 7,    // dots[1] = r.r              -> initial rho (CG)
     FIN_INIT_BI = 8,    // dots[1] = r.r (r^ = r)     -> initial rho = r^.r = r.r, beta
     FIN_SET_BB = 9,     // dots[0] = b.b              -> ||b||^2 and the absolute threshold
+    FIN_CGS_R = 10,     // dots[0] = r.r, dots[1] = r^.r -> convergence, beta = (r^.r)' / (r^.r), rho
 };
 
 template <class T> __device__ __forceinline__ void kstop(KState<T> *s, int status)
@@ -124,6 +125,17 @@ template <class T> __device__ __forceinline__ void run_fin(int fin, void *state,
         if (s->iters >= s->maxit) { kstop(s, SPX_MAX_ITER); break; }
         if (rhr == T(0)) { kstop(s, SPX_BREAKDOWN); break; }
         s->beta = (rhr / s->rho) * (s->alpha / s->omega);
+        s->rho = rhr;
+        break;
+    }
+    case FIN_CGS_R: {
+        const T rr = dots[0], rhr = dots[1];
+        s->iters += 1;
+        s->relres = sqrt(rr / s->bb);
+        if (rr <= s->tol2) { kstop(s, SPX_CONVERGED); break; }
+        if (s->iters >= s->maxit) { kstop(s, SPX_MAX_ITER); break; }
+        if (rhr == T(0)) { kstop(s, SPX_BREAKDOWN); break; }
+        s->beta = rhr / s->rho;
         s->rho = rhr;
         break;
     }

@@ -93,7 +93,7 @@ size_t request_footprint(int64_t n, int64_t nnz, int solver, int precision, int 
     const size_t shadow = precision == SPX_PREC_MIXED ? (size_t)nnz * 4 : 0;
     size_t vecs;
     const size_t V = precision == SPX_PREC_F32 ? 4 : 8;
-    const int nv = solver == SPX_CG ? 4 : (solver == SPX_BICGSTAB ? 7 : restart + 2);
+    const int nv = solver == SPX_CG ? 4 : solver == SPX_BICGSTAB ? 7 : solver == SPX_CGS ? 8 : restart + 2;
     if (precision == SPX_PREC_MIXED) vecs = (size_t)n * (8 * 4 + 4 * (nv + 2)) + (size_t)n * 16;
     else vecs = (size_t)n * V * nv;
     return csr + shadow + vecs + (size_t)n * 16 /* b, x */ + (1u << 20);
@@ -372,7 +372,7 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
 {
     if (!S || !row_ptr || !b || !x || !req_id || n <= 0 || nnz < 0 || (nnz > 0 && (!col_idx || !values)))
         return fail(SPX_ERR_INVALID, "spx_server_submit: bad argument");
-    if (solver < SPX_CG || solver > SPX_GMRES) return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
+    if (solver < SPX_CG || solver > SPX_CGS) return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
     Request *R = new Request();
     R->n = n;
     R->nnz = nnz;

@@ -1,8 +1,8 @@
-// solvers.cu -- Krylov solvers on the device: CG, BiCGSTAB, restarted GMRES(m),
+// solvers.cu -- Krylov solvers on the device: CG, BiCGSTAB, CGS, restarted GMRES(m),
 // and FP64 iterative refinement around an FP32 inner solve.
 //
 // The methods are the ones Section 5 of arXiv 2103.10116 names (CG for SPD
-// systems; BiCGSTAB and GMRES for general ones; GMRES orthogonalises each new
+// systems; BiCGSTAB, CGS and GMRES for general ones; GMRES orthogonalises each new
 // direction against all previous ones).  The GPU form differs from a textbook
 // loop only in scheduling:
 //   * every scalar (alpha, beta, omega, rho, norms, Hessenberg column) stays
@@ -97,6 +97,7 @@ static int nvec_for(int solver, int m)
 {
     if (solver == SPX_CG) return 4;        // r, p, q, scratch
     if (solver == SPX_BICGSTAB) return 7;  // r, rh, p, v, s, t, scratch
+    if (solver == SPX_CGS) return 8;       // r, rh, p, u, q, v, w, scratch
     return m + 2;                          // V[0..m], scratch
 }
 
@@ -251,6 +252,48 @@ __global__ void __launch_bounds__(kVB)
                       r[i] = ri; d0 = fma(ri, ri, d0); d1 = fma(hv[u], ri, d1);)
     }
     grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, FIN_BI_R, st, partials, ticket);
+}
+
+// CGS: q = u - alpha v; w = u + q; x += alpha w
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_cgs_qw(int64_t n, T *__restrict__ x, const T *__restrict__ uu, const T *__restrict__ v, T *__restrict__ q,
+             T *__restrict__ w, const KState<T> *st)
+{
+    if (st->done) return;
+    const T alpha = st->alpha;
+    T xv[kU], uv[kU], vv[kU];
+    SPX_ROWS_LOOP(xv[u] = x[i]; uv[u] = uu[i]; vv[u] = v[i];,
+                  const T qi = fma(-alpha, vv[u], uv[u]); q[i] = qi; const T wi = uv[u] + qi; w[i] = wi;
+                  x[i] = fma(alpha, wi, xv[u]);)
+}
+
+// CGS: r -= alpha v (v = A w); dots r.r and r^.r
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_cgs_r(int64_t n, T *__restrict__ r, const T *__restrict__ rh, const T *__restrict__ v, KState<T> *st,
+            T *partials, unsigned *ticket)
+{
+    if (st->done) return;
+    const T alpha = st->alpha;
+    T d0 = T(0), d1 = T(0);
+    T rv[kU], hv[kU], vv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; hv[u] = rh[i]; vv[u] = v[i];,
+                  const T ri = fma(-alpha, vv[u], rv[u]); r[i] = ri; d0 = fma(ri, ri, d0); d1 = fma(hv[u], ri, d1);)
+    grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, FIN_CGS_R, st, partials, ticket);
+}
+
+// CGS: u = r + beta q; p = u + beta (q + beta p)
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_cgs_up(int64_t n, const T *__restrict__ r, const T *__restrict__ q, T *__restrict__ uu, T *__restrict__ p,
+             const KState<T> *st)
+{
+    if (st->done) return;
+    const T beta = st->beta;
+    T rv[kU], qv[kU], pv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; qv[u] = q[i]; pv[u] = p[i];,
+                  const T ui = fma(beta, qv[u], rv[u]); uu[i] = ui; p[i] = fma(beta, fma(beta, pv[u], qv[u]), ui);)
 }
 
 // ------------------------------------------------------------------ GMRES kernels
@@ -719,6 +762,35 @@ template <class T> int bi_iter(KrylovRun<T> &R)
     return SPX_OK;
 }
 
+// One CGS iteration: v = A p (+ r^.v -> alpha); q, w = u + q, x; v = A w;
+// r update (+ r.r, r^.r -> convergence, beta); u, p updates.
+template <class T> int cgs_iter(KrylovRun<T> &R)
+{
+    SolverWork *w = R.w;
+    KState<T> *st = w->state.as<KState<T>>();
+    T *r = vec<T>(w, 0), *rh = vec<T>(w, 1), *p = vec<T>(w, 2), *u = vec<T>(w, 3), *q = vec<T>(w, 4),
+      *v = vec<T>(w, 5), *ww = vec<T>(w, 6);
+    const int64_t n = R.A->n;
+    const int g = vgrid(R.ctx, n);
+    T *part = w->red.as<T>();
+    unsigned *tk = w->ticket.as<unsigned>();
+    Epi<T> e = epi_plain(v);
+    e.w = rh;
+    e.dots = w->dots.as<T>();
+    e.fin = FIN_BI_RV;  // alpha = rho / (r^.v), breakdown on 0
+    e.fin_state = st;
+    e.skip = &st->done;
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, p, e, R.use32));
+    k_cgs_qw<T><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, st);
+    Epi<T> e2 = epi_plain(v);
+    e2.skip = &st->done;
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, ww, e2, R.use32));
+    k_cgs_r<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, rh, v, st, part, tk);
+    k_cgs_up<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, q, u, p, st);
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
 // r = b - A x with r.r; (re)initialise the recurrences.
 template <class T> int krylov_init(KrylovRun<T> &R)
 {
@@ -733,12 +805,15 @@ template <class T> int krylov_init(KrylovRun<T> &R)
     e.y = r;
     e.want_yy = true;
     e.dots = w->dots.as<T>();
-    e.fin = R.solver == SPX_CG ? FIN_INIT_CG : FIN_INIT_BI;
+    e.fin = R.solver == SPX_BICGSTAB ? FIN_INIT_BI : FIN_INIT_CG;  // CGS: rho = r^.r = r.r like CG
     e.fin_state = st;
     SPX_TRY(spmv_launch<T>(R.ctx, R.A, R.x, e, R.use32));
     const size_t bytes = (size_t)n * sizeof(T);
     if (R.solver == SPX_CG) {
         SPX_CUDA(cudaMemcpyAsync(vec<T>(w, 1), r, bytes, cudaMemcpyDeviceToDevice, R.ctx->stream));
+    } else if (R.solver == SPX_CGS) {
+        for (int k = 1; k <= 3; ++k)  // r^ = p = u = r
+            SPX_CUDA(cudaMemcpyAsync(vec<T>(w, k), r, bytes, cudaMemcpyDeviceToDevice, R.ctx->stream));
     } else {
         SPX_CUDA(cudaMemcpyAsync(vec<T>(w, 1), r, bytes, cudaMemcpyDeviceToDevice, R.ctx->stream));  // r^
         SPX_CUDA(cudaMemsetAsync(vec<T>(w, 2), 0, bytes, R.ctx->stream));                        // p
@@ -830,7 +905,8 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
                                      (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T),
                                      (uint64_t)(uintptr_t)A, 0};
             SPX_TRY(run_chunk(ctx, w, key, graphs, [&]() -> int {
-                for (int c = 0; c < chunk; ++c) SPX_TRY(solver == SPX_CG ? cg_iter(R) : bi_iter(R));
+                for (int c = 0; c < chunk; ++c)
+                    SPX_TRY(solver == SPX_CG ? cg_iter(R) : solver == SPX_CGS ? cgs_iter(R) : bi_iter(R));
                 return SPX_OK;
             }));
             launched += chunk;
@@ -1028,10 +1104,11 @@ int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, 
         SPX_CUDA(cudaGetLastError());
         spx_solve_info ii;
         std::memset(&ii, 0, sizeof(ii));
+        const int64_t cyc_max = std::min<int64_t>(maxit - inner_total, kIrInnerCap);
         if (solver == SPX_GMRES)
-            SPX_TRY(run_gmres<float>(ctx, A, w->inner, r32, d32, inner_tol, maxit - inner_total, m, true, true, 0, &ii));
+            SPX_TRY(run_gmres<float>(ctx, A, w->inner, r32, d32, inner_tol, cyc_max, m, true, true, 0, &ii));
         else
-            SPX_TRY(run_short<float>(ctx, A, w->inner, solver, r32, d32, inner_tol, maxit - inner_total, true, true, 0, &ii));
+            SPX_TRY(run_short<float>(ctx, A, w->inner, solver, r32, d32, inner_tol, cyc_max, true, true, 0, &ii));
         inner_total += ii.iterations;
         k_ir_update<<<g, kVB, 0, ctx->stream>>>(n, x, d32, rn);
         SPX_CUDA(cudaGetLastError());
@@ -1061,7 +1138,7 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
         return fail(SPX_ERR_INVALID, "spx_solve: NULL argument");
     std::memset(info, 0, sizeof(*info));
     if (A->n != A->ncols) return fail(SPX_ERR_INVALID, "spx_solve: the matrix must be square");
-    if (solver < SPX_CG || solver > SPX_GMRES) return fail(SPX_ERR_INVALID, "spx_solve: unknown solver");
+    if (solver < SPX_CG || solver > SPX_CGS) return fail(SPX_ERR_INVALID, "spx_solve: unknown solver");
     if (!(tol >= 0.0) || maxit < 0) return fail(SPX_ERR_INVALID, "spx_solve: bad tol or max_iter");
     if (solver == SPX_GMRES && (restart < 1 || restart > kGmKmax - 1))
         return fail(SPX_ERR_UNSUPPORTED, "GMRES restart length must be in [1, 31]");

@@ -149,6 +149,11 @@ template <class T> int axpby_launch(spx_ctx *ctx, int64_t n, T alpha, const T *x
 // Tile map for merge-path CSR (spmv.cu).
 int ensure_merge_tiles(spx_ctx *ctx, spx_matrix *A, int64_t tile_items, int64_t slack);
 
+// Iterative refinement: FP32 inner iterations per outer cycle are capped, so an
+// inner solve that stagnates (FP32 CGS on large systems) hands back its best
+// correction to the FP64 outer loop instead of running to the global limit.
+constexpr int kIrInnerCap = 500;
+
 // Batched solves without graph capture, at a given block size (batch.cu), and
 // the largest system the batched kernel holds (rows).
 int batch_solve_direct(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int solver, double tol, int64_t max_iter,

@@ -22,7 +22,7 @@ SPX_OK, SPX_ERR_INVALID, SPX_ERR_TOO_LARGE, SPX_ERR_OOM, SPX_ERR_CUDA = 0, 1, 2,
 SPX_ERR_UNSUPPORTED, SPX_ERR_TIMEOUT, SPX_ERR_NOT_FOUND = 5, 6, 7
 SPX_CSR, SPX_ELL, SPX_COO, SPX_HYB = 0, 1, 2, 3
 SPX_F64, SPX_F32 = 0, 1
-SPX_CG, SPX_BICGSTAB, SPX_GMRES = 0, 1, 2
+SPX_CG, SPX_BICGSTAB, SPX_GMRES, SPX_CGS = 0, 1, 2, 3
 SPX_PREC_F64, SPX_PREC_F32, SPX_PREC_MIXED = 0, 1, 2
 SPX_CONVERGED, SPX_MAX_ITER, SPX_BREAKDOWN, SPX_STAGNATED, SPX_SOLVE_TIMEOUT = 0, 1, 2, 3, 4
 SPX_KERNEL_AUTO, SPX_KERNEL_CSR_VECTOR, SPX_KERNEL_CSR_MERGE, SPX_KERNEL_ELL, SPX_KERNEL_COO = 0, 1, 2, 3, 4
@@ -33,7 +33,7 @@ SPX_HOST_INPUT, SPX_MIXED_SHADOW = 1, 2
  SPX_PART_COO_COL, SPX_PART_COO_VAL, SPX_PART_VAL_F32) = range(9)
 
 FORMATS = {"csr": SPX_CSR, "ell": SPX_ELL, "coo": SPX_COO, "hyb": SPX_HYB}
-SOLVERS = {"cg": SPX_CG, "bicgstab": SPX_BICGSTAB, "gmres": SPX_GMRES}
+SOLVERS = {"cg": SPX_CG, "bicgstab": SPX_BICGSTAB, "gmres": SPX_GMRES, "cgs": SPX_CGS}
 PRECISIONS = {"f64": SPX_PREC_F64, "f32": SPX_PREC_F32, "mixed": SPX_PREC_MIXED}
 STATUS_NAMES = {SPX_CONVERGED: "converged", SPX_MAX_ITER: "max_iter", SPX_BREAKDOWN: "breakdown",
                 SPX_STAGNATED: "stagnated", SPX_SOLVE_TIMEOUT: "timeout"}

@@ -103,6 +103,41 @@ def test_bicgstab_convdiff(spx, ctx, fmt):
         spx.spx_matrix_destroy(A)
 
 
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb"])
+def test_cgs_convdiff(spx, ctx, fmt):
+    rp, col, val, xs, b = _problem("convdiff_16")
+    A = _make(spx, ctx, fmt, rp, col, val)
+    try:
+        x = torch.zeros_like(_t(b))
+        info = spx.spx_solve(ctx, A, _t(b), x, "cgs", 1e-10, 5000)
+        _, oinfo = oracle.cgs(rp, col, val, b, tol=1e-10, maxit=5000)
+        xh = x.cpu().numpy()
+        assert info.status == spx.SPX_CONVERGED, info
+        assert info.relres_true <= 1e-10 and _true_relres(rp, col, val, b, xh) <= 1.05e-10
+        # CGS squares the residual polynomial: its convergence is irregular, rounding moves the stop
+        assert abs(info.iterations - oinfo.iterations) <= max(4, oinfo.iterations // 5), (info, oinfo)
+        assert np.linalg.norm(xh - xs) / np.linalg.norm(xs) <= 1e-7
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
+@pytest.mark.parametrize("c", [2.5, -1.5])
+def test_cgs_scaled_identity_one_step(spx, ctx, c):
+    n = 1000
+    rp = np.arange(n + 1, dtype=np.int32)
+    col = np.arange(n, dtype=np.int32)
+    val = np.full(n, c)
+    b = synth.uniform_vector(n, seed=4)
+    A = _make(spx, ctx, "csr", rp, col, val)
+    try:
+        x = torch.zeros(n, dtype=torch.float64, device=DEV)
+        info = spx.spx_solve(ctx, A, _t(b), x, "cgs", 1e-12, 100)
+        assert info.status == spx.SPX_CONVERGED and info.iterations == 1
+        assert np.allclose(x.cpu().numpy(), b / c, rtol=1e-15, atol=0)
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
 @pytest.mark.parametrize("m", [5, 30])
 def test_gmres_convdiff(spx, ctx, m):
     rp, col, val, xs, b = _problem("convdiff_12")
@@ -153,7 +188,8 @@ def test_cg_eigenvector_one_step(spx, ctx):
         spx.spx_matrix_destroy(A)
 
 
-@pytest.mark.parametrize("solver,prob", [("cg", "lap3d_20"), ("bicgstab", "convdiff_16"), ("gmres", "convdiff_12")])
+@pytest.mark.parametrize("solver,prob", [("cg", "lap3d_20"), ("bicgstab", "convdiff_16"), ("cgs", "convdiff_16"),
+                                         ("gmres", "convdiff_12")])
 @pytest.mark.parametrize("fmt", ["csr", "ell", "hyb"])
 def test_mixed_precision_ir(spx, ctx, solver, prob, fmt):
     rp, col, val, xs, b = _problem(prob)
@@ -174,7 +210,7 @@ def test_mixed_precision_ir(spx, ctx, solver, prob, fmt):
         spx.spx_matrix_destroy(A)
 
 
-@pytest.mark.parametrize("solver", ["cg", "bicgstab", "gmres"])
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs", "gmres"])
 def test_fp32_solve(spx, ctx, solver):
     rp, col, val, xs, b = _problem("lap3d_20")
     A = _make(spx, ctx, "csr", rp, col, val, dtype=torch.float32)
@@ -188,7 +224,7 @@ def test_fp32_solve(spx, ctx, solver):
         spx.spx_matrix_destroy(A)
 
 
-@pytest.mark.parametrize("solver", ["cg", "bicgstab", "gmres"])
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs", "gmres"])
 def test_edge_cases(spx, ctx, solver):
     rp, col, val, xs, b = _problem("lap2d_64")
     A = _make(spx, ctx, "csr", rp, col, val)
