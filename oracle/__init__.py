@@ -80,11 +80,13 @@ def _lib(mutant: int = 0) -> C.CDLL:
             lib.orc_csr_to_hyb.argtypes = [i64, i64, i64, p, p, p, C.c_int, p, p, p, p, p]
             lib.orc_hyb_auto_width.restype = i64
             lib.orc_hyb_auto_width.argtypes = [i64, p, C.c_int]
-            for name in ("orc_cg", "orc_bicgstab", "orc_cgs"):
+            for name in ("orc_cg", "orc_bicgstab", "orc_cgs", "orc_cg_jacobi", "orc_bicgstab_jacobi",
+                         "orc_cgs_jacobi"):
                 getattr(lib, name).restype = C.c_int
                 getattr(lib, name).argtypes = [i64, p, p, p, p, p, dbl, i64, C.POINTER(_Info), p]
-            lib.orc_gmres.restype = C.c_int
-            lib.orc_gmres.argtypes = [i64, p, p, p, p, p, C.c_int, dbl, i64, C.POINTER(_Info), p]
+            for name in ("orc_gmres", "orc_gmres_jacobi"):
+                getattr(lib, name).restype = C.c_int
+                getattr(lib, name).argtypes = [i64, p, p, p, p, p, C.c_int, dbl, i64, C.POINTER(_Info), p]
             lib.orc_ir.restype = C.c_int
             lib.orc_ir.argtypes = [i64, p, p, p, C.c_int, p, p, dbl, dbl, C.c_int, i64,
                                    C.POINTER(_Info)]
@@ -223,25 +225,38 @@ def _solve(fn, args, rp, col, val, b, x0, with_hist, maxit, mutant):
     return x, si
 
 
-def cg(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
-    """Conjugate Gradient for SPD A (Section 5 names CG; textbook form)."""
-    return _solve("orc_cg", [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant)
+def _fn(base, precond):
+    if precond is None:
+        return base
+    if precond == "jacobi":
+        return base + "_jacobi"
+    raise ValueError(f"unknown preconditioner {precond!r}")
 
 
-def bicgstab(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
-    """BiCGSTAB for general A (Section 5 names BiCGSTAB; van der Vorst form)."""
-    return _solve("orc_bicgstab", [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit,
+def cg(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+    """Conjugate Gradient for SPD A (Section 5 names CG; textbook form);
+    precond="jacobi": preconditioned CG with M = diag(A)."""
+    return _solve(_fn("orc_cg", precond), [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant)
+
+
+def bicgstab(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+    """BiCGSTAB for general A (Section 5 names BiCGSTAB; van der Vorst form);
+    precond="jacobi": right preconditioning with M = diag(A)."""
+    return _solve(_fn("orc_bicgstab", precond), [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit,
                   mutant)
 
 
-def cgs(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
-    """Conjugate Gradient Squared (Sonneveld) for general A (Section 5 names CGS)."""
-    return _solve("orc_cgs", [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant)
+def cgs(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+    """Conjugate Gradient Squared (Sonneveld) for general A (Section 5 names CGS);
+    precond="jacobi": right preconditioning with M = diag(A)."""
+    return _solve(_fn("orc_cgs", precond), [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit,
+                  mutant)
 
 
-def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0):
-    """Restarted GMRES(m), MGS Arnoldi + Givens rotations (Section 5 names GMRES)."""
-    return _solve("orc_gmres", [int(m), float(tol), int(maxit)], rp, col, val, b, x0, hist,
+def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+    """Restarted GMRES(m), MGS Arnoldi + Givens rotations (Section 5 names GMRES);
+    precond="jacobi": right preconditioning with M = diag(A)."""
+    return _solve(_fn("orc_gmres", precond), [int(m), float(tol), int(maxit)], rp, col, val, b, x0, hist,
                   maxit, mutant)
 
 

@@ -250,8 +250,9 @@ static double true_relres(int64_t n, const int32_t *rp, const int32_t *col, cons
 /* hist (optional) receives the recurrence relative residual after every     */
 /* iteration, hist[0] being the initial one.                                 */
 /* ------------------------------------------------------------------------- */
-int orc_cg(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-           const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+static int cg_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                  const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist,
+                  const double *dinv)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -262,14 +263,18 @@ int orc_cg(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
     }
     double *r = malloc((size_t)n * sizeof(double)), *p = malloc((size_t)n * sizeof(double));
     double *q = malloc((size_t)n * sizeof(double));
+    double *z = dinv ? malloc((size_t)n * sizeof(double)) : NULL; /* z = M^{-1} r */
     int64_t it = 0;
     int status = ORC_MAX_ITER;
     double rel = 0.0, reltrue = 0.0;
     for (int restart = 0;; ++restart) {
         orc_spmv_csr(n, rp, col, val, x, q);
         for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
-        double rho = dot(n, r, r);
-        rel = sqrt(rho) / bnorm;
+        if (dinv)
+            for (int64_t i = 0; i < n; ++i) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
+        double rr = dot(n, r, r);
+        double rho = dinv ? dot(n, r, z) : rr;
+        rel = sqrt(rr) / bnorm;
         if (hist && it == 0) hist[0] = rel;
         status = ORC_MAX_ITER;
         if (rel <= tol) status = ORC_CONVERGED;
@@ -279,17 +284,21 @@ int orc_cg(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
             if (pq == 0.0) { status = ORC_BREAKDOWN; break; }
             double alpha = rho / pq;
             for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
-            double rho1 = dot(n, r, r);
+            double rr1 = dot(n, r, r);
             ++it;
-            rel = sqrt(rho1) / bnorm;
+            rel = sqrt(rr1) / bnorm;
             if (hist) hist[it] = rel;
             if (rel <= tol) { status = ORC_CONVERGED; break; }
+            if (dinv)
+                for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+            double rho1 = dinv ? dot(n, r, z) : rr1;
 #if ORC_MUTANT == 3
             double beta = -rho1 / rho; /* planted: wrong sign */
 #else
             double beta = rho1 / rho;
 #endif
-            for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+            const double *zr = dinv ? z : r;
+            for (int64_t i = 0; i < n; ++i) p[i] = zr[i] + beta * p[i];
             rho = rho1;
         }
         reltrue = true_relres(n, rp, col, val, b, x, bnorm, q);
@@ -301,9 +310,17 @@ int orc_cg(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
     info->iterations = it;
     info->relres_recurrence = rel;
     info->relres_true = reltrue;
-    free(r); free(p); free(q);
+    free(r); free(p); free(q); free(z);
     return 0;
 }
+
+int orc_cg(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+           const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+{
+    return cg_run(n, rp, col, val, b, x, tol, maxit, info, hist, NULL);
+}
+
+
 
 /* ------------------------------------------------------------------------- */
 /* BiCGSTAB (van der Vorst) for general A, shadow residual r^ = r0.          */
@@ -315,9 +332,9 @@ int orc_cg(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
 /*         r = s - omega t; stop if ||r||/||b|| <= tol; rho = rho'            */
 /* Breakdown when rho' = 0, r^.v = 0 or t.t = 0.                             */
 /* ------------------------------------------------------------------------- */
-int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-                 const double *b, double *x, double tol, int64_t maxit, orc_info *info,
-                 double *hist)
+static int bicgstab_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                        const double *b, double *x, double tol, int64_t maxit, orc_info *info,
+                        double *hist, const double *dinv)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -328,6 +345,8 @@ int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double 
     size_t bytes = (size_t)n * sizeof(double);
     double *r = malloc(bytes), *rh = malloc(bytes), *p = malloc(bytes), *v = malloc(bytes);
     double *s = malloc(bytes), *t = malloc(bytes);
+    double *ph = dinv ? malloc(bytes) : NULL, *sh = dinv ? malloc(bytes) : NULL; /* M^{-1} p, M^{-1} s */
+    if (!dinv) { ph = p; sh = s; }
     int64_t it = 0;
     int status = ORC_MAX_ITER;
     double rel = 0.0, reltrue = 0.0;
@@ -343,7 +362,9 @@ int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double 
             if (rho1 == 0.0) { status = ORC_BREAKDOWN; break; }
             double beta = (rho1 / rho) * (alpha / omega);
             for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
-            orc_spmv_csr(n, rp, col, val, p, v);
+            if (dinv)
+                for (int64_t i = 0; i < n; ++i) ph[i] = dinv[i] * p[i];
+            orc_spmv_csr(n, rp, col, val, ph, v);
             double rv = dot(n, rh, v);
             if (rv == 0.0) { status = ORC_BREAKDOWN; break; }
             alpha = rho1 / rv;
@@ -351,21 +372,25 @@ int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double 
             ++it;
             double snorm = nrm2(n, s);
             if (snorm / bnorm <= tol) {
-                for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+                for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i];
                 for (int64_t i = 0; i < n; ++i) r[i] = s[i];
                 rel = snorm / bnorm;
                 if (hist) hist[it] = rel;
                 status = ORC_CONVERGED;
                 break;
             }
-            orc_spmv_csr(n, rp, col, val, s, t);
+            if (dinv)
+                for (int64_t i = 0; i < n; ++i) sh[i] = dinv[i] * s[i];
+            orc_spmv_csr(n, rp, col, val, sh, t);
             double tt = dot(n, t, t);
             if (tt == 0.0) { status = ORC_BREAKDOWN; break; }
             omega = dot(n, t, s) / tt;
 #if ORC_MUTANT == 4
-            for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i] - omega * s[i]; /* planted */
+            for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i] - omega * sh[i]; /* planted */
+#elif ORC_MUTANT == 7
+            for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i] + omega * sh[i]; /* planted: p for M^{-1} p */
 #else
-            for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i] + omega * s[i];
+            for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i] + omega * sh[i];
 #endif
             for (int64_t i = 0; i < n; ++i) r[i] = s[i] - omega * t[i];
             rel = nrm2(n, r) / bnorm;
@@ -383,9 +408,19 @@ int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double 
     info->iterations = it;
     info->relres_recurrence = rel;
     info->relres_true = reltrue;
+    if (dinv) { free(ph); free(sh); }
     free(r); free(rh); free(p); free(v); free(s); free(t);
     return 0;
 }
+
+int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                 const double *b, double *x, double tol, int64_t maxit, orc_info *info,
+                 double *hist)
+{
+    return bicgstab_run(n, rp, col, val, b, x, tol, maxit, info, hist, NULL);
+}
+
+
 
 /* ------------------------------------------------------------------------- */
 /* CGS, Sonneveld's conjugate gradient squared method (the fourth Krylov     */
@@ -396,8 +431,9 @@ int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double 
 /*   beta = (r_new, r^) / (r, r^);  u = r + beta q;  p = u + beta (q + beta p). */
 /* Two SpMVs per iteration.  Breakdown when (A p, r^) or (r, r^) is exactly 0. */
 /* ------------------------------------------------------------------------- */
-int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-            const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+static int cgs_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                   const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist,
+                   const double *dinv)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -408,6 +444,7 @@ int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
     size_t bytes = (size_t)n * sizeof(double);
     double *r = malloc(bytes), *rh = malloc(bytes), *p = malloc(bytes), *u = malloc(bytes);
     double *q = malloc(bytes), *v = malloc(bytes), *w = malloc(bytes);
+    double *ph = dinv ? malloc(bytes) : p;  /* M^{-1} p */
     int64_t it = 0;
     int status = ORC_MAX_ITER;
     double rel = 0.0, reltrue = 0.0;
@@ -420,12 +457,16 @@ int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
         status = rel <= tol ? ORC_CONVERGED : ORC_MAX_ITER;
         while (status == ORC_MAX_ITER && it < maxit) {
             if (rho == 0.0) { status = ORC_BREAKDOWN; break; }
-            orc_spmv_csr(n, rp, col, val, p, v);                       /* v = A p */
+            if (dinv)
+                for (int64_t i = 0; i < n; ++i) ph[i] = dinv[i] * p[i];
+            orc_spmv_csr(n, rp, col, val, ph, v);                      /* v = A M^{-1} p */
             double vr = dot(n, rh, v);
             if (vr == 0.0) { status = ORC_BREAKDOWN; break; }
             double alpha = rho / vr;
             for (int64_t i = 0; i < n; ++i) q[i] = u[i] - alpha * v[i];
             for (int64_t i = 0; i < n; ++i) w[i] = u[i] + q[i];      /* u + q */
+            if (dinv)
+                for (int64_t i = 0; i < n; ++i) w[i] *= dinv[i];      /* M^{-1} (u + q) */
             for (int64_t i = 0; i < n; ++i) x[i] += alpha * w[i];
             orc_spmv_csr(n, rp, col, val, w, v);                       /* A (u + q) */
 #if ORC_MUTANT == 6
@@ -452,9 +493,18 @@ int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
     info->iterations = it;
     info->relres_recurrence = rel;
     info->relres_true = reltrue;
+    if (dinv) free(ph);
     free(r); free(rh); free(p); free(u); free(q); free(v); free(w);
     return 0;
 }
+
+int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+            const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+{
+    return cgs_run(n, rp, col, val, b, x, tol, maxit, info, hist, NULL);
+}
+
+
 
 /* ------------------------------------------------------------------------- */
 /* Restarted GMRES(m) (Saad & Schultz): Arnoldi with modified Gram-Schmidt,  */
@@ -463,9 +513,9 @@ int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
 /* where H_j y_j = g_j is solved by back substitution.  One iteration = one  */
 /* Arnoldi step (one SpMV).                                                  */
 /* ------------------------------------------------------------------------- */
-int orc_gmres(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-              const double *b, double *x, int m, double tol, int64_t maxit, orc_info *info,
-              double *hist)
+static int gmres_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                     const double *b, double *x, int m, double tol, int64_t maxit, orc_info *info,
+                     double *hist, const double *dinv)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -476,6 +526,7 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *col, const double *va
     size_t bytes = (size_t)n * sizeof(double);
     double *V = malloc(bytes * (size_t)(m + 1));
     double *w = malloc(bytes);
+    double *z = dinv ? malloc(bytes) : NULL; /* M^{-1} v_j, and the cycle's update */
     double *H = calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
     double *cs = malloc(sizeof(double) * m), *sn = malloc(sizeof(double) * m);
     double *g = malloc(sizeof(double) * (m + 1)), *yv = malloc(sizeof(double) * m);
@@ -502,7 +553,12 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *col, const double *va
         int j = 0, done = 0;
         for (; j < m && it < maxit; ++j) {
             double *vj = V + (size_t)j * n;
-            orc_spmv_csr(n, rp, col, val, vj, w);
+            if (dinv) {
+                for (int64_t k = 0; k < n; ++k) z[k] = dinv[k] * vj[k];
+                orc_spmv_csr(n, rp, col, val, z, w);   /* w = A M^{-1} v_j */
+            } else {
+                orc_spmv_csr(n, rp, col, val, vj, w);
+            }
             for (int i = 0; i <= j; ++i) {
                 double *vi = V + (size_t)i * n;
                 double h = dot(n, w, vi);
@@ -546,9 +602,18 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *col, const double *va
             for (int k = i + 1; k < j; ++k) s -= H[i * m + k] * yv[k];
             yv[i] = s / H[i * m + i];
         }
-        for (int i = 0; i < j; ++i) {
-            double *vi = V + (size_t)i * n;
-            for (int64_t k = 0; k < n; ++k) x[k] += yv[i] * vi[k];
+        if (dinv) {  /* x += M^{-1} V y */
+            memset(z, 0, bytes);
+            for (int i = 0; i < j; ++i) {
+                double *vi = V + (size_t)i * n;
+                for (int64_t k = 0; k < n; ++k) z[k] += yv[i] * vi[k];
+            }
+            for (int64_t k = 0; k < n; ++k) x[k] += dinv[k] * z[k];
+        } else {
+            for (int i = 0; i < j; ++i) {
+                double *vi = V + (size_t)i * n;
+                for (int64_t k = 0; k < n; ++k) x[k] += yv[i] * vi[k];
+            }
         }
         ++cycles;
         if (done) {
@@ -570,8 +635,73 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *col, const double *va
     info->relres_true = reltrue;
     (void)cycles;
     free(V); free(w); free(H); free(cs); free(sn); free(g); free(yv);
+    free(z);
     return 0;
 }
+
+int orc_gmres(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+              const double *b, double *x, int m, double tol, int64_t maxit, orc_info *info,
+              double *hist)
+{
+    return gmres_run(n, rp, col, val, b, x, m, tol, maxit, info, hist, NULL);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Jacobi preconditioning, M = diag(A) (a zero diagonal entry is taken as 1; */
+/* duplicate diagonal entries are summed in index order).  CG: the textbook  */
+/* preconditioned CG, z = M^{-1} r, convergence on ||r||.  BiCGSTAB, CGS and */
+/* GMRES: right preconditioning, the method runs on A M^{-1} and x gathers  */
+/* M^{-1} times its search directions, so r stays the true residual.        */
+/* ------------------------------------------------------------------------- */
+static double *jacobi_dinv(int64_t n, const int32_t *rp, const int32_t *col, const double *val)
+{
+    double *d = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (col[k] == i) s += val[k];
+        d[i] = s != 0.0 ? 1.0 / s : 1.0;
+    }
+    return d;
+}
+
+int orc_cg_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                  const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+{
+    double *d = jacobi_dinv(n, rp, col, val);
+    int st = cg_run(n, rp, col, val, b, x, tol, maxit, info, hist, d);
+    free(d);
+    return st;
+}
+
+int orc_bicgstab_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                        const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+{
+    double *d = jacobi_dinv(n, rp, col, val);
+    int st = bicgstab_run(n, rp, col, val, b, x, tol, maxit, info, hist, d);
+    free(d);
+    return st;
+}
+
+int orc_cgs_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                   const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
+{
+    double *d = jacobi_dinv(n, rp, col, val);
+    int st = cgs_run(n, rp, col, val, b, x, tol, maxit, info, hist, d);
+    free(d);
+    return st;
+}
+
+int orc_gmres_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                     const double *b, double *x, int m, double tol, int64_t maxit, orc_info *info,
+                     double *hist)
+{
+    double *d = jacobi_dinv(n, rp, col, val);
+    int st = gmres_run(n, rp, col, val, b, x, m, tol, maxit, info, hist, d);
+    free(d);
+    return st;
+}
+
 
 /* ------------------------------------------------------------------------- */
 /* FP32 Krylov for the inner solve of iterative refinement: the same CG and  */
