@@ -283,6 +283,7 @@ def run_gpu(args):
     if not args.no_solve:
         secondary["fixed_iterations"] = fixed_iter_secondary(spx, ctx, stream, dev)
         secondary["vendor_csr_context"] = vendor_secondary(mats, dev)
+        secondary["jacobi"] = jacobi_secondary(spx, ctx, stream, dev)
     if args.batched:
         secondary["batched"] = batched_secondary(spx, ctx, stream, dev)
     if args.serve_seconds > 0:
@@ -400,6 +401,50 @@ def solve_secondary(spx, ctx, stream, dev, peak, fmt="csr"):
                               "frac_of_hbm_peak": round(gbs / peak, 3),
                               "roofline_ms": round(bpi * si.iterations / (peak * 1e9) * 1e3, 2)})
                 res[prec] = r
+            spx.spx_matrix_destroy(A)
+        out[name] = res
+    return out
+
+
+def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
+    """Jacobi preconditioning (M = diag A) against the plain solvers on
+    badly scaled 128^3 matrices, where a diagonal preconditioner matters:
+    the 7-point Poisson matrix scaled symmetrically, S A S with
+    s_i = exp(U[-2, 2]) (CG), and the upwind convection-diffusion matrix
+    (Peclet 10) with rows scaled by exp(U[-3, 3]) (BiCGSTAB, CGS, GMRES(30));
+    b = A x*, tol 1e-10, FP64, CSR.  (On the unscaled benchmark matrices the
+    diagonal is constant and Jacobi changes nothing.)"""
+    import torch
+    from paper_2103_10116_gb300 import synth
+    rng = np.random.default_rng(21)
+
+    def scaled(rp, col, val, rs, cs):
+        rows = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
+        return rp, col, val * rs[rows] * cs[col]
+
+    rp, col, val = synth.laplace3d_7pt(128)
+    sp = np.exp(rng.uniform(-2.0, 2.0, size=rp.shape[0] - 1))
+    poisson = scaled(rp, col, val, sp, sp)
+    rp, col, val = synth.convdiff3d_upwind(128)
+    cdiff = scaled(rp, col, val, np.exp(rng.uniform(-3.0, 3.0, size=rp.shape[0] - 1)), np.ones(rp.shape[0] - 1))
+    out = {}
+    for name, (rp, col, val), solvers in (("poisson128_sym_scaled", poisson, ("cg",)),
+                                          ("convdiff128_row_scaled", cdiff, ("bicgstab", "cgs", "gmres"))):
+        n = rp.shape[0] - 1
+        with torch.cuda.stream(stream):
+            A = spx.spx_matrix_create(ctx, "csr", torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
+                                      torch.from_numpy(val).to(dev))
+            xs = torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, n)).to(dev)
+            b = torch.empty(n, dtype=torch.float64, device=dev)
+            spx.spx_spmv(ctx, A, xs, b)
+            res = {}
+            for solver in solvers:
+                for pc in (None, "jacobi"):
+                    x = torch.zeros(n, dtype=torch.float64, device=dev)
+                    si = spx.spx_solve(ctx, A, b, x, solver, 1e-10, max_iter, restart=30, precond=pc)
+                    res[f"{solver}{'_jacobi' if pc else ''}"] = {
+                        "solve_ms": round(si.time_ms, 2), "iterations": si.iterations, "status": si.status_name,
+                        "relres_true": si.relres_true}
             spx.spx_matrix_destroy(A)
         out[name] = res
     return out

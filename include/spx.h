@@ -51,6 +51,11 @@ typedef enum {
 typedef enum { SPX_CSR = 0, SPX_ELL = 1, SPX_COO = 2, SPX_HYB = 3 } spx_format;
 typedef enum { SPX_F64 = 0, SPX_F32 = 1 } spx_dtype;
 typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2, SPX_CGS = 3 } spx_solver;
+/* OR into the solver argument of spx_solve / spx_solve_fixed / spx_server_submit:
+ * Jacobi preconditioning with M = diag(A) (a zero diagonal entry counts as 1).
+ * CG becomes preconditioned CG; BiCGSTAB, CGS and GMRES are preconditioned from
+ * the right, so the residual they test is always b - A x. */
+#define SPX_PRECOND_JACOBI 0x100
 
 /* Arithmetic of a solve: all FP64; all FP32 (values, vectors, dots and
  * scalars in float); or FP64 iterative refinement around an FP32 inner solve

@@ -42,6 +42,8 @@ enum : int {
     FIN_INIT_BI = 8,    // dots[1] = r.r (r^ = r)     -> initial rho = r^.r = r.r, beta
     FIN_SET_BB = 9,     // dots[0] = b.b              -> ||b||^2 and the absolute threshold
     FIN_CGS_R = 10,     // dots[0] = r.r, dots[1] = r^.r -> convergence, beta = (r^.r)' / (r^.r), rho
+    FIN_PCG_RHO0 = 11,  // dots[0] = r.z (z = M^-1 r)  -> initial rho of preconditioned CG
+    FIN_PCG_R = 12,     // dots[0] = r.r, dots[1] = r.z -> convergence on r, beta = (r.z)' / (r.z), rho
 };
 
 template <class T> __device__ __forceinline__ void kstop(KState<T> *s, int status)
@@ -126,6 +128,23 @@ template <class T> __device__ __forceinline__ void run_fin(int fin, void *state,
         if (rhr == T(0)) { kstop(s, SPX_BREAKDOWN); break; }
         s->beta = (rhr / s->rho) * (s->alpha / s->omega);
         s->rho = rhr;
+        break;
+    }
+    case FIN_PCG_RHO0: {
+        if (s->done) break;
+        if (dots[0] == T(0)) kstop(s, SPX_BREAKDOWN);
+        else s->rho = dots[0];
+        break;
+    }
+    case FIN_PCG_R: {
+        const T rr = dots[0], rz = dots[1];
+        s->iters += 1;
+        s->relres = sqrt(rr / s->bb);
+        if (rr <= s->tol2) { kstop(s, SPX_CONVERGED); break; }
+        if (s->iters >= s->maxit) { kstop(s, SPX_MAX_ITER); break; }
+        if (rz == T(0)) { kstop(s, SPX_BREAKDOWN); break; }
+        s->beta = rz / s->rho;
+        s->rho = rz;
         break;
     }
     case FIN_CGS_R: {

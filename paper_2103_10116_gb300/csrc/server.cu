@@ -372,7 +372,8 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
 {
     if (!S || !row_ptr || !b || !x || !req_id || n <= 0 || nnz < 0 || (nnz > 0 && (!col_idx || !values)))
         return fail(SPX_ERR_INVALID, "spx_server_submit: bad argument");
-    if (solver < SPX_CG || solver > SPX_CGS) return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
+    const int base_solver = solver & ~SPX_PRECOND_JACOBI;
+    if (base_solver < SPX_CG || base_solver > SPX_CGS) return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
     Request *R = new Request();
     R->n = n;
     R->nnz = nnz;
@@ -386,7 +387,8 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     R->restart = restart;
     R->tol = tol;
     R->max_iter = max_iter;
-    R->footprint = request_footprint(n, nnz, solver, precision, restart);
+    R->footprint = request_footprint(n, nnz, base_solver, precision, restart) +
+                   ((solver & SPX_PRECOND_JACOBI) ? (size_t)n * 24 : 0);  // M^-1 and the preconditioned vectors
     R->error = SPX_OK;
     R->t_submit = Clock::now();
     R->block = batch_block_for(n);
@@ -397,7 +399,7 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     {
         std::lock_guard<std::mutex> lk(S->mu);
         R->id = S->next_id++;
-        R->batched = (solver == SPX_CG || solver == SPX_BICGSTAB) &&
+        R->batched = (solver == SPX_CG || solver == SPX_BICGSTAB) &&  // plain CG / BiCGSTAB only
                      (precision == SPX_PREC_F64 || precision == SPX_PREC_MIXED) && n <= S->batch_rows;
         (R->batched ? S->bqueue : S->queue).push_back(R);
     }

@@ -71,13 +71,16 @@ struct SolverWork {
     // mixed precision
     SolverWork *inner = nullptr;
     DBuf ir;  // r (FP64), r32, d32
+    // Jacobi preconditioning: M^{-1} = 1 / diag(A) in the work's precision
+    bool pre = false;
+    DBuf dinv;
 };
 
 void solver_work_release(spx_ctx *ctx, SolverWork *w)
 {
     if (!w) return;
     if (w->gexec) cudaGraphExecDestroy(w->gexec);
-    DBuf *bufs[] = {&w->vecs, &w->state, &w->dots, &w->red, &w->ticket, &w->small, &w->ir};
+    DBuf *bufs[] = {&w->vecs, &w->state, &w->dots, &w->red, &w->ticket, &w->small, &w->ir, &w->dinv};
     for (DBuf *b : bufs) dbuf_free(ctx, *b);
     if (w->host) cudaFreeHost(w->host);
     solver_work_release(ctx, w->inner);
@@ -93,19 +96,19 @@ void solver_work_free(spx_matrix *A)
     A->work = nullptr;
 }
 
-static int nvec_for(int solver, int m)
+static int nvec_for(int solver, int m, bool pre)
 {
-    if (solver == SPX_CG) return 4;        // r, p, q, scratch
-    if (solver == SPX_BICGSTAB) return 7;  // r, rh, p, v, s, t, scratch
-    if (solver == SPX_CGS) return 8;       // r, rh, p, u, q, v, w, scratch
-    return m + 2;                          // V[0..m], scratch
+    if (solver == SPX_CG) return 4;                   // r, p, q, scratch (z = M^-1 r is never stored)
+    if (solver == SPX_BICGSTAB) return pre ? 9 : 7;   // r, rh, p, v, s, t, scratch (+ M^-1 p, M^-1 s)
+    if (solver == SPX_CGS) return pre ? 9 : 8;        // r, rh, p, u, q, v, w, scratch (+ M^-1 p)
+    return m + (pre ? 3 : 2);                         // V[0..m], scratch (+ M^-1 v_j)
 }
 
 template <class T>
-static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, int m)
+static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, int m, bool pre = false)
 {
     const int dtype = sizeof(T) == 8 ? SPX_F64 : SPX_F32;
-    if (wk && (wk->dtype != dtype || wk->n != n || wk->solver != solver || wk->m != m)) {
+    if (wk && (wk->dtype != dtype || wk->n != n || wk->solver != solver || wk->m != m || wk->pre != pre)) {
         SolverWork *inner = wk->inner;
         wk->inner = nullptr;
         cudaStreamSynchronize(ctx->stream);
@@ -122,8 +125,9 @@ static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, in
     wk->n = n;
     wk->solver = solver;
     wk->m = m;
+    wk->pre = pre;
     wk->ld = (int64_t)round_up((size_t)(n > 0 ? n : 1), 64);
-    wk->nvec = nvec_for(solver, m);
+    wk->nvec = nvec_for(solver, m, pre);
     SPX_TRY(dbuf_alloc(ctx, wk->vecs, (size_t)wk->nvec * wk->ld * sizeof(T)));
     SPX_TRY(dbuf_alloc(ctx, wk->state, 512));
     SPX_TRY(dbuf_alloc(ctx, wk->dots, 64));
@@ -178,94 +182,125 @@ __global__ void __launch_bounds__(kVB)
     grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, fin, st, partials, ticket);
 }
 
-// CG: x += alpha p; r -= alpha q; rho' = r.r
-template <class T>
+// CG: x += alpha p; r -= alpha q; rho' = r.r.  PRE (Jacobi): also r.z with
+// z = dinv r, for beta; convergence is tested on r.r either way.
+template <class T, bool PRE>
 __global__ void __launch_bounds__(kVB)
     k_cg_xr(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ q,
-            KState<T> *st, T *partials, unsigned *ticket)
+            const T *__restrict__ dinv, KState<T> *st, T *partials, unsigned *ticket)
 {
     if (st->done) return;
     const T alpha = st->alpha;
-    T d0 = T(0);
-    T xv[kU], rv[kU], pv[kU], qv[kU];
-    SPX_ROWS_LOOP(xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i];,
+    T d0 = T(0), d1 = T(0);
+    T xv[kU], rv[kU], pv[kU], qv[kU], dv[kU];
+    SPX_ROWS_LOOP(xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i]; if (PRE) dv[u] = dinv[i];,
                   x[i] = fma(alpha, pv[u], xv[u]); const T ri = fma(-alpha, qv[u], rv[u]); r[i] = ri;
-                  d0 = fma(ri, ri, d0);)
-    grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, FIN_CG_RHO, st, partials, ticket);
+                  d0 = fma(ri, ri, d0); if (PRE) d1 = fma(ri, dv[u] * ri, d1);)
+    grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, PRE ? FIN_PCG_R : FIN_CG_RHO, st, partials, ticket);
 }
 
-// CG: p = r + beta p
-template <class T>
-__global__ void __launch_bounds__(kVB) k_cg_p(int64_t n, const T *__restrict__ r, T *__restrict__ p, const KState<T> *st)
+// CG: p = r + beta p  (PRE: p = dinv r + beta p)
+template <class T, bool PRE>
+__global__ void __launch_bounds__(kVB)
+    k_cg_p(int64_t n, const T *__restrict__ r, T *__restrict__ p, const T *__restrict__ dinv, const KState<T> *st)
 {
     if (st->done) return;
     const T beta = st->beta;
-    T rv[kU], pv[kU];
-    SPX_ROWS_LOOP(rv[u] = r[i]; pv[u] = p[i];, p[i] = fma(beta, pv[u], rv[u]);)
+    T rv[kU], pv[kU], dv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; pv[u] = p[i]; if (PRE) dv[u] = dinv[i];,
+                  p[i] = fma(beta, pv[u], PRE ? dv[u] * rv[u] : rv[u]);)
 }
 
-// BiCGSTAB: p = r + beta (p - omega v)
+// Preconditioned CG start: p = z = dinv r; rho = r.z
 template <class T>
 __global__ void __launch_bounds__(kVB)
-    k_bi_p(int64_t n, const T *__restrict__ r, T *__restrict__ p, const T *__restrict__ v, const KState<T> *st)
+    k_pcg_init(int64_t n, const T *__restrict__ r, T *__restrict__ p, const T *__restrict__ dinv, KState<T> *st,
+               T *partials, unsigned *ticket)
+{
+    if (st->done) return;
+    T d0 = T(0);
+    T rv[kU], dv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; dv[u] = dinv[i];, const T zi = dv[u] * rv[u]; p[i] = zi; d0 = fma(rv[u], zi, d0);)
+    grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, FIN_PCG_RHO0, st, partials, ticket);
+}
+
+// out = dinv in (M^-1 applied to a vector)
+template <class T>
+__global__ void __launch_bounds__(kVB)
+    k_jscale(int64_t n, const T *__restrict__ in, const T *__restrict__ dinv, T *__restrict__ out, const KState<T> *st)
+{
+    if (st && st->done) return;
+    T iv[kU], dv[kU];
+    SPX_ROWS_LOOP(iv[u] = in[i]; dv[u] = dinv[i];, out[i] = dv[u] * iv[u];)
+}
+
+// BiCGSTAB: p = r + beta (p - omega v)  (PRE: also ph = dinv p)
+template <class T, bool PRE>
+__global__ void __launch_bounds__(kVB)
+    k_bi_p(int64_t n, const T *__restrict__ r, T *__restrict__ p, const T *__restrict__ v, T *__restrict__ ph,
+           const T *__restrict__ dinv, const KState<T> *st)
 {
     if (st->done) return;
     const T beta = st->beta, omega = st->omega;
-    T rv[kU], pv[kU], vv[kU];
-    SPX_ROWS_LOOP(rv[u] = r[i]; pv[u] = p[i]; vv[u] = v[i];, p[i] = fma(beta, fma(-omega, vv[u], pv[u]), rv[u]);)
+    T rv[kU], pv[kU], vv[kU], dv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; pv[u] = p[i]; vv[u] = v[i]; if (PRE) dv[u] = dinv[i];,
+                  const T pi = fma(beta, fma(-omega, vv[u], pv[u]), rv[u]); p[i] = pi; if (PRE) ph[i] = dv[u] * pi;)
 }
 
-// BiCGSTAB: s = r - alpha v; s.s
-template <class T>
+// BiCGSTAB: s = r - alpha v; s.s  (PRE: also sh = dinv s)
+template <class T, bool PRE>
 __global__ void __launch_bounds__(kVB)
-    k_bi_s(int64_t n, const T *__restrict__ r, const T *__restrict__ v, T *__restrict__ s, KState<T> *st,
-           T *partials, unsigned *ticket)
+    k_bi_s(int64_t n, const T *__restrict__ r, const T *__restrict__ v, T *__restrict__ s, T *__restrict__ sh,
+           const T *__restrict__ dinv, KState<T> *st, T *partials, unsigned *ticket)
 {
     if (st->done) return;
     const T alpha = st->alpha;
     T d0 = T(0);
-    T rv[kU], vv[kU];
-    SPX_ROWS_LOOP(rv[u] = r[i]; vv[u] = v[i];, const T si = fma(-alpha, vv[u], rv[u]); s[i] = si;
+    T rv[kU], vv[kU], dv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; vv[u] = v[i]; if (PRE) dv[u] = dinv[i];,
+                  const T si = fma(-alpha, vv[u], rv[u]); s[i] = si; if (PRE) sh[i] = dv[u] * si;
                   d0 = fma(si, si, d0);)
     grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, FIN_BI_S, st, partials, ticket);
 }
 
 // BiCGSTAB: x += alpha p + omega s; r = s - omega t  (or, converged on s:
-// x += alpha p; r = s); dots r.r and r^.r
+// x += alpha p; r = s); dots r.r and r^.r.  Right preconditioning: the x
+// update takes M^-1 p and M^-1 s (pp, ss point at those or at p, s).
 template <class T>
 __global__ void __launch_bounds__(kVB)
-    k_bi_xr(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ rh, const T *__restrict__ p,
-            const T *__restrict__ s, const T *__restrict__ t, KState<T> *st, T *partials, unsigned *ticket)
+    k_bi_xr(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ rh, const T *__restrict__ pp,
+            const T *__restrict__ s, const T *__restrict__ ss, const T *__restrict__ t, KState<T> *st, T *partials,
+            unsigned *ticket)
 {
     if (st->done) return;
     const T alpha = st->alpha, omega = st->omega;
     const bool sconv = st->s_conv != 0;
     T d0 = T(0), d1 = T(0);
-    T xv[kU], pv[kU], sv[kU], tv[kU], hv[kU];
+    T xv[kU], pv[kU], sv[kU], qv[kU], tv[kU], hv[kU];
     if (sconv) {
-        SPX_ROWS_LOOP(xv[u] = x[i]; pv[u] = p[i]; sv[u] = s[i]; hv[u] = rh[i];,
+        SPX_ROWS_LOOP(xv[u] = x[i]; pv[u] = pp[i]; sv[u] = s[i]; hv[u] = rh[i];,
                       x[i] = fma(alpha, pv[u], xv[u]); const T ri = sv[u]; r[i] = ri; d0 = fma(ri, ri, d0);
                       d1 = fma(hv[u], ri, d1);)
     } else {
-        SPX_ROWS_LOOP(xv[u] = x[i]; pv[u] = p[i]; sv[u] = s[i]; tv[u] = t[i]; hv[u] = rh[i];,
-                      x[i] = fma(omega, sv[u], fma(alpha, pv[u], xv[u])); const T ri = fma(-omega, tv[u], sv[u]);
+        SPX_ROWS_LOOP(xv[u] = x[i]; pv[u] = pp[i]; sv[u] = s[i]; qv[u] = ss[i]; tv[u] = t[i]; hv[u] = rh[i];,
+                      x[i] = fma(omega, qv[u], fma(alpha, pv[u], xv[u])); const T ri = fma(-omega, tv[u], sv[u]);
                       r[i] = ri; d0 = fma(ri, ri, d0); d1 = fma(hv[u], ri, d1);)
     }
     grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, FIN_BI_R, st, partials, ticket);
 }
 
-// CGS: q = u - alpha v; w = u + q; x += alpha w
-template <class T>
+// CGS: q = u - alpha v; w = u + q (PRE: w = dinv (u + q)); x += alpha w
+template <class T, bool PRE>
 __global__ void __launch_bounds__(kVB)
     k_cgs_qw(int64_t n, T *__restrict__ x, const T *__restrict__ uu, const T *__restrict__ v, T *__restrict__ q,
-             T *__restrict__ w, const KState<T> *st)
+             T *__restrict__ w, const T *__restrict__ dinv, const KState<T> *st)
 {
     if (st->done) return;
     const T alpha = st->alpha;
-    T xv[kU], uv[kU], vv[kU];
-    SPX_ROWS_LOOP(xv[u] = x[i]; uv[u] = uu[i]; vv[u] = v[i];,
-                  const T qi = fma(-alpha, vv[u], uv[u]); q[i] = qi; const T wi = uv[u] + qi; w[i] = wi;
-                  x[i] = fma(alpha, wi, xv[u]);)
+    T xv[kU], uv[kU], vv[kU], dv[kU];
+    SPX_ROWS_LOOP(xv[u] = x[i]; uv[u] = uu[i]; vv[u] = v[i]; if (PRE) dv[u] = dinv[i];,
+                  const T qi = fma(-alpha, vv[u], uv[u]); q[i] = qi; const T wi = PRE ? dv[u] * (uv[u] + qi) : uv[u] + qi;
+                  w[i] = wi; x[i] = fma(alpha, wi, xv[u]);)
 }
 
 // CGS: r -= alpha v (v = A w); dots r.r and r^.r
@@ -283,17 +318,48 @@ __global__ void __launch_bounds__(kVB)
     grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, FIN_CGS_R, st, partials, ticket);
 }
 
-// CGS: u = r + beta q; p = u + beta (q + beta p)
-template <class T>
+// CGS: u = r + beta q; p = u + beta (q + beta p)  (PRE: also ph = dinv p)
+template <class T, bool PRE>
 __global__ void __launch_bounds__(kVB)
     k_cgs_up(int64_t n, const T *__restrict__ r, const T *__restrict__ q, T *__restrict__ uu, T *__restrict__ p,
-             const KState<T> *st)
+             T *__restrict__ ph, const T *__restrict__ dinv, const KState<T> *st)
 {
     if (st->done) return;
     const T beta = st->beta;
-    T rv[kU], qv[kU], pv[kU];
-    SPX_ROWS_LOOP(rv[u] = r[i]; qv[u] = q[i]; pv[u] = p[i];,
-                  const T ui = fma(beta, qv[u], rv[u]); uu[i] = ui; p[i] = fma(beta, fma(beta, pv[u], qv[u]), ui);)
+    T rv[kU], qv[kU], pv[kU], dv[kU];
+    SPX_ROWS_LOOP(rv[u] = r[i]; qv[u] = q[i]; pv[u] = p[i]; if (PRE) dv[u] = dinv[i];,
+                  const T ui = fma(beta, qv[u], rv[u]); uu[i] = ui; const T pi = fma(beta, fma(beta, pv[u], qv[u]), ui);
+                  p[i] = pi; if (PRE) ph[i] = dv[u] * pi;)
+}
+
+// the inverse diagonal, 1 / sum of the diagonal entries of row i in CSR order
+// (1 where that sum is 0), from whichever storage the matrix holds: CSR
+// arrays, or the ELL slots and then the COO entries of the row (HYB, COO)
+template <class V, class T>
+__global__ void k_jacobi_dinv(int64_t n, const int *__restrict__ rp, const int *__restrict__ col,
+                              const V *__restrict__ val, int64_t ell_ld, int64_t ell_w, const int *__restrict__ ecol,
+                              const V *__restrict__ evals, int64_t coo_nnz, const int *__restrict__ crow,
+                              const int *__restrict__ ccol, const V *__restrict__ cval, T *__restrict__ dinv)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        if (rp)
+            for (int k = rp[i]; k < rp[i + 1]; ++k)
+                if (col[k] == i) d += (double)val[k];
+        for (int64_t j = 0; j < ell_w; ++j)
+            if (ecol[j * ell_ld + i] == i) d += (double)evals[j * ell_ld + i];
+        if (coo_nnz > 0) {  // first entry of row i: rows are sorted
+            int64_t lo = 0, hi = coo_nnz;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (crow[mid] < i) lo = mid + 1;
+                else hi = mid;
+            }
+            for (int64_t k = lo; k < coo_nnz && crow[k] == i; ++k)
+                if (ccol[k] == i) d += (double)cval[k];
+        }
+        dinv[i] = d != 0.0 ? (T)(1.0 / d) : T(1);
+    }
 }
 
 // ------------------------------------------------------------------ GMRES kernels
@@ -548,15 +614,24 @@ __global__ void __launch_bounds__(kVB)
     if (threadIdx.x == 0) gm_finish_column<T>(gs, sm, j, s);
 }
 
-// v_{j+1} = w / ||w||
+// v_{j+1} = w / ||w||  (Jacobi, right: also z = dinv v_{j+1}, the next SpMV's input)
 template <class T>
-__global__ void __launch_bounds__(kVB) k_gm_scale(int64_t n, int64_t ld, T *__restrict__ V, int j, const GState<T> *gs, GSmall<T> sm)
+__global__ void __launch_bounds__(kVB) k_gm_scale(int64_t n, int64_t ld, T *__restrict__ V, int j, const GState<T> *gs,
+                                                  GSmall<T> sm, const T *__restrict__ dinv, T *__restrict__ z)
 {
     // v_{j+1} is needed only while the cycle goes on
     if (gs->skip || gs->cyc_stop || gs->jdone != j + 1) return;
     const T inv = T(1) / ldcg(sm.h1 + kGmKmax);
     T *w = V + (int64_t)(j + 1) * ld;
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) w[i] *= inv;
+    if (dinv) {
+        for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+            const T vi = w[i] * inv;
+            w[i] = vi;
+            z[i] = dinv[i] * vi;
+        }
+    } else {
+        for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) w[i] *= inv;
+    }
 }
 
 // End of a cycle: y = H^{-1} g by back substitution (one thread; m <= 32)
@@ -571,10 +646,11 @@ template <class T> __global__ void k_gm_solve(GState<T> *gs, GSmall<T> sm)
     }
 }
 
-// x += sum_k y_k v_k
+// x += sum_k y_k v_k  (Jacobi, right: x += dinv sum_k y_k v_k)
 template <class T>
 __global__ void __launch_bounds__(kVB)
-    k_gm_update(int64_t n, int64_t ld, const T *__restrict__ V, T *__restrict__ x, const GState<T> *gs, GSmall<T> sm)
+    k_gm_update(int64_t n, int64_t ld, const T *__restrict__ V, T *__restrict__ x, const GState<T> *gs, GSmall<T> sm,
+                const T *__restrict__ dinv)
 {
     if (gs->done) return;
     const int jn = gs->jdone;
@@ -583,18 +659,27 @@ __global__ void __launch_bounds__(kVB)
     if (threadIdx.x < kGmKmax) ys[threadIdx.x] = threadIdx.x < jn ? ldcg(sm.y + threadIdx.x) : T(0);
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        T xi = x[i];
+        if (dinv) {
+            T ui = T(0);
 #pragma unroll
-        for (int k = 0; k < kGmKmax; ++k)
-            if (k < jn) xi = fma(ys[k], V[(int64_t)k * ld + i], xi);
-        x[i] = xi;
+            for (int k = 0; k < kGmKmax; ++k)
+                if (k < jn) ui = fma(ys[k], V[(int64_t)k * ld + i], ui);
+            x[i] = fma(dinv[i], ui, x[i]);
+        } else {
+            T xi = x[i];
+#pragma unroll
+            for (int k = 0; k < kGmKmax; ++k)
+                if (k < jn) xi = fma(ys[k], V[(int64_t)k * ld + i], xi);
+            x[i] = xi;
+        }
     }
 }
 
 // Start of a cycle: V[0] holds r = b - A x and dots[1] = r.r (SpMV epilogue).
 // Decide convergence on the TRUE residual, else v_0 = r / ||r||, g = ||r|| e_1.
 template <class T>
-__global__ void __launch_bounds__(kVB) k_gm_start(int64_t n, T *__restrict__ v0, const T *dots, GState<T> *gs, GSmall<T> sm)
+__global__ void __launch_bounds__(kVB) k_gm_start(int64_t n, T *__restrict__ v0, const T *dots, GState<T> *gs, GSmall<T> sm,
+                                                  const T *__restrict__ dinv, T *__restrict__ z)
 {
     if (gs->done) return;
     const T rr = ldcg(dots + 1);
@@ -613,7 +698,11 @@ __global__ void __launch_bounds__(kVB) k_gm_start(int64_t n, T *__restrict__ v0,
         return;
     }
     const T inv = T(1) / beta;
-    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) v0[i] *= inv;
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
+        const T vi = v0[i] * inv;
+        v0[i] = vi;
+        if (dinv) z[i] = dinv[i] * vi;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (gs->est_conv) gs->restarts += 1;
         gs->beta = beta;
@@ -708,11 +797,13 @@ template <class T> struct KrylovRun {
 };
 
 // One CG iteration: q = A p (+ p.q -> alpha); x, r update (+ r.r -> beta); p update.
+// Jacobi: beta from r.z and p = z + beta p with z = dinv r (preconditioned CG).
 template <class T> int cg_iter(KrylovRun<T> &R)
 {
     SolverWork *w = R.w;
     KState<T> *st = w->state.as<KState<T>>();
     T *r = vec<T>(w, 0), *p = vec<T>(w, 1), *q = vec<T>(w, 2);
+    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
     const int64_t n = R.A->n;
     Epi<T> e = epi_plain(q);
     e.w = p;
@@ -724,31 +815,42 @@ template <class T> int cg_iter(KrylovRun<T> &R)
     const int g = vgrid(R.ctx, n);
     T *part = w->red.as<T>();
     unsigned *tk = w->ticket.as<unsigned>();
-    k_cg_xr<T><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, st, part, tk);
-    k_cg_p<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, st);
+    if (dinv) {
+        k_cg_xr<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, dinv, st, part, tk);
+        k_cg_p<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, dinv, st);
+    } else {
+        k_cg_xr<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, dinv, st, part, tk);
+        k_cg_p<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, dinv, st);
+    }
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
 
+// One BiCGSTAB iteration.  Jacobi (right): the SpMVs take ph = dinv p and
+// sh = dinv s, and x is updated with them.
 template <class T> int bi_iter(KrylovRun<T> &R)
 {
     SolverWork *w = R.w;
     KState<T> *st = w->state.as<KState<T>>();
     T *r = vec<T>(w, 0), *rh = vec<T>(w, 1), *p = vec<T>(w, 2), *v = vec<T>(w, 3), *s = vec<T>(w, 4),
       *t = vec<T>(w, 5);
+    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
+    T *ph = dinv ? vec<T>(w, 6) : p, *sh = dinv ? vec<T>(w, 7) : s;
     const int64_t n = R.A->n;
     const int g = vgrid(R.ctx, n);
     T *part = w->red.as<T>();
     unsigned *tk = w->ticket.as<unsigned>();
-    k_bi_p<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, v, st);
+    if (dinv) k_bi_p<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, v, ph, dinv, st);
+    else k_bi_p<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, v, ph, dinv, st);
     Epi<T> e = epi_plain(v);
     e.w = rh;
     e.dots = w->dots.as<T>();
     e.fin = FIN_BI_RV;
     e.fin_state = st;
     e.skip = &st->done;
-    SPX_TRY(spmv_launch<T>(R.ctx, R.A, p, e, R.use32));
-    k_bi_s<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, v, s, st, part, tk);
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, ph, e, R.use32));
+    if (dinv) k_bi_s<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, v, s, sh, dinv, st, part, tk);
+    else k_bi_s<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, v, s, sh, dinv, st, part, tk);
     Epi<T> e2 = epi_plain(t);
     e2.w = s;
     e2.want_yy = true;
@@ -756,20 +858,23 @@ template <class T> int bi_iter(KrylovRun<T> &R)
     e2.fin = FIN_BI_OMEGA;
     e2.fin_state = st;
     e2.skip = &st->skip_t;
-    SPX_TRY(spmv_launch<T>(R.ctx, R.A, s, e2, R.use32));
-    k_bi_xr<T><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, rh, p, s, t, st, part, tk);
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, sh, e2, R.use32));
+    k_bi_xr<T><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, rh, ph, s, sh, t, st, part, tk);
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
 
 // One CGS iteration: v = A p (+ r^.v -> alpha); q, w = u + q, x; v = A w;
-// r update (+ r.r, r^.r -> convergence, beta); u, p updates.
+// r update (+ r.r, r^.r -> convergence, beta); u, p updates.  Jacobi
+// (right): the first SpMV takes ph = dinv p, and w = dinv (u + q).
 template <class T> int cgs_iter(KrylovRun<T> &R)
 {
     SolverWork *w = R.w;
     KState<T> *st = w->state.as<KState<T>>();
     T *r = vec<T>(w, 0), *rh = vec<T>(w, 1), *p = vec<T>(w, 2), *u = vec<T>(w, 3), *q = vec<T>(w, 4),
       *v = vec<T>(w, 5), *ww = vec<T>(w, 6);
+    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
+    T *ph = dinv ? vec<T>(w, 7) : p;
     const int64_t n = R.A->n;
     const int g = vgrid(R.ctx, n);
     T *part = w->red.as<T>();
@@ -780,13 +885,15 @@ template <class T> int cgs_iter(KrylovRun<T> &R)
     e.fin = FIN_BI_RV;  // alpha = rho / (r^.v), breakdown on 0
     e.fin_state = st;
     e.skip = &st->done;
-    SPX_TRY(spmv_launch<T>(R.ctx, R.A, p, e, R.use32));
-    k_cgs_qw<T><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, st);
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, ph, e, R.use32));
+    if (dinv) k_cgs_qw<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, dinv, st);
+    else k_cgs_qw<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, dinv, st);
     Epi<T> e2 = epi_plain(v);
     e2.skip = &st->done;
     SPX_TRY(spmv_launch<T>(R.ctx, R.A, ww, e2, R.use32));
     k_cgs_r<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, rh, v, st, part, tk);
-    k_cgs_up<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, q, u, p, st);
+    if (dinv) k_cgs_up<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, q, u, p, ph, dinv, st);
+    else k_cgs_up<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, q, u, p, ph, dinv, st);
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
@@ -819,6 +926,41 @@ template <class T> int krylov_init(KrylovRun<T> &R)
         SPX_CUDA(cudaMemsetAsync(vec<T>(w, 2), 0, bytes, R.ctx->stream));                        // p
         SPX_CUDA(cudaMemsetAsync(vec<T>(w, 3), 0, bytes, R.ctx->stream));                        // v
     }
+    if (w->pre) {
+        KState<T> *st = w->state.as<KState<T>>();
+        const int g = vgrid(R.ctx, n);
+        const T *dinv = w->dinv.as<T>();
+        if (R.solver == SPX_CG)  // p = z = dinv r, rho = r.z
+            k_pcg_init<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, vec<T>(w, 1), dinv, st, w->red.as<T>(),
+                                                       w->ticket.as<unsigned>());
+        else if (R.solver == SPX_CGS)  // ph = dinv p
+            k_jscale<T><<<g, kVB, 0, R.ctx->stream>>>(n, vec<T>(w, 2), dinv, vec<T>(w, 7), st);
+        SPX_CUDA(cudaGetLastError());
+    }
+    return SPX_OK;
+}
+
+// M^{-1} = 1 / diag(A) for a Jacobi-preconditioned solve, in the work's precision
+template <class T> int ensure_dinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
+{
+    if (!w->pre || w->dinv.p) return SPX_OK;
+    const int64_t n = A->n;
+    SPX_TRY(dbuf_alloc(ctx, w->dinv, (size_t)(n > 0 ? n : 1) * sizeof(T)));
+    const int g = (int)std::min<int64_t>(ceil_div(n > 0 ? n : 1, 256), (int64_t)ctx->sm_count * 16);
+    const bool csr = A->format == SPX_CSR;
+    const int64_t ew = (A->format == SPX_ELL || A->format == SPX_HYB) ? A->ell_w : 0;
+    const int64_t cn = (A->format == SPX_COO || A->format == SPX_HYB) ? A->coo_nnz : 0;
+    if (A->dtype == SPX_F64)
+        k_jacobi_dinv<double, T><<<g, 256, 0, ctx->stream>>>(
+            n, csr ? A->rp.as<int>() : nullptr, A->col.as<int>(), A->val.as<double>(), A->ell_ld, ew,
+            A->ell_col.as<int>(), A->ell_val.as<double>(), cn, A->coo_row.as<int>(), A->coo_col.as<int>(),
+            A->coo_val.as<double>(), w->dinv.as<T>());
+    else
+        k_jacobi_dinv<float, T><<<g, 256, 0, ctx->stream>>>(
+            n, csr ? A->rp.as<int>() : nullptr, A->col.as<int>(), A->val.as<float>(), A->ell_ld, ew,
+            A->ell_col.as<int>(), A->ell_val.as<float>(), cn, A->coo_row.as<int>(), A->coo_col.as<int>(),
+            A->coo_val.as<float>(), w->dinv.as<T>());
+    SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
 
@@ -902,7 +1044,7 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
         int64_t launched = 0;
         while (!h->done) {
             const uint64_t key[8] = {(uint64_t)solver, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
-                                     (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T),
+                                     (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8),
                                      (uint64_t)(uintptr_t)A, 0};
             SPX_TRY(run_chunk(ctx, w, key, graphs, [&]() -> int {
                 for (int c = 0; c < chunk; ++c)
@@ -939,6 +1081,8 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
 {
     const int64_t n = A->n, ld = w->ld;
     T *V = w->vecs.as<T>();
+    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
+    T *Z = w->pre ? V + (int64_t)(m + 2) * ld : nullptr;  // M^{-1} v_j (right preconditioning)
     GState<T> *gs = w->state.as<GState<T>>();
     GSmall<T> sm;
     T *base = w->small.as<T>();
@@ -992,20 +1136,20 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
         e.dots = dots;
         e.skip = &gs->done;
         SPX_TRY(spmv_launch<T>(ctx, A, x, e, use32));
-        k_gm_start<T><<<g, kVB, 0, ctx->stream>>>(n, V, dots, gs, sm);
+        k_gm_start<T><<<g, kVB, 0, ctx->stream>>>(n, V, dots, gs, sm, dinv, Z);
         for (int j = 0; j < m; ++j) {
             Epi<T> ea = epi_plain(V + (int64_t)(j + 1) * ld);
             ea.skip = &gs->skip;
             ea.want_yy = true;  // ||A v_j||^2 -> dots[1], for the reorthogonalisation test
             ea.dots = dots;
-            SPX_TRY(spmv_launch<T>(ctx, A, V + (int64_t)j * ld, ea, use32));
+            SPX_TRY(spmv_launch<T>(ctx, A, dinv ? Z : V + (int64_t)j * ld, ea, use32));  // A v_j or A M^-1 v_j
             k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk);
             k_gm_upd_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dots, part, tk);
             k_gm_upd2<T><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
-            k_gm_scale<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm);
+            k_gm_scale<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dinv, Z);
         }
         k_gm_solve<T><<<1, 32, 0, ctx->stream>>>(gs, sm);
-        k_gm_update<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, x, gs, sm);
+        k_gm_update<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, x, gs, sm, dinv);
         SPX_CUDA(cudaGetLastError());
         return SPX_OK;
     };
@@ -1013,7 +1157,8 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
     int64_t cycles = 0;
     for (;;) {
         const uint64_t key[8] = {(uint64_t)SPX_GMRES, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
-                                 (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T), (uint64_t)(uintptr_t)A, 1};
+                                 (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8),
+                                 (uint64_t)(uintptr_t)A, 1};
         SPX_TRY(run_chunk(ctx, w, key, n >= kGraphMinRows, cycle));
         SPX_TRY(read_state<T>(ctx, w, sizeof(GState<T>)));
         ++cycles;
@@ -1050,12 +1195,13 @@ __global__ void k_ir_update(int64_t n, double *__restrict__ x, const float *__re
 }
 
 int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, double tol, int64_t maxit,
-           int m, spx_solve_info *info)
+           int m, bool pre, spx_solve_info *info)
 {
     const int64_t n = A->n;
     SolverWork *&w = A->work;
     SPX_TRY(work_prepare<double>(ctx, w, n, SPX_CG, 0));  // outer: r and scratch only
-    SPX_TRY(work_prepare<float>(ctx, w->inner, n, solver, solver == SPX_GMRES ? m : 0));
+    SPX_TRY(work_prepare<float>(ctx, w->inner, n, solver, solver == SPX_GMRES ? m : 0, pre));
+    SPX_TRY(ensure_dinv<float>(ctx, A, w->inner));
     if (!w->ir.p) SPX_TRY(dbuf_alloc(ctx, w->ir, (size_t)n * 8 + 2 * (size_t)round_up(n, 64) * 4 + 256));
     double *r = w->ir.as<double>();
     float *r32 = reinterpret_cast<float *>(w->ir.as<char>() + round_up((size_t)n * 8, 256));
@@ -1124,9 +1270,10 @@ int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, 
 
 template <class T>
 int solve_typed(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, int solver, double tol, int64_t maxit, int m,
-                bool use32, int64_t fixed, spx_solve_info *info)
+                bool use32, int64_t fixed, bool pre, spx_solve_info *info)
 {
-    SPX_TRY(work_prepare<T>(ctx, A->work, A->n, solver, solver == SPX_GMRES ? m : 0));
+    SPX_TRY(work_prepare<T>(ctx, A->work, A->n, solver, solver == SPX_GMRES ? m : 0, pre));
+    SPX_TRY(ensure_dinv<T>(ctx, A, A->work));
     if (solver == SPX_GMRES) return run_gmres<T>(ctx, A, A->work, b, x, tol, maxit, m, use32, false, fixed, info);
     return run_short<T>(ctx, A, A->work, solver, b, x, tol, maxit, use32, false, fixed, info);
 }
@@ -1138,6 +1285,8 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
         return fail(SPX_ERR_INVALID, "spx_solve: NULL argument");
     std::memset(info, 0, sizeof(*info));
     if (A->n != A->ncols) return fail(SPX_ERR_INVALID, "spx_solve: the matrix must be square");
+    const bool pre = (solver & SPX_PRECOND_JACOBI) != 0;
+    solver &= ~SPX_PRECOND_JACOBI;
     if (solver < SPX_CG || solver > SPX_CGS) return fail(SPX_ERR_INVALID, "spx_solve: unknown solver");
     if (!(tol >= 0.0) || maxit < 0) return fail(SPX_ERR_INVALID, "spx_solve: bad tol or max_iter");
     if (solver == SPX_GMRES && (restart < 1 || restart > kGmKmax - 1))
@@ -1152,15 +1301,16 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
         if (A->dtype != SPX_F64 || !(A->val32.p || A->ell_val32.p || A->coo_val32.p))
             return fail(SPX_ERR_UNSUPPORTED, "mixed precision needs an FP64 matrix created with SPX_MIXED_SHADOW");
         if (fixed > 0) return fail(SPX_ERR_UNSUPPORTED, "fixed-iteration mode runs in one precision");
-        st = run_ir(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol, maxit, restart, info);
+        st = run_ir(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol, maxit, restart, pre,
+                    info);
     } else if (precision == SPX_PREC_F64 || precision == SPX_PREC_F32) {
         const int want = precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32;
         if (A->dtype != want) return fail(SPX_ERR_UNSUPPORTED, "precision must match the matrix dtype (or use MIXED)");
         st = A->dtype == SPX_F64
                  ? solve_typed<double>(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol,
-                                       maxit, restart, false, fixed, info)
+                                       maxit, restart, false, fixed, pre, info)
                  : solve_typed<float>(ctx, A, static_cast<const float *>(b), static_cast<float *>(x), solver, tol,
-                                      maxit, restart, false, fixed, info);
+                                      maxit, restart, false, fixed, pre, info);
     } else {
         return fail(SPX_ERR_INVALID, "spx_solve: unknown precision");
     }

@@ -23,6 +23,7 @@ SPX_ERR_UNSUPPORTED, SPX_ERR_TIMEOUT, SPX_ERR_NOT_FOUND = 5, 6, 7
 SPX_CSR, SPX_ELL, SPX_COO, SPX_HYB = 0, 1, 2, 3
 SPX_F64, SPX_F32 = 0, 1
 SPX_CG, SPX_BICGSTAB, SPX_GMRES, SPX_CGS = 0, 1, 2, 3
+SPX_PRECOND_JACOBI = 0x100
 SPX_PREC_F64, SPX_PREC_F32, SPX_PREC_MIXED = 0, 1, 2
 SPX_CONVERGED, SPX_MAX_ITER, SPX_BREAKDOWN, SPX_STAGNATED, SPX_SOLVE_TIMEOUT = 0, 1, 2, 3, 4
 SPX_KERNEL_AUTO, SPX_KERNEL_CSR_VECTOR, SPX_KERNEL_CSR_MERGE, SPX_KERNEL_ELL, SPX_KERNEL_COO = 0, 1, 2, 3, 4
@@ -311,18 +312,27 @@ def _info(i: spx_solve_info) -> SolveInfo:
                      i.inner_iterations)
 
 
+def _solver_code(solver, precond):
+    code = SOLVERS.get(solver, solver)
+    if precond == "jacobi":
+        code |= SPX_PRECOND_JACOBI
+    elif precond is not None:
+        raise ValueError(f"unknown preconditioner {precond!r}")
+    return code
+
+
 def spx_solve(ctx: int, A: int, b: torch.Tensor, x: torch.Tensor, solver="cg", tol: float = 1e-10,
-              max_iter: int = 10000, restart: int = 30, precision="f64") -> SolveInfo:
+              max_iter: int = 10000, restart: int = 30, precision="f64", precond=None) -> SolveInfo:
     info = spx_solve_info()
-    _check(load().spx_solve(ctx, A, _ptr(b), _ptr(x), SOLVERS.get(solver, solver), float(tol), int(max_iter),
+    _check(load().spx_solve(ctx, A, _ptr(b), _ptr(x), _solver_code(solver, precond), float(tol), int(max_iter),
                             int(restart), PRECISIONS.get(precision, precision), C.byref(info)))
     return _info(info)
 
 
 def spx_solve_fixed(ctx: int, A: int, b: torch.Tensor, x: torch.Tensor, solver="cg", iterations: int = 1000,
-                    restart: int = 30, precision="f64") -> SolveInfo:
+                    restart: int = 30, precision="f64", precond=None) -> SolveInfo:
     info = spx_solve_info()
-    _check(load().spx_solve_fixed(ctx, A, _ptr(b), _ptr(x), SOLVERS.get(solver, solver), int(iterations),
+    _check(load().spx_solve_fixed(ctx, A, _ptr(b), _ptr(x), _solver_code(solver, precond), int(iterations),
                                   int(restart), PRECISIONS.get(precision, precision), C.byref(info)))
     return _info(info)
 
