@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(256)
                 int *carry_row_w, T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err,
                 Epi<T> e)
 {
-    constexpr int CH = 8;
+    constexpr int CH = IPT == 8 ? 4 : 8;  // gathers issued together (4: fewer registers, 8-wide granules)
     constexpr int NW = 256 / 32;
     constexpr int CHUNK = 32 * IPT, PADDED = CHUNK + 32;  // element k sits at k + k / IPT
     if (e.skip && *e.skip) return;
@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(256)
                 T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e)
 {
     constexpr bool add_mode = MODE >= 2;  // y += ..., no rows without entries written
-    constexpr int CH = 8;
+    constexpr int CH = IPT == 8 ? 4 : 8;  // gathers issued together (4: fewer registers, 8-wide granules)
     constexpr int NW = 256 / 32;
     constexpr int CHUNK = 32 * IPT, PADDED = CHUNK + 32;  // element k sits at k + k / IPT
     if (e.skip && *e.skip) return;
@@ -1732,11 +1732,10 @@ int dispatch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const E
 template <class T>
 int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
 {
-    // param: 8 / 16 = nonzeros per lane of the warp-independent split kernel (default 16
-    // for FP64, where longer granules amortise the FP64 carry adds; 8 for FP32);
+    // param: 8 / 16 = nonzeros per lane of the warp-independent split kernel (default 8);
     // 104 / 108 / 116 = tiled segmented reduction with 4 / 8 / 16 items per thread
     int p = A->kernel == SPX_KERNEL_COO ? A->kparam : 0;
-    if (p <= 0) p = sizeof(T) == 8 ? 16 : 8;
+    if (p <= 0) p = 8;
     switch (p) {
     case 8: return launch_coo_split<T, 8>(ctx, A, cval, x, e, add);
     case 16: return launch_coo_split<T, 16>(ctx, A, cval, x, e, add);
