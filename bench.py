@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SpMV GB/s and CG solve time vs HBM roofline; batched solves/s; p50/p99 latency"
 WORKLOAD = ("spmv_format_sweep: 27-point 3D stencil 100^3 (n=1,000,000, nnz=26,463,592) and power-law "
             "n=2,000,000 (Pareto tail 1.5, mean 16, max 20,000 nnz/row, nnz=32,000,000); "
-            "CSR(merge-path)/ELL/COO/HYB x FP64/FP32 values, int32 indices")
+            "CSR (kernel chosen from row statistics: row-block for the stencil, nnz-split for the power-law)/ELL/COO/HYB x FP64/FP32 values, int32 indices")
 
 
 def _peaks():
