@@ -161,6 +161,12 @@ def build_workload(only: str = ""):
     return {k: f() for k, f in gens.items() if not only or k in only or "/" not in only and only in k}
 
 
+def _floor_key(entry_name: str) -> str:
+    """'powerlaw_2m/csr/f64' -> 'powerlaw_2m/f64' (the gather floor depends on pattern and value type)."""
+    parts = entry_name.split("/")
+    return f"{parts[0]}/{parts[-1]}"
+
+
 def max_over_ranks(elapsed_ms: float, dist=None, device=None) -> float:
     """The job's time is the slowest replica's: all-reduce MAX, then a barrier.
     Replicas share no data; this is the only collective and it sits outside the
@@ -293,6 +299,7 @@ def run_gpu(args):
     single = [i for i, e in enumerate(entries) if e["launches"] == 1] or list(range(len(entries)))
     dom = max(single, key=lambda i: per_entry_ms[i])
     de = entries[dom]
+    floors = gather_floor(spx, ctx, stream, mats, dev)
     achieved = de["bytes"] / (per_entry_ms[dom] * 1e-3) / 1e9
     traffic = _traffic(de["name"])
     result = {
@@ -319,11 +326,15 @@ def run_gpu(args):
                                      "GB_s": round(e["bytes"] / (per_entry_ms[i] * 1e-3) / 1e9, 1),
                                      "frac_of_peak": round(e["bytes"] / (per_entry_ms[i] * 1e-3) / 1e9 / peak, 3)}
                          for i, e in enumerate(entries)},
+            "gather_floor_us": floors,
         },
         "roofline": {"bound": "hbm", "kernel": de["name"], "achieved": round(achieved, 1), "peak": peak,
                      "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else "fallback",
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "algorithmic_bytes_per_launch": de["bytes"]},
+                     "algorithmic_bytes_per_launch": de["bytes"],
+                     "gather_floor_us": floors.get(_floor_key(de["name"])),
+                     "time_over_gather_floor": round(per_entry_ms[dom] * 1e3 / floors[_floor_key(de["name"])], 2)
+                     if floors.get(_floor_key(de["name"])) else None},
         "e2e": {"value": round(bytes_step / (e2e_step_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": sum(e["launches"] for e in entries) * args.steps,
@@ -492,6 +503,36 @@ def fixed_iter_secondary(spx, ctx, stream, dev, iters: int = 1000):
                                "gflops": round(fl / (si.time_ms * 1e-3) / 1e9, 1)}
             spx.spx_matrix_destroy(A)
         out[name] = res
+    return out
+
+
+def gather_floor(spx, ctx, stream, mats, dev, steps: int = 10):
+    """Per matrix and value type: the time of the gather-only probe
+    (spx_probe_gather: stream the column indices, gather x at each), the
+    floor any SpMV kernel has on that sparsity pattern.  L2 is flushed (a
+    256 MB write) before every launch, as the sweep leaves it cold."""
+    import torch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+    for mname, (rp, col, val) in mats.items():
+        n = rp.shape[0] - 1
+        col_d = torch.from_numpy(col).to(dev)
+        for tdt, tag in ((torch.float64, "f64"), (torch.float32, "f32")):
+            x = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, n)).to(dev).to(tdt)
+            o = torch.zeros(1, dtype=tdt, device=dev)
+            ts = []
+            with torch.cuda.stream(stream):
+                for k in range(steps + 2):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    spx.spx_probe_gather(ctx, col_d, x, o)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if k >= 2:
+                        ts.append(e0.elapsed_time(e1))
+            out[f"{mname}/{tag}"] = round(statistics.median(ts) * 1e3, 1)
+        del col_d
     return out
 
 

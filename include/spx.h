@@ -208,6 +208,15 @@ int spx_spmv_csr_noalloc(void *stream, int dtype, int64_t nrows, int64_t ncols, 
                          const int32_t *row_ptr, const int32_t *col_idx, const void *values, const void *x,
                          void *y);
 
+/* A measurement aid (not part of the paper's method): stream col_idx[nnz]
+ * and gather x (dtype SPX_F64 or SPX_F32) at every index, summing the
+ * gathered values; nothing is stored except, practically never, out[0]
+ * (device, one element).  Its time is the floor any SpMV kernel has on that
+ * sparsity pattern: the gathers of x plus 4 bytes per nonzero.  Device
+ * pointers; every index must lie inside x (not checked).  Asynchronous on the
+ * context stream.  Errors: SPX_ERR_INVALID. */
+int spx_probe_gather(spx_ctx *ctx, int64_t nnz, const int32_t *col_idx, const void *x, int dtype, void *out);
+
 /* ------------------------------------------------------------------ BLAS-1 */
 
 /* *result = sum_i x_i y_i with a deterministic two-stage device reduction

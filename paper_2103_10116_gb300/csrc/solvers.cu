@@ -383,13 +383,34 @@ template <class T>
 __device__ __forceinline__ void gm_chunk_dots(const T *__restrict__ V, int64_t ld, int64_t r0, int nr, const T *ws,
                                               int j, int lane, int wp, T acc[4])
 {
+    if constexpr (sizeof(T) == 8) {
+        // FP64: one owned vector at a time (four loads in flight), so no FP64
+        // instruction is issued for a vector the warp does not own
+        for (int i0 = lane; i0 < nr; i0 += 128) {
+            T wi[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wi[u] = i0 + 32 * u < nr ? ws[i0 + 32 * u] : T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = wp + 8 * q;
+                if (k > j) break;  // warp-uniform
+                const T *vk = V + (int64_t)k * ld + r0;
+                T v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = i0 + 32 * u < nr ? vk[i0 + 32 * u] : T(0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[q] = fma(v[u], wi[u], acc[q]);
+            }
+        }
+        return;
+    }
+    // FP32: every owned vector's rows are loaded before any FMA (up to 16 loads in flight)
     const int nq = wp > j ? 0 : min(4, (j - wp) / 8 + 1);  // vectors this warp owns (warp-uniform)
     if (nq == 0) return;
     for (int i0 = lane; i0 < nr; i0 += 128) {
         T wi[4], v[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) wi[u] = i0 + 32 * u < nr ? ws[i0 + 32 * u] : T(0);
-        // every owned vector's four rows loaded before any FMA: up to 16 loads in flight
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const T *vk = V + (int64_t)(wp + 8 * q) * ld + r0;

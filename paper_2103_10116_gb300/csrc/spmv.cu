@@ -1928,3 +1928,54 @@ extern "C" int spx_spmv_csr_noalloc(void *stream, int dtype, int64_t nrows, int6
     return spmv_noalloc<float>(st, scratch, nrows, nnz, row_ptr, col_idx, static_cast<const float *>(values),
                                static_cast<const float *>(x), static_cast<float *>(y), sms, err);
 }
+
+// ------------------------------------------------------------------ gather probe
+// A measurement aid, not part of SpMV: the part of a CSR / COO SpMV that no
+// kernel can avoid for a given sparsity pattern — stream the column indices
+// and gather x at each of them — with no values, rows or arithmetic beyond a
+// running sum (kept so the gathers are not optimised away).  Its time is a
+// floor for any SpMV kernel on that pattern.
+namespace {
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_gather_probe(int64_t nnz, const int *__restrict__ col, const T *__restrict__ x, T *__restrict__ out)
+{
+    T acc = T(0);
+    const int64_t stride = (int64_t)gridDim.x * 256;
+    int64_t k = blockIdx.x * 256LL + threadIdx.x;
+    for (; k + 7 * stride < nnz; k += 8 * stride) {  // eight gathers in flight per thread
+        int c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c[u] = col[k + u * stride];
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; k < nnz; k += stride) acc += __ldg(x + col[k]);
+    acc = spx::warp_sum(acc);
+    if ((threadIdx.x & 31) == 0 && acc == T(-12345.678)) out[0] = acc;  // practically never stores
+}
+}  // namespace
+
+extern "C" int spx_probe_gather(spx_ctx *ctx, int64_t nnz, const int32_t *col_idx, const void *x, int dtype,
+                                void *out)
+{
+    if (!ctx || nnz < 0 || (nnz > 0 && (!col_idx || !x || !out))) return spx::fail(SPX_ERR_INVALID, "spx_probe_gather: bad argument");
+    if (dtype != SPX_F64 && dtype != SPX_F32) return spx::fail(SPX_ERR_INVALID, "spx_probe_gather: bad dtype");
+    if (nnz == 0) return SPX_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    const int grid = ctx->sm_count * 8;
+    if (dtype == SPX_F64)
+        k_gather_probe<double><<<grid, 256, 0, ctx->stream>>>(nnz, col_idx, static_cast<const double *>(x),
+                                                             static_cast<double *>(out));
+    else
+        k_gather_probe<float><<<grid, 256, 0, ctx->stream>>>(nnz, col_idx, static_cast<const float *>(x),
+                                                            static_cast<float *>(out));
+    const cudaError_t e = cudaGetLastError();
+    if (prev != ctx->device) cudaSetDevice(prev);
+    return e == cudaSuccess ? SPX_OK : spx::cuda_fail(e, "spx_probe_gather");
+}

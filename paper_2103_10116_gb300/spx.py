@@ -100,6 +100,7 @@ SIGNATURES = {
     "spx_server_submit": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(C.c_int64)]),
     "spx_server_poll": (_I, [_P, C.POINTER(spx_server_result), _I, _I, C.POINTER(C.c_int)]),
     "spx_server_set_batching": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
+    "spx_probe_gather": (_I, [_P, _I64, _P, _P, _I, _P]),
     "spx_server_pending": (_I, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spx_server_destroy": (_I, [_P]),
     "spx_last_error": (C.c_char_p, []),
@@ -402,6 +403,11 @@ def spx_server_poll(S: int, max_results: int = 256, wait_ms: int = 0) -> list[di
         out.append({"id": r.id, "error": r.error, "info": _info(r.info), "submit_ms": r.submit_ms,
                     "admit_ms": r.admit_ms, "done_ms": r.done_ms})
     return out
+
+
+def spx_probe_gather(ctx: int, col_idx: torch.Tensor, x: torch.Tensor, out: torch.Tensor):
+    """Gather-only floor of an SpMV on col_idx's pattern (measurement aid)."""
+    _check(load().spx_probe_gather(ctx, col_idx.numel(), _ptr(col_idx), _ptr(x), _dt(x), _ptr(out)))
 
 
 def spx_server_set_batching(S: int, max_rows: int) -> int:

@@ -316,3 +316,18 @@ def test_rows_kernel_tile_too_large(spx, ctx):
         assert_spmv_close(y.cpu().numpy(), yref, oracle.spmv_absbound(rp, col, val, x), TOL["f64"])
     finally:
         spx.spx_matrix_destroy(A)
+
+
+def test_gather_probe_runs_and_checks_arguments(spx, ctx):
+    """The gather-floor measurement aid streams the pattern and stores nothing."""
+    n, nnz = 5000, 120000
+    rng = np.random.default_rng(9)
+    col = torch.from_numpy(rng.integers(0, n, size=nnz).astype(np.int32)).to(DEV)
+    for tdt in (torch.float64, torch.float32):
+        x = torch.from_numpy(rng.uniform(-1, 1, n)).to(DEV).to(tdt)
+        out = torch.zeros(1, dtype=tdt, device=DEV)
+        spx.spx_probe_gather(ctx, col, x, out)
+        torch.cuda.synchronize()
+        assert float(out[0]) == 0.0
+    with pytest.raises((spx.SpxError, TypeError)):  # integer x: rejected before or by the library
+        spx.spx_probe_gather(ctx, col, torch.zeros(n, dtype=torch.int32, device=DEV), out)
