@@ -110,6 +110,20 @@ int spx_ctx_destroy(spx_ctx *ctx);
 /* Rebind the context to another stream of the same device. */
 int spx_ctx_set_stream(spx_ctx *ctx, void *stream);
 
+/* Synchronise ctx's stream and report whether any bounded device-side wait
+ * (look-back flags of the load-balanced SpMV kernels, bulk-copy mbarriers)
+ * gave up since the last check: SPX_ERR_TIMEOUT, after which the error word
+ * is cleared and the context stays usable; else SPX_OK.  Solves check this
+ * themselves; asynchronous calls (spx_spmv) are checked by calling it. */
+int spx_ctx_check(spx_ctx *ctx);
+
+/* Test hook for the failure path: launch one wait that nothing will satisfy
+ * (which = 0: a look-back flag; 1: an mbarrier phase), limited to about a
+ * millisecond of SM clocks.  It gives up, records the error and returns, so
+ * the following spx_ctx_check reports SPX_ERR_TIMEOUT.  Nothing hangs or
+ * faults.  Asynchronous.  Errors: SPX_ERR_INVALID. */
+int spx_selftest_wait_timeout(spx_ctx *ctx, int which);
+
 /* ------------------------------------------------------------------ matrices */
 
 /* Create a matrix in `format` (spx_format) with value type `dtype`

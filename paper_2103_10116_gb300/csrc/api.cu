@@ -277,6 +277,19 @@ extern "C" int spx_ctx_create(spx_ctx **out, int device, void *stream, spx_alloc
     return SPX_OK;
 }
 
+extern "C" int spx_ctx_check(spx_ctx *ctx)
+{
+    if (!ctx) return fail(SPX_ERR_INVALID, "spx_ctx_check: NULL context");
+    DeviceGuard g(ctx->device);
+    unsigned h = 0;
+    SPX_CUDA(cudaMemcpyAsync(&h, ctx->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (h == 0) return SPX_OK;
+    SPX_CUDA(cudaMemsetAsync(ctx->dev_err, 0, sizeof(unsigned), ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    return fail(SPX_ERR_TIMEOUT, "a bounded device-side wait gave up (error word " + std::to_string(h) + ")");
+}
+
 extern "C" int spx_ctx_destroy(spx_ctx *ctx)
 {
     if (!ctx) return SPX_OK;

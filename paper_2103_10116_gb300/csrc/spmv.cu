@@ -1979,3 +1979,42 @@ extern "C" int spx_probe_gather(spx_ctx *ctx, int64_t nnz, const int32_t *col_id
     if (prev != ctx->device) cudaSetDevice(prev);
     return e == cudaSuccess ? SPX_OK : spx::cuda_fail(e, "spx_probe_gather");
 }
+
+// ------------------------------------------------------------------ bounded-wait self-test
+// A test hook for the failure path: one warp waits, with a short limit, on a
+// look-back flag (which = 0) or an mbarrier phase (which = 1) that nothing
+// will ever complete.  The wait gives up, records the error bit in the
+// context's error word and the kernel returns normally; spx_ctx_check then
+// reports SPX_ERR_TIMEOUT.  Nothing hangs and nothing faults.
+namespace {
+__global__ void k_selftest_wait(int which, long long limit_cycles, int *never_set, unsigned *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    if (which == 0) {
+        spx::flag_wait(never_set, err, limit_cycles);
+    } else {
+        spx::mbar_init(&bar, 1);
+        spx::fence_barrier_init();
+        spx::mbar_wait(&bar, 0, err, limit_cycles);  // phase 0 never completes: nobody arrives
+    }
+}
+}  // namespace
+
+extern "C" int spx_selftest_wait_timeout(spx_ctx *ctx, int which)
+{
+    if (!ctx || (which != 0 && which != 1)) return spx::fail(SPX_ERR_INVALID, "spx_selftest_wait_timeout: bad argument");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    int *flag = nullptr;
+    cudaError_t e = cudaMallocAsync(&flag, 16, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, 16, ctx->stream);
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<1, 32, 0, ctx->stream>>>(which, 2000000LL, flag, ctx->dev_err);  // about 1 ms
+        e = cudaGetLastError();
+    }
+    if (flag) cudaFreeAsync(flag, ctx->stream);
+    if (prev != ctx->device) cudaSetDevice(prev);
+    return e == cudaSuccess ? SPX_OK : spx::cuda_fail(e, "spx_selftest_wait_timeout");
+}

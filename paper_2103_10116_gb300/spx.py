@@ -101,6 +101,8 @@ SIGNATURES = {
     "spx_server_poll": (_I, [_P, C.POINTER(spx_server_result), _I, _I, C.POINTER(C.c_int)]),
     "spx_server_set_batching": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
     "spx_probe_gather": (_I, [_P, _I64, _P, _P, _I, _P]),
+    "spx_ctx_check": (_I, [_P]),
+    "spx_selftest_wait_timeout": (_I, [_P, _I]),
     "spx_server_pending": (_I, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "spx_server_destroy": (_I, [_P]),
     "spx_last_error": (C.c_char_p, []),
@@ -403,6 +405,15 @@ def spx_server_poll(S: int, max_results: int = 256, wait_ms: int = 0) -> list[di
         out.append({"id": r.id, "error": r.error, "info": _info(r.info), "submit_ms": r.submit_ms,
                     "admit_ms": r.admit_ms, "done_ms": r.done_ms})
     return out
+
+
+def spx_ctx_check(ctx: int):
+    """Raise SpxError(SPX_ERR_TIMEOUT) if a bounded device-side wait gave up since the last check."""
+    _check(load().spx_ctx_check(ctx))
+
+
+def spx_selftest_wait_timeout(ctx: int, which: int = 0):
+    _check(load().spx_selftest_wait_timeout(ctx, int(which)))
 
 
 def spx_probe_gather(ctx: int, col_idx: torch.Tensor, x: torch.Tensor, out: torch.Tensor):
