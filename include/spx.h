@@ -292,7 +292,7 @@ int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_t nsys, con
                      const void *values, unsigned flags);
 int spx_batch_destroy(spx_batch *B);
 
-/* Solve all systems of B in one persistent kernel launch (CG or BiCGSTAB),
+/* Solve all systems of B in one persistent kernel launch (CG, BiCGSTAB or CGS),
  * b and x concatenated by row_off (device, dtype of the batch; x is the
  * initial guess on entry).  infos: HOST array of nsys entries, or NULL.
  * precision SPX_PREC_MIXED runs FP32 batched inner solves inside FP64
@@ -310,8 +310,8 @@ int spx_batch_tune(spx_ctx *ctx, spx_batch *B, int solver, int precision, int *c
 /* A continuous-batching solve server on ctx's device.  budget_bytes caps the
  * device memory of the requests running at once (<= 0: 90% of the free
  * memory at creation); max_slots is the number of large requests that may
- * run concurrently, each on its own stream (1..64).  Small CG / BiCGSTAB
- * requests (FP64 or MIXED, at most 24 576 rows by default, see
+ * run concurrently, each on its own stream (1..64).  Small CG / BiCGSTAB / CGS
+ * requests (unpreconditioned) (FP64 or MIXED, at most 24 576 rows by default, see
  * spx_server_set_batching) are instead gathered by four batch lanes: each
  * lane solves every queued small request of one kind (same solver, tol,
  * max_iter, precision and size class) in one launch of the batched kernel,

@@ -1,5 +1,5 @@
 // batch.cu -- many independent small sparse systems solved by one persistent
-// kernel launch (CG or BiCGSTAB, FP64, FP32, or FP32 inner iterations inside
+// kernel launch (CG, BiCGSTAB or CGS, FP64, FP32, or FP32 inner iterations inside
 // FP64 iterative refinement).
 //
 // Each thread block takes the next system from a device work queue (largest
@@ -288,6 +288,117 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
     return status;
 }
 
+// One system by CGS (Sonneveld; shadow residual r^ = r0).  The SpMV operands
+// (p, then u + q) are staged in turn through the shared-memory vector ps.
+template <class T, class V, int BLOCK>
+__device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restrict__ col, const V *__restrict__ val,
+                          const T *__restrict__ b, T *__restrict__ x, T *const *w, T *ps, T *red, T tol,
+                          long long maxit, bool zero_x0, bool check_true, long long &iters, T &relres)
+{
+    const int tid = threadIdx.x;
+    T *r = w[0], *rh = w[1], *p = w[2], *u = w[3], *q = w[4], *v = w[5];
+    T bb = T(0);
+    for (int i = tid; i < n; i += BLOCK) bb = fma(b[i], b[i], bb);
+    bb = bsum<T, BLOCK>(bb, red);
+    if (bb == T(0)) {
+        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
+        relres = T(0);
+        return SPX_CONVERGED;
+    }
+    const T tol2 = tol * tol * bb;
+    if (zero_x0)
+        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
+    int status = SPX_MAX_ITER;
+    for (int restart = 0;; ++restart) {
+        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
+        __syncthreads();
+        T rr0 = T(0);
+        for (int i = tid; i < n; i += BLOCK) {
+            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
+            r[i] = ri;
+            rh[i] = ri;
+            p[i] = ri;
+            u[i] = ri;
+            rr0 = fma(ri, ri, rr0);
+        }
+        rr0 = bsum<T, BLOCK>(rr0, red);  // (its barrier also ends every read of ps)
+        for (int i = tid; i < n; i += BLOCK) ps[i] = p[i];
+        __syncthreads();
+        T rho = rr0;
+        relres = sqrt(rr0 / bb);
+        status = rr0 <= tol2 ? SPX_CONVERGED : SPX_MAX_ITER;
+        while (status == SPX_MAX_ITER && iters < maxit) {
+            if (rho == T(0)) {
+                status = SPX_BREAKDOWN;
+                break;
+            }
+            T rv = T(0);
+            for (int i = tid; i < n; i += BLOCK) {  // v = A p
+                const T vi = row_dot<T, V>(rp, col, val, ps, i);
+                v[i] = vi;
+                rv = fma(rh[i], vi, rv);
+            }
+            rv = bsum<T, BLOCK>(rv, red);
+            if (rv == T(0)) {
+                status = SPX_BREAKDOWN;
+                break;
+            }
+            const T alpha = rho / rv;
+            for (int i = tid; i < n; i += BLOCK) {
+                const T qi = fma(-alpha, v[i], u[i]);
+                q[i] = qi;
+                const T wi = u[i] + qi;
+                x[i] = fma(alpha, wi, x[i]);
+                ps[i] = wi;
+            }
+            __syncthreads();
+            T rr = T(0), rhr = T(0);
+            for (int i = tid; i < n; i += BLOCK) {  // r -= alpha A (u + q)
+                const T ri = fma(-alpha, row_dot<T, V>(rp, col, val, ps, i), r[i]);
+                r[i] = ri;
+                rr = fma(ri, ri, rr);
+                rhr = fma(rh[i], ri, rhr);
+            }
+            rr = bsum<T, BLOCK>(rr, red);
+            rhr = bsum<T, BLOCK>(rhr, red);
+            ++iters;
+            relres = sqrt(rr / bb);
+            if (rr <= tol2) {
+                status = SPX_CONVERGED;
+                break;
+            }
+            const T beta = rhr / rho;
+            for (int i = tid; i < n; i += BLOCK) {
+                const T ui = fma(beta, q[i], r[i]);
+                u[i] = ui;
+                const T pi = fma(beta, fma(beta, p[i], q[i]), ui);
+                p[i] = pi;
+                ps[i] = pi;
+            }
+            __syncthreads();
+            rho = rhr;
+        }
+        if (!check_true || status != SPX_CONVERGED) break;
+        __syncthreads();
+        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
+        __syncthreads();
+        T rt = T(0);
+        for (int i = tid; i < n; i += BLOCK) {
+            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
+            rt = fma(ri, ri, rt);
+        }
+        rt = bsum<T, BLOCK>(rt, red);
+        relres = sqrt(rt / bb);
+        if (rt <= tol2) break;
+        if (restart == kBatchMaxRestarts) {
+            status = SPX_STAGNATED;
+            break;
+        }
+    }
+    __syncthreads();
+    return status;
+}
+
 // The persistent kernel.  MIXED: FP64 refinement (r = b - A64 x, x += ||r|| d)
 // around an FP32 inner solve of A32 d = r / ||r|| to 1e-4 on float values.
 template <class T, int BLOCK, int SOLVER, bool MIXED>
@@ -324,6 +435,11 @@ __global__ void __launch_bounds__(BLOCK)
             if (SOLVER == SPX_CG) {
                 status = cg_system<T, T, BLOCK>(n, rp, col, val, b, x, work + ro, work + nrows + ro, ps, red, tol,
                                                 maxit, false, true, iters, relres);
+            } else if (SOLVER == SPX_CGS) {
+                T *w[6];
+                for (int k = 0; k < 6; ++k) w[k] = work + (int64_t)k * nrows + ro;
+                status = cgs_system<T, T, BLOCK>(n, rp, col, val, b, x, w, ps, red, tol, maxit, false, true, iters,
+                                                 relres);
             } else {
                 T *w[6];
                 for (int k = 0; k < 6; ++k) w[k] = work + (int64_t)k * nrows + ro;
@@ -376,6 +492,9 @@ __global__ void __launch_bounds__(BLOCK)
                 if (SOLVER == SPX_CG)
                     cg_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv[0], fv[1], ps32, redf, 1e-4f,
                                                    cyc_max, true, false, iters, rel32);
+                else if (SOLVER == SPX_CGS)
+                    cgs_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, cyc_max, true,
+                                                    false, iters, rel32);
                 else
                     bicgstab_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, cyc_max,
                                                          true, false, iters, rel32);
@@ -439,23 +558,25 @@ int launch_batch(spx_ctx *ctx, spx_batch *B, int block, int solver, int precisio
                                             round_up((size_t)B->nsys * 8, 256));
     unsigned *queue = B->queue.as<unsigned>();
     SPX_CUDA(cudaMemsetAsync(queue, 0, 4, ctx->stream));
-    const bool cg = solver == SPX_CG;
     if (precision == SPX_PREC_MIXED) {
         const double *bd = static_cast<const double *>(b);
         double *xd = static_cast<double *>(x);
-        return cg ? launch_batch_b<double, SPX_CG, true>(ctx, B, block, bd, xd, tol, maxit, out, queue)
-                  : launch_batch_b<double, SPX_BICGSTAB, true>(ctx, B, block, bd, xd, tol, maxit, out, queue);
+        if (solver == SPX_CG) return launch_batch_b<double, SPX_CG, true>(ctx, B, block, bd, xd, tol, maxit, out, queue);
+        if (solver == SPX_CGS) return launch_batch_b<double, SPX_CGS, true>(ctx, B, block, bd, xd, tol, maxit, out, queue);
+        return launch_batch_b<double, SPX_BICGSTAB, true>(ctx, B, block, bd, xd, tol, maxit, out, queue);
     }
     if (B->dtype == SPX_F64) {
         const double *bd = static_cast<const double *>(b);
         double *xd = static_cast<double *>(x);
-        return cg ? launch_batch_b<double, SPX_CG, false>(ctx, B, block, bd, xd, tol, maxit, out, queue)
-                  : launch_batch_b<double, SPX_BICGSTAB, false>(ctx, B, block, bd, xd, tol, maxit, out, queue);
+        if (solver == SPX_CG) return launch_batch_b<double, SPX_CG, false>(ctx, B, block, bd, xd, tol, maxit, out, queue);
+        if (solver == SPX_CGS) return launch_batch_b<double, SPX_CGS, false>(ctx, B, block, bd, xd, tol, maxit, out, queue);
+        return launch_batch_b<double, SPX_BICGSTAB, false>(ctx, B, block, bd, xd, tol, maxit, out, queue);
     }
     const float *bf = static_cast<const float *>(b);
     float *xf = static_cast<float *>(x);
-    return cg ? launch_batch_b<float, SPX_CG, false>(ctx, B, block, bf, xf, tol, maxit, out, queue)
-              : launch_batch_b<float, SPX_BICGSTAB, false>(ctx, B, block, bf, xf, tol, maxit, out, queue);
+    if (solver == SPX_CG) return launch_batch_b<float, SPX_CG, false>(ctx, B, block, bf, xf, tol, maxit, out, queue);
+    if (solver == SPX_CGS) return launch_batch_b<float, SPX_CGS, false>(ctx, B, block, bf, xf, tol, maxit, out, queue);
+    return launch_batch_b<float, SPX_BICGSTAB, false>(ctx, B, block, bf, xf, tol, maxit, out, queue);
 }
 
 int default_block(const spx_batch *B)
@@ -676,7 +797,8 @@ extern "C" int spx_batch_solve(spx_ctx *ctx, spx_batch *B, const void *b, void *
                                int64_t max_iter, int precision, spx_solve_info *infos)
 {
     if (!ctx || !B || (B->nrows > 0 && (!b || !x))) return fail(SPX_ERR_INVALID, "spx_batch_solve: NULL argument");
-    if (solver != SPX_CG && solver != SPX_BICGSTAB) return fail(SPX_ERR_UNSUPPORTED, "batched solver must be CG or BiCGSTAB");
+    if (solver != SPX_CG && solver != SPX_BICGSTAB && solver != SPX_CGS)
+        return fail(SPX_ERR_UNSUPPORTED, "batched solver must be CG, BiCGSTAB or CGS");
     if (!(tol >= 0.0) || max_iter < 0) return fail(SPX_ERR_INVALID, "spx_batch_solve: bad tol or max_iter");
     if (B->nsys == 0) return SPX_OK;
     DevGuardB g(ctx->device);
@@ -687,7 +809,8 @@ extern "C" int spx_batch_solve(spx_ctx *ctx, spx_batch *B, const void *b, void *
 extern "C" int spx_batch_tune(spx_ctx *ctx, spx_batch *B, int solver, int precision, int *chosen)
 {
     if (!ctx || !B) return fail(SPX_ERR_INVALID, "spx_batch_tune: NULL argument");
-    if (solver != SPX_CG && solver != SPX_BICGSTAB) return fail(SPX_ERR_UNSUPPORTED, "batched solver must be CG or BiCGSTAB");
+    if (solver != SPX_CG && solver != SPX_BICGSTAB && solver != SPX_CGS)
+        return fail(SPX_ERR_UNSUPPORTED, "batched solver must be CG, BiCGSTAB or CGS");
     if (B->nsys == 0) {
         if (chosen) *chosen = default_block(B);
         return SPX_OK;

@@ -13,7 +13,7 @@
 // residual, submit / admit / finish times) are collected with
 // spx_server_poll.
 //
-// Small CG / BiCGSTAB requests (up to batch_rows rows, a size the batched
+// Small CG / BiCGSTAB / CGS requests (up to batch_rows rows, a size the batched
 // kernel holds in shared memory) do not take a slot of their own: batch
 // lanes (further worker threads, each with its own context and stream) take
 // every queued small request with the same solver settings and size class
@@ -399,7 +399,7 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     {
         std::lock_guard<std::mutex> lk(S->mu);
         R->id = S->next_id++;
-        R->batched = (solver == SPX_CG || solver == SPX_BICGSTAB) &&  // plain CG / BiCGSTAB only
+        R->batched = (solver == SPX_CG || solver == SPX_BICGSTAB || solver == SPX_CGS) &&  // unpreconditioned
                      (precision == SPX_PREC_F64 || precision == SPX_PREC_MIXED) && n <= S->batch_rows;
         (R->batched ? S->bqueue : S->queue).push_back(R);
     }

@@ -62,12 +62,12 @@ def _check(ro, xs, b, systems, x, tol, err_tol, infos=None, oracle_solver=None):
         assert np.linalg.norm(xb - xs[r0:r1]) / np.linalg.norm(xs[r0:r1]) <= err_tol, s
         if infos is not None and oracle_solver is not None:
             _, oi = oracle_solver(lrp, lcol, lval, b[r0:r1], tol=tol, maxit=20000)
-            # BiCGSTAB convergence is irregular: rounding moves the stop by a few steps
+            # BiCGSTAB / CGS convergence is irregular: rounding moves the stop by a few steps
             slack = max(3, oi.iterations // 10) if oracle_solver is oracle.cg else max(6, oi.iterations // 5)
             assert abs(infos[s].iterations - oi.iterations) <= slack, (s, infos[s], oi)
 
 
-@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs"])
 def test_batch_fp64(spx, ctx, batch, solver):
     ro, no, rp, col, val, xs, b, systems = batch
     B = spx.spx_batch_create(ctx, ro, no, _t(rp), _t(col), _t(val))
@@ -76,7 +76,7 @@ def test_batch_fp64(spx, ctx, batch, solver):
         infos = spx.spx_batch_solve(ctx, B, _t(b), x, len(systems), solver, 1e-10, 20000)
         assert all(i.status == spx.SPX_CONVERGED for i in infos), [i.status for i in infos]
         _check(ro, xs, b, systems, x.cpu().numpy(), 1e-10, 1e-7, infos,
-               oracle.cg if solver == "cg" else oracle.bicgstab)
+               {"cg": oracle.cg, "bicgstab": oracle.bicgstab, "cgs": oracle.cgs}[solver])
         # a second solve replays the captured graph: same bits
         x2 = torch.zeros_like(x)
         spx.spx_batch_solve(ctx, B, _t(b), x2, len(systems), solver, 1e-10, 20000)
@@ -104,7 +104,7 @@ def test_batch_fp32(spx, ctx, batch):
         spx.spx_batch_destroy(B)
 
 
-@pytest.mark.parametrize("solver", ["cg", "bicgstab"])
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs"])
 def test_batch_mixed(spx, ctx, batch, solver):
     ro, no, rp, col, val, xs, b, systems = batch
     B = spx.spx_batch_create(ctx, ro, no, _t(rp), _t(col), _t(val), flags=spx.SPX_MIXED_SHADOW)
