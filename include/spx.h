@@ -77,7 +77,8 @@ typedef enum {
     SPX_KERNEL_CSR_VECTOR = 1,  /* CSR: one sub-warp of `param` lanes (1..32, power of 2) per row */
     SPX_KERNEL_CSR_MERGE = 2,   /* CSR: merge-path split of rows + nonzeros, TMA-staged tiles */
     SPX_KERNEL_ELL = 3,         /* ELL / HYB ELL part: one thread per `param` rows (1, 2 or 4) */
-    SPX_KERNEL_COO = 4,         /* COO / HYB COO part: 8/16 = warp-independent split (default 8),
+    SPX_KERNEL_COO = 4,         /* COO / HYB COO part: 1 = row-block (COO format; the default for short rows
+                                   of similar length), 8/16 = warp-independent split (default otherwise: 8),
                                    104/108/116 = tiled segmented reduction with 4/8/16 items per thread */
     SPX_KERNEL_CSR_SPLIT = 5,   /* CSR: each lane takes `param` (8 or 16) consecutive nonzeros, warps independent */
     SPX_KERNEL_CSR_ROWS = 6     /* CSR: tiles of 128 rows bulk-copied to shared memory, one thread per row

@@ -321,7 +321,7 @@ void free_matrix_arrays(spx_matrix *A)
                     &A->ell_val,  &A->ell_val32, &A->coo_row,  &A->coo_col,   &A->coo_val,
                     &A->coo_val32, &A->tiles,    &A->carry_row, &A->carry_val, &A->partials,
                     &A->ticket,   &A->stage_x,   &A->stage_y,   &A->coo_tiles, &A->flags,
-                    &A->hint};
+                    &A->hint,     &A->coo_rowtiles};
     for (DBuf *b : bufs) dbuf_free(c, *b);
 }
 
@@ -671,8 +671,8 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     if (kernel == SPX_KERNEL_CSR_MERGE && param != 0 && !(param == 4 || param == 8 || param == 16))
         return fail(SPX_ERR_INVALID, "merge items per thread must be 0 (auto), 4, 8 or 16");
     if (kernel == SPX_KERNEL_COO && param != 0 &&
-        !(param == 8 || param == 16 || param == 104 || param == 108 || param == 116))
-        return fail(SPX_ERR_INVALID, "COO parameter must be 0 (auto), 8, 16 (split) or 104, 108, 116 (tiled)");
+        !(param == 1 || param == 8 || param == 16 || param == 104 || param == 108 || param == 116))
+        return fail(SPX_ERR_INVALID, "COO parameter must be 0 (auto), 1 (row-block), 8, 16 (split) or 104, 108, 116 (tiled)");
     if (kernel == SPX_KERNEL_CSR_ROWS && param != 0 && !(param == 1 || param == 2))
         return fail(SPX_ERR_INVALID, "row-block stages must be 0 (auto), 1 or 2");
     if (kernel == SPX_KERNEL_CSR_SPLIT && param != 0 && !(param == 8 || param == 16))

@@ -622,6 +622,177 @@ __global__ void __launch_bounds__(ROWS)
         if (e.dots) finish_dots<T, ROWS>(d0, d1, e, partials, ticket);
 }
 
+// ------------------------------------------------------------------ row-block COO (regular rows)
+// The COO counterpart of k_csr_rows: tiles of ROWS consecutive rows, whose
+// entries [tiles[t], tiles[t+1]) are bulk-copied (row indices, columns,
+// values) into shared memory, double-buffered.  The block then marks where
+// the staged row indices change, which gives every row its range inside the
+// tile, and each thread reduces one row with one FMA per entry.
+template <class T, int ROWS> struct CooRowsShape {
+    static __host__ __device__ int idx_bytes(int cap) { return ((cap + 8) * 4 + 15) & ~15; }
+    static __host__ __device__ int val_bytes(int cap) { return ((cap + 8) * (int)sizeof(T) + 15) & ~15; }
+    static __host__ __device__ int stage(int cap) { return 2 * idx_bytes(cap) + val_bytes(cap); }
+    static __host__ __device__ int smem(int cap) { return 2 * stage(cap) + 32 + 16; }
+};
+
+template <class T, int ROWS, int MODE>
+__global__ void __launch_bounds__(ROWS)
+    k_coo_rows(int n, const int *__restrict__ crow, const int *__restrict__ ccol, const T *__restrict__ cval,
+               const T *__restrict__ x, const int *__restrict__ tiles, int ntiles, int cap, T *partials,
+               unsigned *ticket, unsigned *err, Epi<T> e)
+{
+    using S = CooRowsShape<T, ROWS>;
+    constexpr int VA = 16 / (int)sizeof(T);
+    constexpr int CH = 8;
+    if (e.skip && *e.skip) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_first[ROWS], s_end[ROWS];
+    const int stage_bytes = S::stage(cap);
+    int4 *s_coord = reinterpret_cast<int4 *>(smem + 2 * stage_bytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes + 32);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    // thread 0 only: copy tile t's entries [e0, e1) into `stage`
+    auto issue = [&](int t, int e0, int e1, int stage) {
+        unsigned char *base = smem + stage * stage_bytes;
+        if (e1 - e0 > cap) {  // cannot happen for the matrix the cap was measured on
+            atomicOr(err, DEVERR_BOUNDS);
+            e1 = e0;
+        }
+        const int ia = e0 & ~3, ibytes = e1 > e0 ? ((e1 - ia + 3) & ~3) * 4 : 0;
+        const int va = e0 & ~(VA - 1), vbytes = e1 > e0 ? ((e1 - va + VA - 1) & ~(VA - 1)) * (int)sizeof(T) : 0;
+        s_coord[stage] = make_int4(t * ROWS, e0, min(n, t * ROWS + ROWS), e1);
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)(2 * ibytes + vbytes));
+        if (ibytes) {
+            bulk_g2s(base, crow + ia, (uint32_t)ibytes, &bar[stage]);
+            bulk_g2s(base + S::idx_bytes(cap), ccol + ia, (uint32_t)ibytes, &bar[stage]);
+            bulk_g2s(base + 2 * S::idx_bytes(cap), cval + va, (uint32_t)vbytes, &bar[stage]);
+        }
+    };
+
+    T d0 = T(0), d1 = T(0);
+    int it = 0;
+    bool ok = true, pending_prefetch = false;
+    int ne0 = 0, ne1 = 0;  // thread 0: entry range of the tile after next
+    if (tid == 0 && (int)blockIdx.x < ntiles) {
+        issue(blockIdx.x, tiles[blockIdx.x], tiles[blockIdx.x + 1], 0);
+        const int t2 = (int)blockIdx.x + (int)gridDim.x;
+        if (t2 < ntiles) {
+            ne0 = tiles[t2];
+            ne1 = tiles[t2 + 1];
+        }
+    }
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int stage = it & 1;
+        const int tn = t + gridDim.x;
+        pending_prefetch = tn < ntiles;
+        if (tid == 0 && tn < ntiles) {
+            fence_proxy_async();
+            issue(tn, ne0, ne1, stage ^ 1);
+            const int t3 = tn + gridDim.x;
+            if (t3 < ntiles) {
+                ne0 = tiles[t3];
+                ne1 = tiles[t3 + 1];
+            }
+        }
+        s_first[tid] = 0;
+        s_end[tid] = 0;
+        if (!mbar_wait(&bar[stage], (uint32_t)((it >> 1) & 1), err)) {
+            ok = false;
+            break;
+        }
+        const int4 co = s_coord[stage];
+        const int r0 = co.x, e0 = co.y, r1 = co.z, e1 = co.w;
+        const unsigned char *sb = smem + stage * stage_bytes;
+        const int *s_row = reinterpret_cast<const int *>(sb) + (e0 - (e0 & ~3));
+        const int *s_col = reinterpret_cast<const int *>(sb + S::idx_bytes(cap)) + (e0 - (e0 & ~3));
+        const T *s_val = reinterpret_cast<const T *>(sb + 2 * S::idx_bytes(cap)) + (e0 - (e0 & ~(VA - 1)));
+        const int cnt = e1 - e0;
+        __syncthreads();  // s_first / s_end cleared
+        for (int k = tid; k < cnt; k += ROWS) {  // where the row index changes: row starts and ends
+            const int rk = s_row[k];
+            if (k == 0 || s_row[k - 1] != rk) s_first[rk - r0] = k;
+            if (k == cnt - 1 || s_row[k + 1] != rk) s_end[rk - r0] = k + 1;
+        }
+        __syncthreads();
+        const int q = tid;
+        if (r0 + q < r1) {
+            int a = s_first[q];
+            const int b = s_end[q];
+            T sum = T(0);
+            for (; a + CH <= b; a += CH) {
+                T v[CH], xv[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    v[u] = s_val[a + u];
+                    xv[u] = __ldg(x + s_col[a + u]);
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) sum = fma(v[u], xv[u], sum);
+            }
+            const int rem = b - a;
+            if (rem > 0) {
+                T v[CH - 1], xv[CH - 1];
+#pragma unroll
+                for (int u = 0; u < CH - 1; ++u) {
+                    v[u] = u < rem ? s_val[a + u] : T(0);
+                    xv[u] = u < rem ? __ldg(x + s_col[a + u]) : T(0);
+                }
+                if (rem & 4) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) sum = fma(v[u], xv[u], sum);
+                    v[0] = v[4]; v[1] = v[5]; v[2] = v[6];
+                    xv[0] = xv[4]; xv[1] = xv[5]; xv[2] = xv[6];
+                }
+                if (rem & 2) {
+                    sum = fma(v[0], xv[0], sum);
+                    sum = fma(v[1], xv[1], sum);
+                    v[0] = v[2];
+                    xv[0] = xv[2];
+                }
+                if (rem & 1) sum = fma(v[0], xv[0], sum);
+            }
+            out_row<MODE>(e, r0 + q, sum, d0, d1);
+        }
+        __syncthreads();  // the stage and the row marks are reused
+    }
+    if (!ok && pending_prefetch) mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), err, 200000000LL);
+    if constexpr (MODE == 0)
+        if (e.dots) finish_dots<T, ROWS>(d0, d1, e, partials, ticket);
+}
+
+// tiles[t] = first COO entry of row t * rows (entries are row-sorted), t = 0..ntiles
+__global__ void k_coo_rowtiles(int n, int64_t nnz, const int *__restrict__ crow, int rows, int ntiles, int *tiles,
+                               int *maxcnt)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    const int r = min(n, t * rows);
+    int64_t lo = 0, hi = nnz;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (crow[mid] < r) lo = mid + 1;
+        else hi = mid;
+    }
+    tiles[t] = (int)lo;
+    if (t > 0) {  // entries of tile t-1: lower_bound of its first row, recomputed
+        const int rp = min(n, (t - 1) * rows);
+        int64_t a = 0, b = nnz;
+        while (a < b) {
+            const int64_t mid = (a + b) >> 1;
+            if (crow[mid] < rp) a = mid + 1;
+            else b = mid;
+        }
+        atomicMax(maxcnt, (int)(lo - a));
+    }
+}
+
 // the largest number of nonzeros in a tile of `rows` consecutive rows
 __global__ void k_tile_max_nnz(int n, const int *__restrict__ rp, int rows, int ntiles, int *out)
 {
@@ -1528,6 +1699,66 @@ int launch_rows(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi
     return plain ? launch_rows_m<T, 2, 1>(ctx, A, val, x, e) : launch_rows_m<T, 2, 0>(ctx, A, val, x, e);
 }
 
+int ensure_coo_rowtiles(spx_ctx *ctx, spx_matrix *A)
+{
+    if (A->coo_rows_cap >= 0) return SPX_OK;
+    const int64_t ntiles = ceil_div(A->n, kRowsTile);
+    if (ntiles + 1 > INT_MAX) return fail(SPX_ERR_TOO_LARGE, "too many COO row tiles");
+    dbuf_free(ctx, A->coo_rowtiles);
+    SPX_TRY(dbuf_alloc(ctx, A->coo_rowtiles, (size_t)(ntiles + 2) * 4 + 16));
+    int *mx = A->coo_rowtiles.as<int>() + ntiles + 1;
+    SPX_CUDA(cudaMemsetAsync(mx, 0, 4, ctx->stream));
+    k_coo_rowtiles<<<(int)ceil_div(ntiles + 1, 256), 256, 0, ctx->stream>>>((int)A->n, A->coo_nnz, A->coo_row.as<int>(),
+                                                                          kRowsTile, (int)ntiles,
+                                                                          A->coo_rowtiles.as<int>(), mx);
+    SPX_CUDA(cudaGetLastError());
+    int cap = 0;
+    SPX_CUDA(cudaMemcpyAsync(&cap, mx, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    A->coo_rows_cap = cap;
+    return SPX_OK;
+}
+
+template <class T> int64_t coo_rows_smem(const spx_matrix *A)
+{
+    return CooRowsShape<T, kRowsTile>::smem((int)std::min<int64_t>(A->coo_rows_cap, 1 << 24));
+}
+
+template <class T, int MODE>
+int launch_coo_rows_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e)
+{
+    auto kern = k_coo_rows<T, kRowsTile, MODE>;
+    SPX_TRY(ensure_coo_rowtiles(ctx, A));
+    static std::once_flag once;
+    static int attr_st = SPX_OK, dyn_max = 0;
+    std::call_once(once, [&] {
+        cudaFuncAttributes fa;
+        cudaError_t er = cudaFuncGetAttributes(&fa, kern);
+        if (er == cudaSuccess) {
+            dyn_max = ctx->max_smem_optin - (int)fa.sharedSizeBytes;
+            er = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+        }
+        attr_st = er == cudaSuccess ? SPX_OK : cuda_fail(er, "row-block COO shared-memory limit");
+    });
+    SPX_TRY(attr_st);
+    const int64_t smem = coo_rows_smem<T>(A);
+    if (smem > dyn_max)
+        return fail(SPX_ERR_TOO_LARGE, "row-block COO: a tile of 128 rows does not fit in shared memory");
+    const int64_t ntiles = ceil_div(A->n, kRowsTile);
+    const int grid = grid_for(ctx, kern, kRowsTile, (int)smem, ntiles);
+    SPX_TRY(ensure_scratch(ctx, A, 0, grid, sizeof(T)));
+    kern<<<grid, kRowsTile, (int)smem, ctx->stream>>>((int)A->n, A->coo_row.as<int>(), A->coo_col.as<int>(), cval, x,
+                                                      A->coo_rowtiles.as<int>(), (int)ntiles, (int)A->coo_rows_cap,
+                                                      A->partials.as<T>(), A->ticket.as<unsigned>(), ctx->dev_err, e);
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T> int launch_coo_rows(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e)
+{
+    return epi_is_plain(e) ? launch_coo_rows_m<T, 1>(ctx, A, cval, x, e) : launch_coo_rows_m<T, 0>(ctx, A, cval, x, e);
+}
+
 template <class T, int IPT, int MODE>
 int launch_split_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
 {
@@ -1732,10 +1963,24 @@ int dispatch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const E
 template <class T>
 int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
 {
-    // param: 8 / 16 = nonzeros per lane of the warp-independent split kernel (default 8);
-    // 104 / 108 / 116 = tiled segmented reduction with 4 / 8 / 16 items per thread
+    // param: 1 = row-block (tiles of 128 rows, one thread per row; rows of similar length);
+    // 8 / 16 = nonzeros per lane of the warp-independent split kernel;
+    // 104 / 108 / 116 = tiled segmented reduction with 4 / 8 / 16 items per thread.
+    // Default: row-block for the COO format with short rows of similar length (the
+    // boundary scan of a tile costs about mean-row-length steps per thread: measured
+    // faster than split for the 7-point stencil, slower for the 27-point one), else split.
     int p = A->kernel == SPX_KERNEL_COO ? A->kparam : 0;
-    if (p <= 0) p = 8;
+    if (p <= 0) {
+        p = 8;
+        if (!add && A->format == SPX_COO && A->mean_len <= 16.0 && (double)A->max_len <= 2.0 * A->mean_len + 8.0) {
+            SPX_TRY(ensure_coo_rowtiles(ctx, A));
+            if (coo_rows_smem<T>(A) <= std::min<int64_t>(ctx->max_smem_optin, 120 * 1024)) p = 1;
+        }
+    }
+    if (p == 1) {
+        if (add) return fail(SPX_ERR_UNSUPPORTED, "the row-block COO kernel does not run HYB's COO part");
+        return launch_coo_rows<T>(ctx, A, cval, x, e);
+    }
     switch (p) {
     case 8: return launch_coo_split<T, 8>(ctx, A, cval, x, e, add);
     case 16: return launch_coo_split<T, 16>(ctx, A, cval, x, e, add);

@@ -108,6 +108,9 @@ struct spx_matrix {
     // COO tile map (COO format / HYB COO part)
     spx::DBuf coo_tiles;      // int per tile boundary
     int64_t coo_tiles_items = 0, coo_ntiles = 0, coo_nsplit = 0;
+    // COO row-block kernel: first entry of each tile of 128 rows, and the most entries in a tile
+    spx::DBuf coo_rowtiles;
+    int64_t coo_rows_cap = -1;
     // per-tile carries, look-back flags, reduction scratch of the SpMV kernels
     spx::DBuf carry_row, carry_val, flags, partials;
     spx::DBuf ticket;  // unsigned counters for last-block detection

@@ -69,7 +69,8 @@ VARIANTS = [
     ("csr", "merge", 4), ("csr", "merge", 8), ("csr", "merge", 16),
     ("csr", "split", 8), ("csr", "split", 16), ("csr", "rows", 0), ("csr", "rows", 1),
     ("ell", None, 0), ("ell", "ell", 1),
-    ("coo", None, 0), ("coo", "coo", 16), ("coo", "coo", 104), ("coo", "coo", 116),
+    ("coo", None, 0), ("coo", "coo", 1), ("coo", "coo", 8), ("coo", "coo", 16), ("coo", "coo", 104),
+    ("coo", "coo", 116),
     ("hyb", None, 0), ("hyb0", None, 0), ("hyb3", None, 0),
 ]
 
@@ -122,7 +123,14 @@ def test_spmv_parity(spx, ctx, mname, variant, dtype):
         n = rp.shape[0] - 1
         xd = torch.from_numpy(x).to(DEV).to(tdt)
         y = torch.full((n,), float("nan"), dtype=tdt, device=DEV)
-        spx.spx_spmv(ctx, A, xd, y)
+        try:
+            spx.spx_spmv(ctx, A, xd, y)
+        except spx.SpxError as err:
+            # the row-block kernels hold a tile of 128 rows in shared memory; a
+            # matrix whose tile does not fit is rejected, never computed wrongly
+            if (kname, param) in (("coo", 1), ("rows", 0), ("rows", 1)) and err.status == spx.SPX_ERR_TOO_LARGE:
+                pytest.skip("tile of 128 rows does not fit in shared memory")
+            raise
         torch.cuda.synchronize()
         yref = oracle.spmv_csr(rp, col, val_r, x_r)
         bound = oracle.spmv_absbound(rp, col, val_r, x_r)
