@@ -60,7 +60,10 @@ typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2, SPX_CGS = 3 } spx_so
 /* Arithmetic of a solve: all FP64; all FP32 (values, vectors, dots and
  * scalars in float); or FP64 iterative refinement around an FP32 inner solve
  * (outer residual r = b - A x and update x += d in double on the FP64 values;
- * inner Krylov iterations in float on an FP32 copy of the values). */
+ * inner Krylov iterations in float on an FP32 copy of the values).  An inner
+ * cycle solves A d = r / ||r|| to 1e-4 relative in at most 500 iterations, at
+ * most 20 cycles; an inner CGS cycle also ends once its recurrence residual
+ * has gone 20 iterations without halving. */
 typedef enum { SPX_PREC_F64 = 0, SPX_PREC_F32 = 1, SPX_PREC_MIXED = 2 } spx_precision;
 
 typedef enum {

@@ -788,6 +788,14 @@ static int64_t bicgstab_f32(int64_t n, const int32_t *rp, const int32_t *col, co
     return it;
 }
 
+/* FP32 CGS as the inner solver of refinement.  Besides inner_tol and the    */
+/* cycle cap it stops once the recurrence relative residual has gone        */
+/* CGS_IR_STALL iterations without falling below half of the level it last  */
+/* halved to (1 at x0 = 0).  CGS squares its residual polynomial            */
+/* (Sonneveld, SIAM J. Sci. Stat. Comput. 10, 1989), so from a right-hand   */
+/* side that mixes smooth and rough components an FP32 cycle can blow the   */
+/* residual up and never recover; the FP64 outer residual then restarts it. */
+#define CGS_IR_STALL 20
 static int64_t cgs_f32(int64_t n, const int32_t *rp, const int32_t *col, const float *val,
                        const float *b, float *x, float tol, int64_t maxit)
 {
@@ -797,7 +805,8 @@ static int64_t cgs_f32(int64_t n, const int32_t *rp, const int32_t *col, const f
     float bn = sqrtf(dot_f32(n, b, b));
     for (int64_t i = 0; i < n; ++i) { x[i] = 0.0f; r[i] = b[i]; rh[i] = b[i]; p[i] = b[i]; u[i] = b[i]; }
     float rho = dot_f32(n, rh, r);
-    int64_t it = 0;
+    int64_t it = 0, mark_it = 0;
+    float mark = 1.0f;  /* relative residual of x0 = 0 */
     while (it < maxit && bn > 0.0f && rho != 0.0f) {
         spmv_f32(n, rp, col, val, p, v);
         float vr = dot_f32(n, rh, v);
@@ -807,7 +816,10 @@ static int64_t cgs_f32(int64_t n, const int32_t *rp, const int32_t *col, const f
         spmv_f32(n, rp, col, val, w, v);
         for (int64_t i = 0; i < n; ++i) r[i] -= alpha * v[i];
         ++it;
-        if (sqrtf(dot_f32(n, r, r)) / bn <= tol) break;
+        float rel = sqrtf(dot_f32(n, r, r)) / bn;
+        if (rel <= tol) break;
+        if (rel < 0.5f * mark) { mark = rel; mark_it = it; }
+        else if (it - mark_it >= CGS_IR_STALL) break;
         float rho1 = dot_f32(n, rh, r);
         float beta = rho1 / rho;
         for (int64_t i = 0; i < n; ++i) { u[i] = r[i] + beta * q[i]; p[i] = u[i] + beta * (q[i] + beta * p[i]); }

@@ -290,11 +290,16 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
 
 // One system by CGS (Sonneveld; shadow residual r^ = r0).  The SpMV operands
 // (p, then u + q) are staged in turn through the shared-memory vector ps.
+// stall > 0 (inner cycle of refinement, x0 = 0): also stop once the recurrence
+// residual has gone `stall` iterations without halving.
 template <class T, class V, int BLOCK>
 __device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restrict__ col, const V *__restrict__ val,
                           const T *__restrict__ b, T *__restrict__ x, T *const *w, T *ps, T *red, T tol,
-                          long long maxit, bool zero_x0, bool check_true, long long &iters, T &relres)
+                          long long maxit, bool zero_x0, bool check_true, long long &iters, T &relres,
+                          int stall = 0)
 {
+    T mark = T(1);
+    long long mark_it = iters;
     const int tid = threadIdx.x;
     T *r = w[0], *rh = w[1], *p = w[2], *u = w[3], *q = w[4], *v = w[5];
     T bb = T(0);
@@ -366,6 +371,15 @@ __device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restri
             if (rr <= tol2) {
                 status = SPX_CONVERGED;
                 break;
+            }
+            if (stall > 0) {
+                if (relres < T(0.5) * mark) {
+                    mark = relres;
+                    mark_it = iters;
+                } else if (iters - mark_it >= stall) {
+                    status = SPX_STAGNATED;
+                    break;
+                }
             }
             const T beta = rhr / rho;
             for (int i = tid; i < n; i += BLOCK) {
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(BLOCK)
                                                    cyc_max, true, false, iters, rel32);
                 else if (SOLVER == SPX_CGS)
                     cgs_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, cyc_max, true,
-                                                    false, iters, rel32);
+                                                    false, iters, rel32, kIrCgsStall);
                 else
                     bicgstab_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, cyc_max,
                                                          true, false, iters, rel32);

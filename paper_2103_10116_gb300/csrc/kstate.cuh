@@ -28,6 +28,12 @@ template <class T> struct KState {
     int s_conv;   // BiCGSTAB: converged on s, x += alpha p still to apply
     long long iters;
     long long maxit;
+    // stall rule of an inner CGS cycle (stall > 0): the cycle ends once the
+    // recurrence residual has not fallen below half of `mark` for `stall`
+    // iterations; mark starts at 1 (x0 = 0) and is lowered at each halving
+    T mark;
+    long long mark_it;
+    int stall;
 };
 
 enum : int {
@@ -153,6 +159,15 @@ template <class T> __device__ __forceinline__ void run_fin(int fin, void *state,
         s->relres = sqrt(rr / s->bb);
         if (rr <= s->tol2) { kstop(s, SPX_CONVERGED); break; }
         if (s->iters >= s->maxit) { kstop(s, SPX_MAX_ITER); break; }
+        if (s->stall > 0) {
+            if (s->relres < T(0.5) * s->mark) {
+                s->mark = s->relres;
+                s->mark_it = s->iters;
+            } else if (s->iters - s->mark_it >= s->stall) {
+                kstop(s, SPX_STAGNATED);
+                break;
+            }
+        }
         if (rhr == T(0)) { kstop(s, SPX_BREAKDOWN); break; }
         s->beta = rhr / s->rho;
         s->rho = rhr;

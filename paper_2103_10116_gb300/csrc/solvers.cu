@@ -1029,9 +1029,9 @@ int check_dev_err(spx_ctx *ctx)
     return SPX_OK;
 }
 
-// CG / BiCGSTAB.  inner: FP32 inner solve of refinement (no true-residual
-// check, no restarts; x starts at 0).  fixed > 0: run exactly that many
-// iterations (tol ignored).
+// CG / BiCGSTAB / CGS.  inner: FP32 inner solve of refinement (no
+// true-residual check, no restarts; x starts at 0; CGS also ends on the stall
+// rule).  fixed > 0: run exactly that many iterations (tol ignored).
 template <class T>
 int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b, T *x, double tol,
               int64_t maxit, bool use32, bool inner, int64_t fixed, spx_solve_info *info)
@@ -1042,6 +1042,8 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
     hs.rtol2 = fixed > 0 ? T(0) : (T)(tol * tol);
     hs.maxit = fixed > 0 ? fixed : maxit;
     hs.status = SPX_MAX_ITER;
+    hs.mark = T(1);
+    hs.stall = inner && solver == SPX_CGS ? kIrCgsStall : 0;
     KState<T> *st = w->state.as<KState<T>>();
     SPX_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
     const int64_t n = A->n;

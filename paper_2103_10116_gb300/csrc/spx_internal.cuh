@@ -153,9 +153,16 @@ template <class T> int axpby_launch(spx_ctx *ctx, int64_t n, T alpha, const T *x
 int ensure_merge_tiles(spx_ctx *ctx, spx_matrix *A, int64_t tile_items, int64_t slack);
 
 // Iterative refinement: FP32 inner iterations per outer cycle are capped, so an
-// inner solve that stagnates (FP32 CGS on large systems) hands back its best
-// correction to the FP64 outer loop instead of running to the global limit.
+// inner solve that stagnates (FP32 CGS on large systems) hands its correction
+// back to the FP64 outer loop instead of running to the global limit.
 constexpr int kIrInnerCap = 500;
+// An inner CGS cycle also ends once its recurrence residual has gone this many
+// iterations without falling below half of the level it last halved to
+// (starting from 1 at x0 = 0).  CGS squares its residual polynomial, so a
+// cycle that starts from a residual mixing smooth and rough components can
+// grow it by orders of magnitude in FP32 and never recover; the outer FP64
+// residual then restarts the inner solve from the true residual.
+constexpr int kIrCgsStall = 20;
 
 // Batched solves without graph capture, at a given block size (batch.cu), and
 // the largest system the batched kernel holds (rows).

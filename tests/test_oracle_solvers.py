@@ -289,3 +289,22 @@ def test_ir_reaches_fp64_tolerance_cgs():
     x, info = oracle.ir(rp, col, val, b, solver="cgs", tol=1e-10)
     assert info.status == oracle.CONVERGED and info.relres_true <= 1e-10
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-8
+
+
+def test_ir_cgs_stall_rule_ends_blown_up_cycles():
+    """FP32 CGS inside refinement on the 64^3 upwind convection-diffusion
+    matrix: after the first cycle the inner residual blows up (CGS squares its
+    residual polynomial); with the 500-iteration cap alone the solve needs
+    711 inner iterations, with the 20-iteration stall rule far fewer.  The
+    true residual is recomputed here with scipy, independently of the oracle."""
+    import scipy.sparse as sp
+    rp, col, val = synth.convdiff3d_upwind(64)
+    n = rp.shape[0] - 1
+    xs = np.random.default_rng(3).uniform(-1, 1, n)
+    A = sp.csr_matrix((val, col, rp), shape=(n, n))
+    b = A @ xs
+    x, info = oracle.ir(rp, col, val, b, solver="cgs", tol=1e-10)
+    assert info.status == oracle.CONVERGED
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-10
+    assert info.restarts >= 3  # more than one blown-up cycle was cut short and restarted
+    assert info.iterations < 300, info
