@@ -87,6 +87,14 @@ def _lib(mutant: int = 0) -> C.CDLL:
             for name in ("orc_gmres", "orc_gmres_jacobi"):
                 getattr(lib, name).restype = C.c_int
                 getattr(lib, name).argtypes = [i64, p, p, p, p, p, C.c_int, dbl, i64, C.POINTER(_Info), p]
+            for name in ("orc_cg_bjacobi", "orc_bicgstab_bjacobi", "orc_cgs_bjacobi"):
+                getattr(lib, name).restype = C.c_int
+                getattr(lib, name).argtypes = [i64, p, p, p, p, p, dbl, i64, C.POINTER(_Info), p, C.c_int]
+            lib.orc_gmres_bjacobi.restype = C.c_int
+            lib.orc_gmres_bjacobi.argtypes = [i64, p, p, p, p, p, C.c_int, dbl, i64, C.POINTER(_Info), p,
+                                              C.c_int]
+            lib.orc_block_jacobi_inv.restype = C.c_int
+            lib.orc_block_jacobi_inv.argtypes = [i64, p, p, p, C.c_int, p]
             lib.orc_ir.restype = C.c_int
             lib.orc_ir.argtypes = [i64, p, p, p, C.c_int, p, p, dbl, dbl, C.c_int, i64,
                                    C.POINTER(_Info)]
@@ -209,7 +217,19 @@ def hyb_auto_width(rp, vbytes: int) -> int:
     return int(_lib().orc_hyb_auto_width(rp.shape[0] - 1, _ptr(rp), vbytes))
 
 
-def _solve(fn, args, rp, col, val, b, x0, with_hist, maxit, mutant):
+def block_jacobi_inv(rp, col, val, bs: int, mutant=0) -> np.ndarray:
+    """Inverses of the bs x bs diagonal blocks of A (block-Jacobi, listed among
+    the library's preconditioners in Section 2), shape (ceil(n / bs), bs, bs)."""
+    rp, col, val = _csr(rp, col, val)
+    n = rp.shape[0] - 1
+    nb = (n + bs - 1) // bs
+    out = np.empty((max(nb, 1), bs, bs), dtype=np.float64)
+    if _lib(mutant).orc_block_jacobi_inv(n, _ptr(rp), _ptr(col), _ptr(val), int(bs), _ptr(out)) != 0:
+        raise ValueError("block size must be at least 1")
+    return out[:nb]
+
+
+def _solve(fn, args, rp, col, val, b, x0, with_hist, maxit, mutant, tail=()):
     rp, col, val = _csr(rp, col, val)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = rp.shape[0] - 1
@@ -217,7 +237,7 @@ def _solve(fn, args, rp, col, val, b, x0, with_hist, maxit, mutant):
     info = _Info()
     hist = np.full(maxit + 2, np.nan) if with_hist else None
     getattr(_lib(mutant), fn)(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(b), _ptr(x), *args,
-                              C.byref(info), _ptr(hist) if hist is not None else None)
+                              C.byref(info), _ptr(hist) if hist is not None else None, *tail)
     si = SolveInfo(info.status, info.iterations, info.restarts, info.relres_recurrence,
                    info.relres_true)
     if with_hist:
@@ -225,39 +245,51 @@ def _solve(fn, args, rp, col, val, b, x0, with_hist, maxit, mutant):
     return x, si
 
 
-def _fn(base, precond):
+def _fn(base, precond, block_size):
+    """Entry point and trailing arguments for a preconditioner choice."""
     if precond is None:
-        return base
+        return base, ()
     if precond == "jacobi":
-        return base + "_jacobi"
+        return base + "_jacobi", ()
+    if precond == "block_jacobi":
+        if int(block_size) < 1:
+            raise ValueError("block_size must be at least 1")
+        return base + "_bjacobi", (int(block_size),)
     raise ValueError(f"unknown preconditioner {precond!r}")
 
 
-def cg(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+def cg(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None, block_size=8):
     """Conjugate Gradient for SPD A (Section 5 names CG; textbook form);
-    precond="jacobi": preconditioned CG with M = diag(A)."""
-    return _solve(_fn("orc_cg", precond), [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant)
+    precond="jacobi": preconditioned CG with M = diag(A); "block_jacobi": M =
+    the block diagonal of A with blocks of block_size rows."""
+    fn, tail = _fn("orc_cg", precond, block_size)
+    return _solve(fn, [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant, tail)
 
 
-def bicgstab(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+def bicgstab(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None,
+             block_size=8):
     """BiCGSTAB for general A (Section 5 names BiCGSTAB; van der Vorst form);
-    precond="jacobi": right preconditioning with M = diag(A)."""
-    return _solve(_fn("orc_bicgstab", precond), [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit,
-                  mutant)
+    precond="jacobi" / "block_jacobi": right preconditioning with M = diag(A) /
+    the block diagonal of A."""
+    fn, tail = _fn("orc_bicgstab", precond, block_size)
+    return _solve(fn, [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant, tail)
 
 
-def cgs(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+def cgs(rp, col, val, b, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None, block_size=8):
     """Conjugate Gradient Squared (Sonneveld) for general A (Section 5 names CGS);
-    precond="jacobi": right preconditioning with M = diag(A)."""
-    return _solve(_fn("orc_cgs", precond), [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit,
-                  mutant)
+    precond="jacobi" / "block_jacobi": right preconditioning with M = diag(A) /
+    the block diagonal of A."""
+    fn, tail = _fn("orc_cgs", precond, block_size)
+    return _solve(fn, [float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant, tail)
 
 
-def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None):
+def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mutant=0, precond=None,
+          block_size=8):
     """Restarted GMRES(m), MGS Arnoldi + Givens rotations (Section 5 names GMRES);
-    precond="jacobi": right preconditioning with M = diag(A)."""
-    return _solve(_fn("orc_gmres", precond), [int(m), float(tol), int(maxit)], rp, col, val, b, x0, hist,
-                  maxit, mutant)
+    precond="jacobi" / "block_jacobi": right preconditioning with M = diag(A) /
+    the block diagonal of A."""
+    fn, tail = _fn("orc_gmres", precond, block_size)
+    return _solve(fn, [int(m), float(tol), int(maxit)], rp, col, val, b, x0, hist, maxit, mutant, tail)
 
 
 def ir(rp, col, val, b, solver="cg", tol=1e-10, inner_tol=1e-4, max_outer=20,

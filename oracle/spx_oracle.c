@@ -242,6 +242,39 @@ static double true_relres(int64_t n, const int32_t *rp, const int32_t *col, cons
 #define ORC_MAX_RESTARTS 3
 
 /* ------------------------------------------------------------------------- */
+/* A preconditioner M^{-1} given as the inverses of the diagonal blocks of A: */
+/* block k covers rows and columns [k bs, (k+1) bs) (the last one clipped to */
+/* n); minv holds each block's bs x bs inverse row-major.  bs = 1 is Jacobi, */
+/* minv[i] = 1 / a_ii.  out = M^{-1} in, each row summed in column order.    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int bs;
+    const double *minv;
+} orc_prec;
+
+static void prec_apply(const orc_prec *M, int64_t n, const double *in, double *out)
+{
+    if (M->bs == 1) {
+        for (int64_t i = 0; i < n; ++i) out[i] = M->minv[i] * in[i];
+        return;
+    }
+    const int64_t bs = M->bs;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t k = i / bs, r = i % bs, c0 = k * bs;
+        const double *row = M->minv + (size_t)(k * bs + r) * (size_t)bs;
+        double s = 0.0;
+#if ORC_MUTANT == 8
+        for (int64_t j = 0; j < bs && c0 + j < n; ++j) /* planted: the block's transpose */
+            s += M->minv[(size_t)(k * bs + j) * (size_t)bs + (size_t)r] * in[c0 + j];
+        (void)row;
+#else
+        for (int64_t j = 0; j < bs && c0 + j < n; ++j) s += row[j] * in[c0 + j];
+#endif
+        out[i] = s;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* CG (Hestenes-Stiefel) for symmetric positive definite A.                  */
 /*   r = b - A x, p = r, rho = r.r                                           */
 /*   loop: q = A p; alpha = rho / (p.q); x += alpha p; r -= alpha q;         */
@@ -252,7 +285,7 @@ static double true_relres(int64_t n, const int32_t *rp, const int32_t *col, cons
 /* ------------------------------------------------------------------------- */
 static int cg_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                   const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist,
-                  const double *dinv)
+                  const orc_prec *M)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -263,17 +296,19 @@ static int cg_run(int64_t n, const int32_t *rp, const int32_t *col, const double
     }
     double *r = malloc((size_t)n * sizeof(double)), *p = malloc((size_t)n * sizeof(double));
     double *q = malloc((size_t)n * sizeof(double));
-    double *z = dinv ? malloc((size_t)n * sizeof(double)) : NULL; /* z = M^{-1} r */
+    double *z = M ? malloc((size_t)n * sizeof(double)) : NULL; /* z = M^{-1} r */
     int64_t it = 0;
     int status = ORC_MAX_ITER;
     double rel = 0.0, reltrue = 0.0;
     for (int restart = 0;; ++restart) {
         orc_spmv_csr(n, rp, col, val, x, q);
         for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
-        if (dinv)
-            for (int64_t i = 0; i < n; ++i) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
+        if (M) {
+            prec_apply(M, n, r, z);
+            for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+        }
         double rr = dot(n, r, r);
-        double rho = dinv ? dot(n, r, z) : rr;
+        double rho = M ? dot(n, r, z) : rr;
         rel = sqrt(rr) / bnorm;
         if (hist && it == 0) hist[0] = rel;
         status = ORC_MAX_ITER;
@@ -289,15 +324,14 @@ static int cg_run(int64_t n, const int32_t *rp, const int32_t *col, const double
             rel = sqrt(rr1) / bnorm;
             if (hist) hist[it] = rel;
             if (rel <= tol) { status = ORC_CONVERGED; break; }
-            if (dinv)
-                for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
-            double rho1 = dinv ? dot(n, r, z) : rr1;
+            if (M) prec_apply(M, n, r, z);
+            double rho1 = M ? dot(n, r, z) : rr1;
 #if ORC_MUTANT == 3
             double beta = -rho1 / rho; /* planted: wrong sign */
 #else
             double beta = rho1 / rho;
 #endif
-            const double *zr = dinv ? z : r;
+            const double *zr = M ? z : r;
             for (int64_t i = 0; i < n; ++i) p[i] = zr[i] + beta * p[i];
             rho = rho1;
         }
@@ -334,7 +368,7 @@ int orc_cg(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
 /* ------------------------------------------------------------------------- */
 static int bicgstab_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                         const double *b, double *x, double tol, int64_t maxit, orc_info *info,
-                        double *hist, const double *dinv)
+                        double *hist, const orc_prec *M)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -345,8 +379,8 @@ static int bicgstab_run(int64_t n, const int32_t *rp, const int32_t *col, const 
     size_t bytes = (size_t)n * sizeof(double);
     double *r = malloc(bytes), *rh = malloc(bytes), *p = malloc(bytes), *v = malloc(bytes);
     double *s = malloc(bytes), *t = malloc(bytes);
-    double *ph = dinv ? malloc(bytes) : NULL, *sh = dinv ? malloc(bytes) : NULL; /* M^{-1} p, M^{-1} s */
-    if (!dinv) { ph = p; sh = s; }
+    double *ph = M ? malloc(bytes) : NULL, *sh = M ? malloc(bytes) : NULL; /* M^{-1} p, M^{-1} s */
+    if (!M) { ph = p; sh = s; }
     int64_t it = 0;
     int status = ORC_MAX_ITER;
     double rel = 0.0, reltrue = 0.0;
@@ -362,8 +396,7 @@ static int bicgstab_run(int64_t n, const int32_t *rp, const int32_t *col, const 
             if (rho1 == 0.0) { status = ORC_BREAKDOWN; break; }
             double beta = (rho1 / rho) * (alpha / omega);
             for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
-            if (dinv)
-                for (int64_t i = 0; i < n; ++i) ph[i] = dinv[i] * p[i];
+            if (M) prec_apply(M, n, p, ph);
             orc_spmv_csr(n, rp, col, val, ph, v);
             double rv = dot(n, rh, v);
             if (rv == 0.0) { status = ORC_BREAKDOWN; break; }
@@ -379,8 +412,7 @@ static int bicgstab_run(int64_t n, const int32_t *rp, const int32_t *col, const 
                 status = ORC_CONVERGED;
                 break;
             }
-            if (dinv)
-                for (int64_t i = 0; i < n; ++i) sh[i] = dinv[i] * s[i];
+            if (M) prec_apply(M, n, s, sh);
             orc_spmv_csr(n, rp, col, val, sh, t);
             double tt = dot(n, t, t);
             if (tt == 0.0) { status = ORC_BREAKDOWN; break; }
@@ -408,7 +440,7 @@ static int bicgstab_run(int64_t n, const int32_t *rp, const int32_t *col, const 
     info->iterations = it;
     info->relres_recurrence = rel;
     info->relres_true = reltrue;
-    if (dinv) { free(ph); free(sh); }
+    if (M) { free(ph); free(sh); }
     free(r); free(rh); free(p); free(v); free(s); free(t);
     return 0;
 }
@@ -433,7 +465,7 @@ int orc_bicgstab(int64_t n, const int32_t *rp, const int32_t *col, const double 
 /* ------------------------------------------------------------------------- */
 static int cgs_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                    const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist,
-                   const double *dinv)
+                   const orc_prec *M)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -444,7 +476,7 @@ static int cgs_run(int64_t n, const int32_t *rp, const int32_t *col, const doubl
     size_t bytes = (size_t)n * sizeof(double);
     double *r = malloc(bytes), *rh = malloc(bytes), *p = malloc(bytes), *u = malloc(bytes);
     double *q = malloc(bytes), *v = malloc(bytes), *w = malloc(bytes);
-    double *ph = dinv ? malloc(bytes) : p;  /* M^{-1} p */
+    double *ph = M ? malloc(bytes) : p;  /* M^{-1} p, and M^{-1} (u + q) on its way into w */
     int64_t it = 0;
     int status = ORC_MAX_ITER;
     double rel = 0.0, reltrue = 0.0;
@@ -457,16 +489,17 @@ static int cgs_run(int64_t n, const int32_t *rp, const int32_t *col, const doubl
         status = rel <= tol ? ORC_CONVERGED : ORC_MAX_ITER;
         while (status == ORC_MAX_ITER && it < maxit) {
             if (rho == 0.0) { status = ORC_BREAKDOWN; break; }
-            if (dinv)
-                for (int64_t i = 0; i < n; ++i) ph[i] = dinv[i] * p[i];
+            if (M) prec_apply(M, n, p, ph);
             orc_spmv_csr(n, rp, col, val, ph, v);                      /* v = A M^{-1} p */
             double vr = dot(n, rh, v);
             if (vr == 0.0) { status = ORC_BREAKDOWN; break; }
             double alpha = rho / vr;
             for (int64_t i = 0; i < n; ++i) q[i] = u[i] - alpha * v[i];
             for (int64_t i = 0; i < n; ++i) w[i] = u[i] + q[i];      /* u + q */
-            if (dinv)
-                for (int64_t i = 0; i < n; ++i) w[i] *= dinv[i];      /* M^{-1} (u + q) */
+            if (M) {                                                    /* M^{-1} (u + q) */
+                prec_apply(M, n, w, ph);
+                for (int64_t i = 0; i < n; ++i) w[i] = ph[i];
+            }
             for (int64_t i = 0; i < n; ++i) x[i] += alpha * w[i];
             orc_spmv_csr(n, rp, col, val, w, v);                       /* A (u + q) */
 #if ORC_MUTANT == 6
@@ -493,7 +526,7 @@ static int cgs_run(int64_t n, const int32_t *rp, const int32_t *col, const doubl
     info->iterations = it;
     info->relres_recurrence = rel;
     info->relres_true = reltrue;
-    if (dinv) free(ph);
+    if (M) free(ph);
     free(r); free(rh); free(p); free(u); free(q); free(v); free(w);
     return 0;
 }
@@ -515,7 +548,7 @@ int orc_cgs(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
 /* ------------------------------------------------------------------------- */
 static int gmres_run(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                      const double *b, double *x, int m, double tol, int64_t maxit, orc_info *info,
-                     double *hist, const double *dinv)
+                     double *hist, const orc_prec *M)
 {
     memset(info, 0, sizeof(*info));
     double bnorm = nrm2(n, b);
@@ -526,7 +559,7 @@ static int gmres_run(int64_t n, const int32_t *rp, const int32_t *col, const dou
     size_t bytes = (size_t)n * sizeof(double);
     double *V = malloc(bytes * (size_t)(m + 1));
     double *w = malloc(bytes);
-    double *z = dinv ? malloc(bytes) : NULL; /* M^{-1} v_j, and the cycle's update */
+    double *z = M ? malloc(bytes) : NULL; /* M^{-1} v_j, and the cycle's update */
     double *H = calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
     double *cs = malloc(sizeof(double) * m), *sn = malloc(sizeof(double) * m);
     double *g = malloc(sizeof(double) * (m + 1)), *yv = malloc(sizeof(double) * m);
@@ -553,8 +586,8 @@ static int gmres_run(int64_t n, const int32_t *rp, const int32_t *col, const dou
         int j = 0, done = 0;
         for (; j < m && it < maxit; ++j) {
             double *vj = V + (size_t)j * n;
-            if (dinv) {
-                for (int64_t k = 0; k < n; ++k) z[k] = dinv[k] * vj[k];
+            if (M) {
+                prec_apply(M, n, vj, z);
                 orc_spmv_csr(n, rp, col, val, z, w);   /* w = A M^{-1} v_j */
             } else {
                 orc_spmv_csr(n, rp, col, val, vj, w);
@@ -602,13 +635,14 @@ static int gmres_run(int64_t n, const int32_t *rp, const int32_t *col, const dou
             for (int k = i + 1; k < j; ++k) s -= H[i * m + k] * yv[k];
             yv[i] = s / H[i * m + i];
         }
-        if (dinv) {  /* x += M^{-1} V y */
+        if (M) {  /* x += M^{-1} V y */
             memset(z, 0, bytes);
             for (int i = 0; i < j; ++i) {
                 double *vi = V + (size_t)i * n;
                 for (int64_t k = 0; k < n; ++k) z[k] += yv[i] * vi[k];
             }
-            for (int64_t k = 0; k < n; ++k) x[k] += dinv[k] * z[k];
+            prec_apply(M, n, z, w);
+            for (int64_t k = 0; k < n; ++k) x[k] += w[k];
         } else {
             for (int i = 0; i < j; ++i) {
                 double *vi = V + (size_t)i * n;
@@ -669,7 +703,8 @@ int orc_cg_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double
                   const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
 {
     double *d = jacobi_dinv(n, rp, col, val);
-    int st = cg_run(n, rp, col, val, b, x, tol, maxit, info, hist, d);
+    orc_prec M = {1, d};
+    int st = cg_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
     free(d);
     return st;
 }
@@ -678,7 +713,8 @@ int orc_bicgstab_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const 
                         const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
 {
     double *d = jacobi_dinv(n, rp, col, val);
-    int st = bicgstab_run(n, rp, col, val, b, x, tol, maxit, info, hist, d);
+    orc_prec M = {1, d};
+    int st = bicgstab_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
     free(d);
     return st;
 }
@@ -687,7 +723,8 @@ int orc_cgs_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const doubl
                    const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist)
 {
     double *d = jacobi_dinv(n, rp, col, val);
-    int st = cgs_run(n, rp, col, val, b, x, tol, maxit, info, hist, d);
+    orc_prec M = {1, d};
+    int st = cgs_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
     free(d);
     return st;
 }
@@ -697,8 +734,120 @@ int orc_gmres_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const dou
                      double *hist)
 {
     double *d = jacobi_dinv(n, rp, col, val);
-    int st = gmres_run(n, rp, col, val, b, x, m, tol, maxit, info, hist, d);
+    orc_prec M = {1, d};
+    int st = gmres_run(n, rp, col, val, b, x, m, tol, maxit, info, hist, &M);
     free(d);
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Block-Jacobi preconditioning, M = the block diagonal of A with blocks of  */
+/* bs consecutive rows and columns (Section 2 lists block-Jacobi, in its    */
+/* adaptive-precision form, among the library's preconditioners; here the   */
+/* inverses are kept at the solve's precision).  Block k's dense matrix D_k  */
+/* gathers the entries of rows [k bs, (k+1) bs) whose columns fall in the    */
+/* same range (duplicates summed in index order); rows past n are identity  */
+/* rows.  D_k^{-1} by Gauss-Jordan elimination on [D_k | I] with partial     */
+/* pivoting (the largest |entry| of the pivot column at or below the        */
+/* diagonal, the first one on ties): swap, scale the pivot row by the       */
+/* reciprocal of the pivot, subtract multiples of it from every other row.  */
+/* A block with an exactly zero pivot is taken as the identity, as Jacobi   */
+/* takes a zero diagonal as 1.  bs = 1 gives exactly Jacobi's 1 / a_ii.     */
+/* ------------------------------------------------------------------------- */
+int orc_block_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs,
+                         double *minv)
+{
+    if (bs < 1) return -1;
+    const int64_t nb = (n + bs - 1) / bs;
+    double *aug = malloc(sizeof(double) * (size_t)bs * (size_t)(2 * bs));
+    for (int64_t k = 0; k < nb; ++k) {
+        const int64_t c0 = k * bs;
+        const int w = 2 * bs;
+        memset(aug, 0, sizeof(double) * (size_t)bs * (size_t)w);
+        for (int r = 0; r < bs; ++r) {
+            const int64_t i = c0 + r;
+            aug[r * w + bs + r] = 1.0;
+            if (i >= n) { aug[r * w + r] = 1.0; continue; }
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
+                if (col[e] >= c0 && col[e] < c0 + bs) aug[r * w + (col[e] - c0)] += val[e];
+        }
+        int singular = 0;
+        for (int p = 0; p < bs && !singular; ++p) {
+            int piv = p;
+            for (int r = p + 1; r < bs; ++r)
+                if (fabs(aug[r * w + p]) > fabs(aug[piv * w + p])) piv = r;
+            if (aug[piv * w + p] == 0.0) { singular = 1; break; }
+            if (piv != p)
+                for (int c = 0; c < w; ++c) {
+                    double t = aug[p * w + c];
+                    aug[p * w + c] = aug[piv * w + c];
+                    aug[piv * w + c] = t;
+                }
+            const double inv = 1.0 / aug[p * w + p];
+            for (int c = 0; c < w; ++c) aug[p * w + c] *= inv;
+            for (int r = 0; r < bs; ++r) {
+                if (r == p) continue;
+                const double f = aug[r * w + p];
+                if (f == 0.0) continue;
+                for (int c = 0; c < w; ++c) aug[r * w + c] -= f * aug[p * w + c];
+            }
+        }
+        double *out = minv + (size_t)k * (size_t)bs * (size_t)bs;
+        for (int r = 0; r < bs; ++r)
+            for (int c = 0; c < bs; ++c)
+                out[r * bs + c] = singular ? (r == c ? 1.0 : 0.0) : aug[r * w + bs + c];
+    }
+    free(aug);
+    return 0;
+}
+
+static double *block_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs)
+{
+    const int64_t nb = (n + bs - 1) / bs;
+    double *m = malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1) * (size_t)bs * (size_t)bs);
+    orc_block_jacobi_inv(n, rp, col, val, bs, m);
+    return m;
+}
+
+int orc_cg_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                   const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist, int bs)
+{
+    double *m = block_jacobi(n, rp, col, val, bs);
+    orc_prec M = {bs, m};
+    int st = cg_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
+    free(m);
+    return st;
+}
+
+int orc_bicgstab_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                         const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist,
+                         int bs)
+{
+    double *m = block_jacobi(n, rp, col, val, bs);
+    orc_prec M = {bs, m};
+    int st = bicgstab_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
+    free(m);
+    return st;
+}
+
+int orc_cgs_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                    const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist, int bs)
+{
+    double *m = block_jacobi(n, rp, col, val, bs);
+    orc_prec M = {bs, m};
+    int st = cgs_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
+    free(m);
+    return st;
+}
+
+int orc_gmres_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                      const double *b, double *x, int m, double tol, int64_t maxit, orc_info *info,
+                      double *hist, int bs)
+{
+    double *mi = block_jacobi(n, rp, col, val, bs);
+    orc_prec M = {bs, mi};
+    int st = gmres_run(n, rp, col, val, b, x, m, tol, maxit, info, hist, &M);
+    free(mi);
     return st;
 }
 
