@@ -418,13 +418,14 @@ def solve_secondary(spx, ctx, stream, dev, peak, fmt="csr"):
 
 
 def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
-    """Jacobi preconditioning (M = diag A) against the plain solvers on
-    badly scaled 128^3 matrices, where a diagonal preconditioner matters:
-    the 7-point Poisson matrix scaled symmetrically, S A S with
-    s_i = exp(U[-2, 2]) (CG), and the upwind convection-diffusion matrix
-    (Peclet 10) with rows scaled by exp(U[-3, 3]) (BiCGSTAB, CGS, GMRES(30));
-    b = A x*, tol 1e-10, FP64, CSR.  (On the unscaled benchmark matrices the
-    diagonal is constant and Jacobi changes nothing.)"""
+    """Jacobi (M = diag A) and block-Jacobi (blocks of 8 rows) preconditioning
+    against the plain solvers on 128^3 matrices: the 7-point Poisson matrix
+    scaled symmetrically, S A S with s_i = exp(U[-2, 2]) (CG); the upwind
+    convection-diffusion matrix (Peclet 10) with rows scaled by exp(U[-3, 3])
+    (BiCGSTAB, CGS, GMRES(30)); and the stress variant with cell Peclet
+    number 10 (Peclet 10 * 129), unscaled, where the constant diagonal leaves
+    Jacobi nothing to do and the blocks hold the strong upwind couplings along
+    x.  b = A x*, tol 1e-10, FP64, CSR."""
     import torch
     from paper_2103_10116_gb300 import synth
     rng = np.random.default_rng(21)
@@ -438,9 +439,11 @@ def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
     poisson = scaled(rp, col, val, sp, sp)
     rp, col, val = synth.convdiff3d_upwind(128)
     cdiff = scaled(rp, col, val, np.exp(rng.uniform(-3.0, 3.0, size=rp.shape[0] - 1)), np.ones(rp.shape[0] - 1))
+    stress = synth.convdiff3d_upwind(128, peclet=10.0 * 129)
     out = {}
     for name, (rp, col, val), solvers in (("poisson128_sym_scaled", poisson, ("cg",)),
-                                          ("convdiff128_row_scaled", cdiff, ("bicgstab", "cgs", "gmres"))):
+                                          ("convdiff128_row_scaled", cdiff, ("bicgstab", "cgs", "gmres")),
+                                          ("convdiff128_cell_peclet10", stress, ("bicgstab", "cgs", "gmres"))):
         n = rp.shape[0] - 1
         with torch.cuda.stream(stream):
             A = spx.spx_matrix_create(ctx, "csr", torch.from_numpy(rp).to(dev), torch.from_numpy(col).to(dev),
@@ -450,10 +453,10 @@ def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
             spx.spx_spmv(ctx, A, xs, b)
             res = {}
             for solver in solvers:
-                for pc in (None, "jacobi"):
+                for pc, tag in ((None, ""), ("jacobi", "_jacobi"), ("block_jacobi", "_block8")):
                     x = torch.zeros(n, dtype=torch.float64, device=dev)
-                    si = spx.spx_solve(ctx, A, b, x, solver, 1e-10, max_iter, restart=30, precond=pc)
-                    res[f"{solver}{'_jacobi' if pc else ''}"] = {
+                    si = spx.spx_solve(ctx, A, b, x, solver, 1e-10, max_iter, restart=30, precond=pc, block_size=8)
+                    res[f"{solver}{tag}"] = {
                         "solve_ms": round(si.time_ms, 2), "iterations": si.iterations, "status": si.status_name,
                         "relres_true": si.relres_true}
             spx.spx_matrix_destroy(A)

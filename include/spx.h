@@ -56,6 +56,18 @@ typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2, SPX_CGS = 3 } spx_so
  * CG becomes preconditioned CG; BiCGSTAB, CGS and GMRES are preconditioned from
  * the right, so the residual they test is always b - A x. */
 #define SPX_PRECOND_JACOBI 0x100
+/* OR SPX_PRECOND_BLOCK(bs) instead for block-Jacobi preconditioning (Section 2
+ * lists block-Jacobi among the library's preconditioners): M = the block
+ * diagonal of A with blocks of bs consecutive rows and columns, bs in
+ * {1, 2, 4, 8, 16, 32}; the last block holds the remaining rows.  Each block is
+ * inverted once per matrix and solve precision by Gauss-Jordan elimination
+ * with partial pivoting in FP64 (a block with an exactly zero pivot counts as
+ * the identity) and applied as a dense bs x bs product; the inverses take
+ * n * bs values of device memory.  Applied as Jacobi is: preconditioned CG, right
+ * preconditioning for the others.  Any other flag bits give SPX_ERR_INVALID. */
+#define SPX_PRECOND_BLOCK_JACOBI 0x200
+#define SPX_PRECOND_BLOCK_SHIFT 16
+#define SPX_PRECOND_BLOCK(bs) (SPX_PRECOND_BLOCK_JACOBI | ((bs) << SPX_PRECOND_BLOCK_SHIFT))
 
 /* Arithmetic of a solve: all FP64; all FP32 (values, vectors, dots and
  * scalars in float); or FP64 iterative refinement around an FP32 inner solve

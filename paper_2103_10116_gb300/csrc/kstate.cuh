@@ -50,6 +50,8 @@ enum : int {
     FIN_CGS_R = 10,     // dots[0] = r.r, dots[1] = r^.r -> convergence, beta = (r^.r)' / (r^.r), rho
     FIN_PCG_RHO0 = 11,  // dots[0] = r.z (z = M^-1 r)  -> initial rho of preconditioned CG
     FIN_PCG_R = 12,     // dots[0] = r.r, dots[1] = r.z -> convergence on r, beta = (r.z)' / (r.z), rho
+    FIN_CG_RR = 13,     // dots[0] = r.r              -> convergence only (block-PCG: r.z comes next)
+    FIN_PCG_RZ = 14,    // dots[0] = r.z (z = M^-1 r) -> beta = (r.z)' / (r.z), rho (block-PCG)
 };
 
 template <class T> __device__ __forceinline__ void kstop(KState<T> *s, int status)
@@ -148,6 +150,21 @@ template <class T> __device__ __forceinline__ void run_fin(int fin, void *state,
         s->relres = sqrt(rr / s->bb);
         if (rr <= s->tol2) { kstop(s, SPX_CONVERGED); break; }
         if (s->iters >= s->maxit) { kstop(s, SPX_MAX_ITER); break; }
+        if (rz == T(0)) { kstop(s, SPX_BREAKDOWN); break; }
+        s->beta = rz / s->rho;
+        s->rho = rz;
+        break;
+    }
+    case FIN_CG_RR: {
+        const T rr = dots[0];
+        s->iters += 1;
+        s->relres = sqrt(rr / s->bb);
+        if (rr <= s->tol2) { kstop(s, SPX_CONVERGED); break; }
+        if (s->iters >= s->maxit) { kstop(s, SPX_MAX_ITER); break; }
+        break;
+    }
+    case FIN_PCG_RZ: {
+        const T rz = dots[0];
         if (rz == T(0)) { kstop(s, SPX_BREAKDOWN); break; }
         s->beta = rz / s->rho;
         s->rho = rz;

@@ -372,8 +372,10 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
 {
     if (!S || !row_ptr || !b || !x || !req_id || n <= 0 || nnz < 0 || (nnz > 0 && (!col_idx || !values)))
         return fail(SPX_ERR_INVALID, "spx_server_submit: bad argument");
-    const int base_solver = solver & ~SPX_PRECOND_JACOBI;
-    if (base_solver < SPX_CG || base_solver > SPX_CGS) return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
+    int base_solver = 0, bs = 0;
+    bool jacobi = false;
+    if (parse_solver_code(solver, &base_solver, &jacobi, &bs) != SPX_OK)
+        return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
     Request *R = new Request();
     R->n = n;
     R->nnz = nnz;
@@ -388,7 +390,8 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     R->tol = tol;
     R->max_iter = max_iter;
     R->footprint = request_footprint(n, nnz, base_solver, precision, restart) +
-                   ((solver & SPX_PRECOND_JACOBI) ? (size_t)n * 24 : 0);  // M^-1 and the preconditioned vectors
+                   (jacobi ? (size_t)n * 24 : 0) +  // M^-1 and the preconditioned vectors
+                   (size_t)n * (size_t)bs * 8;      // block-Jacobi inverses
     R->error = SPX_OK;
     R->t_submit = Clock::now();
     R->block = batch_block_for(n);

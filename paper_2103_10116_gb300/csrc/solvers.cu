@@ -71,16 +71,19 @@ struct SolverWork {
     // mixed precision
     SolverWork *inner = nullptr;
     DBuf ir;  // r (FP64), r32, d32
-    // Jacobi preconditioning: M^{-1} = 1 / diag(A) in the work's precision
+    // Jacobi preconditioning: M^{-1} = 1 / diag(A) in the work's precision;
+    // block-Jacobi (bs > 0, pre also set): inverses of the bs x bs diagonal
+    // blocks, row-major per block
     bool pre = false;
-    DBuf dinv;
+    int bs = 0;
+    DBuf dinv, bjinv;
 };
 
 void solver_work_release(spx_ctx *ctx, SolverWork *w)
 {
     if (!w) return;
     if (w->gexec) cudaGraphExecDestroy(w->gexec);
-    DBuf *bufs[] = {&w->vecs, &w->state, &w->dots, &w->red, &w->ticket, &w->small, &w->ir, &w->dinv};
+    DBuf *bufs[] = {&w->vecs, &w->state, &w->dots, &w->red, &w->ticket, &w->small, &w->ir, &w->dinv, &w->bjinv};
     for (DBuf *b : bufs) dbuf_free(ctx, *b);
     if (w->host) cudaFreeHost(w->host);
     solver_work_release(ctx, w->inner);
@@ -98,17 +101,18 @@ void solver_work_free(spx_matrix *A)
 
 static int nvec_for(int solver, int m, bool pre)
 {
-    if (solver == SPX_CG) return 4;                   // r, p, q, scratch (z = M^-1 r is never stored)
+    if (solver == SPX_CG) return 4;                   // r, p, q, scratch (z = M^-1 r in q's place, or never stored)
     if (solver == SPX_BICGSTAB) return pre ? 9 : 7;   // r, rh, p, v, s, t, scratch (+ M^-1 p, M^-1 s)
     if (solver == SPX_CGS) return pre ? 9 : 8;        // r, rh, p, u, q, v, w, scratch (+ M^-1 p)
     return m + (pre ? 3 : 2);                         // V[0..m], scratch (+ M^-1 v_j)
 }
 
 template <class T>
-static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, int m, bool pre = false)
+static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, int m, bool pre = false, int bs = 0)
 {
     const int dtype = sizeof(T) == 8 ? SPX_F64 : SPX_F32;
-    if (wk && (wk->dtype != dtype || wk->n != n || wk->solver != solver || wk->m != m || wk->pre != pre)) {
+    if (wk && (wk->dtype != dtype || wk->n != n || wk->solver != solver || wk->m != m || wk->pre != pre ||
+               wk->bs != bs)) {
         SolverWork *inner = wk->inner;
         wk->inner = nullptr;
         cudaStreamSynchronize(ctx->stream);
@@ -126,6 +130,7 @@ static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, in
     wk->solver = solver;
     wk->m = m;
     wk->pre = pre;
+    wk->bs = bs;
     wk->ld = (int64_t)round_up((size_t)(n > 0 ? n : 1), 64);
     wk->nvec = nvec_for(solver, m, pre);
     SPX_TRY(dbuf_alloc(ctx, wk->vecs, (size_t)wk->nvec * wk->ld * sizeof(T)));
@@ -182,9 +187,10 @@ __global__ void __launch_bounds__(kVB)
     grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, fin, st, partials, ticket);
 }
 
-// CG: x += alpha p; r -= alpha q; rho' = r.r.  PRE (Jacobi): also r.z with
-// z = dinv r, for beta; convergence is tested on r.r either way.
-template <class T, bool PRE>
+// CG: x += alpha p; r -= alpha q; rho' = r.r.  PRE 1 (Jacobi): also r.z with
+// z = dinv r, for beta; PRE 2 (block-Jacobi): r.r for the convergence test
+// only, r.z follows from the block apply.  Convergence is tested on r.r.
+template <class T, int PRE>
 __global__ void __launch_bounds__(kVB)
     k_cg_xr(int64_t n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ q,
             const T *__restrict__ dinv, KState<T> *st, T *partials, unsigned *ticket)
@@ -193,10 +199,11 @@ __global__ void __launch_bounds__(kVB)
     const T alpha = st->alpha;
     T d0 = T(0), d1 = T(0);
     T xv[kU], rv[kU], pv[kU], qv[kU], dv[kU];
-    SPX_ROWS_LOOP(xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i]; if (PRE) dv[u] = dinv[i];,
+    SPX_ROWS_LOOP(xv[u] = x[i]; rv[u] = r[i]; pv[u] = p[i]; qv[u] = q[i]; if (PRE == 1) dv[u] = dinv[i];,
                   x[i] = fma(alpha, pv[u], xv[u]); const T ri = fma(-alpha, qv[u], rv[u]); r[i] = ri;
-                  d0 = fma(ri, ri, d0); if (PRE) d1 = fma(ri, dv[u] * ri, d1);)
-    grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, PRE ? FIN_PCG_R : FIN_CG_RHO, st, partials, ticket);
+                  d0 = fma(ri, ri, d0); if (PRE == 1) d1 = fma(ri, dv[u] * ri, d1);)
+    grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, PRE == 1 ? FIN_PCG_R : PRE == 2 ? FIN_CG_RR : FIN_CG_RHO, st,
+                             partials, ticket);
 }
 
 // CG: p = r + beta p  (PRE: p = dinv r + beta p)
@@ -289,8 +296,10 @@ __global__ void __launch_bounds__(kVB)
     grid_dots_finish<T, kVB>(d0, d1, (T *)nullptr, FIN_BI_R, st, partials, ticket);
 }
 
-// CGS: q = u - alpha v; w = u + q (PRE: w = dinv (u + q)); x += alpha w
-template <class T, bool PRE>
+// CGS: q = u - alpha v; w = u + q (PRE 1: w = dinv (u + q)); x += alpha w.
+// PRE 2 (block-Jacobi): q and w = u + q only; the block apply forms
+// M^-1 (u + q) and updates x.
+template <class T, int PRE>
 __global__ void __launch_bounds__(kVB)
     k_cgs_qw(int64_t n, T *__restrict__ x, const T *__restrict__ uu, const T *__restrict__ v, T *__restrict__ q,
              T *__restrict__ w, const T *__restrict__ dinv, const KState<T> *st)
@@ -298,9 +307,10 @@ __global__ void __launch_bounds__(kVB)
     if (st->done) return;
     const T alpha = st->alpha;
     T xv[kU], uv[kU], vv[kU], dv[kU];
-    SPX_ROWS_LOOP(xv[u] = x[i]; uv[u] = uu[i]; vv[u] = v[i]; if (PRE) dv[u] = dinv[i];,
-                  const T qi = fma(-alpha, vv[u], uv[u]); q[i] = qi; const T wi = PRE ? dv[u] * (uv[u] + qi) : uv[u] + qi;
-                  w[i] = wi; x[i] = fma(alpha, wi, xv[u]);)
+    SPX_ROWS_LOOP(if (PRE != 2) xv[u] = x[i]; uv[u] = uu[i]; vv[u] = v[i]; if (PRE == 1) dv[u] = dinv[i];,
+                  const T qi = fma(-alpha, vv[u], uv[u]); q[i] = qi;
+                  const T wi = PRE == 1 ? dv[u] * (uv[u] + qi) : uv[u] + qi; w[i] = wi;
+                  if (PRE != 2) x[i] = fma(alpha, wi, xv[u]);)
 }
 
 // CGS: r -= alpha v (v = A w); dots r.r and r^.r
@@ -360,6 +370,196 @@ __global__ void k_jacobi_dinv(int64_t n, const int *__restrict__ rp, const int *
         }
         dinv[i] = d != 0.0 ? (T)(1.0 / d) : T(1);
     }
+}
+
+// ------------------------------------------------------------------ block-Jacobi
+// M = the block diagonal of A, blocks of bs consecutive rows and columns
+// (bs a power of two up to 32, so a block never straddles a warp); the last
+// block is padded with identity rows.  Section 2 lists block-Jacobi among the
+// library's preconditioners.
+constexpr int kBjWarps = 2;  // warps per block of the inversion kernel
+
+// One warp per diagonal block: gather the block's entries (the block's rows,
+// columns inside the block; duplicates summed in storage order) into the
+// augmented matrix [D | I] (bs x 2bs, FP64, shared memory), then Gauss-Jordan
+// with partial pivoting: pick the largest |entry| at or below the diagonal of
+// the pivot column (the first one on ties), swap, scale the pivot row by the
+// reciprocal of the pivot, subtract multiples of it from the other rows.  A
+// block with an exactly zero pivot is stored as the identity (Jacobi's rule
+// for a zero diagonal).  Lanes own rows while gathering, columns while
+// eliminating.
+template <class V, class T>
+__global__ void __launch_bounds__(32 * kBjWarps)
+    k_bj_build(int64_t n, int bs, const int *__restrict__ rp, const int *__restrict__ col, const V *__restrict__ val,
+               int64_t ell_ld, int64_t ell_w, const int *__restrict__ ecol, const V *__restrict__ evals,
+               int64_t coo_nnz, const int *__restrict__ crow, const int *__restrict__ ccol,
+               const V *__restrict__ cval, T *__restrict__ minv)
+{
+    extern __shared__ double bj_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int w2 = 2 * bs;
+    double *aug = bj_smem + (size_t)wib * (size_t)(bs * w2 + bs);
+    double *fcol = aug + bs * w2;  // the pivot column, read before the rows change
+    const int64_t nb = (n + bs - 1) / bs;
+    for (int64_t k = (int64_t)blockIdx.x * kBjWarps + wib; k < nb; k += (int64_t)gridDim.x * kBjWarps) {
+        const int64_t c0 = k * bs;
+        for (int e = lane; e < bs * w2; e += 32) aug[e] = 0.0;
+        __syncwarp();
+        if (lane < bs) {
+            const int r = lane;
+            const int64_t i = c0 + r;
+            double *row = aug + r * w2;
+            row[bs + r] = 1.0;
+            if (i >= n) {
+                row[r] = 1.0;
+            } else {
+                if (rp)
+                    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                        const int64_t c = col[e];
+                        if (c >= c0 && c < c0 + bs) row[c - c0] += (double)val[e];
+                    }
+                for (int64_t j = 0; j < ell_w; ++j) {
+                    const int64_t c = ecol[j * ell_ld + i];
+                    if (c >= c0 && c < c0 + bs) row[c - c0] += (double)evals[j * ell_ld + i];
+                }
+                if (coo_nnz > 0) {  // the row's entries: rows are sorted
+                    int64_t lo = 0, hi = coo_nnz;
+                    while (lo < hi) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if (crow[mid] < i) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    for (int64_t e = lo; e < coo_nnz && crow[e] == i; ++e) {
+                        const int64_t c = ccol[e];
+                        if (c >= c0 && c < c0 + bs) row[c - c0] += (double)cval[e];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        bool singular = false;
+        for (int p = 0; p < bs; ++p) {
+            double best = -1.0;
+            int piv = p;
+            if (lane >= p && lane < bs) {
+                best = fabs(aug[lane * w2 + p]);
+                piv = lane;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, off);
+                const int op = __shfl_down_sync(0xffffffffu, piv, off);
+                if (ob > best || (ob == best && op < piv)) {
+                    best = ob;
+                    piv = op;
+                }
+            }
+            best = __shfl_sync(0xffffffffu, best, 0);
+            piv = __shfl_sync(0xffffffffu, piv, 0);
+            if (best == 0.0) {  // warp-uniform
+                singular = true;
+                break;
+            }
+            if (piv != p) {
+                for (int c = lane; c < w2; c += 32) {
+                    const double t = aug[p * w2 + c];
+                    aug[p * w2 + c] = aug[piv * w2 + c];
+                    aug[piv * w2 + c] = t;
+                }
+                __syncwarp();
+            }
+            const double inv = 1.0 / aug[p * w2 + p];
+            __syncwarp();
+            for (int c = lane; c < w2; c += 32) aug[p * w2 + c] *= inv;
+            if (lane < bs) fcol[lane] = aug[lane * w2 + p];
+            __syncwarp();
+            for (int c = lane; c < w2; c += 32) {
+                const double pc = aug[p * w2 + c];
+                for (int r = 0; r < bs; ++r) {
+                    const double f = fcol[r];
+                    if (r != p && f != 0.0) aug[r * w2 + c] -= f * pc;
+                }
+            }
+            __syncwarp();
+        }
+        T *out = minv + (size_t)k * (size_t)(bs * bs);
+        for (int e = lane; e < bs * bs; e += 32) {
+            const int r = e / bs, c = e - r * bs;
+            out[e] = singular ? (r == c ? T(1) : T(0)) : (T)aug[r * w2 + bs + c];
+        }
+        __syncwarp();
+    }
+}
+
+// out = M^-1 in, one element per thread: the lanes of a warp hold 32
+// consecutive elements, so a block's inputs are exchanged with shuffles
+// inside a group of BS lanes and each lane forms its row of the block times
+// them (column order).  Modes: BJ_PLAIN; BJ_DOT also reduces in.out (r.z
+// with in = r) and runs `fin`; BJ_AXPY also does x += alpha out (CGS, alpha
+// from the state); BJ_ADDX does x += M^-1 in and stores nothing (GMRES's
+// cycle update).  Returns at once while *skip is set.
+enum { BJ_PLAIN = 0, BJ_DOT = 1, BJ_AXPY = 2, BJ_ADDX = 3 };
+
+template <class T, int BS> __device__ __forceinline__ void bj_load_row(const T *__restrict__ row, T (&m)[BS])
+{
+    if constexpr (sizeof(T) == 8 && BS >= 2) {
+#pragma unroll
+        for (int j = 0; j < BS; j += 2) {
+            const double2 t = __ldg(reinterpret_cast<const double2 *>(row + j));
+            m[j] = t.x;
+            m[j + 1] = t.y;
+        }
+    } else if constexpr (sizeof(T) == 4 && BS >= 4) {
+#pragma unroll
+        for (int j = 0; j < BS; j += 4) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(row + j));
+            m[j] = t.x;
+            m[j + 1] = t.y;
+            m[j + 2] = t.z;
+            m[j + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < BS; ++j) m[j] = __ldg(row + j);
+    }
+}
+
+template <class T, int BS, int MODE>
+__global__ void __launch_bounds__(kVB)
+    k_bj_apply(int64_t n, const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ minv,
+               const int *skip, T *__restrict__ x, KState<T> *st, int fin, T *partials, unsigned *ticket)
+{
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int g0 = lane & ~(BS - 1);
+    const T alpha = MODE == BJ_AXPY ? st->alpha : T(0);
+    T d0 = T(0);
+    const int64_t stride = (int64_t)gridDim.x * kVB;
+    // warp-uniform trip count: every lane takes part in the shuffles
+    for (int64_t base = (int64_t)blockIdx.x * kVB + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool act = i < n;
+        const T v = act ? in[i] : T(0);
+        T s = T(0);
+        if constexpr (BS == 1) {
+            if (act) s = minv[i] * v;
+        } else {
+            T m[BS];
+            if (act) bj_load_row<T, BS>(minv + i * BS, m);
+#pragma unroll
+            for (int j = 0; j < BS; ++j) {
+                const T vj = __shfl_sync(0xffffffffu, v, g0 + j);
+                if (act) s = fma(m[j], vj, s);
+            }
+        }
+        if (act) {
+            if (MODE == BJ_DOT) d0 = fma(v, s, d0);
+            if (MODE != BJ_ADDX) out[i] = s;
+            if (MODE == BJ_AXPY) x[i] = fma(alpha, s, x[i]);
+            if (MODE == BJ_ADDX) x[i] += s;
+        }
+    }
+    if constexpr (MODE == BJ_DOT) grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, fin, st, partials, ticket);
 }
 
 // ------------------------------------------------------------------ GMRES kernels
@@ -671,25 +871,33 @@ template <class T> __global__ void k_gm_solve(GState<T> *gs, GSmall<T> sm)
     }
 }
 
-// x += sum_k y_k v_k  (Jacobi, right: x += dinv sum_k y_k v_k)
+// x += sum_k y_k v_k  (Jacobi, right: x += dinv sum_k y_k v_k; uout != null
+// (block-Jacobi): u = sum_k y_k v_k goes to uout and x is left to the block
+// apply, which adds M^-1 u)
 template <class T>
 __global__ void __launch_bounds__(kVB)
     k_gm_update(int64_t n, int64_t ld, const T *__restrict__ V, T *__restrict__ x, const GState<T> *gs, GSmall<T> sm,
-                const T *__restrict__ dinv)
+                const T *__restrict__ dinv, T *__restrict__ uout)
 {
     if (gs->done) return;
     const int jn = gs->jdone;
-    if (jn == 0) return;
+    if (jn == 0) {
+        if (uout)
+            for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB)
+                uout[i] = T(0);
+        return;
+    }
     __shared__ T ys[kGmKmax];
     if (threadIdx.x < kGmKmax) ys[threadIdx.x] = threadIdx.x < jn ? ldcg(sm.y + threadIdx.x) : T(0);
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVB) {
-        if (dinv) {
+        if (dinv || uout) {
             T ui = T(0);
 #pragma unroll
             for (int k = 0; k < kGmKmax; ++k)
                 if (k < jn) ui = fma(ys[k], V[(int64_t)k * ld + i], ui);
-            x[i] = fma(dinv[i], ui, x[i]);
+            if (uout) uout[i] = ui;
+            else x[i] = fma(dinv[i], ui, x[i]);
         } else {
             T xi = x[i];
 #pragma unroll
@@ -739,6 +947,30 @@ __global__ void __launch_bounds__(kVB) k_gm_start(int64_t n, T *__restrict__ v0,
         sm.g[0] = beta;
         for (int k = 1; k <= gs->m; ++k) sm.g[k] = T(0);
     }
+}
+
+// Splits a solver code of the ABI into the method, the Jacobi flag and the
+// block-Jacobi block size (0: none).
+int parse_solver_code(int code, int *solver, bool *jacobi, int *bs)
+{
+    const int base = code & 0xff;
+    const int flags = code & ~0xff;
+    *jacobi = false;
+    *bs = 0;
+    if (base < SPX_CG || base > SPX_CGS) return fail(SPX_ERR_INVALID, "unknown solver");
+    if (flags == SPX_PRECOND_JACOBI) {
+        *jacobi = true;
+    } else if ((flags & 0xffff) == SPX_PRECOND_BLOCK_JACOBI) {
+        const int b = (int)((unsigned)code >> SPX_PRECOND_BLOCK_SHIFT);
+        if (b != 1 && b != 2 && b != 4 && b != 8 && b != 16 && b != 32)
+            return fail(SPX_ERR_INVALID, "block-Jacobi block size must be 1, 2, 4, 8, 16 or 32");
+        *jacobi = true;
+        *bs = b;
+    } else if (flags != 0) {
+        return fail(SPX_ERR_INVALID, "unknown preconditioner flags in the solver code");
+    }
+    *solver = base;
+    return SPX_OK;
 }
 
 // ------------------------------------------------------------------ host drivers
@@ -821,14 +1053,52 @@ template <class T> struct KrylovRun {
     int solver;
 };
 
+// out = M^-1 in for block-Jacobi (see k_bj_apply for the modes)
+template <class T, int BS>
+int bj_apply_bs(spx_ctx *ctx, SolverWork *w, int64_t n, const T *in, T *out, int mode, const int *skip, T *x,
+                int fin)
+{
+    const int g = vgrid(ctx, n);
+    const T *minv = w->bjinv.as<T>();
+    KState<T> *st = w->state.as<KState<T>>();
+    T *part = w->red.as<T>();
+    unsigned *tk = w->ticket.as<unsigned>();
+    cudaStream_t sm = ctx->stream;
+    switch (mode) {
+    case BJ_PLAIN: k_bj_apply<T, BS, BJ_PLAIN><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
+    case BJ_DOT: k_bj_apply<T, BS, BJ_DOT><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
+    case BJ_AXPY: k_bj_apply<T, BS, BJ_AXPY><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
+    default: k_bj_apply<T, BS, BJ_ADDX><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
+    }
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T>
+int bj_apply(spx_ctx *ctx, SolverWork *w, int64_t n, const T *in, T *out, int mode, const int *skip, T *x = nullptr,
+             int fin = FIN_NONE)
+{
+    switch (w->bs) {
+    case 1: return bj_apply_bs<T, 1>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 2: return bj_apply_bs<T, 2>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 4: return bj_apply_bs<T, 4>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 8: return bj_apply_bs<T, 8>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 16: return bj_apply_bs<T, 16>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 32: return bj_apply_bs<T, 32>(ctx, w, n, in, out, mode, skip, x, fin);
+    default: return fail(SPX_ERR_INVALID, "block-Jacobi block size must be 1, 2, 4, 8, 16 or 32");
+    }
+}
+
 // One CG iteration: q = A p (+ p.q -> alpha); x, r update (+ r.r -> beta); p update.
 // Jacobi: beta from r.z and p = z + beta p with z = dinv r (preconditioned CG).
+// Block-Jacobi: x, r update with r.r (convergence); z = M^-1 r with r.z (beta)
+// into q's place, q being spent; p = z + beta p.
 template <class T> int cg_iter(KrylovRun<T> &R)
 {
     SolverWork *w = R.w;
     KState<T> *st = w->state.as<KState<T>>();
     T *r = vec<T>(w, 0), *p = vec<T>(w, 1), *q = vec<T>(w, 2);
-    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
+    const T *dinv = w->pre && !w->bs ? w->dinv.as<T>() : nullptr;
     const int64_t n = R.A->n;
     Epi<T> e = epi_plain(q);
     e.w = p;
@@ -840,33 +1110,38 @@ template <class T> int cg_iter(KrylovRun<T> &R)
     const int g = vgrid(R.ctx, n);
     T *part = w->red.as<T>();
     unsigned *tk = w->ticket.as<unsigned>();
-    if (dinv) {
-        k_cg_xr<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, dinv, st, part, tk);
+    if (w->bs) {
+        k_cg_xr<T, 2><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, nullptr, st, part, tk);
+        SPX_TRY(bj_apply<T>(R.ctx, w, n, r, q, BJ_DOT, &st->done, nullptr, FIN_PCG_RZ));
+        k_cg_p<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, q, p, nullptr, st);
+    } else if (dinv) {
+        k_cg_xr<T, 1><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, dinv, st, part, tk);
         k_cg_p<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, dinv, st);
     } else {
-        k_cg_xr<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, dinv, st, part, tk);
+        k_cg_xr<T, 0><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, r, p, q, dinv, st, part, tk);
         k_cg_p<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, dinv, st);
     }
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
 
-// One BiCGSTAB iteration.  Jacobi (right): the SpMVs take ph = dinv p and
-// sh = dinv s, and x is updated with them.
+// One BiCGSTAB iteration.  Jacobi / block-Jacobi (right): the SpMVs take
+// ph = M^-1 p and sh = M^-1 s, and x is updated with them.
 template <class T> int bi_iter(KrylovRun<T> &R)
 {
     SolverWork *w = R.w;
     KState<T> *st = w->state.as<KState<T>>();
     T *r = vec<T>(w, 0), *rh = vec<T>(w, 1), *p = vec<T>(w, 2), *v = vec<T>(w, 3), *s = vec<T>(w, 4),
       *t = vec<T>(w, 5);
-    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
-    T *ph = dinv ? vec<T>(w, 6) : p, *sh = dinv ? vec<T>(w, 7) : s;
+    const T *dinv = w->pre && !w->bs ? w->dinv.as<T>() : nullptr;
+    T *ph = w->pre ? vec<T>(w, 6) : p, *sh = w->pre ? vec<T>(w, 7) : s;
     const int64_t n = R.A->n;
     const int g = vgrid(R.ctx, n);
     T *part = w->red.as<T>();
     unsigned *tk = w->ticket.as<unsigned>();
     if (dinv) k_bi_p<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, v, ph, dinv, st);
     else k_bi_p<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, p, v, ph, dinv, st);
+    if (w->bs) SPX_TRY(bj_apply<T>(R.ctx, w, n, p, ph, BJ_PLAIN, &st->done));
     Epi<T> e = epi_plain(v);
     e.w = rh;
     e.dots = w->dots.as<T>();
@@ -876,6 +1151,7 @@ template <class T> int bi_iter(KrylovRun<T> &R)
     SPX_TRY(spmv_launch<T>(R.ctx, R.A, ph, e, R.use32));
     if (dinv) k_bi_s<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, v, s, sh, dinv, st, part, tk);
     else k_bi_s<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, v, s, sh, dinv, st, part, tk);
+    if (w->bs) SPX_TRY(bj_apply<T>(R.ctx, w, n, s, sh, BJ_PLAIN, &st->skip_t));
     Epi<T> e2 = epi_plain(t);
     e2.w = s;
     e2.want_yy = true;
@@ -892,14 +1168,16 @@ template <class T> int bi_iter(KrylovRun<T> &R)
 // One CGS iteration: v = A p (+ r^.v -> alpha); q, w = u + q, x; v = A w;
 // r update (+ r.r, r^.r -> convergence, beta); u, p updates.  Jacobi
 // (right): the first SpMV takes ph = dinv p, and w = dinv (u + q).
+// Block-Jacobi: w = u + q, then M^-1 w (in ph's place, ph being spent) with
+// x += alpha M^-1 w, the second SpMV's input; after the p update ph = M^-1 p.
 template <class T> int cgs_iter(KrylovRun<T> &R)
 {
     SolverWork *w = R.w;
     KState<T> *st = w->state.as<KState<T>>();
     T *r = vec<T>(w, 0), *rh = vec<T>(w, 1), *p = vec<T>(w, 2), *u = vec<T>(w, 3), *q = vec<T>(w, 4),
       *v = vec<T>(w, 5), *ww = vec<T>(w, 6);
-    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
-    T *ph = dinv ? vec<T>(w, 7) : p;
+    const T *dinv = w->pre && !w->bs ? w->dinv.as<T>() : nullptr;
+    T *ph = w->pre ? vec<T>(w, 7) : p;
     const int64_t n = R.A->n;
     const int g = vgrid(R.ctx, n);
     T *part = w->red.as<T>();
@@ -911,14 +1189,21 @@ template <class T> int cgs_iter(KrylovRun<T> &R)
     e.fin_state = st;
     e.skip = &st->done;
     SPX_TRY(spmv_launch<T>(R.ctx, R.A, ph, e, R.use32));
-    if (dinv) k_cgs_qw<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, dinv, st);
-    else k_cgs_qw<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, dinv, st);
+    if (w->bs) {
+        k_cgs_qw<T, 2><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, nullptr, st);
+        SPX_TRY(bj_apply<T>(R.ctx, w, n, ww, ph, BJ_AXPY, &st->done, R.x));
+    } else if (dinv) {
+        k_cgs_qw<T, 1><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, dinv, st);
+    } else {
+        k_cgs_qw<T, 0><<<g, kVB, 0, R.ctx->stream>>>(n, R.x, u, v, q, ww, dinv, st);
+    }
     Epi<T> e2 = epi_plain(v);
     e2.skip = &st->done;
-    SPX_TRY(spmv_launch<T>(R.ctx, R.A, ww, e2, R.use32));
+    SPX_TRY(spmv_launch<T>(R.ctx, R.A, w->bs ? ph : ww, e2, R.use32));
     k_cgs_r<T><<<g, kVB, 0, R.ctx->stream>>>(n, r, rh, v, st, part, tk);
     if (dinv) k_cgs_up<T, true><<<g, kVB, 0, R.ctx->stream>>>(n, r, q, u, p, ph, dinv, st);
     else k_cgs_up<T, false><<<g, kVB, 0, R.ctx->stream>>>(n, r, q, u, p, ph, dinv, st);
+    if (w->bs) SPX_TRY(bj_apply<T>(R.ctx, w, n, p, ph, BJ_PLAIN, &st->done));
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
@@ -951,7 +1236,13 @@ template <class T> int krylov_init(KrylovRun<T> &R)
         SPX_CUDA(cudaMemsetAsync(vec<T>(w, 2), 0, bytes, R.ctx->stream));                        // p
         SPX_CUDA(cudaMemsetAsync(vec<T>(w, 3), 0, bytes, R.ctx->stream));                        // v
     }
-    if (w->pre) {
+    if (w->bs) {
+        KState<T> *st = w->state.as<KState<T>>();
+        if (R.solver == SPX_CG)  // p = z = M^-1 r, rho = r.z
+            SPX_TRY(bj_apply<T>(R.ctx, w, n, r, vec<T>(w, 1), BJ_DOT, &st->done, nullptr, FIN_PCG_RHO0));
+        else if (R.solver == SPX_CGS)  // ph = M^-1 p
+            SPX_TRY(bj_apply<T>(R.ctx, w, n, vec<T>(w, 2), vec<T>(w, 7), BJ_PLAIN, &st->done));
+    } else if (w->pre) {
         KState<T> *st = w->state.as<KState<T>>();
         const int g = vgrid(R.ctx, n);
         const T *dinv = w->dinv.as<T>();
@@ -968,7 +1259,7 @@ template <class T> int krylov_init(KrylovRun<T> &R)
 // M^{-1} = 1 / diag(A) for a Jacobi-preconditioned solve, in the work's precision
 template <class T> int ensure_dinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
 {
-    if (!w->pre || w->dinv.p) return SPX_OK;
+    if (!w->pre || w->bs || w->dinv.p) return SPX_OK;
     const int64_t n = A->n;
     SPX_TRY(dbuf_alloc(ctx, w->dinv, (size_t)(n > 0 ? n : 1) * sizeof(T)));
     const int g = (int)std::min<int64_t>(ceil_div(n > 0 ? n : 1, 256), (int64_t)ctx->sm_count * 16);
@@ -987,6 +1278,37 @@ template <class T> int ensure_dinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
             A->coo_val.as<float>(), w->dinv.as<T>());
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
+}
+
+// block-Jacobi inverses (FP64 elimination, stored in the work's precision)
+template <class T> int ensure_bjinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
+{
+    if (!w->bs || w->bjinv.p) return SPX_OK;
+    const int64_t n = A->n, bs = w->bs;
+    const int64_t nb = ceil_div(n > 0 ? n : 1, bs);
+    SPX_TRY(dbuf_alloc(ctx, w->bjinv, (size_t)(nb * bs * bs) * sizeof(T)));
+    const int g = (int)std::min<int64_t>(ceil_div(nb, kBjWarps), (int64_t)ctx->sm_count * 32);
+    const int smem = kBjWarps * (int)(bs * 2 * bs + bs) * 8;
+    const bool csr = A->format == SPX_CSR;
+    const int64_t ew = (A->format == SPX_ELL || A->format == SPX_HYB) ? A->ell_w : 0;
+    const int64_t cn = (A->format == SPX_COO || A->format == SPX_HYB) ? A->coo_nnz : 0;
+    if (A->dtype == SPX_F64)
+        k_bj_build<double, T><<<g, 32 * kBjWarps, smem, ctx->stream>>>(
+            n, (int)bs, csr ? A->rp.as<int>() : nullptr, A->col.as<int>(), A->val.as<double>(), A->ell_ld, ew,
+            A->ell_col.as<int>(), A->ell_val.as<double>(), cn, A->coo_row.as<int>(), A->coo_col.as<int>(),
+            A->coo_val.as<double>(), w->bjinv.as<T>());
+    else
+        k_bj_build<float, T><<<g, 32 * kBjWarps, smem, ctx->stream>>>(
+            n, (int)bs, csr ? A->rp.as<int>() : nullptr, A->col.as<int>(), A->val.as<float>(), A->ell_ld, ew,
+            A->ell_col.as<int>(), A->ell_val.as<float>(), cn, A->coo_row.as<int>(), A->coo_col.as<int>(),
+            A->coo_val.as<float>(), w->bjinv.as<T>());
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
+template <class T> int ensure_prec(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
+{
+    return w->bs ? ensure_bjinv<T>(ctx, A, w) : ensure_dinv<T>(ctx, A, w);
 }
 
 // true residual ||b - A x||^2 -> dots[1] (scratch vector)
@@ -1071,7 +1393,7 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
         int64_t launched = 0;
         while (!h->done) {
             const uint64_t key[8] = {(uint64_t)solver, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
-                                     (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8),
+                                     (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16),
                                      (uint64_t)(uintptr_t)A, 0};
             SPX_TRY(run_chunk(ctx, w, key, graphs, [&]() -> int {
                 for (int c = 0; c < chunk; ++c)
@@ -1108,8 +1430,9 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
 {
     const int64_t n = A->n, ld = w->ld;
     T *V = w->vecs.as<T>();
-    const T *dinv = w->pre ? w->dinv.as<T>() : nullptr;
+    const T *dinv = w->pre && !w->bs ? w->dinv.as<T>() : nullptr;
     T *Z = w->pre ? V + (int64_t)(m + 2) * ld : nullptr;  // M^{-1} v_j (right preconditioning)
+    const bool bj = w->bs > 0;
     GState<T> *gs = w->state.as<GState<T>>();
     GSmall<T> sm;
     T *base = w->small.as<T>();
@@ -1164,19 +1487,24 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
         e.skip = &gs->done;
         SPX_TRY(spmv_launch<T>(ctx, A, x, e, use32));
         k_gm_start<T><<<g, kVB, 0, ctx->stream>>>(n, V, dots, gs, sm, dinv, Z);
+        if (bj) SPX_TRY(bj_apply<T>(ctx, w, n, V, Z, BJ_PLAIN, &gs->skip));
         for (int j = 0; j < m; ++j) {
             Epi<T> ea = epi_plain(V + (int64_t)(j + 1) * ld);
             ea.skip = &gs->skip;
             ea.want_yy = true;  // ||A v_j||^2 -> dots[1], for the reorthogonalisation test
             ea.dots = dots;
-            SPX_TRY(spmv_launch<T>(ctx, A, dinv ? Z : V + (int64_t)j * ld, ea, use32));  // A v_j or A M^-1 v_j
+            SPX_TRY(spmv_launch<T>(ctx, A, Z ? Z : V + (int64_t)j * ld, ea, use32));  // A v_j or A M^-1 v_j
             k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk);
             k_gm_upd_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dots, part, tk);
             k_gm_upd2<T><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
             k_gm_scale<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dinv, Z);
+            // (when this step ended the cycle, the apply's Z is never read: the next
+            // cycle's start recomputes it)
+            if (bj) SPX_TRY(bj_apply<T>(ctx, w, n, V + (int64_t)(j + 1) * ld, Z, BJ_PLAIN, &gs->skip));
         }
         k_gm_solve<T><<<1, 32, 0, ctx->stream>>>(gs, sm);
-        k_gm_update<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, x, gs, sm, dinv);
+        k_gm_update<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, x, gs, sm, dinv, bj ? Z : nullptr);
+        if (bj) SPX_TRY(bj_apply<T>(ctx, w, n, Z, (T *)nullptr, BJ_ADDX, &gs->done, x));
         SPX_CUDA(cudaGetLastError());
         return SPX_OK;
     };
@@ -1184,7 +1512,7 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
     int64_t cycles = 0;
     for (;;) {
         const uint64_t key[8] = {(uint64_t)SPX_GMRES, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
-                                 (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8),
+                                 (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16),
                                  (uint64_t)(uintptr_t)A, 1};
         SPX_TRY(run_chunk(ctx, w, key, n >= kGraphMinRows, cycle));
         SPX_TRY(read_state<T>(ctx, w, sizeof(GState<T>)));
@@ -1222,13 +1550,13 @@ __global__ void k_ir_update(int64_t n, double *__restrict__ x, const float *__re
 }
 
 int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, double tol, int64_t maxit,
-           int m, bool pre, spx_solve_info *info)
+           int m, bool pre, int bs, spx_solve_info *info)
 {
     const int64_t n = A->n;
     SolverWork *&w = A->work;
     SPX_TRY(work_prepare<double>(ctx, w, n, SPX_CG, 0));  // outer: r and scratch only
-    SPX_TRY(work_prepare<float>(ctx, w->inner, n, solver, solver == SPX_GMRES ? m : 0, pre));
-    SPX_TRY(ensure_dinv<float>(ctx, A, w->inner));
+    SPX_TRY(work_prepare<float>(ctx, w->inner, n, solver, solver == SPX_GMRES ? m : 0, pre, bs));
+    SPX_TRY(ensure_prec<float>(ctx, A, w->inner));
     if (!w->ir.p) SPX_TRY(dbuf_alloc(ctx, w->ir, (size_t)n * 8 + 2 * (size_t)round_up(n, 64) * 4 + 256));
     double *r = w->ir.as<double>();
     float *r32 = reinterpret_cast<float *>(w->ir.as<char>() + round_up((size_t)n * 8, 256));
@@ -1297,10 +1625,10 @@ int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, 
 
 template <class T>
 int solve_typed(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, int solver, double tol, int64_t maxit, int m,
-                bool use32, int64_t fixed, bool pre, spx_solve_info *info)
+                bool use32, int64_t fixed, bool pre, int bs, spx_solve_info *info)
 {
-    SPX_TRY(work_prepare<T>(ctx, A->work, A->n, solver, solver == SPX_GMRES ? m : 0, pre));
-    SPX_TRY(ensure_dinv<T>(ctx, A, A->work));
+    SPX_TRY(work_prepare<T>(ctx, A->work, A->n, solver, solver == SPX_GMRES ? m : 0, pre, bs));
+    SPX_TRY(ensure_prec<T>(ctx, A, A->work));
     if (solver == SPX_GMRES) return run_gmres<T>(ctx, A, A->work, b, x, tol, maxit, m, use32, false, fixed, info);
     return run_short<T>(ctx, A, A->work, solver, b, x, tol, maxit, use32, false, fixed, info);
 }
@@ -1312,9 +1640,9 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
         return fail(SPX_ERR_INVALID, "spx_solve: NULL argument");
     std::memset(info, 0, sizeof(*info));
     if (A->n != A->ncols) return fail(SPX_ERR_INVALID, "spx_solve: the matrix must be square");
-    const bool pre = (solver & SPX_PRECOND_JACOBI) != 0;
-    solver &= ~SPX_PRECOND_JACOBI;
-    if (solver < SPX_CG || solver > SPX_CGS) return fail(SPX_ERR_INVALID, "spx_solve: unknown solver");
+    bool pre = false;
+    int bs = 0;
+    SPX_TRY(parse_solver_code(solver, &solver, &pre, &bs));
     if (!(tol >= 0.0) || maxit < 0) return fail(SPX_ERR_INVALID, "spx_solve: bad tol or max_iter");
     if (solver == SPX_GMRES && (restart < 1 || restart > kGmKmax - 1))
         return fail(SPX_ERR_UNSUPPORTED, "GMRES restart length must be in [1, 31]");
@@ -1329,15 +1657,15 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
             return fail(SPX_ERR_UNSUPPORTED, "mixed precision needs an FP64 matrix created with SPX_MIXED_SHADOW");
         if (fixed > 0) return fail(SPX_ERR_UNSUPPORTED, "fixed-iteration mode runs in one precision");
         st = run_ir(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol, maxit, restart, pre,
-                    info);
+                    bs, info);
     } else if (precision == SPX_PREC_F64 || precision == SPX_PREC_F32) {
         const int want = precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32;
         if (A->dtype != want) return fail(SPX_ERR_UNSUPPORTED, "precision must match the matrix dtype (or use MIXED)");
         st = A->dtype == SPX_F64
                  ? solve_typed<double>(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol,
-                                       maxit, restart, false, fixed, pre, info)
+                                       maxit, restart, false, fixed, pre, bs, info)
                  : solve_typed<float>(ctx, A, static_cast<const float *>(b), static_cast<float *>(x), solver, tol,
-                                      maxit, restart, false, fixed, pre, info);
+                                      maxit, restart, false, fixed, pre, bs, info);
     } else {
         return fail(SPX_ERR_INVALID, "spx_solve: unknown precision");
     }

@@ -24,6 +24,13 @@ SPX_CSR, SPX_ELL, SPX_COO, SPX_HYB = 0, 1, 2, 3
 SPX_F64, SPX_F32 = 0, 1
 SPX_CG, SPX_BICGSTAB, SPX_GMRES, SPX_CGS = 0, 1, 2, 3
 SPX_PRECOND_JACOBI = 0x100
+SPX_PRECOND_BLOCK_JACOBI = 0x200
+SPX_PRECOND_BLOCK_SHIFT = 16
+
+
+def SPX_PRECOND_BLOCK(bs: int) -> int:
+    """Block-Jacobi flag with block size bs (1, 2, 4, 8, 16 or 32), OR-ed into a solver code."""
+    return SPX_PRECOND_BLOCK_JACOBI | (int(bs) << SPX_PRECOND_BLOCK_SHIFT)
 SPX_PREC_F64, SPX_PREC_F32, SPX_PREC_MIXED = 0, 1, 2
 SPX_CONVERGED, SPX_MAX_ITER, SPX_BREAKDOWN, SPX_STAGNATED, SPX_SOLVE_TIMEOUT = 0, 1, 2, 3, 4
 SPX_KERNEL_AUTO, SPX_KERNEL_CSR_VECTOR, SPX_KERNEL_CSR_MERGE, SPX_KERNEL_ELL, SPX_KERNEL_COO = 0, 1, 2, 3, 4
@@ -315,28 +322,33 @@ def _info(i: spx_solve_info) -> SolveInfo:
                      i.inner_iterations)
 
 
-def _solver_code(solver, precond):
+def _solver_code(solver, precond, block_size=8):
+    """precond: None, "jacobi" or "block_jacobi" (blocks of block_size rows)."""
     code = SOLVERS.get(solver, solver)
     if precond == "jacobi":
         code |= SPX_PRECOND_JACOBI
+    elif precond == "block_jacobi":
+        code |= SPX_PRECOND_BLOCK(block_size)
     elif precond is not None:
         raise ValueError(f"unknown preconditioner {precond!r}")
     return code
 
 
 def spx_solve(ctx: int, A: int, b: torch.Tensor, x: torch.Tensor, solver="cg", tol: float = 1e-10,
-              max_iter: int = 10000, restart: int = 30, precision="f64", precond=None) -> SolveInfo:
+              max_iter: int = 10000, restart: int = 30, precision="f64", precond=None,
+              block_size: int = 8) -> SolveInfo:
     info = spx_solve_info()
-    _check(load().spx_solve(ctx, A, _ptr(b), _ptr(x), _solver_code(solver, precond), float(tol), int(max_iter),
-                            int(restart), PRECISIONS.get(precision, precision), C.byref(info)))
+    _check(load().spx_solve(ctx, A, _ptr(b), _ptr(x), _solver_code(solver, precond, block_size), float(tol),
+                            int(max_iter), int(restart), PRECISIONS.get(precision, precision), C.byref(info)))
     return _info(info)
 
 
 def spx_solve_fixed(ctx: int, A: int, b: torch.Tensor, x: torch.Tensor, solver="cg", iterations: int = 1000,
-                    restart: int = 30, precision="f64", precond=None) -> SolveInfo:
+                    restart: int = 30, precision="f64", precond=None, block_size: int = 8) -> SolveInfo:
     info = spx_solve_info()
-    _check(load().spx_solve_fixed(ctx, A, _ptr(b), _ptr(x), _solver_code(solver, precond), int(iterations),
-                                  int(restart), PRECISIONS.get(precision, precision), C.byref(info)))
+    _check(load().spx_solve_fixed(ctx, A, _ptr(b), _ptr(x), _solver_code(solver, precond, block_size),
+                                  int(iterations), int(restart), PRECISIONS.get(precision, precision),
+                                  C.byref(info)))
     return _info(info)
 
 
