@@ -89,12 +89,15 @@ def _lib(mutant: int = 0) -> C.CDLL:
                 getattr(lib, name).argtypes = [i64, p, p, p, p, p, C.c_int, dbl, i64, C.POINTER(_Info), p]
             for name in ("orc_cg_bjacobi", "orc_bicgstab_bjacobi", "orc_cgs_bjacobi"):
                 getattr(lib, name).restype = C.c_int
-                getattr(lib, name).argtypes = [i64, p, p, p, p, p, dbl, i64, C.POINTER(_Info), p, C.c_int]
+                getattr(lib, name).argtypes = [i64, p, p, p, p, p, dbl, i64, C.POINTER(_Info), p, C.c_int,
+                                               C.c_int]
             lib.orc_gmres_bjacobi.restype = C.c_int
             lib.orc_gmres_bjacobi.argtypes = [i64, p, p, p, p, p, C.c_int, dbl, i64, C.POINTER(_Info), p,
-                                              C.c_int]
+                                              C.c_int, C.c_int]
             lib.orc_block_jacobi_inv.restype = C.c_int
             lib.orc_block_jacobi_inv.argtypes = [i64, p, p, p, C.c_int, p]
+            lib.orc_block_jacobi_inv_adaptive.restype = C.c_int
+            lib.orc_block_jacobi_inv_adaptive.argtypes = [i64, p, p, p, C.c_int, p, p]
             lib.orc_ir.restype = C.c_int
             lib.orc_ir.argtypes = [i64, p, p, p, C.c_int, p, p, dbl, dbl, C.c_int, i64,
                                    C.POINTER(_Info)]
@@ -217,16 +220,24 @@ def hyb_auto_width(rp, vbytes: int) -> int:
     return int(_lib().orc_hyb_auto_width(rp.shape[0] - 1, _ptr(rp), vbytes))
 
 
-def block_jacobi_inv(rp, col, val, bs: int, mutant=0) -> np.ndarray:
+def block_jacobi_inv(rp, col, val, bs: int, mutant=0, adaptive=False):
     """Inverses of the bs x bs diagonal blocks of A (block-Jacobi, listed among
-    the library's preconditioners in Section 2), shape (ceil(n / bs), bs, bs)."""
+    the library's preconditioners in Section 2), shape (ceil(n / bs), bs, bs).
+    adaptive=True: also the per-block storage flags (1 = FP64, 0 = FP32, the
+    block's inverse then rounded to FP32); returns (inverses, flags)."""
     rp, col, val = _csr(rp, col, val)
     n = rp.shape[0] - 1
     nb = (n + bs - 1) // bs
     out = np.empty((max(nb, 1), bs, bs), dtype=np.float64)
-    if _lib(mutant).orc_block_jacobi_inv(n, _ptr(rp), _ptr(col), _ptr(val), int(bs), _ptr(out)) != 0:
+    if adaptive:
+        flags = np.zeros(max(nb, 1), dtype=np.uint8)
+        st = _lib(mutant).orc_block_jacobi_inv_adaptive(n, _ptr(rp), _ptr(col), _ptr(val), int(bs), _ptr(out),
+                                                        _ptr(flags))
+    else:
+        st = _lib(mutant).orc_block_jacobi_inv(n, _ptr(rp), _ptr(col), _ptr(val), int(bs), _ptr(out))
+    if st != 0:
         raise ValueError("block size must be at least 1")
-    return out[:nb]
+    return (out[:nb], flags[:nb]) if adaptive else out[:nb]
 
 
 def _solve(fn, args, rp, col, val, b, x0, with_hist, maxit, mutant, tail=()):
@@ -251,10 +262,10 @@ def _fn(base, precond, block_size):
         return base, ()
     if precond == "jacobi":
         return base + "_jacobi", ()
-    if precond == "block_jacobi":
+    if precond in ("block_jacobi", "adaptive_block_jacobi"):
         if int(block_size) < 1:
             raise ValueError("block_size must be at least 1")
-        return base + "_bjacobi", (int(block_size),)
+        return base + "_bjacobi", (int(block_size), int(precond == "adaptive_block_jacobi"))
     raise ValueError(f"unknown preconditioner {precond!r}")
 
 

@@ -754,8 +754,16 @@ int orc_gmres_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const dou
 /* A block with an exactly zero pivot is taken as the identity, as Jacobi   */
 /* takes a zero diagonal as 1.  bs = 1 gives exactly Jacobi's 1 / a_ii.     */
 /* ------------------------------------------------------------------------- */
-int orc_block_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs,
-                         double *minv)
+/* Adaptive storage (flags != NULL): each block's inverse is kept in FP32    */
+/* when its 1-norm condition number kappa = ||D_k||_1 ||D_k^{-1}||_1 times   */
+/* the FP32 unit roundoff 2^-24 is at most 1e-2, so that the rounded        */
+/* inverse differs from the exact one by at most 1% of the identity in the  */
+/* preconditioned block; otherwise in FP64.  The FP32 entries are returned  */
+/* as the doubles they round to; flags[k] = 1 marks an FP64 block.          */
+#define ORC_BJ_FP32_BOUND 1e-2
+
+static int block_jacobi_inv_impl(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs,
+                                 double *minv, unsigned char *flags)
 {
     if (bs < 1) return -1;
     const int64_t nb = (n + bs - 1) / bs;
@@ -770,6 +778,12 @@ int orc_block_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const
             if (i >= n) { aug[r * w + r] = 1.0; continue; }
             for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
                 if (col[e] >= c0 && col[e] < c0 + bs) aug[r * w + (col[e] - c0)] += val[e];
+        }
+        double dnorm = 0.0; /* ||D_k||_1, the largest column sum of |entries| */
+        for (int c = 0; c < bs; ++c) {
+            double cs = 0.0;
+            for (int r = 0; r < bs; ++r) cs += fabs(aug[r * w + c]);
+            if (cs > dnorm) dnorm = cs;
         }
         int singular = 0;
         for (int p = 0; p < bs && !singular; ++p) {
@@ -796,23 +810,51 @@ int orc_block_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const
         for (int r = 0; r < bs; ++r)
             for (int c = 0; c < bs; ++c)
                 out[r * bs + c] = singular ? (r == c ? 1.0 : 0.0) : aug[r * w + bs + c];
+        if (flags) {
+            double inorm = 0.0;
+            for (int c = 0; c < bs; ++c) {
+                double cs = 0.0;
+                for (int r = 0; r < bs; ++r) cs += fabs(out[r * bs + c]);
+                if (cs > inorm) inorm = cs;
+            }
+            const int fp64 = !singular && dnorm * inorm * ldexp(1.0, -24) > ORC_BJ_FP32_BOUND;
+            flags[k] = (unsigned char)fp64;
+            if (!fp64)
+                for (int e = 0; e < bs * bs; ++e) out[e] = (double)(float)out[e];
+        }
     }
     free(aug);
     return 0;
 }
 
-static double *block_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs)
+int orc_block_jacobi_inv(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs,
+                         double *minv)
+{
+    return block_jacobi_inv_impl(n, rp, col, val, bs, minv, NULL);
+}
+
+int orc_block_jacobi_inv_adaptive(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs,
+                                  double *minv, unsigned char *flags)
+{
+    return block_jacobi_inv_impl(n, rp, col, val, bs, minv, flags);
+}
+
+static double *block_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs,
+                            int adaptive)
 {
     const int64_t nb = (n + bs - 1) / bs;
     double *m = malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1) * (size_t)bs * (size_t)bs);
-    orc_block_jacobi_inv(n, rp, col, val, bs, m);
+    unsigned char *f = adaptive ? malloc((size_t)(nb > 0 ? nb : 1)) : NULL;
+    block_jacobi_inv_impl(n, rp, col, val, bs, m, f);
+    free(f);
     return m;
 }
 
 int orc_cg_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-                   const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist, int bs)
+                   const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist, int bs,
+                   int adaptive)
 {
-    double *m = block_jacobi(n, rp, col, val, bs);
+    double *m = block_jacobi(n, rp, col, val, bs, adaptive);
     orc_prec M = {bs, m};
     int st = cg_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
     free(m);
@@ -821,9 +863,9 @@ int orc_cg_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const doubl
 
 int orc_bicgstab_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                          const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist,
-                         int bs)
+                         int bs, int adaptive)
 {
-    double *m = block_jacobi(n, rp, col, val, bs);
+    double *m = block_jacobi(n, rp, col, val, bs, adaptive);
     orc_prec M = {bs, m};
     int st = bicgstab_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
     free(m);
@@ -831,9 +873,10 @@ int orc_bicgstab_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const
 }
 
 int orc_cgs_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
-                    const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist, int bs)
+                    const double *b, double *x, double tol, int64_t maxit, orc_info *info, double *hist, int bs,
+                   int adaptive)
 {
-    double *m = block_jacobi(n, rp, col, val, bs);
+    double *m = block_jacobi(n, rp, col, val, bs, adaptive);
     orc_prec M = {bs, m};
     int st = cgs_run(n, rp, col, val, b, x, tol, maxit, info, hist, &M);
     free(m);
@@ -842,9 +885,9 @@ int orc_cgs_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const doub
 
 int orc_gmres_bjacobi(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                       const double *b, double *x, int m, double tol, int64_t maxit, orc_info *info,
-                      double *hist, int bs)
+                      double *hist, int bs, int adaptive)
 {
-    double *mi = block_jacobi(n, rp, col, val, bs);
+    double *mi = block_jacobi(n, rp, col, val, bs, adaptive);
     orc_prec M = {bs, mi};
     int st = gmres_run(n, rp, col, val, b, x, m, tol, maxit, info, hist, &M);
     free(mi);

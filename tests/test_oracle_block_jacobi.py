@@ -190,3 +190,98 @@ def test_planted_transposed_block_is_caught():
     _, good = oracle.bicgstab(rp, col, val, b, tol=1e-12, precond="block_jacobi", block_size=bs)
     _, bad = oracle.bicgstab(rp, col, val, b, tol=1e-12, precond="block_jacobi", block_size=bs, mutant=8)
     assert good.iterations == 1 and bad.iterations > 1
+
+
+# ---------------------------------------------------------------- adaptive storage
+# Reading (the paper cites adaptive-precision block-Jacobi without a rule): a
+# block's inverse is stored in FP32 when kappa_1(D_k) * 2^-24 <= 1e-2, else FP64.
+
+def test_adaptive_flags_follow_the_condition_number():
+    # block k = diag(1, ..., 1, c_k): kappa_1 = c_k exactly
+    bs = 4
+    cs = [1.0, 1e3, 1.6e5, 1.7e5, 1e8, 3.0]
+    d = np.ones(bs * len(cs))
+    for k, c in enumerate(cs):
+        d[k * bs + bs - 1] = c
+    a = np.diag(d)
+    rp, col, val = csr_from_dense(a)
+    inv, flags = oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)
+    want = [int(c * 2.0**-24 > 1e-2) for c in cs]
+    assert flags.tolist() == want == [0, 0, 0, 1, 1, 0]
+    for k, c in enumerate(cs):
+        e = inv[k][bs - 1, bs - 1]
+        assert e == (1.0 / c if want[k] else float(np.float32(1.0 / c)))
+
+
+def test_adaptive_fp32_blocks_stay_within_the_bound():
+    rng = np.random.default_rng(12)
+    bs, n = 8, 8 * 40
+    a = np.zeros((n, n))
+    for k, c0 in enumerate(range(0, n, bs)):
+        g = rng.standard_normal((bs, bs))
+        if k % 3 == 0:  # every third block ill-conditioned: kappa ~ 1e7
+            q, _ = np.linalg.qr(g)
+            a[c0:c0 + bs, c0:c0 + bs] = q @ np.diag(np.geomspace(1.0, 1e-7, bs)) @ q.T
+        else:
+            a[c0:c0 + bs, c0:c0 + bs] = g + rng.choice([3.0, 30.0]) * np.eye(bs)
+    rp, col, val = csr_from_dense(a)
+    inv, flags = oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)
+    exact = oracle.block_jacobi_inv(rp, col, val, bs)
+    assert flags.tolist() == [int(k % 3 == 0) for k in range(n // bs)]
+    for k in range(n // bs):
+        blk = a[k * bs:(k + 1) * bs, k * bs:(k + 1) * bs]
+        kappa = np.linalg.norm(blk, 1) * np.linalg.norm(np.linalg.inv(blk), 1)
+        assert flags[k] == int(kappa * 2.0**-24 > 1e-2)
+        if flags[k]:
+            assert np.array_equal(inv[k], exact[k])
+        else:
+            assert np.array_equal(inv[k], exact[k].astype(np.float32).astype(np.float64))
+            assert np.linalg.norm(blk @ inv[k] - np.eye(bs), 1) <= 1e-2
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs", "gmres"])
+def test_adaptive_all_fp64_blocks_equals_block_jacobi(solver):
+    # blocks with kappa > 1.7e5: every one stays FP64, the solve is the FP64 one bit for bit
+    bs = 4
+    rng = np.random.default_rng(3)
+    n = 4 * 30
+    a = np.zeros((n, n))
+    for c0 in range(0, n, bs):
+        q, _ = np.linalg.qr(rng.standard_normal((bs, bs)))
+        s = np.diag([1.0, 10.0, 1e3, 1e6])
+        blk = q @ s @ q.T
+        a[c0:c0 + bs, c0:c0 + bs] = blk if solver == "cg" else blk + 0.1 * rng.standard_normal((bs, bs))
+    a += np.diag(np.full(n - 1, 0.01), 1) + np.diag(np.full(n - 1, 0.01), -1)
+    rp, col, val = csr_from_dense(a)
+    _, flags = oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)
+    assert flags.all()
+    b = rng.standard_normal(n)
+    kw = {"m": 20} if solver == "gmres" else {}
+    x1, i1 = getattr(oracle, solver)(rp, col, val, b, tol=0.0, maxit=6, precond="block_jacobi", block_size=bs, **kw)
+    x2, i2 = getattr(oracle, solver)(rp, col, val, b, tol=0.0, maxit=6, precond="adaptive_block_jacobi",
+                                     block_size=bs, **kw)
+    assert np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "gmres"])
+def test_adaptive_block_diagonal_converges_in_few_steps(solver):
+    # well-conditioned blocks go to FP32: M^-1 A = I + O(1e-7), so each step
+    # gains about seven digits instead of converging in one
+    bs = 8
+    rng = np.random.default_rng(5)
+    n = bs * 30 + 5
+    a = np.zeros((n, n))
+    for c0 in range(0, n, bs):
+        k = min(bs, n - c0)
+        a[c0:c0 + k, c0:c0 + k] = rng.standard_normal((k, k)) + 2 * k * np.eye(k)
+    rp, col, val = csr_from_dense(a)
+    _, flags = oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)
+    assert not flags.any()
+    b = rng.standard_normal(n)
+    kw = {"m": 10} if solver == "gmres" else {}
+    x, info = getattr(oracle, solver)(rp, col, val, b, tol=1e-12, precond="adaptive_block_jacobi", block_size=bs,
+                                      **kw)
+    # (a BiCGSTAB iteration applies the preconditioner twice)
+    lo, hi = (2, 3) if solver == "gmres" else (1, 2)
+    assert info.status == oracle.CONVERGED and lo <= info.iterations <= hi, info
+    assert np.allclose(x, np.linalg.solve(a, b), rtol=0, atol=1e-11)
