@@ -418,8 +418,9 @@ def solve_secondary(spx, ctx, stream, dev, peak, fmt="csr"):
 
 
 def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
-    """Jacobi (M = diag A) and block-Jacobi (blocks of 8 rows) preconditioning
-    against the plain solvers on 128^3 matrices: the 7-point Poisson matrix
+    """Jacobi (M = diag A) and block-Jacobi (blocks of 8 rows; FP64 inverses,
+    and adaptive storage with FP32 copies of well-conditioned blocks)
+    preconditioning against the plain solvers on 128^3 matrices: the 7-point Poisson matrix
     scaled symmetrically, S A S with s_i = exp(U[-2, 2]) (CG); the upwind
     convection-diffusion matrix (Peclet 10) with rows scaled by exp(U[-3, 3])
     (BiCGSTAB, CGS, GMRES(30)); and the stress variant with cell Peclet
@@ -453,7 +454,8 @@ def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
             spx.spx_spmv(ctx, A, xs, b)
             res = {}
             for solver in solvers:
-                for pc, tag in ((None, ""), ("jacobi", "_jacobi"), ("block_jacobi", "_block8")):
+                for pc, tag in ((None, ""), ("jacobi", "_jacobi"), ("block_jacobi", "_block8"),
+                                ("adaptive_block_jacobi", "_block8_adaptive")):
                     x = torch.zeros(n, dtype=torch.float64, device=dev)
                     si = spx.spx_solve(ctx, A, b, x, solver, 1e-10, max_iter, restart=30, precond=pc, block_size=8)
                     res[f"{solver}{tag}"] = {

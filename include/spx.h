@@ -68,6 +68,12 @@ typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2, SPX_CGS = 3 } spx_so
 #define SPX_PRECOND_BLOCK_JACOBI 0x200
 #define SPX_PRECOND_BLOCK_SHIFT 16
 #define SPX_PRECOND_BLOCK(bs) (SPX_PRECOND_BLOCK_JACOBI | ((bs) << SPX_PRECOND_BLOCK_SHIFT))
+/* OR into SPX_PRECOND_BLOCK(bs) for adaptive storage of the block inverses in
+ * FP64 solves (the adaptive-precision block-Jacobi Section 2 cites): a block
+ * whose 1-norm condition number times 2^-24 is at most 1e-2 is applied from an
+ * FP32 copy of its inverse (half the bytes), the others from FP64; the
+ * arithmetic stays FP64.  Ignored by FP32 solves, which store FP32 inverses. */
+#define SPX_PRECOND_BLOCK_ADAPTIVE 0x400
 
 /* Arithmetic of a solve: all FP64; all FP32 (values, vectors, dots and
  * scalars in float); or FP64 iterative refinement around an FP32 inner solve

@@ -26,6 +26,7 @@
  * of iterative refinement is "parity unpinned": only its end state (the true
  * FP64 residual) is checked.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -758,8 +759,9 @@ int orc_gmres_jacobi(int64_t n, const int32_t *rp, const int32_t *col, const dou
 /* when its 1-norm condition number kappa = ||D_k||_1 ||D_k^{-1}||_1 times   */
 /* the FP32 unit roundoff 2^-24 is at most 1e-2, so that the rounded        */
 /* inverse differs from the exact one by at most 1% of the identity in the  */
-/* preconditioned block; otherwise in FP64.  The FP32 entries are returned  */
-/* as the doubles they round to; flags[k] = 1 marks an FP64 block.          */
+/* preconditioned block, and every nonzero entry lies in FP32's normal      */
+/* range; otherwise in FP64.  The FP32 entries are returned as the doubles  */
+/* they round to; flags[k] = 1 marks an FP64 block.                         */
 #define ORC_BJ_FP32_BOUND 1e-2
 
 static int block_jacobi_inv_impl(int64_t n, const int32_t *rp, const int32_t *col, const double *val, int bs,
@@ -817,7 +819,15 @@ static int block_jacobi_inv_impl(int64_t n, const int32_t *rp, const int32_t *co
                 for (int r = 0; r < bs; ++r) cs += fabs(out[r * bs + c]);
                 if (cs > inorm) inorm = cs;
             }
-            const int fp64 = !singular && dnorm * inorm * ldexp(1.0, -24) > ORC_BJ_FP32_BOUND;
+            /* FP32 also needs every nonzero entry inside FP32's normal range */
+            double amax = 0.0, amin = INFINITY;
+            for (int e = 0; e < bs * bs; ++e) {
+                const double v = fabs(out[e]);
+                if (v > amax) amax = v;
+                if (v != 0.0 && v < amin) amin = v;
+            }
+            const int in_range = amax <= (double)FLT_MAX && (amin == INFINITY || amin >= (double)FLT_MIN);
+            const int fp64 = !singular && (dnorm * inorm * ldexp(1.0, -24) > ORC_BJ_FP32_BOUND || !in_range);
             flags[k] = (unsigned char)fp64;
             if (!fp64)
                 for (int e = 0; e < bs * bs; ++e) out[e] = (double)(float)out[e];

@@ -373,8 +373,8 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     if (!S || !row_ptr || !b || !x || !req_id || n <= 0 || nnz < 0 || (nnz > 0 && (!col_idx || !values)))
         return fail(SPX_ERR_INVALID, "spx_server_submit: bad argument");
     int base_solver = 0, bs = 0;
-    bool jacobi = false;
-    if (parse_solver_code(solver, &base_solver, &jacobi, &bs) != SPX_OK)
+    bool jacobi = false, adaptive = false;
+    if (parse_solver_code(solver, &base_solver, &jacobi, &bs, &adaptive) != SPX_OK)
         return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
     Request *R = new Request();
     R->n = n;
@@ -391,7 +391,7 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     R->max_iter = max_iter;
     R->footprint = request_footprint(n, nnz, base_solver, precision, restart) +
                    (jacobi ? (size_t)n * 24 : 0) +  // M^-1 and the preconditioned vectors
-                   (size_t)n * (size_t)bs * 8;      // block-Jacobi inverses
+                   (size_t)n * (size_t)bs * (adaptive ? 12 : 8);  // block-Jacobi inverses (+ FP32 copies)
     R->error = SPX_OK;
     R->t_submit = Clock::now();
     R->block = batch_block_for(n);

@@ -18,6 +18,7 @@
 // Convergence policy: recurrence residual ||r||/||b|| <= tol, then the true
 // residual b - A x is formed; if it misses tol the solve restarts from x (at
 // most 3 times, then STAGNATED).
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -76,14 +77,16 @@ struct SolverWork {
     // blocks, row-major per block
     bool pre = false;
     int bs = 0;
-    DBuf dinv, bjinv;
+    bool bj_adapt = false;  // adaptive storage: FP32 copies of the blocks that qualify
+    DBuf dinv, bjinv, bjinv32;
 };
 
 void solver_work_release(spx_ctx *ctx, SolverWork *w)
 {
     if (!w) return;
     if (w->gexec) cudaGraphExecDestroy(w->gexec);
-    DBuf *bufs[] = {&w->vecs, &w->state, &w->dots, &w->red, &w->ticket, &w->small, &w->ir, &w->dinv, &w->bjinv};
+    DBuf *bufs[] = {&w->vecs, &w->state, &w->dots, &w->red, &w->ticket, &w->small, &w->ir, &w->dinv, &w->bjinv,
+                    &w->bjinv32};
     for (DBuf *b : bufs) dbuf_free(ctx, *b);
     if (w->host) cudaFreeHost(w->host);
     solver_work_release(ctx, w->inner);
@@ -108,11 +111,13 @@ static int nvec_for(int solver, int m, bool pre)
 }
 
 template <class T>
-static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, int m, bool pre = false, int bs = 0)
+static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, int m, bool pre = false, int bs = 0,
+                        bool adapt = false)
 {
     const int dtype = sizeof(T) == 8 ? SPX_F64 : SPX_F32;
+    adapt = adapt && sizeof(T) == 8;  // FP32 solves store FP32 inverses anyway
     if (wk && (wk->dtype != dtype || wk->n != n || wk->solver != solver || wk->m != m || wk->pre != pre ||
-               wk->bs != bs)) {
+               wk->bs != bs || wk->bj_adapt != adapt)) {
         SolverWork *inner = wk->inner;
         wk->inner = nullptr;
         cudaStreamSynchronize(ctx->stream);
@@ -131,6 +136,7 @@ static int work_prepare(spx_ctx *ctx, SolverWork *&wk, int64_t n, int solver, in
     wk->m = m;
     wk->pre = pre;
     wk->bs = bs;
+    wk->bj_adapt = adapt;
     wk->ld = (int64_t)round_up((size_t)(n > 0 ? n : 1), 64);
     wk->nvec = nvec_for(solver, m, pre);
     SPX_TRY(dbuf_alloc(ctx, wk->vecs, (size_t)wk->nvec * wk->ld * sizeof(T)));
@@ -378,6 +384,19 @@ __global__ void k_jacobi_dinv(int64_t n, const int *__restrict__ rp, const int *
 // block is padded with identity rows.  Section 2 lists block-Jacobi among the
 // library's preconditioners.
 constexpr int kBjWarps = 2;  // warps per block of the inversion kernel
+// Adaptive storage (the adaptive-precision block-Jacobi Section 2 cites, with
+// this rule read into it): a block's inverse is applied from an FP32 copy when
+// its 1-norm condition number times the FP32 unit roundoff is at most this,
+// so that the rounded inverse stays within 1% of the identity in the
+// preconditioned block; else from the FP64 inverse.
+constexpr double kBjFp32Bound = 1e-2;
+
+__device__ __forceinline__ double bj_warp_max(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
 
 // One warp per diagonal block: gather the block's entries (the block's rows,
 // columns inside the block; duplicates summed in storage order) into the
@@ -393,7 +412,7 @@ __global__ void __launch_bounds__(32 * kBjWarps)
     k_bj_build(int64_t n, int bs, const int *__restrict__ rp, const int *__restrict__ col, const V *__restrict__ val,
                int64_t ell_ld, int64_t ell_w, const int *__restrict__ ecol, const V *__restrict__ evals,
                int64_t coo_nnz, const int *__restrict__ crow, const int *__restrict__ ccol,
-               const V *__restrict__ cval, T *__restrict__ minv)
+               const V *__restrict__ cval, T *__restrict__ minv, float *__restrict__ minv32)
 {
     extern __shared__ double bj_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -437,6 +456,14 @@ __global__ void __launch_bounds__(32 * kBjWarps)
             }
         }
         __syncwarp();
+        // ||D||_1 (adaptive storage): column sums in row order, then the largest
+        double dnorm = 0.0;
+        if (minv32) {
+            double cs = 0.0;
+            if (lane < bs)
+                for (int r = 0; r < bs; ++r) cs += fabs(aug[r * w2 + lane]);
+            dnorm = bj_warp_max(cs);
+        }
         bool singular = false;
         for (int p = 0; p < bs; ++p) {
             double best = -1.0;
@@ -487,8 +514,164 @@ __global__ void __launch_bounds__(32 * kBjWarps)
             const int r = e / bs, c = e - r * bs;
             out[e] = singular ? (r == c ? T(1) : T(0)) : (T)aug[r * w2 + bs + c];
         }
+        if (minv32) {
+            // FP32 copy when kappa_1 * 2^-24 <= kBjFp32Bound and every nonzero
+            // entry is inside FP32's normal range; else every row of the copy
+            // starts with a NaN, which sends the apply to the FP64 inverse
+            double cs = 0.0, amax = 0.0, amin = INFINITY;
+            if (lane < bs)
+                for (int r = 0; r < bs; ++r) {
+                    const double v = fabs(singular ? (r == lane ? 1.0 : 0.0) : aug[r * w2 + bs + lane]);
+                    cs += v;
+                    amax = fmax(amax, v);
+                    if (v != 0.0) amin = fmin(amin, v);
+                }
+            const double inorm = bj_warp_max(cs);
+            amax = bj_warp_max(amax);
+            amin = -bj_warp_max(-amin);
+            const bool in_range = amax <= (double)FLT_MAX && (amin == INFINITY || amin >= (double)FLT_MIN);
+            const bool fp64 = !singular && (dnorm * inorm * 0x1p-24 > kBjFp32Bound || !in_range);
+            float *o32 = minv32 + (size_t)k * (size_t)(bs * bs);
+            for (int e = lane; e < bs * bs; e += 32) {
+                const int r = e / bs, c = e - r * bs;
+                o32[e] = fp64 ? (c == 0 ? __int_as_float(0x7fc00000) : 0.0f)
+                              : (singular ? (r == c ? 1.0f : 0.0f) : (float)aug[r * w2 + bs + c]);
+            }
+        }
         __syncwarp();
     }
+}
+
+// Small blocks (bs <= 8): one thread per diagonal block, so that each FP64
+// warp instruction works on 32 blocks (GB300 issues two FP64 lanes per SM
+// per clock; a warp per 8 x 8 block left most of every instruction idle).
+// The block sits in shared memory interleaved across the threads (element
+// e of thread t at e * kBjTpb + t: no bank conflicts) and is inverted in
+// place by Gauss-Jordan with partial pivoting (the same pivot choice and
+// zero-pivot rule as the warp kernel; the row swaps are undone on the
+// columns at the end).
+constexpr int kBjTpb = 64;
+
+template <class V, class T, int BS>
+__global__ void __launch_bounds__(kBjTpb)
+    k_bj_build_t(int64_t n, const int *__restrict__ rp, const int *__restrict__ col, const V *__restrict__ val,
+                 int64_t ell_ld, int64_t ell_w, const int *__restrict__ ecol, const V *__restrict__ evals,
+                 int64_t coo_nnz, const int *__restrict__ crow, const int *__restrict__ ccol,
+                 const V *__restrict__ cval, T *__restrict__ minv, float *__restrict__ minv32)
+{
+    __shared__ double sa[BS * BS * kBjTpb];
+    const int t = threadIdx.x;
+    const int64_t nb = (n + BS - 1) / BS;
+#define BJA(r_, c_) sa[((r_) * BS + (c_)) * kBjTpb + t]
+    for (int64_t k = (int64_t)blockIdx.x * kBjTpb + t; k - t < nb; k += (int64_t)gridDim.x * kBjTpb) {
+        if (k >= nb) continue;
+        const int64_t c0 = k * BS;
+#pragma unroll
+        for (int e = 0; e < BS * BS; ++e) sa[e * kBjTpb + t] = 0.0;
+        for (int r = 0; r < BS; ++r) {
+            const int64_t i = c0 + r;
+            if (i >= n) {
+                BJA(r, r) = 1.0;
+                continue;
+            }
+            if (rp)
+                for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                    const int64_t c = col[e];
+                    if (c >= c0 && c < c0 + BS) BJA(r, c - c0) += (double)val[e];
+                }
+            for (int64_t j = 0; j < ell_w; ++j) {
+                const int64_t c = ecol[j * ell_ld + i];
+                if (c >= c0 && c < c0 + BS) BJA(r, c - c0) += (double)evals[j * ell_ld + i];
+            }
+            if (coo_nnz > 0) {
+                int64_t lo = 0, hi = coo_nnz;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (crow[mid] < i) lo = mid + 1;
+                    else hi = mid;
+                }
+                for (int64_t e = lo; e < coo_nnz && crow[e] == i; ++e) {
+                    const int64_t c = ccol[e];
+                    if (c >= c0 && c < c0 + BS) BJA(r, c - c0) += (double)cval[e];
+                }
+            }
+        }
+        double dnorm = 0.0;
+        if (minv32)
+            for (int c = 0; c < BS; ++c) {
+                double cs = 0.0;
+                for (int r = 0; r < BS; ++r) cs += fabs(BJA(r, c));
+                dnorm = fmax(dnorm, cs);
+            }
+        int perm[BS];
+        bool singular = false;
+#pragma unroll
+        for (int p = 0; p < BS; ++p) {
+            int piv = p;
+            double best = fabs(BJA(p, p));
+            for (int r = p + 1; r < BS; ++r) {
+                const double a = fabs(BJA(r, p));
+                if (a > best) {
+                    best = a;
+                    piv = r;
+                }
+            }
+            perm[p] = piv;
+            if (best == 0.0) {
+                singular = true;
+                break;
+            }
+            if (piv != p)
+                for (int c = 0; c < BS; ++c) {
+                    const double tmp = BJA(p, c);
+                    BJA(p, c) = BJA(piv, c);
+                    BJA(piv, c) = tmp;
+                }
+            const double inv = 1.0 / BJA(p, p);
+            BJA(p, p) = 1.0;
+            for (int c = 0; c < BS; ++c) BJA(p, c) *= inv;
+            for (int r = 0; r < BS; ++r) {
+                if (r == p) continue;
+                const double f = BJA(r, p);
+                if (f == 0.0) continue;
+                BJA(r, p) = 0.0;
+                for (int c = 0; c < BS; ++c) BJA(r, c) -= f * BJA(p, c);
+            }
+        }
+        if (!singular)
+#pragma unroll
+            for (int p = BS - 1; p >= 0; --p)
+                if (perm[p] != p)
+                    for (int r = 0; r < BS; ++r) {
+                        const double tmp = BJA(r, p);
+                        BJA(r, p) = BJA(r, perm[p]);
+                        BJA(r, perm[p]) = tmp;
+                    }
+        T *out = minv + (size_t)k * (BS * BS);
+        for (int r = 0; r < BS; ++r)
+            for (int c = 0; c < BS; ++c) out[r * BS + c] = singular ? (r == c ? T(1) : T(0)) : (T)BJA(r, c);
+        if (minv32) {
+            double inorm = 0.0, amax = 0.0, amin = INFINITY;
+            for (int c = 0; c < BS; ++c) {
+                double cs = 0.0;
+                for (int r = 0; r < BS; ++r) {
+                    const double v = fabs(singular ? (r == c ? 1.0 : 0.0) : BJA(r, c));
+                    cs += v;
+                    amax = fmax(amax, v);
+                    if (v != 0.0) amin = fmin(amin, v);
+                }
+                inorm = fmax(inorm, cs);
+            }
+            const bool in_range = amax <= (double)FLT_MAX && (amin == INFINITY || amin >= (double)FLT_MIN);
+            const bool fp64 = !singular && (dnorm * inorm * 0x1p-24 > kBjFp32Bound || !in_range);
+            float *o32 = minv32 + (size_t)k * (BS * BS);
+            for (int r = 0; r < BS; ++r)
+                for (int c = 0; c < BS; ++c)
+                    o32[r * BS + c] = fp64 ? (c == 0 ? __int_as_float(0x7fc00000) : 0.0f)
+                                           : (singular ? (r == c ? 1.0f : 0.0f) : (float)BJA(r, c));
+        }
+    }
+#undef BJA
 }
 
 // out = M^-1 in, one element per thread: the lanes of a warp hold 32
@@ -524,39 +707,104 @@ template <class T, int BS> __device__ __forceinline__ void bj_load_row(const T *
     }
 }
 
-template <class T, int BS, int MODE>
+// FP32 -> FP64 widening of a zero, normal, infinite or NaN number (IEEE 754
+// binary32 to binary64: same sign, exponent rebiased by 1023 - 127 or kept
+// all-ones, fraction shifted up by 29 bits), on the integer units: a
+// float-to-double conversion instruction runs on GB300's FP64 pipe, which the
+// block apply's FMAs already fill.  The adaptive storage rule keeps every
+// nonzero FP32 entry normal, and the NaN marker of an FP64 block stays a NaN.
+__device__ __forceinline__ double bj_widen(unsigned b)
+{
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned mag = b & 0x7fffffffu;
+    const unsigned e = mag >> 23;
+    const unsigned long long ex = e == 0xffu ? 0x7ffull : (unsigned long long)(e + (1023u - 127u));
+    const unsigned long long body = (ex << 52) | ((unsigned long long)(mag & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)(sign | (mag ? body : 0ull)));
+}
+
+template <int BS> __device__ __forceinline__ void bj_load_row32(const float *__restrict__ row, double (&m)[BS])
+{
+    if constexpr (BS >= 4) {
+#pragma unroll
+        for (int j = 0; j < BS; j += 4) {
+            const uint4 t = __ldg(reinterpret_cast<const uint4 *>(row + j));
+            m[j] = bj_widen(t.x);
+            m[j + 1] = bj_widen(t.y);
+            m[j + 2] = bj_widen(t.z);
+            m[j + 3] = bj_widen(t.w);
+        }
+    } else if constexpr (BS == 2) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(row));
+        m[0] = bj_widen(t.x);
+        m[1] = bj_widen(t.y);
+    } else {
+        m[0] = bj_widen(__ldg(reinterpret_cast<const unsigned *>(row)));
+    }
+}
+
+// ADAPT (FP64 solves with adaptive storage): each row comes from the FP32
+// copy unless that row starts with the NaN marker of an FP64 block; the
+// arithmetic stays FP64.  Each thread takes U elements per step (warp-uniform
+// bounds; all loads before the shuffles) so that U rows are in flight.
+template <class T, int BS, int MODE, bool ADAPT>
 __global__ void __launch_bounds__(kVB)
     k_bj_apply(int64_t n, const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ minv,
-               const int *skip, T *__restrict__ x, KState<T> *st, int fin, T *partials, unsigned *ticket)
+               const float *__restrict__ minv32, const int *skip, T *__restrict__ x, KState<T> *st, int fin,
+               T *partials, unsigned *ticket)
 {
     if (skip && *skip) return;
+    constexpr int U = BS >= 16 ? 1 : BS == 8 ? 2 : 4;  // at most 16 row values in registers
     const int lane = threadIdx.x & 31;
     const int g0 = lane & ~(BS - 1);
     const T alpha = MODE == BJ_AXPY ? st->alpha : T(0);
     T d0 = T(0);
     const int64_t stride = (int64_t)gridDim.x * kVB;
-    // warp-uniform trip count: every lane takes part in the shuffles
-    for (int64_t base = (int64_t)blockIdx.x * kVB + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t i = base + lane;
-        const bool act = i < n;
-        const T v = act ? in[i] : T(0);
-        T s = T(0);
-        if constexpr (BS == 1) {
-            if (act) s = minv[i] * v;
-        } else {
-            T m[BS];
-            if (act) bj_load_row<T, BS>(minv + i * BS, m);
+    for (int64_t base = (int64_t)blockIdx.x * kVB + (threadIdx.x & ~31); base < n; base += U * stride) {
+        T v[U], m[U][BS];
+        bool act[U];
 #pragma unroll
-            for (int j = 0; j < BS; ++j) {
-                const T vj = __shfl_sync(0xffffffffu, v, g0 + j);
-                if (act) s = fma(m[j], vj, s);
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + u * stride + lane;
+            act[u] = i < n;
+            v[u] = act[u] ? in[i] : T(0);
+        }
+        // every row load of the step is issued before the first use; the FP64
+        // rows of an adaptive matrix follow only where the marker asks for them
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + u * stride + lane;
+            if (!act[u]) continue;
+            if constexpr (ADAPT) bj_load_row32<BS>(minv32 + i * BS, m[u]);
+            else if constexpr (BS == 1) m[u][0] = minv[i];
+            else bj_load_row<T, BS>(minv + i * BS, m[u]);
+        }
+        if constexpr (ADAPT) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = base + u * stride + lane;
+                if (act[u] && isnan(m[u][0])) bj_load_row<T, BS>(minv + i * BS, m[u]);
             }
         }
-        if (act) {
-            if (MODE == BJ_DOT) d0 = fma(v, s, d0);
-            if (MODE != BJ_ADDX) out[i] = s;
-            if (MODE == BJ_AXPY) x[i] = fma(alpha, s, x[i]);
-            if (MODE == BJ_ADDX) x[i] += s;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + u * stride + lane;
+            T s = T(0);
+            if constexpr (BS == 1 && !ADAPT) {
+                if (act[u]) s = m[u][0] * v[u];
+            } else {
+#pragma unroll
+                for (int j = 0; j < BS; ++j) {
+                    const T vj = __shfl_sync(0xffffffffu, v[u], g0 + j);
+                    if (act[u]) s = fma(m[u][j], vj, s);
+                }
+            }
+            if (act[u]) {
+                if (MODE == BJ_DOT) d0 = fma(v[u], s, d0);
+                if (MODE != BJ_ADDX) out[i] = s;
+                if (MODE == BJ_AXPY) x[i] = fma(alpha, s, x[i]);
+                if (MODE == BJ_ADDX) x[i] += s;
+            }
         }
     }
     if constexpr (MODE == BJ_DOT) grid_dots_finish<T, kVB>(d0, T(0), (T *)nullptr, fin, st, partials, ticket);
@@ -949,18 +1197,21 @@ __global__ void __launch_bounds__(kVB) k_gm_start(int64_t n, T *__restrict__ v0,
     }
 }
 
-// Splits a solver code of the ABI into the method, the Jacobi flag and the
-// block-Jacobi block size (0: none).
-int parse_solver_code(int code, int *solver, bool *jacobi, int *bs)
+// Splits a solver code of the ABI into the method, the Jacobi flag, the
+// block-Jacobi block size (0: none) and block-Jacobi's adaptive storage.
+int parse_solver_code(int code, int *solver, bool *jacobi, int *bs, bool *adaptive)
 {
     const int base = code & 0xff;
     const int flags = code & ~0xff;
     *jacobi = false;
     *bs = 0;
+    *adaptive = false;
     if (base < SPX_CG || base > SPX_CGS) return fail(SPX_ERR_INVALID, "unknown solver");
     if (flags == SPX_PRECOND_JACOBI) {
         *jacobi = true;
-    } else if ((flags & 0xffff) == SPX_PRECOND_BLOCK_JACOBI) {
+    } else if ((flags & 0xffff) == SPX_PRECOND_BLOCK_JACOBI ||
+               (flags & 0xffff) == (SPX_PRECOND_BLOCK_JACOBI | SPX_PRECOND_BLOCK_ADAPTIVE)) {
+        *adaptive = (flags & SPX_PRECOND_BLOCK_ADAPTIVE) != 0;
         const int b = (int)((unsigned)code >> SPX_PRECOND_BLOCK_SHIFT);
         if (b != 1 && b != 2 && b != 4 && b != 8 && b != 16 && b != 32)
             return fail(SPX_ERR_INVALID, "block-Jacobi block size must be 1, 2, 4, 8, 16 or 32");
@@ -1054,24 +1305,42 @@ template <class T> struct KrylovRun {
 };
 
 // out = M^-1 in for block-Jacobi (see k_bj_apply for the modes)
-template <class T, int BS>
+template <class T, int BS, bool ADAPT>
 int bj_apply_bs(spx_ctx *ctx, SolverWork *w, int64_t n, const T *in, T *out, int mode, const int *skip, T *x,
                 int fin)
 {
     const int g = vgrid(ctx, n);
     const T *minv = w->bjinv.as<T>();
+    const float *m32 = ADAPT ? w->bjinv32.as<float>() : nullptr;
     KState<T> *st = w->state.as<KState<T>>();
     T *part = w->red.as<T>();
     unsigned *tk = w->ticket.as<unsigned>();
     cudaStream_t sm = ctx->stream;
     switch (mode) {
-    case BJ_PLAIN: k_bj_apply<T, BS, BJ_PLAIN><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
-    case BJ_DOT: k_bj_apply<T, BS, BJ_DOT><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
-    case BJ_AXPY: k_bj_apply<T, BS, BJ_AXPY><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
-    default: k_bj_apply<T, BS, BJ_ADDX><<<g, kVB, 0, sm>>>(n, in, out, minv, skip, x, st, fin, part, tk); break;
+    case BJ_PLAIN:
+        k_bj_apply<T, BS, BJ_PLAIN, ADAPT><<<g, kVB, 0, sm>>>(n, in, out, minv, m32, skip, x, st, fin, part, tk);
+        break;
+    case BJ_DOT:
+        k_bj_apply<T, BS, BJ_DOT, ADAPT><<<g, kVB, 0, sm>>>(n, in, out, minv, m32, skip, x, st, fin, part, tk);
+        break;
+    case BJ_AXPY:
+        k_bj_apply<T, BS, BJ_AXPY, ADAPT><<<g, kVB, 0, sm>>>(n, in, out, minv, m32, skip, x, st, fin, part, tk);
+        break;
+    default:
+        k_bj_apply<T, BS, BJ_ADDX, ADAPT><<<g, kVB, 0, sm>>>(n, in, out, minv, m32, skip, x, st, fin, part, tk);
+        break;
     }
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
+}
+
+template <class T, int BS>
+int bj_apply_sel(spx_ctx *ctx, SolverWork *w, int64_t n, const T *in, T *out, int mode, const int *skip, T *x,
+                 int fin)
+{
+    if constexpr (sizeof(T) == 8)
+        if (w->bj_adapt) return bj_apply_bs<T, BS, true>(ctx, w, n, in, out, mode, skip, x, fin);
+    return bj_apply_bs<T, BS, false>(ctx, w, n, in, out, mode, skip, x, fin);
 }
 
 template <class T>
@@ -1079,12 +1348,12 @@ int bj_apply(spx_ctx *ctx, SolverWork *w, int64_t n, const T *in, T *out, int mo
              int fin = FIN_NONE)
 {
     switch (w->bs) {
-    case 1: return bj_apply_bs<T, 1>(ctx, w, n, in, out, mode, skip, x, fin);
-    case 2: return bj_apply_bs<T, 2>(ctx, w, n, in, out, mode, skip, x, fin);
-    case 4: return bj_apply_bs<T, 4>(ctx, w, n, in, out, mode, skip, x, fin);
-    case 8: return bj_apply_bs<T, 8>(ctx, w, n, in, out, mode, skip, x, fin);
-    case 16: return bj_apply_bs<T, 16>(ctx, w, n, in, out, mode, skip, x, fin);
-    case 32: return bj_apply_bs<T, 32>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 1: return bj_apply_sel<T, 1>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 2: return bj_apply_sel<T, 2>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 4: return bj_apply_sel<T, 4>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 8: return bj_apply_sel<T, 8>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 16: return bj_apply_sel<T, 16>(ctx, w, n, in, out, mode, skip, x, fin);
+    case 32: return bj_apply_sel<T, 32>(ctx, w, n, in, out, mode, skip, x, fin);
     default: return fail(SPX_ERR_INVALID, "block-Jacobi block size must be 1, 2, 4, 8, 16 or 32");
     }
 }
@@ -1280,6 +1549,31 @@ template <class T> int ensure_dinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
     return SPX_OK;
 }
 
+template <class V, class T>
+int bj_build_small(spx_ctx *ctx, spx_matrix *A, SolverWork *w, float *m32)
+{
+    const int64_t n = A->n, nb = ceil_div(n > 0 ? n : 1, (int64_t)w->bs);
+    const int g = (int)std::min<int64_t>(ceil_div(nb, kBjTpb), (int64_t)ctx->sm_count * 16);
+    const bool csr = A->format == SPX_CSR;
+    const int64_t ew = (A->format == SPX_ELL || A->format == SPX_HYB) ? A->ell_w : 0;
+    const int64_t cn = (A->format == SPX_COO || A->format == SPX_HYB) ? A->coo_nnz : 0;
+    const V *val = A->val.as<V>(), *ev = A->ell_val.as<V>(), *cv = A->coo_val.as<V>();
+#define SPX_BJ_SMALL(B_)                                                                                            \
+    k_bj_build_t<V, T, B_><<<g, kBjTpb, 0, ctx->stream>>>(n, csr ? A->rp.as<int>() : nullptr, A->col.as<int>(), val, \
+                                                         A->ell_ld, ew, A->ell_col.as<int>(), ev, cn,               \
+                                                         A->coo_row.as<int>(), A->coo_col.as<int>(), cv,             \
+                                                         w->bjinv.as<T>(), m32)
+    switch (w->bs) {
+    case 1: SPX_BJ_SMALL(1); break;
+    case 2: SPX_BJ_SMALL(2); break;
+    case 4: SPX_BJ_SMALL(4); break;
+    default: SPX_BJ_SMALL(8); break;
+    }
+#undef SPX_BJ_SMALL
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
+}
+
 // block-Jacobi inverses (FP64 elimination, stored in the work's precision)
 template <class T> int ensure_bjinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
 {
@@ -1287,6 +1581,9 @@ template <class T> int ensure_bjinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
     const int64_t n = A->n, bs = w->bs;
     const int64_t nb = ceil_div(n > 0 ? n : 1, bs);
     SPX_TRY(dbuf_alloc(ctx, w->bjinv, (size_t)(nb * bs * bs) * sizeof(T)));
+    if (w->bj_adapt) SPX_TRY(dbuf_alloc(ctx, w->bjinv32, (size_t)(nb * bs * bs) * sizeof(float)));
+    float *m32 = w->bj_adapt ? w->bjinv32.as<float>() : nullptr;
+    if (bs <= 8) return A->dtype == SPX_F64 ? bj_build_small<double, T>(ctx, A, w, m32) : bj_build_small<float, T>(ctx, A, w, m32);
     const int g = (int)std::min<int64_t>(ceil_div(nb, kBjWarps), (int64_t)ctx->sm_count * 32);
     const int smem = kBjWarps * (int)(bs * 2 * bs + bs) * 8;
     const bool csr = A->format == SPX_CSR;
@@ -1296,12 +1593,12 @@ template <class T> int ensure_bjinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
         k_bj_build<double, T><<<g, 32 * kBjWarps, smem, ctx->stream>>>(
             n, (int)bs, csr ? A->rp.as<int>() : nullptr, A->col.as<int>(), A->val.as<double>(), A->ell_ld, ew,
             A->ell_col.as<int>(), A->ell_val.as<double>(), cn, A->coo_row.as<int>(), A->coo_col.as<int>(),
-            A->coo_val.as<double>(), w->bjinv.as<T>());
+            A->coo_val.as<double>(), w->bjinv.as<T>(), m32);
     else
         k_bj_build<float, T><<<g, 32 * kBjWarps, smem, ctx->stream>>>(
             n, (int)bs, csr ? A->rp.as<int>() : nullptr, A->col.as<int>(), A->val.as<float>(), A->ell_ld, ew,
             A->ell_col.as<int>(), A->ell_val.as<float>(), cn, A->coo_row.as<int>(), A->coo_col.as<int>(),
-            A->coo_val.as<float>(), w->bjinv.as<T>());
+            A->coo_val.as<float>(), w->bjinv.as<T>(), m32);
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
@@ -1393,7 +1690,8 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
         int64_t launched = 0;
         while (!h->done) {
             const uint64_t key[8] = {(uint64_t)solver, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
-                                     (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16),
+                                     (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16) |
+                                     ((uint64_t)w->bj_adapt << 24),
                                      (uint64_t)(uintptr_t)A, 0};
             SPX_TRY(run_chunk(ctx, w, key, graphs, [&]() -> int {
                 for (int c = 0; c < chunk; ++c)
@@ -1512,7 +1810,8 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
     int64_t cycles = 0;
     for (;;) {
         const uint64_t key[8] = {(uint64_t)SPX_GMRES, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
-                                 (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16),
+                                 (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16) |
+                                     ((uint64_t)w->bj_adapt << 24),
                                  (uint64_t)(uintptr_t)A, 1};
         SPX_TRY(run_chunk(ctx, w, key, n >= kGraphMinRows, cycle));
         SPX_TRY(read_state<T>(ctx, w, sizeof(GState<T>)));
@@ -1550,12 +1849,12 @@ __global__ void k_ir_update(int64_t n, double *__restrict__ x, const float *__re
 }
 
 int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, double tol, int64_t maxit,
-           int m, bool pre, int bs, spx_solve_info *info)
+           int m, bool pre, int bs, bool adapt, spx_solve_info *info)
 {
     const int64_t n = A->n;
     SolverWork *&w = A->work;
     SPX_TRY(work_prepare<double>(ctx, w, n, SPX_CG, 0));  // outer: r and scratch only
-    SPX_TRY(work_prepare<float>(ctx, w->inner, n, solver, solver == SPX_GMRES ? m : 0, pre, bs));
+    SPX_TRY(work_prepare<float>(ctx, w->inner, n, solver, solver == SPX_GMRES ? m : 0, pre, bs, adapt));
     SPX_TRY(ensure_prec<float>(ctx, A, w->inner));
     if (!w->ir.p) SPX_TRY(dbuf_alloc(ctx, w->ir, (size_t)n * 8 + 2 * (size_t)round_up(n, 64) * 4 + 256));
     double *r = w->ir.as<double>();
@@ -1625,9 +1924,9 @@ int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, 
 
 template <class T>
 int solve_typed(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, int solver, double tol, int64_t maxit, int m,
-                bool use32, int64_t fixed, bool pre, int bs, spx_solve_info *info)
+                bool use32, int64_t fixed, bool pre, int bs, bool adapt, spx_solve_info *info)
 {
-    SPX_TRY(work_prepare<T>(ctx, A->work, A->n, solver, solver == SPX_GMRES ? m : 0, pre, bs));
+    SPX_TRY(work_prepare<T>(ctx, A->work, A->n, solver, solver == SPX_GMRES ? m : 0, pre, bs, adapt));
     SPX_TRY(ensure_prec<T>(ctx, A, A->work));
     if (solver == SPX_GMRES) return run_gmres<T>(ctx, A, A->work, b, x, tol, maxit, m, use32, false, fixed, info);
     return run_short<T>(ctx, A, A->work, solver, b, x, tol, maxit, use32, false, fixed, info);
@@ -1640,9 +1939,9 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
         return fail(SPX_ERR_INVALID, "spx_solve: NULL argument");
     std::memset(info, 0, sizeof(*info));
     if (A->n != A->ncols) return fail(SPX_ERR_INVALID, "spx_solve: the matrix must be square");
-    bool pre = false;
+    bool pre = false, adapt = false;
     int bs = 0;
-    SPX_TRY(parse_solver_code(solver, &solver, &pre, &bs));
+    SPX_TRY(parse_solver_code(solver, &solver, &pre, &bs, &adapt));
     if (!(tol >= 0.0) || maxit < 0) return fail(SPX_ERR_INVALID, "spx_solve: bad tol or max_iter");
     if (solver == SPX_GMRES && (restart < 1 || restart > kGmKmax - 1))
         return fail(SPX_ERR_UNSUPPORTED, "GMRES restart length must be in [1, 31]");
@@ -1657,15 +1956,15 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
             return fail(SPX_ERR_UNSUPPORTED, "mixed precision needs an FP64 matrix created with SPX_MIXED_SHADOW");
         if (fixed > 0) return fail(SPX_ERR_UNSUPPORTED, "fixed-iteration mode runs in one precision");
         st = run_ir(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol, maxit, restart, pre,
-                    bs, info);
+                    bs, adapt, info);
     } else if (precision == SPX_PREC_F64 || precision == SPX_PREC_F32) {
         const int want = precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32;
         if (A->dtype != want) return fail(SPX_ERR_UNSUPPORTED, "precision must match the matrix dtype (or use MIXED)");
         st = A->dtype == SPX_F64
                  ? solve_typed<double>(ctx, A, static_cast<const double *>(b), static_cast<double *>(x), solver, tol,
-                                       maxit, restart, false, fixed, pre, bs, info)
+                                       maxit, restart, false, fixed, pre, bs, adapt, info)
                  : solve_typed<float>(ctx, A, static_cast<const float *>(b), static_cast<float *>(x), solver, tol,
-                                      maxit, restart, false, fixed, pre, bs, info);
+                                      maxit, restart, false, fixed, pre, bs, adapt, info);
     } else {
         return fail(SPX_ERR_INVALID, "spx_solve: unknown precision");
     }

@@ -152,8 +152,9 @@ template <class T> int axpby_launch(spx_ctx *ctx, int64_t n, T alpha, const T *x
 // Tile map for merge-path CSR (spmv.cu).
 int ensure_merge_tiles(spx_ctx *ctx, spx_matrix *A, int64_t tile_items, int64_t slack);
 
-// Solver code of the ABI -> method, Jacobi flag, block-Jacobi block size (0: none).
-int parse_solver_code(int code, int *solver, bool *jacobi, int *bs);
+// Solver code of the ABI -> method, Jacobi flag, block-Jacobi block size (0: none),
+// block-Jacobi adaptive storage.
+int parse_solver_code(int code, int *solver, bool *jacobi, int *bs, bool *adaptive);
 
 // Iterative refinement: FP32 inner iterations per outer cycle are capped, so an
 // inner solve that stagnates (FP32 CGS on large systems) hands its correction

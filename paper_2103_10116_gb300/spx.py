@@ -26,6 +26,7 @@ SPX_CG, SPX_BICGSTAB, SPX_GMRES, SPX_CGS = 0, 1, 2, 3
 SPX_PRECOND_JACOBI = 0x100
 SPX_PRECOND_BLOCK_JACOBI = 0x200
 SPX_PRECOND_BLOCK_SHIFT = 16
+SPX_PRECOND_BLOCK_ADAPTIVE = 0x400
 
 
 def SPX_PRECOND_BLOCK(bs: int) -> int:
@@ -323,12 +324,15 @@ def _info(i: spx_solve_info) -> SolveInfo:
 
 
 def _solver_code(solver, precond, block_size=8):
-    """precond: None, "jacobi" or "block_jacobi" (blocks of block_size rows)."""
+    """precond: None, "jacobi", "block_jacobi" (blocks of block_size rows) or
+    "adaptive_block_jacobi" (the same with FP32 storage of well-conditioned blocks)."""
     code = SOLVERS.get(solver, solver)
     if precond == "jacobi":
         code |= SPX_PRECOND_JACOBI
     elif precond == "block_jacobi":
         code |= SPX_PRECOND_BLOCK(block_size)
+    elif precond == "adaptive_block_jacobi":
+        code |= SPX_PRECOND_BLOCK(block_size) | SPX_PRECOND_BLOCK_ADAPTIVE
     elif precond is not None:
         raise ValueError(f"unknown preconditioner {precond!r}")
     return code

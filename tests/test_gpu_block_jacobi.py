@@ -256,3 +256,144 @@ def test_invalid_block_size_is_rejected(spx, ctx, bs):
         assert ei.value.status == spx.SPX_ERR_INVALID
     finally:
         spx.spx_matrix_destroy(A)
+
+
+# ---------------------------------------------------------------- adaptive storage
+def _alternating(solver, bs, nblk=60, seed=7):
+    """Block-diagonal A whose even blocks (kappa ~ 3e3) are stored in FP32 and
+    odd ones (kappa ~ 1e6) in FP64; b takes each FP32 block's leading left
+    singular vector, where rounding the inverse to FP32 shows most (~kappa *
+    2^-24), and random entries elsewhere."""
+    rng = np.random.default_rng(seed)
+    n = bs * nblk + bs // 2
+    a = np.zeros((n, n))
+    b = np.zeros(n)
+    for k, c0 in enumerate(range(0, n, bs)):
+        kk = min(bs, n - c0)
+        q1, _ = np.linalg.qr(rng.standard_normal((kk, kk)))
+        q2 = q1 if solver == "cg" else np.linalg.qr(rng.standard_normal((kk, kk)))[0]
+        fp64 = bool(k % 2) and kk > 1
+        sv = np.geomspace(1.0, 1e-6 if fp64 else 3e-4, kk) if kk > 1 else np.ones(1)
+        a[c0:c0 + kk, c0:c0 + kk] = q1 @ np.diag(sv) @ q2.T
+        b[c0:c0 + kk] = rng.standard_normal(kk) if fp64 else q1[:, 0]
+    return a, b
+
+
+def _block_rel(x, y, bs):
+    return np.array([np.linalg.norm(x[c:c + bs] - y[c:c + bs]) / np.linalg.norm(y[c:c + bs])
+                     for c in range(0, len(y), bs)])
+
+
+@pytest.mark.parametrize("solver", ["cg", "gmres"])
+@pytest.mark.parametrize("bs", [2, 4, 8, 32])
+def test_adaptive_storage_reads_each_block_from_its_precision(spx, ctx, solver, bs):
+    a, b = _alternating(solver, bs)
+    rp, col, val = csr_from_dense(a)
+    n = b.shape[0]
+    _, flags = oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)
+    assert flags.tolist() == [int(k % 2 == 1 and min(bs, n - k * bs) > 1) for k in range(len(flags))]
+    kw = {"m": 5} if solver == "gmres" else {}
+    xo, _ = _oracle_1(solver, rp, col, val, b, "adaptive_block_jacobi", bs, kw)
+    x64, _ = _oracle_1(solver, rp, col, val, b, "block_jacobi", bs, kw)
+    # the FP32 blocks' rounding is visible at this right-hand side
+    f32 = [k for k in range(len(flags)) if not flags[k] and min(bs, n - k * bs) > 1]
+    assert _block_rel(x64, xo, bs)[f32].min() > 5e-8
+    A = _make(spx, ctx, "csr", rp, col, val)
+    try:
+        x = torch.zeros(n, dtype=torch.float64, device=DEV)
+        spx.spx_solve_fixed(ctx, A, _t(b), x, solver, 1, restart=5, precond="adaptive_block_jacobi", block_size=bs)
+        assert _block_rel(x.cpu().numpy(), xo, bs).max() <= 2e-8
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
+def _oracle_1(solver, rp, col, val, b, precond, bs, kw, j=1):
+    return getattr(oracle, solver)(rp, col, val, b, tol=0.0, maxit=j, precond=precond, block_size=bs, **kw)
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs", "gmres"])
+def test_adaptive_storage_fixed_iterations_match_oracle(spx, ctx, solver):
+    bs = 8
+    a, b = _alternating(solver, bs, seed=9)
+    rp, col, val = csr_from_dense(a)
+    kw = {"m": 5} if solver == "gmres" else {}
+    xo, _ = _oracle_1(solver, rp, col, val, b, "adaptive_block_jacobi", bs, kw, j=3)
+    A = _make(spx, ctx, "csr", rp, col, val)
+    try:
+        x = torch.zeros(b.shape[0], dtype=torch.float64, device=DEV)
+        spx.spx_solve_fixed(ctx, A, _t(b), x, solver, 3, restart=5, precond="adaptive_block_jacobi", block_size=bs)
+        assert _block_rel(x.cpu().numpy(), xo, bs).max() <= 1e-6
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs", "gmres"])
+def test_adaptive_solve_matches_oracle(spx, ctx, solver):
+    bs = 8
+    rp, col, val, xs, b = _coupled(solver, bs=bs)
+    _, flags = oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)
+    assert not flags.any()  # well-conditioned blocks: all stored in FP32
+    A = _make(spx, ctx, "csr", rp, col, val)
+    try:
+        x = torch.zeros(b.shape[0], dtype=torch.float64, device=DEV)
+        info = spx.spx_solve(ctx, A, _t(b), x, solver, 1e-10, 20000, restart=30, precond="adaptive_block_jacobi",
+                             block_size=bs)
+        _, oinfo = _oracle(solver, rp, col, val, b, tol=1e-10, maxit=20000, precond="adaptive_block_jacobi",
+                           block_size=bs)
+        assert info.status == spx.SPX_CONVERGED and oinfo.status == oracle.CONVERGED, (info, oinfo)
+        assert _relres(rp, col, val, b, x.cpu().numpy()) <= 1.05e-10
+        assert abs(info.iterations - oinfo.iterations) <= max(4, oinfo.iterations // 10), (info, oinfo)
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
+@pytest.mark.parametrize("solver", ["cg", "gmres"])
+def test_adaptive_with_every_block_fp64_is_block_jacobi_bitwise(spx, ctx, solver):
+    bs = 4
+    rng = np.random.default_rng(3)
+    n = bs * 50
+    a = np.zeros((n, n))
+    for c0 in range(0, n, bs):
+        q, _ = np.linalg.qr(rng.standard_normal((bs, bs)))
+        a[c0:c0 + bs, c0:c0 + bs] = q @ np.diag([1.0, 10.0, 1e3, 1e6]) @ q.T
+    a += np.diag(np.full(n - 1, 0.01), 1) + np.diag(np.full(n - 1, 0.01), -1)
+    rp, col, val = csr_from_dense(a)
+    assert oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)[1].all()
+    b = rng.standard_normal(n)
+    A = _make(spx, ctx, "csr", rp, col, val)
+    try:
+        out = []
+        for pc in ("block_jacobi", "adaptive_block_jacobi"):
+            x = torch.zeros(n, dtype=torch.float64, device=DEV)
+            spx.spx_solve_fixed(ctx, A, _t(b), x, solver, 6, restart=20, precond=pc, block_size=bs)
+            out.append(x.cpu().numpy())
+        assert np.array_equal(out[0], out[1])
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
+@pytest.mark.parametrize("bs", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("solver", ["bicgstab", "gmres"])
+def test_block_inverse_with_row_pivoting_one_step(spx, ctx, solver, bs):
+    """Blocks that are row permutations of diagonally dominant ones: their
+    diagonals hold small or zero entries, so the inversion has to pivot."""
+    rng = np.random.default_rng(50 + bs)
+    n = 30 * bs + 1
+    a = np.zeros((n, n))
+    for c0 in range(0, n, bs):
+        k = min(bs, n - c0)
+        blk = 0.3 * rng.standard_normal((k, k)) + 3.0 * np.eye(k)
+        perm = np.roll(np.arange(k), 1)  # a cyclic shift: every diagonal entry moves off the diagonal
+        a[c0:c0 + k, c0:c0 + k] = blk[perm]
+    rp, col, val = csr_from_dense(a)
+    b = rng.standard_normal(n)
+    A = _make(spx, ctx, "csr", rp, col, val)
+    try:
+        for pc in ("block_jacobi", "adaptive_block_jacobi"):
+            x = torch.zeros(n, dtype=torch.float64, device=DEV)
+            info = spx.spx_solve(ctx, A, _t(b), x, solver, 1e-12, 100, restart=10, precond=pc, block_size=bs)
+            assert info.status == spx.SPX_CONVERGED and info.iterations <= (1 if pc == "block_jacobi" else 3), info
+            want = np.linalg.solve(a, b)
+            assert np.allclose(x.cpu().numpy(), want, rtol=0, atol=1e-11 * np.abs(want).max())
+    finally:
+        spx.spx_matrix_destroy(A)

@@ -285,3 +285,14 @@ def test_adaptive_block_diagonal_converges_in_few_steps(solver):
     lo, hi = (2, 3) if solver == "gmres" else (1, 2)
     assert info.status == oracle.CONVERGED and lo <= info.iterations <= hi, info
     assert np.allclose(x, np.linalg.solve(a, b), rtol=0, atol=1e-11)
+
+
+def test_adaptive_needs_fp32_range():
+    # kappa = 1, but the inverse of 1e-40 * I overflows FP32 (and that of 1e39 * I
+    # is subnormal in FP32): both stay FP64; a moderate scale goes to FP32
+    bs = 2
+    d = np.array([1e-40, 1e-40, 1e39, 1e39, 3.0, 3.0])
+    rp, col, val = csr_from_dense(np.diag(d))
+    inv, flags = oracle.block_jacobi_inv(rp, col, val, bs, adaptive=True)
+    assert flags.tolist() == [1, 1, 0]
+    assert inv[0][0, 0] == 1e40 and inv[1][0, 0] == 1.0 / 1e39
