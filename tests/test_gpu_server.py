@@ -128,3 +128,35 @@ def test_invalid_operator_in_batch_is_rejected_alone(spx, ctx):
             assert srv.results[i]["error"] == 0 and srv.results[i]["info"].status == spx.SPX_CONVERGED
     finally:
         srv.close()
+
+
+def test_preconditioned_requests_alone_equal_mix(spx, ctx):
+    """Jacobi and block-Jacobi requests (a slot each: the batch lanes do not
+    precondition) converge and give the same result alone and in a mix."""
+    from paper_2103_10116_gb300.serving import Server
+    rp, col, val = synth.laplace3d_7pt(14)
+    b = synth.uniform_vector(14**3, seed=7)
+    rp2, col2, val2 = synth.diagdom_random(6000, seed=8)
+    b2 = synth.uniform_vector(6000, seed=9)
+    codes = [(rp, col, val, b, spx.SPX_CG | spx.SPX_PRECOND_JACOBI),
+             (rp, col, val, b, spx.SPX_CG | spx.SPX_PRECOND_BLOCK(8)),
+             (rp2, col2, val2, b2, spx.SPX_BICGSTAB | spx.SPX_PRECOND_BLOCK(4) | spx.SPX_PRECOND_BLOCK_ADAPTIVE),
+             (rp2, col2, val2, b2, spx.SPX_GMRES | spx.SPX_PRECOND_BLOCK(16))]
+    srv = Server(ctx, 0, max_slots=4)
+    try:
+        alone = []
+        for rpx, colx, valx, bx, code in codes:
+            rid = srv.submit(rpx, colx, valx, bx, solver=code, tol=1e-8)
+            srv.drain()
+            alone.append(srv.results[rid])
+        ids = [srv.submit(c[0], c[1], c[2], c[3], solver=c[4], tol=1e-8) for c in codes * 2]
+        srv.drain()
+        for k, (rpx, colx, valx, bx, code) in enumerate(codes):
+            ra = alone[k]
+            assert ra["error"] == 0 and ra["info"].status == spx.SPX_CONVERGED, ra
+            r = bx - oracle.spmv_csr(rpx, colx, valx, ra["x"])
+            assert np.linalg.norm(r) / np.linalg.norm(bx) <= 1.05e-8
+            for rid in (ids[k], ids[k + len(codes)]):
+                assert np.array_equal(srv.results[rid]["x"], ra["x"])
+    finally:
+        srv.close()
