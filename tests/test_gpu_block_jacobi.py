@@ -397,3 +397,36 @@ def test_block_inverse_with_row_pivoting_one_step(spx, ctx, solver, bs):
             assert np.allclose(x.cpu().numpy(), want, rtol=0, atol=1e-11 * np.abs(want).max())
     finally:
         spx.spx_matrix_destroy(A)
+
+
+@pytest.mark.parametrize("n,bs", [(1, 1), (1, 8), (3, 32), (31, 16), (33, 32), (5, 4)])
+@pytest.mark.parametrize("precond", ["block_jacobi", "adaptive_block_jacobi"])
+def test_tiny_systems(spx, ctx, n, bs, precond):
+    """Fewer rows than one block, one row, and ragged tails inside a single warp."""
+    rng = np.random.default_rng(n * 100 + bs)
+    a = rng.standard_normal((n, n)) + 2 * n * np.eye(n)
+    rp, col, val = csr_from_dense(a)
+    b = rng.standard_normal(n)
+    A = _make(spx, ctx, "csr", rp, col, val)
+    try:
+        for solver in ("bicgstab", "gmres"):
+            x = torch.zeros(n, dtype=torch.float64, device=DEV)
+            info = spx.spx_solve(ctx, A, _t(b), x, solver, 1e-12, 100, restart=10, precond=precond, block_size=bs)
+            assert info.status == spx.SPX_CONVERGED, (solver, info)
+            want = np.linalg.solve(a, b)
+            assert np.allclose(x.cpu().numpy(), want, rtol=0, atol=1e-11 * np.abs(want).max())
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
+def test_empty_system_with_block_jacobi(spx, ctx):
+    rp = np.zeros(1, dtype=np.int32)
+    A = spx.spx_matrix_create(ctx, "csr", _t(rp), torch.zeros(0, dtype=torch.int32, device=DEV),
+                              torch.zeros(0, dtype=torch.float64, device=DEV))
+    try:
+        x = torch.zeros(0, dtype=torch.float64, device=DEV)
+        info = spx.spx_solve(ctx, A, torch.zeros(0, dtype=torch.float64, device=DEV), x, "cg", 1e-10, 10,
+                             precond="block_jacobi", block_size=8)
+        assert info.status == spx.SPX_CONVERGED and info.iterations == 0
+    finally:
+        spx.spx_matrix_destroy(A)
