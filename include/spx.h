@@ -200,6 +200,17 @@ int spx_matrix_export(spx_ctx *ctx, const spx_matrix *A, int part, void *dst, si
  * Errors: SPX_ERR_UNSUPPORTED if the kernel does not apply to A's format. */
 int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param);
 
+/* Autotune A's SpMV kernel: time every kernel variant spx_matrix_set_kernel
+ * accepts for A's format and dtype (the automatic choice included) with CUDA
+ * events on the context stream, `reps` back-to-back products y = A x each after
+ * one warm-up (x = 0, in the handle's staging buffers), and keep the fastest.
+ * Variants that do not fit A (SPX_ERR_TOO_LARGE, SPX_ERR_UNSUPPORTED) are
+ * skipped.  Outputs (may be NULL): the chosen kernel, its parameter and its
+ * time per product in microseconds.  Synchronous.  reps must be in [1, 1000];
+ * on any other error A keeps its previous kernel.  The Python binding adds a
+ * JSON cache of choices keyed by GPU name and the matrix's shape statistics. */
+int spx_matrix_tune(spx_ctx *ctx, spx_matrix *A, int reps, int *kernel, int *param, float *best_us);
+
 /* ------------------------------------------------------------------ SpMV */
 
 /* y = A x (Section 5), x[ncols] and y[nrows] of A's dtype, device pointers,

@@ -684,6 +684,104 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     return SPX_OK;
 }
 
+// ------------------------------------------------------------------ kernel autotuning
+namespace {
+// Kernel variants worth timing for a matrix (those spx_matrix_set_kernel accepts).
+std::vector<std::pair<int, int>> tune_candidates(const spx_matrix *A)
+{
+    std::vector<std::pair<int, int>> c;
+    switch (A->format) {
+    case SPX_CSR:
+        c = {{SPX_KERNEL_CSR_ROWS, 1}, {SPX_KERNEL_CSR_ROWS, 2}, {SPX_KERNEL_CSR_MERGE, 4},
+             {SPX_KERNEL_CSR_MERGE, 8}, {SPX_KERNEL_CSR_MERGE, 16}, {SPX_KERNEL_CSR_SPLIT, 8},
+             {SPX_KERNEL_CSR_SPLIT, 16}};
+        for (int sw = 1; sw <= 32; sw *= 2) c.push_back({SPX_KERNEL_CSR_VECTOR, sw});
+        break;
+    case SPX_ELL:
+        c = {{SPX_KERNEL_ELL, 1}, {SPX_KERNEL_ELL, 2}};
+        if (A->dtype == SPX_F32) c.push_back({SPX_KERNEL_ELL, 4});
+        break;
+    case SPX_COO:
+        c = {{SPX_KERNEL_COO, 1}, {SPX_KERNEL_COO, 8}, {SPX_KERNEL_COO, 16}, {SPX_KERNEL_COO, 104},
+             {SPX_KERNEL_COO, 108}, {SPX_KERNEL_COO, 116}};
+        break;
+    default:  // HYB: its ELL part's rows per thread, or its COO part's kernel
+        c = {{SPX_KERNEL_ELL, 1}, {SPX_KERNEL_ELL, 2}, {SPX_KERNEL_COO, 8}, {SPX_KERNEL_COO, 16},
+             {SPX_KERNEL_COO, 104}, {SPX_KERNEL_COO, 116}};
+        if (A->dtype == SPX_F32) c.push_back({SPX_KERNEL_ELL, 4});
+        break;
+    }
+    c.insert(c.begin(), {SPX_KERNEL_AUTO, 0});
+    return c;
+}
+
+template <class T> int time_spmv(spx_ctx *ctx, spx_matrix *A, int reps, cudaEvent_t e0, cudaEvent_t e1, float *us)
+{
+    const T *x = A->stage_x.as<T>();
+    T *y = A->stage_y.as<T>();
+    Epi<T> e;
+    e.y = y;
+    SPX_TRY(spmv_launch<T>(ctx, A, x, e, false));  // warm-up; builds the variant's tile maps
+    SPX_CUDA(cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < reps; ++r) SPX_TRY(spmv_launch<T>(ctx, A, x, e, false));
+    SPX_CUDA(cudaEventRecord(e1, ctx->stream));
+    SPX_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    SPX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    *us = ms * 1000.f / (float)reps;
+    return SPX_OK;
+}
+}  // namespace
+
+extern "C" int spx_matrix_tune(spx_ctx *ctx, spx_matrix *A, int reps, int *kernel, int *param, float *best_us)
+{
+    if (!ctx || !A) return fail(SPX_ERR_INVALID, "spx_matrix_tune: ctx or A is NULL");
+    if (reps < 1 || reps > 1000) return fail(SPX_ERR_INVALID, "spx_matrix_tune: reps must be in [1, 1000]");
+    DeviceGuard g(ctx->device);
+    const size_t V = A->dtype == SPX_F64 ? 8 : 4;
+    if (!A->stage_x.p) SPX_TRY(dbuf_alloc(ctx, A->stage_x, (size_t)(A->ncols > 0 ? A->ncols : 1) * V));
+    if (!A->stage_y.p) SPX_TRY(dbuf_alloc(ctx, A->stage_y, (size_t)(A->n > 0 ? A->n : 1) * V));
+    if (A->ncols) SPX_CUDA(cudaMemsetAsync(A->stage_x.p, 0, (size_t)A->ncols * V, ctx->stream));
+    const int k0 = A->kernel, p0 = A->kparam;
+    cudaEvent_t e0, e1;
+    SPX_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(SPX_ERR_CUDA, "cudaEventCreate");
+    }
+    int bk = k0, bp = p0, st = SPX_OK;
+    float best = -1.f;
+    for (const auto &kp : tune_candidates(A)) {
+        if (spx_matrix_set_kernel(A, kp.first, kp.second) != SPX_OK) continue;
+        float us = 0.f;
+        const int r = A->dtype == SPX_F64 ? time_spmv<double>(ctx, A, reps, e0, e1, &us)
+                                          : time_spmv<float>(ctx, A, reps, e0, e1, &us);
+        if (r == SPX_ERR_TOO_LARGE || r == SPX_ERR_UNSUPPORTED) continue;  // variant does not fit this matrix
+        if (r != SPX_OK) {
+            st = r;
+            break;
+        }
+        if (best < 0.f || us < best) {
+            best = us;
+            bk = kp.first;
+            bp = kp.second;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPX_OK || best < 0.f) {
+        A->kernel = k0;
+        A->kparam = p0;
+        return st != SPX_OK ? st : fail(SPX_ERR_UNSUPPORTED, "spx_matrix_tune: no kernel variant ran");
+    }
+    A->kernel = bk;
+    A->kparam = bp;
+    if (kernel) *kernel = bk;
+    if (param) *param = bp;
+    if (best_us) *best_us = best;
+    return SPX_OK;
+}
+
 // ------------------------------------------------------------------ SpMV entry points
 namespace {
 template <class T>

@@ -47,21 +47,73 @@ __device__ __forceinline__ void final_write(const Epi<T> &e, int64_t r, T t, T &
     if (e.want_yy) d1 = fma(v, v, d1);
 }
 
-// Row output of the nnz-split kernels.  MODE 0: the general epilogue; 1: plain
-// store y = t; 2: y += alpha t (the COO part of HYB); 3: y += t.  Fixing the
-// mode at compile time keeps the unused epilogue terms out of the row-emission
-// code: predicated-off FP64 instructions still take FP64 issue slots, and the
-// FP64 pipe is what bounds these kernels.
+// Row output.  MODE 0: the general epilogue; 1: plain store y = t; 2: y +=
+// alpha t (the COO part of HYB); 3: y += t.  The row-block kernels also take
+// the Krylov solvers' epilogues as modes of their own: 4: y = t with w.y (CG's
+// q = A p with p.q, BiCGSTAB's and CGS's v = A p with r^.v); 5: the same and
+// y.y (BiCGSTAB's t = A s with t.s, t.t); 6: y = t with y.y (GMRES's A v);
+// 7: y = z - t with y.y (the residual b - A x).  Fixing the mode at compile
+// time keeps the unused epilogue terms out of the row-emission code:
+// predicated-off FP64 instructions still take FP64 issue slots, and the FP64
+// pipe is what bounds these kernels.  Every mode rounds as MODE 0 does.
 template <int MODE, class T>
 __device__ __forceinline__ void out_row(const Epi<T> &e, int64_t r, T t, T &d0, T &d1)
 {
     if constexpr (MODE == 0) final_write(e, r, t, d0, d1);
     else if constexpr (MODE == 1) e.y[r] = t;
+    else if constexpr (MODE >= 4) {
+        const T v = MODE == 7 ? fma(T(1), e.z[r], -t) : t;
+        e.y[r] = v;
+        if constexpr (MODE == 4 || MODE == 5) d0 = fma(e.w[r], v, d0);
+        if constexpr (MODE >= 5) d1 = fma(v, v, d1);
+    }
     // add modes: one add per row into a y no other thread touches in this launch,
     // so a fire-and-forget atomic gives the same bits as load + store without
     // stalling the emitting lane on the load
     else if constexpr (MODE == 2) atomicAdd(e.y + r, e.alpha * t);
     else atomicAdd(e.y + r, t);
+}
+
+// The general epilogue's row operands z[r] and w[r], loaded when the row index
+// is known and before the row's sum, so that their latency overlaps the tile's
+// copy and gathers instead of following the sum (the row-block kernels end each
+// tile with a block barrier, so a load issued after the sum stalls the block).
+// out_row_pre is final_write with those operands already in registers.
+template <class T> struct EpiRow {
+    T z, w;
+};
+
+template <int MODE, class T> __device__ __forceinline__ EpiRow<T> epi_row_load(const Epi<T> &e, int64_t r)
+{
+    EpiRow<T> o{T(0), T(0)};
+    if constexpr (MODE == 0) {
+        if (e.z) o.z = e.z[r];
+        if (e.w) o.w = e.w[r];
+    } else if constexpr (MODE == 4 || MODE == 5) {
+        o.w = e.w[r];
+    } else if constexpr (MODE == 7) {
+        o.z = e.z[r];
+    }
+    return o;
+}
+
+template <int MODE, class T>
+__device__ __forceinline__ void out_row_pre(const Epi<T> &e, int64_t r, T t, const EpiRow<T> &pre, T &d0, T &d1)
+{
+    if constexpr (MODE == 0) {
+        if (!is_one(e.alpha)) t *= e.alpha;
+        if (e.z) t = fma(e.beta, pre.z, t);
+        e.y[r] = t;
+        if (e.w) d0 = fma(pre.w, t, d0);
+        if (e.want_yy) d1 = fma(t, t, d1);
+    } else if constexpr (MODE >= 4) {
+        const T v = MODE == 7 ? fma(T(1), pre.z, -t) : t;
+        e.y[r] = v;
+        if constexpr (MODE == 4 || MODE == 5) d0 = fma(pre.w, v, d0);
+        if constexpr (MODE >= 5) d1 = fma(v, v, d1);
+    } else {
+        out_row<MODE>(e, r, t, d0, d1);
+    }
 }
 
 // Reduce (d0, d1) over the grid; the last block stores dots and runs the
@@ -562,6 +614,8 @@ __global__ void __launch_bounds__(ROWS)
             fence_proxy_async();
             issue_next(0);  // this tile
         }
+        const int rq = t * ROWS + tid;  // this thread's row of the tile
+        const EpiRow<T> pre = rq < n ? epi_row_load<MODE>(e, rq) : EpiRow<T>{T(0), T(0)};
         const uint32_t parity = STAGES == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
         if (!mbar_wait(&bar[stage], parity, err)) {
             ok = false;
@@ -610,7 +664,7 @@ __global__ void __launch_bounds__(ROWS)
                 }
                 if (rem & 1) sum = fma(v[0], xv[0], sum);
             }
-            out_row<MODE>(e, r0 + q, sum, d0, d1);
+            out_row_pre<MODE>(e, r0 + q, sum, pre, d0, d1);
         }
         __syncthreads();  // the stage is refilled by a later copy
     }
@@ -618,7 +672,7 @@ __global__ void __launch_bounds__(ROWS)
         // do not leave a bulk copy in flight into this block's shared memory
         mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), err, 200000000LL);
     }
-    if constexpr (MODE == 0)
+    if constexpr (MODE == 0 || MODE >= 4)
         if (e.dots) finish_dots<T, ROWS>(d0, d1, e, partials, ticket);
 }
 
@@ -703,6 +757,8 @@ __global__ void __launch_bounds__(ROWS)
         }
         s_first[tid] = 0;
         s_end[tid] = 0;
+        const int rq = t * ROWS + tid;  // this thread's row of the tile
+        const EpiRow<T> pre = rq < n ? epi_row_load<MODE>(e, rq) : EpiRow<T>{T(0), T(0)};
         if (!mbar_wait(&bar[stage], (uint32_t)((it >> 1) & 1), err)) {
             ok = false;
             break;
@@ -758,12 +814,12 @@ __global__ void __launch_bounds__(ROWS)
                 }
                 if (rem & 1) sum = fma(v[0], xv[0], sum);
             }
-            out_row<MODE>(e, r0 + q, sum, d0, d1);
+            out_row_pre<MODE>(e, r0 + q, sum, pre, d0, d1);
         }
         __syncthreads();  // the stage and the row marks are reused
     }
     if (!ok && pending_prefetch) mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), err, 200000000LL);
-    if constexpr (MODE == 0)
+    if constexpr (MODE == 0 || MODE >= 4)
         if (e.dots) finish_dots<T, ROWS>(d0, d1, e, partials, ticket);
 }
 
@@ -1630,6 +1686,20 @@ template <class T> bool epi_is_plain(const Epi<T> &e)
     return e.alpha == T(1) && !e.z && !e.w && !e.want_yy && !e.dots;
 }
 
+// Compile-time epilogue of the row-block kernels (see out_row): 1 plain, 4-7
+// the solvers' forms, 0 anything else.
+template <class T> int epi_mode(const Epi<T> &e)
+{
+    if (epi_is_plain(e)) return 1;
+    if (!e.dots) return 0;
+    if (e.alpha == T(1) && !e.z) {
+        if (e.w) return e.want_yy ? 5 : 4;
+        if (e.want_yy) return 6;
+    }
+    if (e.alpha == T(-1) && e.beta == T(1) && e.z && !e.w && e.want_yy) return 7;
+    return 0;
+}
+
 constexpr int kRowsTile = 128;
 constexpr int kRowsStages = 2;  // default shared-memory stages per block of the row-block kernel
 
@@ -1695,9 +1765,20 @@ int launch_rows_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const E
 template <class T>
 int launch_rows(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e, int stages)
 {
-    const bool plain = epi_is_plain(e);
-    if (stages == 1) return plain ? launch_rows_m<T, 1, 1>(ctx, A, val, x, e) : launch_rows_m<T, 1, 0>(ctx, A, val, x, e);
-    return plain ? launch_rows_m<T, 2, 1>(ctx, A, val, x, e) : launch_rows_m<T, 2, 0>(ctx, A, val, x, e);
+#define SPX_ROWS_MODES(ST_)                                                   \
+    switch (epi_mode(e)) {                                                    \
+    case 1: return launch_rows_m<T, ST_, 1>(ctx, A, val, x, e);               \
+    case 4: return launch_rows_m<T, ST_, 4>(ctx, A, val, x, e);               \
+    case 5: return launch_rows_m<T, ST_, 5>(ctx, A, val, x, e);               \
+    case 6: return launch_rows_m<T, ST_, 6>(ctx, A, val, x, e);               \
+    case 7: return launch_rows_m<T, ST_, 7>(ctx, A, val, x, e);               \
+    default: return launch_rows_m<T, ST_, 0>(ctx, A, val, x, e);              \
+    }
+    if (stages == 1) {
+        SPX_ROWS_MODES(1)
+    }
+    SPX_ROWS_MODES(2)
+#undef SPX_ROWS_MODES
 }
 
 int ensure_coo_rowtiles(spx_ctx *ctx, spx_matrix *A)
@@ -1757,7 +1838,14 @@ int launch_coo_rows_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, co
 
 template <class T> int launch_coo_rows(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e)
 {
-    return epi_is_plain(e) ? launch_coo_rows_m<T, 1>(ctx, A, cval, x, e) : launch_coo_rows_m<T, 0>(ctx, A, cval, x, e);
+    switch (epi_mode(e)) {
+    case 1: return launch_coo_rows_m<T, 1>(ctx, A, cval, x, e);
+    case 4: return launch_coo_rows_m<T, 4>(ctx, A, cval, x, e);
+    case 5: return launch_coo_rows_m<T, 5>(ctx, A, cval, x, e);
+    case 6: return launch_coo_rows_m<T, 6>(ctx, A, cval, x, e);
+    case 7: return launch_coo_rows_m<T, 7>(ctx, A, cval, x, e);
+    default: return launch_coo_rows_m<T, 0>(ctx, A, cval, x, e);
+    }
 }
 
 template <class T, int IPT, int MODE>

@@ -92,6 +92,7 @@ SIGNATURES = {
     "spx_matrix_get_info": (_I, [_P, C.POINTER(spx_matrix_info)]),
     "spx_matrix_export": (_I, [_P, _P, _I, _P, _SZ, C.POINTER(C.c_size_t)]),
     "spx_matrix_set_kernel": (_I, [_P, _I, _I]),
+    "spx_matrix_tune": (_I, [_P, _P, _I, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "spx_spmv": (_I, [_P, _P, _P, _P]),
     "spx_spmv_axpby": (_I, [_P, _P, _D, _P, _D, _P]),
     "spx_spmv_host": (_I, [_P, _P, _P, _P]),
@@ -264,6 +265,61 @@ def spx_matrix_export(ctx: int, A: int, part: int, device: int = 0) -> torch.Ten
 
 def spx_matrix_set_kernel(A: int, kernel: int, param: int = 0):
     _check(load().spx_matrix_set_kernel(A, kernel, param))
+
+
+def spx_matrix_tune(ctx: int, A: int, reps: int = 10) -> tuple:
+    """Time every SpMV kernel variant for A and keep the fastest; returns (kernel, param, us per product)."""
+    k, p, us = C.c_int(), C.c_int(), C.c_float()
+    _check(load().spx_matrix_tune(ctx, A, int(reps), C.byref(k), C.byref(p), C.byref(us)))
+    return k.value, p.value, us.value
+
+
+def tune_key(A: int, device_name: str) -> str:
+    """Cache key of an autotuned choice: the GPU and the matrix's format, dtype and shape statistics
+    (sizes to two significant digits, row lengths to the nearest power of two)."""
+    import math
+    i = spx_matrix_get_info(A)
+
+    def sig(v):
+        v = int(v)
+        return 0 if v <= 0 else int(float(f"{v:.2g}"))
+
+    def p2(v):
+        return 0 if v <= 0 else 1 << int(math.ceil(math.log2(max(1.0, float(v)))))
+    return (f"{device_name}|fmt{i['format']}|dt{i['dtype']}|n{sig(i['nrows'])}|nnz{sig(i['nnz'])}"
+            f"|max{p2(i['max_row_len'])}|mean{p2(i['mean_row_len'])}|ell{i['ell_width']}")
+
+
+def tune_cached(ctx: int, A: int, cache_path: str | None = None, reps: int = 10, device: int = 0,
+                device_name: str | None = None, tuner=None) -> tuple:
+    """Autotune with a JSON cache (default: $SPX_TUNE_CACHE or ~/.cache/spx/tune.json): a matrix whose key
+    (tune_key) is in the cache gets the stored kernel without timing; otherwise spx_matrix_tune runs and
+    the choice is stored.  Returns (kernel, param, us or None when it came from the cache).  `tuner`
+    replaces spx_matrix_tune (same signature), e.g. to test the cache without a GPU."""
+    import json
+    import os
+    path = cache_path or os.environ.get("SPX_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "spx",
+                                                                        "tune.json")
+    key = tune_key(A, device_name if device_name is not None else torch.cuda.get_device_name(device))
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        k, p = cache[key]["kernel"], cache[key]["param"]
+        spx_matrix_set_kernel(A, k, p)
+        return k, p, None
+    k, p, us = (tuner or spx_matrix_tune)(ctx, A, reps)
+    cache[key] = {"kernel": k, "param": p, "us": us}
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return k, p, us
 
 
 # ------------------------------------------------------------------ SpMV / BLAS-1

@@ -339,3 +339,46 @@ def test_gather_probe_runs_and_checks_arguments(spx, ctx):
         assert float(out[0]) == 0.0
     with pytest.raises((spx.SpxError, TypeError)):  # integer x: rejected before or by the library
         spx.spx_probe_gather(ctx, col, torch.zeros(n, dtype=torch.int32, device=DEV), out)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("mname,fmt", [("st27_23", "csr"), ("powerlaw_60k", "csr"), ("longrow", "csr"),
+                                       ("st27_23", "ell"), ("powerlaw_60k", "coo"), ("powerlaw_60k", "hyb")])
+def test_tune_keeps_a_correct_kernel(spx, ctx, mname, fmt, dtype, tmp_path):
+    """The autotuner times every variant (skipping those that do not fit, e.g.
+    the row-block kernels on the long-row matrix), keeps the fastest, and the
+    kept kernel computes the product correctly; the JSON cache replays it."""
+    rp, col, val, ncols, x = _mat(mname)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    val_r, x_r = (val.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64)) \
+        if dtype == "f32" else (val, x)
+    A = _make(spx, ctx, fmt, rp, col, val, ncols, tdt)
+    try:
+        k, p, us = spx.spx_matrix_tune(ctx, A, reps=3)
+        info = spx.spx_matrix_get_info(A)
+        assert (info["kernel"], info["kernel_param"]) == (k, p) and us > 0
+        n = rp.shape[0] - 1
+        y = torch.full((n,), float("nan"), dtype=tdt, device=DEV)
+        spx.spx_spmv(ctx, A, torch.from_numpy(x).to(DEV).to(tdt), y)
+        torch.cuda.synchronize()
+        assert_spmv_close(y.double().cpu().numpy(), oracle.spmv_csr(rp, col, val_r, x_r),
+                          oracle.spmv_absbound(rp, col, val_r, x_r), TOL[dtype])
+        path = str(tmp_path / "tune.json")
+        k1, p1, us1 = spx.tune_cached(ctx, A, path, reps=3)
+        spx.spx_matrix_set_kernel(A, spx.SPX_KERNEL_AUTO, 0)
+        assert spx.tune_cached(ctx, A, path) == (k1, p1, None) and us1 is not None
+        info = spx.spx_matrix_get_info(A)
+        assert (info["kernel"], info["kernel_param"]) == (k1, p1)
+    finally:
+        spx.spx_matrix_destroy(A)
+
+
+def test_tune_rejects_bad_reps(spx, ctx):
+    rp, col, val, ncols, x = _mat("lap2d_64")
+    A = _make(spx, ctx, "csr", rp, col, val, ncols, torch.float64)
+    try:
+        with pytest.raises(spx.SpxError) as ei:
+            spx.spx_matrix_tune(ctx, A, reps=0)
+        assert ei.value.status == spx.SPX_ERR_INVALID
+    finally:
+        spx.spx_matrix_destroy(A)
