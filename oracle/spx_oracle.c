@@ -12,9 +12,13 @@
  *   - the storage conversions CSR -> COO, ELL, HYB as plain byte copies;
  *   - textbook CG, BiCGSTAB, CGS and restarted GMRES(m) with modified
  *     Gram-Schmidt and Givens rotations (the Krylov methods Section 5 names, in
- *     the form of the textbooks it cites);
+ *     the form of the textbooks it cites), each also with Jacobi or
+ *     block-Jacobi preconditioning (preconditioned CG; right preconditioning
+ *     for the others; block inverses by Gauss-Jordan with partial pivoting,
+ *     optionally stored in FP32 for well-conditioned blocks);
  *   - iterative refinement with an FP32 inner Krylov solve and FP64 outer
- *     residual and update.
+ *     residual and update (its iterate path is parity unpinned: only the end
+ *     state, the true FP64 residual, is checked).
  *
  * Build flags must keep IEEE semantics: -O2 -ffp-contract=off, no fast-math,
  * so that x86-64 and aarch64 hosts produce identical bits.
