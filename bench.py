@@ -285,6 +285,7 @@ def run_gpu(args):
     peak, peak_src = _peaks()
     secondary = {}
     if not args.no_solve:
+        secondary["small_case"] = small_case_secondary(spx, ctx, stream, dev)
         secondary["solves"] = solve_secondary(spx, ctx, stream, dev, peak)
     if not args.no_solve:
         secondary["fixed_iterations"] = fixed_iter_secondary(spx, ctx, stream, dev)
@@ -370,6 +371,44 @@ def solve_bytes_per_iter(solver: str, fmt_bytes: int, n: int, m: int = 30) -> in
         return 2 * fmt_bytes + V * n + 6 * V * n + 4 * V * n + 5 * V * n
     jbar = (m + 1) / 2.0
     return int(fmt_bytes + 2 * (jbar + 1) * V * n + 2 * V * n + 2 * V * n)
+
+
+def small_case_secondary(spx, ctx, stream, dev, reps: int = 50):
+    """The small configuration (latency-bound, reported in microseconds): the 2D
+    5-point Laplacian on a 64 x 64 grid (n = 4096, 20,224 nonzeros), FP64 CSR,
+    b = A x* with x* ~ U[-1, 1]: one SpMV (median of `reps` CUDA-event timings)
+    and unpreconditioned CG to relative residual 1e-10."""
+    import torch
+    from paper_2103_10116_gb300 import synth
+    rp, col, val = synth.laplace2d_5pt(64)
+    n = rp.shape[0] - 1
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    out = {"n": n, "nnz": int(col.shape[0])}
+    with torch.cuda.stream(stream):
+        A = spx.spx_matrix_create(ctx, "csr", t(rp), t(col), t(val))
+        xs = t(np.random.default_rng(0).uniform(-1, 1, n))
+        b = torch.empty_like(xs)
+        for _ in range(3):
+            spx.spx_spmv(ctx, A, xs, b)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            spx.spx_spmv(ctx, A, xs, b)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        out["spmv_us"] = round(statistics.median(ts), 2)
+        x = torch.zeros_like(xs)
+        spx.spx_solve(ctx, A, b, x, "cg", 1e-10, 10000)  # warm-up
+        x.zero_()
+        si = spx.spx_solve(ctx, A, b, x, "cg", 1e-10, 10000)
+        out["cg"] = {"solve_ms": round(si.time_ms, 3), "iterations": si.iterations, "status": si.status_name,
+                     "relres_true": si.relres_true,
+                     "err_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))}
+        spx.spx_matrix_destroy(A)
+    return out
 
 
 def solve_secondary(spx, ctx, stream, dev, peak, fmt="csr"):

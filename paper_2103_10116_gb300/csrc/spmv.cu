@@ -48,8 +48,9 @@ __device__ __forceinline__ void final_write(const Epi<T> &e, int64_t r, T t, T &
 }
 
 // Row output.  MODE 0: the general epilogue; 1: plain store y = t; 2: y +=
-// alpha t (the COO part of HYB); 3: y += t.  The row-block kernels also take
-// the Krylov solvers' epilogues as modes of their own: 4: y = t with w.y (CG's
+// alpha t (the COO part of HYB); 3: y += t.  The row-block, nnz-split and ELL
+// kernels also take the Krylov solvers' epilogues as modes of their own: 4:
+// y = t with w.y (CG's
 // q = A p with p.q, BiCGSTAB's and CGS's v = A p with r^.v); 5: the same and
 // y.y (BiCGSTAB's t = A s with t.s, t.t); 6: y = t with y.y (GMRES's A v);
 // 7: y = z - t with y.y (the residual b - A x).  Fixing the mode at compile
@@ -1031,7 +1032,7 @@ __global__ void __launch_bounds__(256)
         }
         out_row<MODE>(e, first_row, tot, d0, d1);
     }
-    if constexpr (MODE == 0)
+    if constexpr (MODE == 0 || MODE >= 4)
         if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
 #undef SPX_SPLIT_EMIT
 }
@@ -1049,7 +1050,7 @@ __global__ void __launch_bounds__(256)
                 const T *__restrict__ cval, const T *__restrict__ x, int nchunks, int *carry_row_w,
                 T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e)
 {
-    constexpr bool add_mode = MODE >= 2;  // y += ..., no rows without entries written
+    constexpr bool add_mode = MODE == 2 || MODE == 3;  // y += ..., no rows without entries written
     constexpr int CH = IPT == 8 ? 4 : 8;  // gathers issued together (4: fewer registers, 8-wide granules)
     constexpr int NW = 256 / 32;
     constexpr int CHUNK = 32 * IPT, PADDED = CHUNK + 32;  // element k sits at k + k / IPT
@@ -1201,7 +1202,7 @@ __global__ void __launch_bounds__(256)
         }
         SPX_COO_OUT(first_row, tot);
     }
-    if constexpr (MODE == 0)
+    if constexpr (MODE == 0 || MODE >= 4)
         if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
 #undef SPX_COO_OUT
 }
@@ -1293,7 +1294,7 @@ __global__ void __launch_bounds__(BLOCK)
         for (int q = 0; q < R; ++q)
             if (i + q < n) out_row<MODE>(e, i + q, s[q], d0, d1);
     }
-    if constexpr (MODE == 0)
+    if constexpr (MODE == 0 || MODE >= 4)
         if (e.dots) finish_dots<T, BLOCK>(d0, d1, e, partials, ticket);
 }
 
@@ -1686,8 +1687,8 @@ template <class T> bool epi_is_plain(const Epi<T> &e)
     return e.alpha == T(1) && !e.z && !e.w && !e.want_yy && !e.dots;
 }
 
-// Compile-time epilogue of the row-block kernels (see out_row): 1 plain, 4-7
-// the solvers' forms, 0 anything else.
+// Compile-time epilogue (see out_row): 1 plain, 4-7 the solvers' forms, 0
+// anything else.
 template <class T> int epi_mode(const Epi<T> &e)
 {
     if (epi_is_plain(e)) return 1;
@@ -1875,8 +1876,14 @@ int launch_split_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const 
 template <class T, int IPT>
 int launch_split(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
 {
-    return epi_is_plain(e) ? launch_split_m<T, IPT, 1>(ctx, A, val, x, e)
-                           : launch_split_m<T, IPT, 0>(ctx, A, val, x, e);
+    switch (epi_mode(e)) {
+    case 1: return launch_split_m<T, IPT, 1>(ctx, A, val, x, e);
+    case 4: return launch_split_m<T, IPT, 4>(ctx, A, val, x, e);
+    case 5: return launch_split_m<T, IPT, 5>(ctx, A, val, x, e);
+    case 6: return launch_split_m<T, IPT, 6>(ctx, A, val, x, e);
+    case 7: return launch_split_m<T, IPT, 7>(ctx, A, val, x, e);
+    default: return launch_split_m<T, IPT, 0>(ctx, A, val, x, e);
+    }
 }
 
 template <class T, int IPT, int MODE>
@@ -1908,8 +1915,14 @@ int launch_coo_split(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, con
 {
     if (add) return e.alpha == T(1) ? launch_coo_split_m<T, IPT, 3>(ctx, A, cval, x, e)
                                     : launch_coo_split_m<T, IPT, 2>(ctx, A, cval, x, e);
-    return epi_is_plain(e) ? launch_coo_split_m<T, IPT, 1>(ctx, A, cval, x, e)
-                           : launch_coo_split_m<T, IPT, 0>(ctx, A, cval, x, e);
+    switch (epi_mode(e)) {
+    case 1: return launch_coo_split_m<T, IPT, 1>(ctx, A, cval, x, e);
+    case 4: return launch_coo_split_m<T, IPT, 4>(ctx, A, cval, x, e);
+    case 5: return launch_coo_split_m<T, IPT, 5>(ctx, A, cval, x, e);
+    case 6: return launch_coo_split_m<T, IPT, 6>(ctx, A, cval, x, e);
+    case 7: return launch_coo_split_m<T, IPT, 7>(ctx, A, cval, x, e);
+    default: return launch_coo_split_m<T, IPT, 0>(ctx, A, cval, x, e);
+    }
 }
 
 template <class T, int SW>
@@ -1944,8 +1957,14 @@ int launch_ell_m(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const E
 template <class T, int R>
 int launch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const Epi<T> &e)
 {
-    if (sizeof(T) == 4 && epi_is_plain(e)) return launch_ell_m<T, R, 1>(ctx, A, eval, x, e);
-    return launch_ell_m<T, R, 0>(ctx, A, eval, x, e);
+    switch (epi_mode(e)) {
+    case 1: return sizeof(T) == 4 ? launch_ell_m<T, R, 1>(ctx, A, eval, x, e) : launch_ell_m<T, R, 0>(ctx, A, eval, x, e);
+    case 4: return launch_ell_m<T, R, 4>(ctx, A, eval, x, e);
+    case 5: return launch_ell_m<T, R, 5>(ctx, A, eval, x, e);
+    case 6: return launch_ell_m<T, R, 6>(ctx, A, eval, x, e);
+    case 7: return launch_ell_m<T, R, 7>(ctx, A, eval, x, e);
+    default: return launch_ell_m<T, R, 0>(ctx, A, eval, x, e);
+    }
 }
 
 template <class T, int IPT>
