@@ -102,10 +102,14 @@ typedef enum {
                                    of similar length), 8/16 = warp-independent split (default otherwise: 8),
                                    104/108/116 = tiled segmented reduction with 4/8/16 items per thread */
     SPX_KERNEL_CSR_SPLIT = 5,   /* CSR: each lane takes `param` (8 or 16) consecutive nonzeros, warps independent */
-    SPX_KERNEL_CSR_ROWS = 6     /* CSR: tiles of 128 rows bulk-copied to shared memory, one thread per row
-                                   (rows of similar length; SPX_ERR_TOO_LARGE if a tile's nonzeros do not
-                                   fit in shared memory); param = shared-memory stages per block:
-                                   2 (default, the next tile copied while this one is reduced) or 1 */
+    SPX_KERNEL_CSR_ROWS = 6     /* CSR: tiles of 128 rows bulk-copied to shared memory, 1, 2 or 4 threads
+                                   per row (rows of similar length; SPX_ERR_TOO_LARGE if a tile's nonzeros
+                                   do not fit in shared memory); param = stages + 10 x threads per row,
+                                   stages = shared-memory stages per block (2: the next tile copied while
+                                   this one is reduced): 1 or 2 = that many stages, one thread per row;
+                                   12, 22, 42 = two stages, 1, 2 or 4 threads per row; 0 = two stages,
+                                   and when the mean row length is 16 or more 2 (FP64) or 4 (FP32)
+                                   threads per row, else one */
 } spx_kernel;
 
 /* spx_matrix_create flags */

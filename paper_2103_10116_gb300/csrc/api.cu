@@ -673,8 +673,9 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     if (kernel == SPX_KERNEL_COO && param != 0 &&
         !(param == 1 || param == 8 || param == 16 || param == 104 || param == 108 || param == 116))
         return fail(SPX_ERR_INVALID, "COO parameter must be 0 (auto), 1 (row-block), 8, 16 (split) or 104, 108, 116 (tiled)");
-    if (kernel == SPX_KERNEL_CSR_ROWS && param != 0 && !(param == 1 || param == 2))
-        return fail(SPX_ERR_INVALID, "row-block stages must be 0 (auto), 1 or 2");
+    if (kernel == SPX_KERNEL_CSR_ROWS && param != 0 &&
+        !(param == 1 || param == 2 || param == 12 || param == 22 || param == 42))
+        return fail(SPX_ERR_INVALID, "row-block parameter must be 0 (auto), 1, 2, 12, 22 or 42");
     if (kernel == SPX_KERNEL_CSR_SPLIT && param != 0 && !(param == 8 || param == 16))
         return fail(SPX_ERR_INVALID, "split nonzeros per lane must be 0 (auto), 8 or 16");
     if (kernel == SPX_KERNEL_ELL && param != 0 && !(param == 1 || param == 2 || (param == 4 && A->dtype == SPX_F32)))
@@ -692,7 +693,8 @@ std::vector<std::pair<int, int>> tune_candidates(const spx_matrix *A)
     std::vector<std::pair<int, int>> c;
     switch (A->format) {
     case SPX_CSR:
-        c = {{SPX_KERNEL_CSR_ROWS, 1}, {SPX_KERNEL_CSR_ROWS, 2}, {SPX_KERNEL_CSR_MERGE, 4},
+        c = {{SPX_KERNEL_CSR_ROWS, 1}, {SPX_KERNEL_CSR_ROWS, 2}, {SPX_KERNEL_CSR_ROWS, 22},
+             {SPX_KERNEL_CSR_ROWS, 42}, {SPX_KERNEL_CSR_MERGE, 4},
              {SPX_KERNEL_CSR_MERGE, 8}, {SPX_KERNEL_CSR_MERGE, 16}, {SPX_KERNEL_CSR_SPLIT, 8},
              {SPX_KERNEL_CSR_SPLIT, 16}};
         for (int sw = 1; sw <= 32; sw *= 2) c.push_back({SPX_KERNEL_CSR_VECTOR, sw});

@@ -528,7 +528,10 @@ __device__ __forceinline__ T chunk_combine(bool has_pend, int rstart, T pend, co
 // column indices and values into shared memory with three 1-D bulk copies
 // (double-buffered: the next tile is in flight while this one is reduced),
 // and each thread then reduces one row sequentially from shared memory, one
-// FMA per stored entry — ELL's arithmetic without ELL's padding.  `cap` is
+// FMA per stored entry — ELL's arithmetic without ELL's padding.  With TPR > 1
+// threads per row (longer rows), TPR adjacent lanes take every TPR-th entry of
+// the row and a shuffle adds their sums: more gathers in flight per SM when
+// shared memory caps the resident tiles.  `cap` is
 // the largest number of nonzeros in any tile (measured on the host), so the
 // copies always fit; a tile above it (never, for an unmodified matrix) sets
 // DEVERR_BOUNDS and is skipped.
@@ -541,8 +544,8 @@ template <class T, int ROWS> struct RowsShape {
     static __host__ __device__ int smem(int cap, int stages) { return stages * stage(cap) + 32 + 16; }
 };
 
-template <class T, int ROWS, int STAGES, int MODE>
-__global__ void __launch_bounds__(ROWS)
+template <class T, int ROWS, int STAGES, int MODE, int TPR>
+__global__ void __launch_bounds__(ROWS * TPR)
     k_csr_rows(int n, const int *__restrict__ rp, const int *__restrict__ col, const T *__restrict__ val,
                const T *__restrict__ x, int ntiles, int cap, T *partials, unsigned *ticket, unsigned *err, Epi<T> e)
 {
@@ -550,6 +553,7 @@ __global__ void __launch_bounds__(ROWS)
     constexpr int VA = 16 / (int)sizeof(T);
     constexpr int CH = 8;
     static_assert(STAGES == 1 || STAGES == 2, "one or two stages");
+    static_assert(TPR == 1 || TPR == 2 || TPR == 4, "1, 2 or 4 threads per row");
     if (e.skip && *e.skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int stage_bytes = S::stage(cap);
@@ -615,10 +619,13 @@ __global__ void __launch_bounds__(ROWS)
             fence_proxy_async();
             issue_next(0);  // this tile
         }
-        const int rq = t * ROWS + tid;  // this thread's row of the tile
-        const EpiRow<T> pre = rq < n ? epi_row_load<MODE>(e, rq) : EpiRow<T>{T(0), T(0)};
+        const int q = tid / TPR, sub = tid % TPR;  // this thread's row of the tile; its lane within the row
+        const int rq = t * ROWS + q;
+        const EpiRow<T> pre = rq < n && sub == 0 ? epi_row_load<MODE>(e, rq) : EpiRow<T>{T(0), T(0)};
         const uint32_t parity = STAGES == 2 ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
-        if (!mbar_wait(&bar[stage], parity, err)) {
+        bool waited = mbar_wait(&bar[stage], parity, err);
+        if constexpr (TPR > 1) waited = __all_sync(0xffffffffu, waited);  // the shuffle below needs whole warps
+        if (!waited) {
             ok = false;
             break;
         }
@@ -628,28 +635,33 @@ __global__ void __launch_bounds__(ROWS)
         const int *s_rp = reinterpret_cast<const int *>(sb) + (r0 - (r0 & ~3));
         const int *s_col = reinterpret_cast<const int *>(sb + S::RP_BYTES) + (j0 - (j0 & ~3));
         const T *s_val = reinterpret_cast<const T *>(sb + S::RP_BYTES + S::col_bytes(cap)) + (j0 - (j0 & ~(VA - 1)));
-        const int q = tid;
-        if (r0 + q < r1) {
-            int a = s_rp[q] - j0;
-            const int b = j1 > j0 ? s_rp[q + 1] - j0 : a;
-            T sum = T(0);
-            for (; a + CH <= b; a += CH) {  // full chunks: CH gathers in flight, then CH FMAs
+        const bool live = r0 + q < r1;
+        T sum = T(0);
+        if (live) {
+            const int a0 = s_rp[q] - j0;
+            const int len = (j1 > j0 ? s_rp[q + 1] - j0 : a0) - a0;
+            // this lane's entries: a0 + sub + TPR*u for u < cnt
+            const int cnt = TPR == 1 ? len : (len - sub + TPR - 1) / TPR;
+            const int *pc = s_col + a0 + sub;
+            const T *pv = s_val + a0 + sub;
+            int a = 0;
+            for (; a + CH <= cnt; a += CH) {  // full chunks: CH gathers in flight, then CH FMAs
                 T v[CH], xv[CH];
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
-                    v[u] = s_val[a + u];
-                    xv[u] = __ldg(x + s_col[a + u]);
+                    v[u] = pv[(a + u) * TPR];
+                    xv[u] = __ldg(x + pc[(a + u) * TPR]);
                 }
 #pragma unroll
                 for (int u = 0; u < CH; ++u) sum = fma(v[u], xv[u], sum);
             }
-            const int rem = b - a;  // 0 .. CH-1: gathers issued together, FMAs only for real entries
+            const int rem = cnt - a;  // 0 .. CH-1: gathers issued together, FMAs only for real entries
             if (rem > 0) {
                 T v[CH - 1], xv[CH - 1];
 #pragma unroll
                 for (int u = 0; u < CH - 1; ++u) {
-                    v[u] = u < rem ? s_val[a + u] : T(0);
-                    xv[u] = u < rem ? __ldg(x + s_col[a + u]) : T(0);
+                    v[u] = u < rem ? pv[(a + u) * TPR] : T(0);
+                    xv[u] = u < rem ? __ldg(x + pc[(a + u) * TPR]) : T(0);
                 }
                 if (rem & 4) {
 #pragma unroll
@@ -665,8 +677,12 @@ __global__ void __launch_bounds__(ROWS)
                 }
                 if (rem & 1) sum = fma(v[0], xv[0], sum);
             }
-            out_row_pre<MODE>(e, r0 + q, sum, pre, d0, d1);
         }
+        if constexpr (TPR > 1) {  // lanes of a row are adjacent and in one warp; every lane takes part
+#pragma unroll
+            for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, TPR);
+        }
+        if (live && sub == 0) out_row_pre<MODE>(e, r0 + q, sum, pre, d0, d1);
         __syncthreads();  // the stage is refilled by a later copy
     }
     if (!ok && pending_prefetch) {
@@ -674,7 +690,7 @@ __global__ void __launch_bounds__(ROWS)
         mbar_wait(&bar[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1), err, 200000000LL);
     }
     if constexpr (MODE == 0 || MODE >= 4)
-        if (e.dots) finish_dots<T, ROWS>(d0, d1, e, partials, ticket);
+        if (e.dots) finish_dots<T, ROWS * TPR>(d0, d1, e, partials, ticket);
 }
 
 // ------------------------------------------------------------------ row-block COO (regular rows)
@@ -1731,10 +1747,11 @@ template <class T> int64_t rows_smem(const spx_matrix *A, int stages)
     return RowsShape<T, kRowsTile>::smem((int)std::min<int64_t>(A->rows_cap, 1 << 24), stages);
 }
 
-template <class T, int STAGES, int MODE>
+template <class T, int STAGES, int MODE, int TPR>
 int launch_rows_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
 {
-    auto kern = k_csr_rows<T, kRowsTile, STAGES, MODE>;
+    auto kern = k_csr_rows<T, kRowsTile, STAGES, MODE, TPR>;
+    constexpr int block = kRowsTile * TPR;
     SPX_TRY(ensure_rows_cap(ctx, A));
     // the dynamic shared memory may reach the opt-in limit less the static part
     static std::once_flag once;
@@ -1753,32 +1770,50 @@ int launch_rows_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const E
     if (smem > dyn_max)
         return fail(SPX_ERR_TOO_LARGE, "row-block CSR: a tile of 128 rows does not fit in shared memory");
     const int64_t ntiles = ceil_div(A->n, kRowsTile);
-    const int grid = grid_for(ctx, kern, kRowsTile, (int)smem, ntiles);
+    const int grid = grid_for(ctx, kern, block, (int)smem, ntiles);
     SPX_TRY(ensure_scratch(ctx, A, 0, grid, sizeof(T)));
-    kern<<<grid, kRowsTile, (int)smem, ctx->stream>>>((int)A->n, A->rp.as<int>(), A->col.as<int>(), val, x,
+    kern<<<grid, block, (int)smem, ctx->stream>>>((int)A->n, A->rp.as<int>(), A->col.as<int>(), val, x,
                                                       (int)ntiles, (int)A->rows_cap, A->partials.as<T>(),
                                                       A->ticket.as<unsigned>(), ctx->dev_err, e);
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;
 }
 
-// stages: 1 or 2 (param of SPX_KERNEL_CSR_ROWS; 0 = 2)
-template <class T>
-int launch_rows(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e, int stages)
+// Threads per row when the caller leaves it open.  Rows of 16 or more entries
+// make a 128-row tile large enough that only two tiles stay resident per SM,
+// and one thread per row then leaves too few gathers in flight: two threads per
+// row for FP64, four for FP32 (measured best on the 27-point stencil, 100^3:
+// 88.7 -> 80.5 us FP64, 51.9 -> 47.8 us FP32).  Shorter rows keep one thread
+// (the 7-point stencil, 128^3, FP64: 45.7 us with one, 70.3 us with two).
+template <class T> int rows_auto_tpr(const spx_matrix *A)
 {
-#define SPX_ROWS_MODES(ST_)                                                   \
+    return A->mean_len < 16.0 ? 1 : sizeof(T) == 4 ? 4 : 2;
+}
+
+// stages: 1 or 2; tpr: threads per row, 1, 2 or 4 (2 and 4 with two stages only)
+template <class T>
+int launch_rows(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e, int stages, int tpr)
+{
+#define SPX_ROWS_MODES(ST_, TPR_)                                             \
     switch (epi_mode(e)) {                                                    \
-    case 1: return launch_rows_m<T, ST_, 1>(ctx, A, val, x, e);               \
-    case 4: return launch_rows_m<T, ST_, 4>(ctx, A, val, x, e);               \
-    case 5: return launch_rows_m<T, ST_, 5>(ctx, A, val, x, e);               \
-    case 6: return launch_rows_m<T, ST_, 6>(ctx, A, val, x, e);               \
-    case 7: return launch_rows_m<T, ST_, 7>(ctx, A, val, x, e);               \
-    default: return launch_rows_m<T, ST_, 0>(ctx, A, val, x, e);              \
+    case 1: return launch_rows_m<T, ST_, 1, TPR_>(ctx, A, val, x, e);         \
+    case 4: return launch_rows_m<T, ST_, 4, TPR_>(ctx, A, val, x, e);         \
+    case 5: return launch_rows_m<T, ST_, 5, TPR_>(ctx, A, val, x, e);         \
+    case 6: return launch_rows_m<T, ST_, 6, TPR_>(ctx, A, val, x, e);         \
+    case 7: return launch_rows_m<T, ST_, 7, TPR_>(ctx, A, val, x, e);         \
+    default: return launch_rows_m<T, ST_, 0, TPR_>(ctx, A, val, x, e);        \
     }
     if (stages == 1) {
-        SPX_ROWS_MODES(1)
+        if (tpr != 1) return fail(SPX_ERR_INVALID, "row-block CSR: several threads per row need two stages");
+        SPX_ROWS_MODES(1, 1)
     }
-    SPX_ROWS_MODES(2)
+    if (tpr == 2) {
+        SPX_ROWS_MODES(2, 2)
+    }
+    if (tpr == 4) {
+        SPX_ROWS_MODES(2, 4)
+    }
+    SPX_ROWS_MODES(2, 1)
 #undef SPX_ROWS_MODES
 }
 
@@ -2018,14 +2053,16 @@ int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
         if (mx <= 2.0 * mean + 8.0) {
             SPX_TRY(ensure_rows_cap(ctx, A));
             if (rows_smem<T>(A, kRowsStages) <= std::min<int64_t>(ctx->max_smem_optin, 120 * 1024))
-                return launch_rows<T>(ctx, A, val, x, e, kRowsStages);
+                return launch_rows<T>(ctx, A, val, x, e, kRowsStages, rows_auto_tpr<T>(A));
         }
         kern = mx <= 4.0 * mean + 8.0 ? SPX_KERNEL_CSR_MERGE : SPX_KERNEL_CSR_SPLIT;
         p = kern == SPX_KERNEL_CSR_SPLIT ? 8 : 0;
     }
-    if (kern == SPX_KERNEL_CSR_ROWS) {
-        if (p != 0 && p != 1 && p != 2) return fail(SPX_ERR_INVALID, "row-block stages must be 1 or 2");
-        return launch_rows<T>(ctx, A, val, x, e, p == 0 ? kRowsStages : p);
+    if (kern == SPX_KERNEL_CSR_ROWS) {  // param: stages + 10 x threads per row (0 = automatic)
+        if (p == 0) return launch_rows<T>(ctx, A, val, x, e, kRowsStages, rows_auto_tpr<T>(A));
+        if (p != 1 && p != 2 && p != 12 && p != 22 && p != 42)
+            return fail(SPX_ERR_INVALID, "row-block parameter must be 0, 1, 2, 12, 22 or 42");
+        return launch_rows<T>(ctx, A, val, x, e, p % 10, p < 10 ? 1 : p / 10);
     }
     if (kern == SPX_KERNEL_CSR_VECTOR) {
         if (p <= 0) {  // sub-warp width from the mean row length

@@ -62,7 +62,15 @@ def _make(spx, ctx, fmt, rp, col, val, flags=0, kernel=None, param=0, dtype=torc
     return A
 
 
-FMTS = [("csr", None, 0), ("csr", 1, 4), ("csr", 2, 16), ("csr", 5, 16), ("csr", 6, 0), ("ell", None, 0),
+def _fmt_kernel(spx, fmt):
+    """'csr-rowsP' names the row-block CSR kernel with parameter P; returns (format, kernel, param)."""
+    if fmt.startswith("csr-rows"):
+        return "csr", spx.SPX_KERNEL_CSR_ROWS, int(fmt[8:])
+    return fmt, None, 0
+
+
+FMTS = [("csr", None, 0), ("csr", 1, 4), ("csr", 2, 16), ("csr", 5, 16), ("csr", 6, 0), ("csr", 6, 22),
+        ("csr", 6, 42), ("ell", None, 0),
         ("coo", None, 0), ("hyb", None, 0)]
 
 
@@ -86,10 +94,11 @@ def test_cg_laplace2d_64(spx, ctx, fmt):
         spx.spx_matrix_destroy(A)
 
 
-@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb", "csr-rows22", "csr-rows42"])
 def test_bicgstab_convdiff(spx, ctx, fmt):
     rp, col, val, xs, b = _problem("convdiff_16")
-    A = _make(spx, ctx, fmt, rp, col, val)
+    f, kernel, param = _fmt_kernel(spx, fmt)
+    A = _make(spx, ctx, f, rp, col, val, kernel=kernel, param=param)
     try:
         x = torch.zeros_like(_t(b))
         info = spx.spx_solve(ctx, A, _t(b), x, "bicgstab", 1e-10, 5000)
@@ -103,10 +112,11 @@ def test_bicgstab_convdiff(spx, ctx, fmt):
         spx.spx_matrix_destroy(A)
 
 
-@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb", "csr-rows22", "csr-rows42"])
 def test_cgs_convdiff(spx, ctx, fmt):
     rp, col, val, xs, b = _problem("convdiff_16")
-    A = _make(spx, ctx, fmt, rp, col, val)
+    f, kernel, param = _fmt_kernel(spx, fmt)
+    A = _make(spx, ctx, f, rp, col, val, kernel=kernel, param=param)
     try:
         x = torch.zeros_like(_t(b))
         info = spx.spx_solve(ctx, A, _t(b), x, "cgs", 1e-10, 5000)
