@@ -142,7 +142,7 @@ __global__ void k_cast(int64_t m, const S *__restrict__ src, D *__restrict__ dst
 }
 
 // COO row indices: one warp per row writes row i over [rp[i], rp[i+1]).
-__global__ void k_coo_rows(int64_t n, const int *__restrict__ rp, int *__restrict__ row)
+__global__ void k_expand_rows(int64_t n, const int *__restrict__ rp, int *__restrict__ row)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
@@ -424,7 +424,7 @@ int matrix_build(spx_ctx *ctx, spx_matrix *A, const int32_t *rp_in, const int32_
         A->coo_nnz = nnz;
         SPX_TRY(dbuf_alloc(ctx, A->coo_row, (size_t)nnz * 4));
         if (nnz > 0) {
-            k_coo_rows<<<grid1d(ctx, n * 32), 256, 0, ctx->stream>>>(n, A->rp.as<int>(), A->coo_row.as<int>());
+            k_expand_rows<<<grid1d(ctx, n * 32), 256, 0, ctx->stream>>>(n, A->rp.as<int>(), A->coo_row.as<int>());
             SPX_CUDA(cudaGetLastError());
         }
         A->coo_col = A->col;
