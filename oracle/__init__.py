@@ -304,7 +304,7 @@ def gmres(rp, col, val, b, m=30, tol=1e-10, maxit=10000, x0=None, hist=False, mu
 
 
 def ir(rp, col, val, b, solver="cg", tol=1e-10, inner_tol=1e-4, max_outer=20,
-       maxit_inner=500, x0=None):
+       maxit_inner=500, x0=None, mutant=0):
     """FP64 iterative refinement around an FP32 CG / BiCGSTAB / CGS inner solve
     (at most maxit_inner inner iterations per refinement cycle)."""
     rp, col, val = _csr(rp, col, val)
@@ -312,7 +312,7 @@ def ir(rp, col, val, b, solver="cg", tol=1e-10, inner_tol=1e-4, max_outer=20,
     n = rp.shape[0] - 1
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     info = _Info()
-    _lib().orc_ir(n, _ptr(rp), _ptr(col), _ptr(val), {"cg": 0, "bicgstab": 1, "cgs": 3}[solver], _ptr(b),
+    _lib(mutant).orc_ir(n, _ptr(rp), _ptr(col), _ptr(val), {"cg": 0, "bicgstab": 1, "cgs": 3}[solver], _ptr(b),
                   _ptr(x), float(tol), float(inner_tol), int(max_outer), int(maxit_inner),
                   C.byref(info))
     return x, SolveInfo(info.status, info.iterations, info.restarts, info.relres_recurrence,

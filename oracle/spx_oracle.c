@@ -17,8 +17,7 @@
  *     for the others; block inverses by Gauss-Jordan with partial pivoting,
  *     optionally stored in FP32 for well-conditioned blocks);
  *   - iterative refinement with an FP32 inner Krylov solve and FP64 outer
- *     residual and update (its iterate path is parity unpinned: only the end
- *     state, the true FP64 residual, is checked).
+ *     residual and update.
  *
  * Build flags must keep IEEE semantics: -O2 -ffp-contract=off, no fast-math,
  * so that x86-64 and aarch64 hosts produce identical bits.
@@ -26,9 +25,10 @@
  * Pins (the tests in tests/test_oracle_*.py) tie every function here to facts
  * that do not come from this file: exact dense products on integer data,
  * closed-form Laplacian eigenpairs, finite termination of CG / GMRES, one-step
- * convergence on scaled identities, and hand-worked examples.  The iterate path
- * of iterative refinement is "parity unpinned": only its end state (the true
- * FP64 residual) is checked.
+ * convergence on scaled identities, and hand-worked examples.  Iterative
+ * refinement is pinned cycle by cycle on scaled identities c*I (c a power of
+ * two), where FP32 rounding bounds fix each cycle's error: 2^-24 after one,
+ * 2^-47 after two.
  */
 #include <float.h>
 #include <math.h>
@@ -1063,7 +1063,16 @@ int orc_ir(int64_t n, const int32_t *rp, const int32_t *col, const double *val, 
     double rel = 0.0;
     int outer = 0;
     for (;; ++outer) {
+#if ORC_MUTANT == 11
+        {  /* planted: residual with the FP32 values */
+            double *v = malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+            for (int64_t k = 0; k < nnz; ++k) v[k] = (double)v32[k];
+            orc_spmv_csr(n, rp, col, v, x, r);
+            free(v);
+        }
+#else
         orc_spmv_csr(n, rp, col, val, x, r);
+#endif
         for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
         double rn = nrm2(n, r);
         rel = rn / bnorm;
@@ -1073,7 +1082,13 @@ int orc_ir(int64_t n, const int32_t *rp, const int32_t *col, const double *val, 
         inner += solver == 0   ? cg_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner)
                  : solver == 3 ? cgs_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner)
                                : bicgstab_f32(n, rp, col, v32, r32, d32, (float)inner_tol, maxit_inner);
+#if ORC_MUTANT == 9
+        for (int64_t i = 0; i < n; ++i) x[i] += (double)d32[i];  /* planted: correction not scaled back */
+#elif ORC_MUTANT == 10
+        for (int64_t i = 0; i < n; ++i) x[i] = (float)(x[i] + rn * (double)d32[i]);  /* planted: FP32 update */
+#else
         for (int64_t i = 0; i < n; ++i) x[i] += rn * (double)d32[i];
+#endif
     }
     info->status = status;
     info->iterations = inner;

@@ -8,7 +8,9 @@ residual polynomial is the square of CG's on an SPD matrix with r^ = r0 (by
 its construction), so it also terminates in d steps; GMRES on a matrix whose
 minimal polynomial has degree d terminates in at most d steps and its residual
 never increases; manufactured solutions b = A x* with the error bounded by
-kappa * tol; numpy's dense LU as an independent solve.
+kappa * tol; numpy's dense LU as an independent solve; the rounding bounds of
+FP32 and FP64 arithmetic (unit roundoffs 2^-24 and 2^-53) for each cycle of
+iterative refinement on c*I.
 """
 import numpy as np
 import pytest
@@ -308,3 +310,71 @@ def test_ir_cgs_stall_rule_ends_blown_up_cycles():
     assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-10
     assert info.restarts >= 3  # more than one blown-up cycle was cut short and restarted
     assert info.iterations < 300, info
+
+
+# ---------------------------------------------------------------- IR: the iterate path
+# On A = c*I with c a power of two every FP32 inner solver takes one step and
+# returns d = r32 / c exactly (see the one-step pins above), so a refinement
+# cycle adds to x the FP32 rounding of the normalised FP64 residual, scaled back.
+# Rounding arithmetic then fixes each cycle's result: after one cycle
+# |b_i - c x_i| <= 2^-24 |b_i| (one FP32 rounding, plus FP64 roundings of
+# order 2^-53); after two, <= 2^-47 |b_i| (the second cycle rounds a residual
+# already 2^-24 small, and the FP64 update adds at most 2^-53 |b_i|).  So a solve
+# to 1e-10 ends after exactly two cycles.  A residual or an update taken in FP32,
+# a correction not scaled back by the residual norm, or a wrong sign breaks one
+# of these bounds.
+def _scaled_identity(n, c):
+    return np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, c)
+
+
+def _ir_scaled_identity_pins(solver, c, mutant=0):
+    """The cycle-by-cycle facts above, each as a bool."""
+    n = 257
+    rp, col, val = _scaled_identity(n, c)
+    b = np.random.default_rng(5).uniform(-1, 1, n)
+    b[np.abs(b) < 1e-3] = 0.5  # keep every component well inside the normal FP32 range after scaling
+    x1, i1 = oracle.ir(rp, col, val, b, solver=solver, tol=1e-10, max_outer=1, mutant=mutant)
+    err1 = np.abs(b - c * x1)
+    x2, _ = oracle.ir(rp, col, val, b, solver=solver, tol=1e-10, max_outer=2, mutant=mutant)
+    err2 = np.abs(b - c * x2)
+    x, info = oracle.ir(rp, col, val, b, solver=solver, tol=1e-10, mutant=mutant)
+    return {
+        "one cycle stops": i1.status == oracle.MAX_ITER and i1.restarts == 1,
+        "one cycle: 2^-24": bool(np.all(err1 <= 2.0 ** -24 * (1 + 1e-6) * np.abs(b))),
+        "one cycle leaves an FP32 rounding": bool(np.max(err1 / np.abs(b)) > 2.0 ** -30),
+        "two cycles: 2^-47": bool(np.all(err2 <= 2.0 ** -47 * np.abs(b))),
+        "converged after two cycles": info.status == oracle.CONVERGED and info.restarts == 2,
+        "one inner step per cycle": info.iterations == 2,
+        "same two cycles": bool(np.array_equal(x, x2)),
+    }
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs"])
+@pytest.mark.parametrize("c", [0.25, 8.0])
+def test_ir_cycles_on_scaled_identity_follow_fp32_rounding(solver, c):
+    pins = _ir_scaled_identity_pins(solver, c)
+    assert all(pins.values()), pins
+
+
+@pytest.mark.parametrize("mutant", [9, 10])
+def test_ir_planted_update_mistakes_are_caught(mutant):
+    """9: the correction is not scaled back by the residual norm; 10: the update is
+    rounded to FP32.  Each breaks a cycle-by-cycle pin."""
+    pins = _ir_scaled_identity_pins("cg", 0.25, mutant=mutant)
+    assert not all(pins.values()), pins
+
+
+def test_ir_planted_fp32_residual_is_caught():
+    """11: the outer residual uses the FP32 values.  On c*I with c a power of two
+    that changes nothing, so the pin is a matrix whose values FP32 cannot hold:
+    refinement then converges to the FP32 matrix's solution, and the true FP64
+    residual, recomputed with scipy, stays far above the tolerance."""
+    import scipy.sparse as sp
+    rp, col, val = synth.convdiff3d_upwind(8)
+    n = rp.shape[0] - 1
+    assert np.any(val.astype(np.float32).astype(np.float64) != val)
+    A = sp.csr_matrix((val, col, rp), shape=(n, n))
+    b = A @ np.random.default_rng(3).uniform(-1, 1, n)
+    for mutant, ok in ((0, True), (11, False)):
+        x, _ = oracle.ir(rp, col, val, b, solver="bicgstab", tol=1e-10, mutant=mutant)
+        assert (np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-10) == ok, mutant
