@@ -1,15 +1,18 @@
-"""Bounds of the row-block SpMV kernels' bulk copies, checked on the CPU.
+"""Bounds of the tiled SpMV kernels' bulk copies, checked on the CPU.
 
-The row-block CSR and COO kernels copy each tile of 128 rows into a shared-memory
+The row-block CSR and COO kernels copy each tile of 128 rows, and the merge-path
+CSR kernel each tile of merge items (row ends and nonzeros), into a shared-memory
 stage with 1-D bulk copies (`cp.async.bulk`), whose source and size must be
 multiples of 16 bytes.  This file restates the tile arithmetic of the kernels
-(copy start rounded down to 16 bytes, size rounded up, stage slots sized from the
-largest tile) and checks, for the test and benchmark matrices, that
+(the merge-path tile map, copy start rounded down to 16 bytes, size rounded up,
+stage slots sized from the largest tile) and checks, for the test and benchmark
+matrices, that
 
 * every copy starts on a 16-byte boundary and moves a multiple of 16 bytes;
 * every copy stays inside the library's device array, which is allocated with
   its size rounded up to 16 bytes plus 64 bytes of padding;
-* every copy fits its stage slot, and every shared-memory read of the reduction
+* every copy fits its stage slot (for the merge-path kernel, together with the
+  row sums stored after it), and every shared-memory read of the reduction
   (row pointers, columns, values, for 1, 2 or 4 threads per row) lands in data
   the copy brought in;
 * with several threads per row, the lanes of a row take each entry exactly once.
@@ -34,6 +37,15 @@ def _alloc(nbytes):
     return int(_r16(nbytes)) + PAD
 
 
+def _long_row():
+    """Rows of 3 entries and one of 50,000: longer than any merge tile's slack."""
+    lens = np.full(3000, 3, np.int64)
+    lens[7] = 50000
+    rp = np.zeros(lens.size + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    return rp, None, None
+
+
 MATS = {
     "lap2d_64": lambda: synth.laplace2d_5pt(64),
     "st27_23": lambda: synth.stencil3d_27pt(23),
@@ -42,6 +54,7 @@ MATS = {
     "ragged_tail": lambda: synth.laplace2d_5pt(37),  # n = 1369: a last tile of 89 rows
     "stencil27_100": lambda: synth.stencil3d_27pt(100),
     "poisson128": lambda: synth.laplace3d_7pt(128),
+    "long_row": _long_row,
 }
 _cache = {}
 
@@ -84,7 +97,7 @@ def test_csr_row_block_copies_stay_in_bounds(name, V):
     val_bytes = ((cap + 8) * V + 15) & ~15
     smem = 2 * (rp_bytes + col_bytes + val_bytes) + 32 + 16
     if smem > SMEM_OPTIN:  # the launcher returns SPX_ERR_TOO_LARGE; nothing is copied
-        assert name == "powerlaw_60k"
+        assert name in ("powerlaw_60k", "long_row")
         return
     ra = r0 & ~3
     rbytes = ((r1 + 1 - ra + 3) & ~3) * 4
@@ -138,6 +151,68 @@ def test_coo_row_block_copies_stay_in_bounds(name, V):
     # every staged row index belongs to the tile, so the row marks s_first/s_end[row - r0] stay in [0, ROWS)
     t_of_entry = np.repeat(np.arange(ntiles), e1 - e0)
     assert np.all((crow - t_of_entry * ROWS >= 0) & (crow - t_of_entry * ROWS < ROWS))
+
+
+def _merge_tiles(rp, tile, slack):
+    """Tile boundaries (row, nonzero) of the merge-path CSR kernel: the merge of the row ends
+    with the nonzeros cut every `tile` items, each cut moved forward to the next row end when
+    that is at most `slack` items away."""
+    n = rp.shape[0] - 1
+    nnz = int(rp[-1])
+    ntiles = -(-(n + nnz) // tile)
+    d = np.minimum(np.arange(ntiles + 1, dtype=np.int64) * tile, n + nnz)
+    # the first row i with i + rp[i + 1] >= d (row ends before the cut), within the feasible range
+    i = np.searchsorted(np.arange(n, dtype=np.int64) + rp[1:], d, side="left")
+    i = np.clip(i, np.maximum(0, d - nnz), np.minimum(d, n))
+    j = d - i
+    inner = (i < n) & (j > rp[np.minimum(i, n)])
+    dn = i + 1 + rp[np.minimum(i + 1, n)]
+    snap = inner & (dn - d <= slack)
+    i = np.where(snap, i + 1, i)
+    j = np.where(snap, rp[np.minimum(i, n)], j)
+    return i, j
+
+
+@pytest.mark.parametrize("ipt", [4, 8, 16])
+@pytest.mark.parametrize("V", [8, 4], ids=["f64", "f32"])
+@pytest.mark.parametrize("name", ["lap2d_64", "st27_23", "convdiff_20", "powerlaw_60k", "ragged_tail", "long_row"])
+def test_merge_path_copies_stay_in_bounds(name, V, ipt):
+    rp = _rp(name)
+    n = rp.shape[0] - 1
+    nnz = int(rp[-1])
+    block = 256
+    tile = block * ipt
+    slack = tile // 4
+    stage = (4 + V) * (tile + slack) + 256
+    smem = 2 * stage + block * 4 + block * V + (block + 1) * 4 + 12 + 32 + 16
+    assert smem <= SMEM_OPTIN
+    ti, tj = _merge_tiles(rp, tile, slack)
+    assert ti[0] == 0 and tj[0] == 0 and ti[-1] == n and tj[-1] == nnz
+    assert np.all(np.diff(ti) >= 0) and np.all(np.diff(tj) >= 0)
+    i0, j0, i1, j1 = ti[:-1], tj[:-1], ti[1:], tj[1:]
+    assert np.all((i1 - i0) + (j1 - j0) <= tile + slack)
+    VA = 16 // V
+    ra = i0 & ~3
+    rend = np.minimum(i1 + 2, n + 1)
+    rbytes = ((rend - ra + 3) & ~3) * 4
+    ca = j0 & ~3
+    va = j0 & ~(VA - 1)
+    has = j1 > j0
+    cbytes = np.where(has, ((j1 - ca + 3) & ~3) * 4, 0)
+    vbytes = np.where(has, ((j1 - va + VA - 1) & ~(VA - 1)) * V, 0)
+    for start, size in ((ra * 4, rbytes), (ca * 4, cbytes), (va * V, vbytes)):
+        assert np.all(start % 16 == 0) and np.all(size % 16 == 0)
+    assert np.all(ra * 4 + rbytes <= _alloc((n + 1) * 4))
+    assert np.all(np.where(has, ca * 4 + cbytes, 0) <= _alloc(nnz * 4))
+    assert np.all(np.where(has, va * V + vbytes, 0) <= _alloc(nnz * V))
+    # the copies, then one row sum per row end of the tile, fit the stage
+    assert np.all(rbytes + cbytes + vbytes + V * (i1 - i0) <= stage)
+    # rp[i0 .. min(i1 + 1, n)] and the tile's nonzeros were copied
+    assert np.all((np.minimum(i1 + 1, n) - ra + 1) * 4 <= rbytes)
+    assert np.all(np.where(has, (j1 - ca) * 4 <= cbytes, True))
+    assert np.all(np.where(has, (j1 - va) * V <= vbytes, True))
+    if name == "long_row":  # the 50,000-entry row straddles tiles: the cut inside it was not snapped
+        assert np.any((j0 > rp[np.minimum(i0, n)]) & (i0 < n))
 
 
 def test_lane_partition_detects_a_wrong_split():
