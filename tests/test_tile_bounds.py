@@ -220,3 +220,19 @@ def test_lane_partition_detects_a_wrong_split():
     lengths = np.array([0, 1, 5, 27])
     assert _lane_partition_ok(lengths, 2) and _lane_partition_ok(lengths, 4)
     assert not _lane_partition_ok(lengths, 2, count=lambda L, sub, tpr: L // tpr)
+
+
+@pytest.mark.parametrize("R,V", [(1, 8), (2, 8), (1, 4), (2, 4), (4, 4)])
+def test_ell_vector_loads_stay_in_bounds(R, V):
+    """The ELL kernel gives each thread R consecutive rows and reads each slab's R
+    columns and values with one vector load: slab j, rows [i, i + R), i = g*R.  The
+    column-major arrays have ld = n rounded up to 32 rows per slab (HYB's ELL part
+    too), so every load is aligned to its own size and stays inside its slab.  The
+    rows-per-thread choices the library accepts (1 or 2 in FP64, up to 4 in FP32)
+    keep each vector load within 16 bytes."""
+    n = np.arange(1, 4200, dtype=np.int64)
+    ld = (n + 31) // 32 * 32
+    last = ((n + R - 1) // R - 1) * R  # first row of the last group
+    assert np.all(last + R <= ld)
+    assert np.all(ld % R == 0)  # slab starts j*ld and group starts i are multiples of R
+    assert R * V <= 16 and R * 4 <= 16
