@@ -146,13 +146,13 @@ def spmv_csr_plain(rp, col, val, x) -> np.ndarray:
     return y
 
 
-def spmv_absbound(rp, col, val, x) -> np.ndarray:
+def spmv_absbound(rp, col, val, x, mutant=0) -> np.ndarray:
     """(|A| |x|)_i: the scale against which a row's rounding error is judged."""
     rp, col, val = _csr(rp, col, val)
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = rp.shape[0] - 1
     y = np.empty(n, dtype=np.float64)
-    _lib().orc_spmv_csr_absbound(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y))
+    _lib(mutant).orc_spmv_csr_absbound(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y))
     return y
 
 

@@ -105,7 +105,16 @@ void orc_spmv_csr_absbound(int64_t n, const int32_t *rp, const int32_t *col, con
 {
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
-        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += fabs(val[k]) * fabs(x[col[k]]);
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+#if ORC_MUTANT == 13
+            s += fabs(val[k]) * fabs(x[i + 0 * col[k]]); /* planted: wrong operand index */
+#else
+            s += fabs(val[k]) * fabs(x[col[k]]);
+#endif
+        }
+#if ORC_MUTANT == 12
+        s *= 2.0; /* planted: an inflated bound */
+#endif
         y[i] = s;
     }
 }

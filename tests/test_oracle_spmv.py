@@ -136,6 +136,45 @@ def test_compensated_sum_is_correctly_rounded_scale():
         assert bound[i] >= abs(y[i])
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_absbound_exact_against_dense_on_integers(seed):
+    # (|A||x|)_i scales every GPU parity tolerance, so it is pinned exactly:
+    # on integer A and x (|entries| <= 8, short rows) every partial sum is an
+    # exact integer, and the bound must equal the dense product |A|.|x| bit for
+    # bit.  Duplicates count once each (|a|+|b|, not |a+b|), as the dense
+    # matrix of absolute entries below does.
+    rng = np.random.default_rng(200 + seed)
+    n = int(rng.integers(1, 40))
+    ncols = int(rng.integers(1, 40))
+    rp, col, val = random_int_csr(rng, n, ncols)
+    x = rng.integers(-8, 9, size=ncols).astype(np.float64)
+    absdense = np.zeros((n, ncols))
+    for i in range(n):
+        for k in range(rp[i], rp[i + 1]):
+            absdense[i, col[k]] += abs(val[k])
+    got = oracle.spmv_absbound(rp, col, val, x)
+    assert np.array_equal(got, absdense @ np.abs(x))
+    # and it bounds the product itself, with equality on non-negative data
+    assert np.all(got >= np.abs(oracle.spmv_csr(rp, col, val, x)))
+    assert np.array_equal(oracle.spmv_absbound(rp, col, np.abs(val), np.abs(x)),
+                          oracle.spmv_csr(rp, col, np.abs(val), np.abs(x)))
+
+
+@pytest.mark.parametrize("mutant", [12, 13])
+def test_planted_absbound_mistakes_are_caught(mutant):
+    # 12 doubles the bound (a loosened tolerance), 13 reads x at the row index
+    # instead of the column index: the exact dense pin above fails for both.
+    caught = False
+    for seed in range(6):
+        rng = np.random.default_rng(seed)
+        rp, col, val = random_int_csr(rng, 20, 20, empty_frac=0.0)
+        x = rng.integers(-8, 9, size=20).astype(np.float64)
+        absdense = np.abs(to_dense(rp, col, np.abs(val)))
+        got = oracle.spmv_absbound(rp, col, val, x, mutant=mutant)
+        caught |= not np.array_equal(got, absdense @ np.abs(x))
+    assert caught
+
+
 # ---------------------------------------------------------------- CSR check
 def test_csr_check():
     g = _golden("spmv_4x4.json")
