@@ -234,26 +234,35 @@ int spx_spmv_host(spx_ctx *ctx, const spx_matrix *A, const void *x_host, void *y
 
 /* SpMV for callers that cannot allocate device memory.
  *
- * The paper has no counterpart for this entry point.  It exists for callers
- * that may not call cudaMalloc (or any allocating routine) when they need a
- * product: code running while a CUDA graph is captured, real-time loops whose
- * memory is fixed up front, or frameworks that own every allocation.  It
- * computes y = A x with the merge-path CSR kernel directly from the caller's
- * CSR arrays (no matrix handle, no context) on `stream` (a cudaStream_t) of
- * the current device, and allocates nothing: the kernel's scratch (tile map,
- * per-tile carries, look-back flags) lives in one fixed 1 MiB array that the
- * library declares in device global memory; every GPU that loads the library
- * holds it until the process exits.
+ * The paper has no counterpart for this entry point.  Some callers may not
+ * call cudaMalloc, or any routine that allocates, at the moment they need a
+ * product: a real-time loop whose memory is fixed before it starts (an
+ * allocation can block, fail or synchronise the device at a bad moment), or a
+ * host framework that owns all device memory and forbids libraries to take
+ * their own.  This call computes y = A x with the merge-path CSR kernel
+ * straight from the caller's CSR arrays (no matrix handle, no context) on
+ * `stream` (a cudaStream_t) of the current device, and allocates nothing: the
+ * kernel's scratch (tile map, per-tile carries, look-back flags, an error
+ * word) lives in one fixed 1 MiB array that the library declares in device
+ * global memory; every GPU that loads the library holds it until the process
+ * exits.
  *   - Limit: nrows + nnz <= SPX_NOALLOC_MAX_TILES * 2048 (67,108,864);
  *     larger problems return SPX_ERR_TOO_LARGE and launch nothing.
  *   - row_ptr, col_idx and values must be 16-byte aligned (SPX_ERR_INVALID
  *     otherwise) and form a valid CSR matrix (not checked here).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
- *   - Every call shares the one array and clears what must start at zero, so
- *     calls whose kernels overlap on the GPU (different streams, no ordering)
- *     race and give wrong results; order them on one stream.
- *   - dtype: SPX_F64 or SPX_F32 for values, x and y.  Asynchronous. */
+ *   - The first call on a device sets that device up: it looks up the array's
+ *     device address (cudaGetSymbolAddress) and opts the kernel in to its
+ *     shared memory; make that first call before any stream capture.
+ *   - Every call shares the one array, which keeps the previous call's
+ *     contents; each call clears what must start at zero.  Calls whose kernels
+ *     overlap on the GPU (different streams with no ordering between them)
+ *     race on the array and give wrong results; order them on one stream.
+ *   - The return code reports argument and launch errors only; the work runs
+ *     asynchronously.  If one of the kernel's bounded waits gives up (about a
+ *     second without progress, which a valid matrix never causes), every
+ *     element of y is set to NaN, so the failure shows in the result without
+ *     a host synchronisation.
+ *   - dtype: SPX_F64 or SPX_F32 for values, x and y. */
 #define SPX_NOALLOC_MAX_TILES 32768
 int spx_spmv_csr_noalloc(void *stream, int dtype, int64_t nrows, int64_t ncols, int64_t nnz,
                          const int32_t *row_ptr, const int32_t *col_idx, const void *values, const void *x,

@@ -16,7 +16,9 @@
 // and the dot-product partials are finished by the last block to arrive, in
 // index order, so every run gives the same bits.
 #include <climits>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "dev_common.cuh"
 #include "kstate.cuh"
@@ -1590,11 +1592,40 @@ template <class K> int grid_for(spx_ctx *ctx, K kernel, int block, int smem, int
     return (int)(g < 1 ? 1 : g);
 }
 
+std::mutex g_smem_mu;
+std::map<std::pair<const void *, int>, int> g_smem_granted;  // (kernel, device) -> dynamic bytes
+
+}  // namespace
+
+int smem_optin(const void *kernel, int bytes, int *granted)
+{
+    int dev = 0;
+    SPX_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    const auto key = std::make_pair(kernel, dev);
+    auto it = g_smem_granted.find(key);
+    if (it == g_smem_granted.end() || (bytes >= 0 && bytes > it->second)) {
+        int want = bytes;
+        if (want < 0) {
+            cudaFuncAttributes fa;
+            int optin = 0;
+            SPX_CUDA(cudaFuncGetAttributes(&fa, kernel));
+            SPX_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            want = optin - (int)fa.sharedSizeBytes;
+        }
+        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(max dynamic shared memory)");
+        it = g_smem_granted.insert_or_assign(key, want).first;
+    }
+    if (granted) *granted = it->second;
+    return SPX_OK;
+}
+
+namespace {
+
 template <class K> int set_smem(K kernel, int bytes)
 {
-    static_assert(sizeof(K) > 0, "");
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return e == cudaSuccess ? SPX_OK : cuda_fail(e, "cudaFuncSetAttribute(max dynamic smem)");
+    return smem_optin(reinterpret_cast<const void *>(kernel), bytes);
 }
 
 // Scratch (carries, look-back flags, partials, ticket) sized for the largest
@@ -1670,10 +1701,7 @@ int launch_merge(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
     using S = MergeShape<T, kMergeBlock, IPT>;
     auto kern = k_csr_merge<T, kMergeBlock, IPT>;
     SPX_TRY(ensure_merge_tiles(ctx, A, S::TILE, S::SLACK));
-    static std::once_flag once;
-    static int attr_st = SPX_OK;
-    std::call_once(once, [&] { attr_st = set_smem(kern, S::SMEM); });
-    SPX_TRY(attr_st);
+    SPX_TRY(set_smem(kern, S::SMEM));
     const int grid = grid_for(ctx, kern, kMergeBlock, S::SMEM, A->ntiles);
     SPX_TRY(ensure_scratch(ctx, A, A->ntiles, grid, sizeof(T)));
     return launch_k(kern, grid, kMergeBlock, S::SMEM, ctx->stream, A->nsplit > 0, (int)A->n,
@@ -1754,18 +1782,8 @@ int launch_rows_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const E
     constexpr int block = kRowsTile * TPR;
     SPX_TRY(ensure_rows_cap(ctx, A));
     // the dynamic shared memory may reach the opt-in limit less the static part
-    static std::once_flag once;
-    static int attr_st = SPX_OK, dyn_max = 0;
-    std::call_once(once, [&] {
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-        if (e == cudaSuccess) {
-            dyn_max = ctx->max_smem_optin - (int)fa.sharedSizeBytes;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-        }
-        attr_st = e == cudaSuccess ? SPX_OK : cuda_fail(e, "row-block CSR shared-memory limit");
-    });
-    SPX_TRY(attr_st);
+    int dyn_max = 0;
+    SPX_TRY(smem_optin(reinterpret_cast<const void *>(kern), -1, &dyn_max));
     const int64_t smem = rows_smem<T>(A, STAGES);
     if (smem > dyn_max)
         return fail(SPX_ERR_TOO_LARGE, "row-block CSR: a tile of 128 rows does not fit in shared memory");
@@ -1847,18 +1865,8 @@ int launch_coo_rows_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, co
 {
     auto kern = k_coo_rows<T, kRowsTile, MODE>;
     SPX_TRY(ensure_coo_rowtiles(ctx, A));
-    static std::once_flag once;
-    static int attr_st = SPX_OK, dyn_max = 0;
-    std::call_once(once, [&] {
-        cudaFuncAttributes fa;
-        cudaError_t er = cudaFuncGetAttributes(&fa, kern);
-        if (er == cudaSuccess) {
-            dyn_max = ctx->max_smem_optin - (int)fa.sharedSizeBytes;
-            er = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-        }
-        attr_st = er == cudaSuccess ? SPX_OK : cuda_fail(er, "row-block COO shared-memory limit");
-    });
-    SPX_TRY(attr_st);
+    int dyn_max = 0;
+    SPX_TRY(smem_optin(reinterpret_cast<const void *>(kern), -1, &dyn_max));
     const int64_t smem = coo_rows_smem<T>(A);
     if (smem > dyn_max)
         return fail(SPX_ERR_TOO_LARGE, "row-block COO: a tile of 128 rows does not fit in shared memory");
@@ -1889,10 +1897,7 @@ int launch_split_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const 
 {
     auto kern = k_csr_split<T, IPT, MODE>;
     const int smem = 8 * (32 * IPT + 32) * (4 + (int)sizeof(T));
-    static std::once_flag once;
-    static int attr_st = SPX_OK;
-    std::call_once(once, [&] { attr_st = set_smem(kern, smem); });
-    SPX_TRY(attr_st);
+    SPX_TRY(set_smem(kern, smem));
     SPX_TRY(ensure_hint(ctx, A, IPT));
     const int64_t nchunks = ceil_div(ceil_div(A->nnz, IPT), 32);
     int per_sm = 0;
@@ -1926,10 +1931,7 @@ int launch_coo_split_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, c
 {
     auto kern = k_coo_split<T, IPT, MODE>;
     const int smem = 8 * (32 * IPT + 32) * (8 + (int)sizeof(T));
-    static std::once_flag once;
-    static int attr_st = SPX_OK;
-    std::call_once(once, [&] { attr_st = set_smem(kern, smem); });
-    SPX_TRY(attr_st);
+    SPX_TRY(set_smem(kern, smem));
     const int64_t nchunks = ceil_div(ceil_div(A->coo_nnz, IPT), 32);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
@@ -2007,10 +2009,7 @@ int launch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi
 {
     using S = CooShape<T, kCooBlock, IPT>;
     auto kern = k_coo<T, kCooBlock, IPT>;
-    static std::once_flag once;
-    static int attr_st = SPX_OK;
-    std::call_once(once, [&] { attr_st = set_smem(kern, S::SMEM); });
-    SPX_TRY(attr_st);
+    SPX_TRY(set_smem(kern, S::SMEM));
     SPX_TRY(ensure_coo_tiles(ctx, A, S::TILE, S::SLACK));
     const int64_t ntiles = A->coo_ntiles;
     const int grid = grid_for(ctx, kern, kCooBlock, S::SMEM, ntiles);
@@ -2216,10 +2215,10 @@ template int spmv_launch<float>(spx_ctx *, const spx_matrix *, const float *, co
 
 // ------------------------------------------------------------------ SpMV without allocation
 // Some callers cannot allocate device memory at the point where they need a
-// product: code that runs while a CUDA graph is being captured, a real-time
-// loop whose memory is fixed up front, or a host framework that owns every
-// allocation and forbids libraries from calling cudaMalloc (which may also
-// synchronise the device).  For them this entry point runs the merge-path
+// product: a real-time loop whose memory is fixed up front (an allocation can
+// block, fail or synchronise the device), or a host framework that owns every
+// allocation and forbids libraries from calling cudaMalloc.  For them this
+// entry point runs the merge-path
 // CSR kernel straight from the caller's CSR arrays with all of its scratch
 // (tile map, per-tile carries, look-back flags) in one fixed array in device
 // global memory that the library declares at file scope.  Every GPU that
@@ -2231,7 +2230,8 @@ constexpr int kNoAllocIpt = 8;
 constexpr int64_t kNoAllocMaxTiles = SPX_NOALLOC_MAX_TILES;
 constexpr size_t kNoAllocBytes = 1u << 20;  // 1 MiB
 
-// scratch layout: tiles int2[max+1] | carry_val 8B[max] | carry_row int[max] | flags int[max] | counters
+// scratch layout: tiles int2[max+1] | carry_val 8B[max] | carry_row int[max] | flags int[max] | counters,
+// and the error word of the bounded waits in the last 64 bytes
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 static_assert((kNoAllocMaxTiles + 1) * 8 + kNoAllocMaxTiles * (8 + 4 + 4) + 256 <= (int64_t)kNoAllocBytes,
               "no-alloc scratch too small for its tile limit");
@@ -2254,6 +2254,16 @@ int noalloc_scratch(int dev, void **out)
     return SPX_OK;
 }
 
+// After the product: if any bounded wait of this call gave up (its bit is in
+// *err, cleared at the start of the call), y is not the product, and every
+// element becomes NaN so the caller sees the failure in the result itself.
+template <class T> __global__ void __launch_bounds__(256) k_noalloc_poison(const unsigned *err, int64_t n, T *y)
+{
+    if (ldcg(err) == 0u) return;
+    const T nan = T(NAN);
+    for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) y[i] = nan;
+}
+
 template <class T>
 int spmv_noalloc(cudaStream_t st, void *scratch, int64_t n, int64_t nnz, const int *rp, const int *col, const T *val,
                  const T *x, T *y, int sm_count, unsigned *err)
@@ -2270,13 +2280,11 @@ int spmv_noalloc(cudaStream_t st, void *scratch, int64_t n, int64_t nnz, const i
     // the array keeps the previous call's contents: flags and counters must start at zero
     SPX_CUDA(cudaMemsetAsync(flags, 0, (size_t)ntiles * 4, st));
     SPX_CUDA(cudaMemsetAsync(counters, 0, 64, st));
+    SPX_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
     k_merge_tiles<<<(int)ceil_div(ntiles + 1, 256), 256, 0, st>>>((int)n, (int)nnz, rp, S::TILE, S::SLACK, (int)ntiles,
                                                                  tiles, counters);
     SPX_CUDA(cudaGetLastError());
-    static std::once_flag once;
-    static int attr_st = SPX_OK;
-    std::call_once(once, [&] { attr_st = set_smem(kern, S::SMEM); });
-    SPX_TRY(attr_st);
+    SPX_TRY(set_smem(kern, S::SMEM));
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMergeBlock, S::SMEM) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -2285,8 +2293,12 @@ int spmv_noalloc(cudaStream_t st, void *scratch, int64_t n, int64_t nnz, const i
     Epi<T> e;
     e.y = y;
     // the split count is not read back (no synchronisation): always launch cooperatively
-    return launch_k(kern, (int)grid, kMergeBlock, S::SMEM, st, true, (int)n, rp, col, val, x, (const int2 *)tiles,
-                    (int)ntiles, carry_row, carry_val, flags, (T *)nullptr, counters + 1, err, e);
+    SPX_TRY(launch_k(kern, (int)grid, kMergeBlock, S::SMEM, st, true, (int)n, rp, col, val, x, (const int2 *)tiles,
+                     (int)ntiles, carry_row, carry_val, flags, (T *)nullptr, counters + 1, err, e));
+    const int pgrid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)sm_count * 4);
+    k_noalloc_poison<T><<<pgrid, 256, 0, st>>>(err, n, y);
+    SPX_CUDA(cudaGetLastError());
+    return SPX_OK;
 }
 
 }  // namespace

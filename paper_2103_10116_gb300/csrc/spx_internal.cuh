@@ -27,6 +27,14 @@ int cuda_fail(cudaError_t e, const char *what);
         if (s_ != SPX_OK) return s_;                                     \
     } while (0)
 
+// ------------------------------------------------------------------ shared-memory opt-in
+// cudaFuncSetAttribute acts on the current device only, so the opt-in to more
+// than 48 KB of dynamic shared memory is made once per (kernel, device) pair
+// on the device current at the call.  bytes < 0 asks for the device's opt-in
+// limit less the kernel's static shared memory.  *granted, if given, receives
+// the limit set for this pair.
+int smem_optin(const void *kernel, int bytes, int *granted = nullptr);
+
 // ------------------------------------------------------------------ device error word
 // Bit flags a kernel may set in ctx->dev_err instead of trapping.
 enum : unsigned { DEVERR_MBAR_TIMEOUT = 1u, DEVERR_BOUNDS = 2u, DEVERR_QUEUE_TIMEOUT = 4u };

@@ -75,3 +75,24 @@ def assert_spmv_close(y, yref, bound, rel):
     ny = np.linalg.norm(yref)
     if ny > 0:
         assert np.linalg.norm(y - yref) <= rel * ny
+
+
+# ---------------------------------------------------------------- residual slack
+def residual_limit(rp, col, val, b, x, tol):
+    """Largest oracle-formed relative residual ||b - A x|| / ||b|| that is
+    consistent with a solver that reported its own FP64 true residual <= tol.
+
+    The two evaluations of r = b - A x (the library's and the oracle's) sum the
+    same terms in different orders.  Each lies within gamma_{L+1} (|b| + |A||x|)
+    of the exact residual, componentwise, where L is the longest row and
+    gamma_k = k u / (1 - k u), u = 2^-53 (Higham, Accuracy and Stability of
+    Numerical Algorithms, 2nd ed., section 3.5).  Their difference is then at
+    most 2 gamma_{L+1} || |b| + |A||x| ||_2, which is added to tol after dividing
+    by ||b||."""
+    import oracle
+    rp = np.asarray(rp)
+    L = int(np.diff(rp).max()) if rp.shape[0] > 1 else 0
+    u = 2.0 ** -53
+    g = (L + 1) * u / (1 - (L + 1) * u)
+    s = np.abs(np.asarray(b, dtype=np.float64)) + oracle.spmv_absbound(rp, col, val, x)
+    return tol + 2 * g * np.linalg.norm(s) / np.linalg.norm(b)

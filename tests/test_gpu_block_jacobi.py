@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2103_10116_gb300 import synth
-from tests._helpers import to_dense
+from tests._helpers import to_dense, residual_limit
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -135,7 +135,7 @@ def test_block_jacobi_solve_matches_oracle(spx, ctx, solver, fmt):
                              block_size=bs)
         _, oinfo = _oracle(solver, rp, col, val, b, tol=1e-10, maxit=20000, precond="block_jacobi", block_size=bs)
         assert info.status == spx.SPX_CONVERGED and oinfo.status == oracle.CONVERGED, (info, oinfo)
-        assert info.relres_true <= 1e-10 and _relres(rp, col, val, b, x.cpu().numpy()) <= 1.05e-10
+        assert info.relres_true <= 1e-10 and _relres(rp, col, val, b, x.cpu().numpy()) <= residual_limit(rp, col, val, b, x.cpu().numpy(), 1e-10)
         slack = max(4, oinfo.iterations // (5 if solver == "cgs" else 10))
         assert abs(info.iterations - oinfo.iterations) <= slack, (info, oinfo)
         # the blocks carry the strong couplings: block-Jacobi beats Jacobi
@@ -224,7 +224,7 @@ def test_block_jacobi_mixed_precision(spx, ctx, solver):
         info = spx.spx_solve(ctx, A, _t(b), x, solver, 1e-10, 20000, restart=30, precision="mixed",
                              precond="block_jacobi", block_size=8)
         assert info.status == spx.SPX_CONVERGED, info
-        assert _relres(rp, col, val, b, x.cpu().numpy()) <= 1.05e-10
+        assert _relres(rp, col, val, b, x.cpu().numpy()) <= residual_limit(rp, col, val, b, x.cpu().numpy(), 1e-10)
     finally:
         spx.spx_matrix_destroy(A)
 
@@ -341,7 +341,7 @@ def test_adaptive_solve_matches_oracle(spx, ctx, solver):
         _, oinfo = _oracle(solver, rp, col, val, b, tol=1e-10, maxit=20000, precond="adaptive_block_jacobi",
                            block_size=bs)
         assert info.status == spx.SPX_CONVERGED and oinfo.status == oracle.CONVERGED, (info, oinfo)
-        assert _relres(rp, col, val, b, x.cpu().numpy()) <= 1.05e-10
+        assert _relres(rp, col, val, b, x.cpu().numpy()) <= residual_limit(rp, col, val, b, x.cpu().numpy(), 1e-10)
         assert abs(info.iterations - oinfo.iterations) <= max(4, oinfo.iterations // 10), (info, oinfo)
     finally:
         spx.spx_matrix_destroy(A)

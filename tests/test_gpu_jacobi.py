@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 from paper_2103_10116_gb300 import synth
+from tests._helpers import residual_limit
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -78,7 +79,7 @@ def test_jacobi_solve_matches_oracle(spx, ctx, solver, fmt):
         _, oinfo = _oracle(solver, rp, col, val, b, tol=1e-10, maxit=20000, precond="jacobi")
         assert info.status == spx.SPX_CONVERGED, info
         xh = x.cpu().numpy()
-        assert info.relres_true <= 1e-10 and _relres(rp, col, val, b, xh) <= 1.05e-10
+        assert info.relres_true <= 1e-10 and _relres(rp, col, val, b, xh) <= residual_limit(rp, col, val, b, xh, 1e-10)
         slack = max(4, oinfo.iterations // (5 if solver == "cgs" else 10))
         assert abs(info.iterations - oinfo.iterations) <= slack, (info, oinfo)
         # the preconditioner pays off on these badly scaled matrices
@@ -133,7 +134,7 @@ def test_jacobi_mixed_precision(spx, ctx, solver):
         info = spx.spx_solve(ctx, A, _t(b), x, solver, 1e-10, 20000, restart=30, precision="mixed",
                              precond="jacobi")
         assert info.status == spx.SPX_CONVERGED, info
-        assert _relres(rp, col, val, b, x.cpu().numpy()) <= 1.05e-10
+        assert _relres(rp, col, val, b, x.cpu().numpy()) <= residual_limit(rp, col, val, b, x.cpu().numpy(), 1e-10)
     finally:
         spx.spx_matrix_destroy(A)
 
