@@ -99,9 +99,15 @@ typedef enum {
     SPX_KERNEL_CSR_MERGE = 2,   /* CSR: merge-path split of rows + nonzeros, TMA-staged tiles */
     SPX_KERNEL_ELL = 3,         /* ELL / HYB ELL part: one thread per `param` rows (1, 2 or 4) */
     SPX_KERNEL_COO = 4,         /* COO / HYB COO part: 1 = row-block (COO format; the default for short rows
-                                   of similar length), 8/16 = warp-independent split (default otherwise: 8),
+                                   of similar length), 8/16 = warp-independent split,
+                                   216/232 = the split on tile-transposed copies of the COO arrays with 16/32
+                                   entries per lane (built on first use; default otherwise: 216),
                                    104/108/116 = tiled segmented reduction with 4/8/16 items per thread */
     SPX_KERNEL_CSR_SPLIT = 5,   /* CSR: each lane takes `param` (8 or 16) consecutive nonzeros, warps independent */
+    SPX_KERNEL_CSR_TILED = 7,   /* CSR: as SPX_KERNEL_CSR_SPLIT with `param` (16 or 32) nonzeros per lane, on
+                                   a tile-transposed copy of the nonzeros with per-granule row descriptors
+                                   (built on first use; one more copy of the column indices and values).
+                                   The automatic choice for heavy-tailed rows, with 32 */
     SPX_KERNEL_CSR_ROWS = 6     /* CSR: tiles of 128 rows bulk-copied to shared memory, 1, 2 or 4 threads
                                    per row (rows of similar length; SPX_ERR_TOO_LARGE if a tile's nonzeros
                                    do not fit in shared memory); param = stages + 10 x threads per row,

@@ -46,19 +46,49 @@ class SolveInfo:
     relres_true: float
 
 
-def build(mutant: int = 0) -> str:
+def build(mutant: int = 0, openmp: bool = False) -> str:
     """Compile the oracle with gcc; ``mutant`` > 0 plants a known mistake (used
-    only by the mutation tests that show the pins catch it)."""
+    only by the mutation tests that show the pins catch it).  ``openmp`` builds
+    the all-cores variant of the plain SpMV used by the CPU baseline (same
+    arithmetic, rows shared among threads)."""
     os.makedirs(_BUILD, exist_ok=True)
-    out = os.path.join(_BUILD, f"liboracle_m{mutant}.so")
+    out = os.path.join(_BUILD, "liboracle_omp.so" if openmp else f"liboracle_m{mutant}.so")
     if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
         return out
     tmp = out + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           f"-DORC_MUTANT={mutant}", _SRC, "-o", tmp, "-lm"]
+           f"-DORC_MUTANT={mutant}"]
+    if openmp:
+        cmd += ["-O3", "-fopenmp", "-DORC_OPENMP"]
+    cmd += [_SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
+
+
+_OMP = None
+
+
+def spmv_csr_plain_omp(rp, col, val, x) -> np.ndarray:
+    """spmv_csr_plain on all host cores (OpenMP over rows; the same bits)."""
+    global _OMP
+    with _LOCK:
+        if _OMP is None:
+            _OMP = C.CDLL(build(openmp=True))
+            _OMP.orc_spmv_csr_plain.restype = None
+            _OMP.orc_spmv_csr_plain.argtypes = [C.c_int64] + [C.c_void_p] * 5
+    rp, col, val = _csr(rp, col, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = rp.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    _OMP.orc_spmv_csr_plain(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(x), _ptr(y))
+    return y
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else the host's cores)."""
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
 def _lib(mutant: int = 0) -> C.CDLL:

@@ -20,7 +20,9 @@
  *     residual and update.
  *
  * Build flags must keep IEEE semantics: -O2 -ffp-contract=off, no fast-math,
- * so that x86-64 and aarch64 hosts produce identical bits.
+ * so that x86-64 and aarch64 hosts produce identical bits.  A second build with
+ * -DORC_OPENMP -fopenmp (same arithmetic) times the plain SpMV on all host cores
+ * for the CPU baseline.
  *
  * Pins (the tests in tests/test_oracle_*.py) tie every function here to facts
  * that do not come from this file: exact dense products on integer data,
@@ -120,10 +122,16 @@ void orc_spmv_csr_absbound(int64_t n, const int32_t *rp, const int32_t *col, con
 }
 
 /* Plain index-order SpMV without compensation, the literal definition.  Used
- * only by the CPU-baseline timing and the fixed-iteration solver loops. */
+ * only by the CPU-baseline timing and the fixed-iteration solver loops.  In the
+ * build with -DORC_OPENMP (the all-cores CPU baseline) rows are shared among
+ * threads; each row is still summed alone, in index order, so the result is
+ * the same bits. */
 static void spmv_plain(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
                        const double *x, double *y)
 {
+#ifdef ORC_OPENMP
+#pragma omp parallel for schedule(static, 1024)
+#endif
     for (int64_t i = 0; i < n; ++i) {
         double s = 0.0;
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += val[k] * x[col[k]];

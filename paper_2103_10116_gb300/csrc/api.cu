@@ -321,7 +321,8 @@ void free_matrix_arrays(spx_matrix *A)
                     &A->ell_val,  &A->ell_val32, &A->coo_row,  &A->coo_col,   &A->coo_val,
                     &A->coo_val32, &A->tiles,    &A->carry_row, &A->carry_val, &A->partials,
                     &A->ticket,   &A->stage_x,   &A->stage_y,   &A->coo_tiles, &A->flags,
-                    &A->hint,     &A->coo_rowtiles};
+                    &A->hint,     &A->coo_rowtiles, &A->tc_col, &A->tc_val, &A->tc_val32, &A->tc_row,
+                    &A->tc_mask,  &A->empty_rows, &A->ct_row, &A->ct_col, &A->ct_val, &A->ct_val32};
     for (DBuf *b : bufs) dbuf_free(c, *b);
 }
 
@@ -658,7 +659,7 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     switch (A->format) {
     case SPX_CSR:
         okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_CSR_VECTOR || kernel == SPX_KERNEL_CSR_MERGE ||
-              kernel == SPX_KERNEL_CSR_SPLIT || kernel == SPX_KERNEL_CSR_ROWS;
+              kernel == SPX_KERNEL_CSR_SPLIT || kernel == SPX_KERNEL_CSR_ROWS || kernel == SPX_KERNEL_CSR_TILED;
         break;
     case SPX_ELL: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_ELL; break;
     case SPX_COO: okk = kernel == SPX_KERNEL_AUTO || kernel == SPX_KERNEL_COO; break;
@@ -668,11 +669,15 @@ extern "C" int spx_matrix_set_kernel(spx_matrix *A, int kernel, int param)
     if (kernel == SPX_KERNEL_CSR_VECTOR && param != 0 &&
         !(param == 1 || param == 2 || param == 4 || param == 8 || param == 16 || param == 32))
         return fail(SPX_ERR_INVALID, "CSR vector width must be 0 (auto) or 1..32, a power of 2");
+    if (kernel == SPX_KERNEL_CSR_TILED && param != 0 && !(param == 16 || param == 32))
+        return fail(SPX_ERR_INVALID, "tiled CSR nonzeros per lane must be 0 (auto: 32), 16 or 32");
     if (kernel == SPX_KERNEL_CSR_MERGE && param != 0 && !(param == 4 || param == 8 || param == 16))
         return fail(SPX_ERR_INVALID, "merge items per thread must be 0 (auto), 4, 8 or 16");
     if (kernel == SPX_KERNEL_COO && param != 0 &&
-        !(param == 1 || param == 8 || param == 16 || param == 104 || param == 108 || param == 116))
-        return fail(SPX_ERR_INVALID, "COO parameter must be 0 (auto), 1 (row-block), 8, 16 (split) or 104, 108, 116 (tiled)");
+        !(param == 1 || param == 8 || param == 16 || param == 216 || param == 232 || param == 104 || param == 108 ||
+          param == 116))
+        return fail(SPX_ERR_INVALID, "COO parameter must be 0 (auto), 1 (row-block), 8, 16 (split), 216, 232 "
+                                     "(tiled split) or 104, 108, 116 (tiled segmented reduction)");
     if (kernel == SPX_KERNEL_CSR_ROWS && param != 0 &&
         !(param == 1 || param == 2 || param == 12 || param == 22 || param == 42))
         return fail(SPX_ERR_INVALID, "row-block parameter must be 0 (auto), 1, 2, 12, 22 or 42");
@@ -696,7 +701,7 @@ std::vector<std::pair<int, int>> tune_candidates(const spx_matrix *A)
         c = {{SPX_KERNEL_CSR_ROWS, 1}, {SPX_KERNEL_CSR_ROWS, 2}, {SPX_KERNEL_CSR_ROWS, 22},
              {SPX_KERNEL_CSR_ROWS, 42}, {SPX_KERNEL_CSR_MERGE, 4},
              {SPX_KERNEL_CSR_MERGE, 8}, {SPX_KERNEL_CSR_MERGE, 16}, {SPX_KERNEL_CSR_SPLIT, 8},
-             {SPX_KERNEL_CSR_SPLIT, 16}};
+             {SPX_KERNEL_CSR_SPLIT, 16}, {SPX_KERNEL_CSR_TILED, 16}, {SPX_KERNEL_CSR_TILED, 32}};
         for (int sw = 1; sw <= 32; sw *= 2) c.push_back({SPX_KERNEL_CSR_VECTOR, sw});
         break;
     case SPX_ELL:
@@ -704,12 +709,12 @@ std::vector<std::pair<int, int>> tune_candidates(const spx_matrix *A)
         if (A->dtype == SPX_F32) c.push_back({SPX_KERNEL_ELL, 4});
         break;
     case SPX_COO:
-        c = {{SPX_KERNEL_COO, 1}, {SPX_KERNEL_COO, 8}, {SPX_KERNEL_COO, 16}, {SPX_KERNEL_COO, 104},
-             {SPX_KERNEL_COO, 108}, {SPX_KERNEL_COO, 116}};
+        c = {{SPX_KERNEL_COO, 1},   {SPX_KERNEL_COO, 8},   {SPX_KERNEL_COO, 16},  {SPX_KERNEL_COO, 216},
+             {SPX_KERNEL_COO, 232}, {SPX_KERNEL_COO, 104}, {SPX_KERNEL_COO, 108}, {SPX_KERNEL_COO, 116}};
         break;
     default:  // HYB: its ELL part's rows per thread, or its COO part's kernel
-        c = {{SPX_KERNEL_ELL, 1}, {SPX_KERNEL_ELL, 2}, {SPX_KERNEL_COO, 8}, {SPX_KERNEL_COO, 16},
-             {SPX_KERNEL_COO, 104}, {SPX_KERNEL_COO, 116}};
+        c = {{SPX_KERNEL_ELL, 1},   {SPX_KERNEL_ELL, 2},   {SPX_KERNEL_COO, 8},   {SPX_KERNEL_COO, 16},
+             {SPX_KERNEL_COO, 216}, {SPX_KERNEL_COO, 232}, {SPX_KERNEL_COO, 104}, {SPX_KERNEL_COO, 116}};
         if (A->dtype == SPX_F32) c.push_back({SPX_KERNEL_ELL, 4});
         break;
     }

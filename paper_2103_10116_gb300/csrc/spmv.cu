@@ -1055,6 +1055,264 @@ __global__ void __launch_bounds__(256)
 #undef SPX_SPLIT_EMIT
 }
 
+// ------------------------------------------------------------------ tiled nnz-split CSR
+// The lane-granule decomposition of k_csr_split on a copy of the nonzeros
+// laid out for it once per matrix.  In a chunk of 32 granules of IPT
+// consecutive nonzeros, slot u of lane l is stored at
+//     (u / VEC) * 32 VEC + l VEC + u % VEC,  VEC = elements per 16 bytes,
+// so one 16-byte load per lane reads VEC slots of all 32 lanes coalesced, and
+// the chunk goes straight to registers (no shared-memory staging, whose
+// stores and loads share the L1 data path with the random gathers of x).
+// Row boundaries come from a per-granule descriptor instead of row pointers:
+// trow[g] = the row holding the granule's first nonzero (bit 31 set when an
+// empty row lies between two rows of the granule), tmask[g] bit u = a row
+// starts at slot u.  So the only dependent loads in a granule are the
+// gathers.  Empty rows are listed once per matrix and written (t = 0) by all
+// threads at the start; flagged granules step over them through the row
+// pointers.  Lanes, chunks and warp ranges are combined as in k_csr_split.
+// (Storing a tile transposed with per-tile row descriptors follows the CSR5
+// format of Liu and Vinter, ICS 2015; written from that description.)
+template <class T, int IPT, int MODE>
+__global__ void __launch_bounds__(256)
+    k_csr_tiled(int n, int nnz, const int *__restrict__ rp, const int *__restrict__ tcol,
+                const T *__restrict__ tval, const int *__restrict__ trow, const unsigned *__restrict__ tmask,
+                const int *__restrict__ empty, int nempty, const T *__restrict__ x, int nchunks, int *carry_row_w,
+                T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e)
+{
+    constexpr int CH = 8;                    // gathers issued together
+    constexpr int VC = 4;                    // column slots per 16-byte load
+    constexpr int VV = 16 / (int)sizeof(T);  // value slots per 16-byte load
+    constexpr int NW = 256 / 32;
+    constexpr int CHUNK = 32 * IPT;
+    static_assert(IPT % CH == 0 && CH % VC == 0 && CH % VV == 0 && IPT <= 32, "tiled CSR shape");
+    if (e.skip && *e.skip) return;
+    __shared__ int s_cr[NW][32];
+    __shared__ T s_cv[NW][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int W = gridDim.x * NW;
+    const int w = blockIdx.x * NW + wib;
+    T d0 = T(0), d1 = T(0);
+    for (int q = blockIdx.x * 256 + threadIdx.x; q < nempty; q += gridDim.x * 256)
+        out_row<MODE>(e, empty[q], T(0), d0, d1);
+    const int c_begin = (int)(((int64_t)nchunks * w) / W), c_end = (int)(((int64_t)nchunks * (w + 1)) / W);
+
+    // the range's first row, if it began before the range, is completed last
+    const int64_t range_a = (int64_t)c_begin * CHUNK;
+    int first_row = -1;
+    bool range_inside = false;
+    if (c_begin < c_end && range_a < nnz) {
+        first_row = trow[(int64_t)c_begin * 32] & 0x7fffffff;
+        range_inside = (tmask[(int64_t)c_begin * 32] & 1u) == 0u;
+    }
+    T first_val = T(0);
+    bool first_ready = false;
+    int run_row = -1;
+    T run_val = T(0);
+
+    for (int c = c_begin; c < c_end; ++c) {
+        const int64_t g = (int64_t)c * 32 + lane;
+        const int64_t a = g * IPT;
+        const int cnt = (int)max((int64_t)0, min((int64_t)IPT, (int64_t)nnz - a));
+        const bool active = cnt > 0;
+        const int rd = trow[g];
+        const unsigned m = tmask[g];
+        const bool ends_b = a + IPT >= nnz || (tmask[g + 1] & 1u) != 0u;  // the last row ends with the granule
+        const bool slow = rd < 0;
+        int r = rd & 0x7fffffff;
+        const int rstart = r;
+        const bool pend_possible = active && (m & 1u) == 0u;
+        T sum = T(0), pend = T(0);
+        bool first = true, has_pend = false;
+        const int *cp = tcol + (int64_t)c * CHUNK + lane * VC;
+        const T *vp = tval + (int64_t)c * CHUNK + lane * VV;
+#define SPX_TILED_EMIT(row_, s_)                       \
+    do {                                               \
+        if (first && pend_possible) {                  \
+            pend = (s_);                               \
+            has_pend = true;                           \
+        } else {                                       \
+            out_row<MODE>(e, (row_), (s_), d0, d1);    \
+        }                                              \
+        first = false;                                 \
+    } while (0)
+#pragma unroll
+        for (int kk = 0; kk < IPT; kk += CH) {
+            int cc[CH];
+            T v[CH], xv[CH];
+#pragma unroll
+            for (int q = 0; q < CH / VC; ++q) {
+                const int4 t4 = __ldcs(reinterpret_cast<const int4 *>(cp + (kk / VC + q) * 32 * VC));
+                cc[4 * q + 0] = t4.x;
+                cc[4 * q + 1] = t4.y;
+                cc[4 * q + 2] = t4.z;
+                cc[4 * q + 3] = t4.w;
+            }
+#pragma unroll
+            for (int q = 0; q < CH / VV; ++q) {
+                if constexpr (sizeof(T) == 8) {
+                    const double2 t2 = __ldcs(reinterpret_cast<const double2 *>(vp + (kk / VV + q) * 32 * VV));
+                    v[2 * q + 0] = t2.x;
+                    v[2 * q + 1] = t2.y;
+                } else {
+                    const float4 t4 = __ldcs(reinterpret_cast<const float4 *>(vp + (kk / VV + q) * 32 * VV));
+                    v[4 * q + 0] = t4.x;
+                    v[4 * q + 1] = t4.y;
+                    v[4 * q + 2] = t4.z;
+                    v[4 * q + 3] = t4.w;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) xv[u] = kk + u < cnt ? __ldg(x + cc[u]) : T(0);
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int sl = kk + u;
+                if (sl > 0 && sl < cnt && ((m >> sl) & 1u)) {  // a row starts here: the previous one is complete
+                    SPX_TILED_EMIT(r, sum);
+                    sum = T(0);
+                    if (slow) {  // step over empty rows (written at the start)
+                        ++r;
+                        while (rp[r + 1] == rp[r]) ++r;
+                    } else {
+                        ++r;
+                    }
+                }
+                if (sl < cnt) sum = fma(v[u], xv[u], sum);
+            }
+        }
+        int cr = kEmpty;
+        if (active) {
+            if (ends_b) {
+                SPX_TILED_EMIT(r, sum);
+                sum = T(0);
+                cr = kNoCarry;
+            } else {
+                cr = r;
+            }
+        }
+#undef SPX_TILED_EMIT
+        s_cr[wib][lane] = cr;
+        s_cv[wib][lane] = sum;
+        __syncwarp();
+        int nrow;
+        T nval;
+        const T tot = chunk_combine<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val, nrow,
+                                       nval);
+        if (has_pend) {
+            if (range_inside && rstart == first_row) {
+                first_val = tot;
+                first_ready = true;
+            } else {
+                out_row<MODE>(e, rstart, tot, d0, d1);
+            }
+        }
+        run_row = nrow;
+        run_val = nval;
+        const unsigned fm = __ballot_sync(0xffffffffu, first_ready);
+        if (fm) {
+            const int src = __ffs(fm) - 1;
+            first_val = __shfl_sync(0xffffffffu, first_val, src);
+            first_ready = true;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && run_row >= 0) {
+        carry_row_w[w] = run_row;
+        carry_val_w[w] = run_val;
+        flag_publish(flags + w);
+    }
+    if (lane == 0 && range_inside && first_ready) {
+        T tot = first_val;
+        const int rs = rp[first_row];
+        for (int wp = w - 1; wp >= 0; --wp) {
+            const int pb = (int)(((int64_t)nchunks * wp) / W), pe = (int)(((int64_t)nchunks * (wp + 1)) / W);
+            if (pb >= pe) continue;
+            if (!flag_wait(flags + wp, err)) break;
+            tot += ldcg(carry_val_w + wp);
+            flags[wp] = 0;
+            if (!(rs < (int64_t)pb * CHUNK)) break;
+        }
+        out_row<MODE>(e, first_row, tot, d0, d1);
+    }
+    if constexpr (MODE == 0 || MODE >= 4)
+        if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
+}
+
+// Tiled copy of the nonzeros: source entry k (thread k) goes to its slot in
+// the transposed chunk layout; the padded slots past nnz hold column 0 and
+// value 0 (never used: the kernel predicates on the granule's count).
+template <class T, int VEC>
+__global__ void k_tile_transpose(int64_t nnz, int64_t total, int ipt, const T *__restrict__ src, T *__restrict__ dst)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int64_t chunk = 32LL * ipt;
+    const int64_t c = k / chunk;
+    const int wi = (int)(k - c * chunk);
+    const int l = wi / ipt, u = wi - l * ipt;
+    dst[c * chunk + (int64_t)(u / VEC) * 32 * VEC + l * VEC + u % VEC] = k < nnz ? src[k] : T(0);
+}
+
+// Granule descriptors, step 1: trow[g] = the row holding nonzero g * ipt
+// (the first row r with rp[r+1] > g * ipt, so never an empty row); tmask
+// cleared.  Granules past nnz get row 0.
+__global__ void k_tile_rows(int n, int64_t nnz, const int *__restrict__ rp, int ipt, int64_t ngran, int *trow,
+                            unsigned *tmask)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g > ngran) return;
+    tmask[g] = 0u;
+    if (g == ngran) return;
+    const int64_t a = g * ipt;
+    int r = 0;
+    if (a < nnz) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((int64_t)rp[mid + 1] > a) hi = mid;
+            else lo = mid + 1;
+        }
+        r = lo;
+    }
+    trow[g] = r;
+}
+
+// Step 2, one thread per row: a non-empty row sets the bit of its first slot;
+// an empty row that falls strictly inside a granule flags that granule.
+__global__ void k_tile_marks(int n, int64_t nnz, const int *__restrict__ rp, int ipt, int *trow, unsigned *tmask)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int p = rp[r];
+    const int64_t g = p / ipt;
+    const int u = p - (int)(g * ipt);
+    if (rp[r + 1] > p) atomicOr(tmask + g, 1u << u);
+    else if (u != 0 && p < nnz) atomicOr(reinterpret_cast<unsigned *>(trow + g), 0x80000000u);
+}
+
+// Empty rows in increasing order (one block: deterministic, so the kernels'
+// dot products sum them in a fixed order).  *count receives their number.
+__global__ void __launch_bounds__(1024) k_empty_rows(int n, const int *__restrict__ rp, int *out, int *count)
+{
+    __shared__ int s[1024];
+    const int t = threadIdx.x;
+    const int64_t r0 = (int64_t)n * t / 1024, r1 = (int64_t)n * (t + 1) / 1024;
+    int c = 0;
+    for (int64_t r = r0; r < r1; ++r) c += rp[r + 1] == rp[r];
+    s[t] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan
+        const int v = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    int pos = s[t] - c;
+    if (out)
+        for (int64_t r = r0; r < r1; ++r)
+            if (rp[r + 1] == rp[r]) out[pos++] = (int)r;
+    if (t == 1023) *count = s[1023];
+}
+
 // ------------------------------------------------------------------ nnz-split COO (warp-independent)
 // The COO counterpart of k_csr_split: lane granules of IPT consecutive
 // entries, the row of every entry read from the row array.  A lane ends row r
@@ -1223,6 +1481,181 @@ __global__ void __launch_bounds__(256)
     if constexpr (MODE == 0 || MODE >= 4)
         if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
 #undef SPX_COO_OUT
+}
+
+// ------------------------------------------------------------------ tiled nnz-split COO
+// k_coo_split on tile-transposed copies of the row, column and value arrays
+// (the layout of k_csr_tiled): a lane's granule arrives by coalesced 16-byte
+// loads straight into registers.  Row boundaries come from the row indices
+// themselves, as the COO format defines them; the rows on either side of the
+// granule (entries a-1 and b) are read from the plain row array.  Rows without
+// entries are written by the lane that sees the jump, carries as in k_coo_split.
+template <class T, int IPT, int MODE>
+__global__ void __launch_bounds__(256, 4)
+    k_coo_tiled(int n, int nnz, const int *__restrict__ crow, const int *__restrict__ trowi,
+                const int *__restrict__ tcol, const T *__restrict__ tval, const T *__restrict__ x, int nchunks,
+                int *carry_row_w, T *carry_val_w, int *flags, T *partials, unsigned *ticket, unsigned *err, Epi<T> e)
+{
+    constexpr bool add_mode = MODE == 2 || MODE == 3;
+    constexpr int CH = sizeof(T) == 8 ? 4 : 8;
+    constexpr int VC = 4, VV = 16 / (int)sizeof(T);
+    constexpr int NW = 256 / 32;
+    constexpr int CHUNK = 32 * IPT;
+    static_assert(IPT % CH == 0 && CH % VC == 0 && CH % VV == 0 && IPT <= 32, "tiled COO shape");
+    if (e.skip && *e.skip) return;
+    __shared__ int s_cr[NW][32];
+    __shared__ T s_cv[NW][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int W = gridDim.x * NW;
+    const int w = blockIdx.x * NW + wib;
+    const int c_begin = (int)(((int64_t)nchunks * w) / W), c_end = (int)(((int64_t)nchunks * (w + 1)) / W);
+    T d0 = T(0), d1 = T(0);
+
+    const int64_t range_a = (int64_t)c_begin * CHUNK;
+    int first_row = -1;
+    bool range_inside = false;
+    if (c_begin < c_end && range_a < nnz) {
+        first_row = crow[range_a];
+        range_inside = range_a > 0 && crow[range_a - 1] == first_row;
+    }
+    T first_val = T(0);
+    bool first_ready = false;
+    int run_row = -1;
+    T run_val = T(0);
+
+    for (int c = c_begin; c < c_end; ++c) {
+        const int64_t g = (int64_t)c * 32 + lane;
+        const int64_t a = g * IPT;
+        const int cnt = (int)max((int64_t)0, min((int64_t)IPT, (int64_t)nnz - a));
+        const bool active = cnt > 0;
+        const int b = (int)(a + cnt);
+        const int prev = active && a > 0 ? crow[a - 1] : -1;   // row of the entry before the granule
+        const int nr = active && b < nnz ? crow[b] : n;        // row of the entry after it
+        const int *rq = trowi + (int64_t)c * CHUNK + lane * VC;
+        const int *cp = tcol + (int64_t)c * CHUNK + lane * VC;
+        const T *vp = tval + (int64_t)c * CHUNK + lane * VV;
+        int r = active ? __ldcs(rq) : n;
+        const bool pend_possible = active && prev == r;
+        const int rstart = r;
+        T sum = T(0), pend = T(0);
+        bool first = true, has_pend = false;
+#define SPX_CT_EMIT(row_, s_)                              \
+    do {                                                   \
+        if (first && pend_possible) {                      \
+            pend = (s_);                                   \
+            has_pend = true;                               \
+        } else {                                           \
+            out_row<MODE>(e, (row_), (s_), d0, d1);        \
+        }                                                  \
+        first = false;                                     \
+    } while (0)
+        if (!add_mode && active && prev + 1 < r)  // rows without entries before this granule's first row
+            for (int q = prev + 1; q < r; ++q) out_row<MODE>(e, q, T(0), d0, d1);
+        int cr = kEmpty;
+        if (active) {
+#pragma unroll
+            for (int kk = 0; kk < IPT; kk += CH) {
+                int rr[CH], cc[CH];
+                T v[CH], xv[CH];
+#pragma unroll
+                for (int q = 0; q < CH / VC; ++q) {
+                    const int4 r4 = __ldcs(reinterpret_cast<const int4 *>(rq + (kk / VC + q) * 32 * VC));
+                    const int4 c4 = __ldcs(reinterpret_cast<const int4 *>(cp + (kk / VC + q) * 32 * VC));
+                    rr[4 * q + 0] = r4.x;
+                    rr[4 * q + 1] = r4.y;
+                    rr[4 * q + 2] = r4.z;
+                    rr[4 * q + 3] = r4.w;
+                    cc[4 * q + 0] = c4.x;
+                    cc[4 * q + 1] = c4.y;
+                    cc[4 * q + 2] = c4.z;
+                    cc[4 * q + 3] = c4.w;
+                }
+#pragma unroll
+                for (int q = 0; q < CH / VV; ++q) {
+                    if constexpr (sizeof(T) == 8) {
+                        const double2 t2 = __ldcs(reinterpret_cast<const double2 *>(vp + (kk / VV + q) * 32 * VV));
+                        v[2 * q + 0] = t2.x;
+                        v[2 * q + 1] = t2.y;
+                    } else {
+                        const float4 t4 = __ldcs(reinterpret_cast<const float4 *>(vp + (kk / VV + q) * 32 * VV));
+                        v[4 * q + 0] = t4.x;
+                        v[4 * q + 1] = t4.y;
+                        v[4 * q + 2] = t4.z;
+                        v[4 * q + 3] = t4.w;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) xv[u] = kk + u < cnt ? __ldg(x + cc[u]) : T(0);
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                    if (kk + u < cnt && rr[u] != r) {
+                        SPX_CT_EMIT(r, sum);
+                        if (!add_mode)
+                            for (int q = r + 1; q < rr[u]; ++q) out_row<MODE>(e, q, T(0), d0, d1);
+                        r = rr[u];
+                        sum = T(0);
+                    }
+                    if (kk + u < cnt) sum = fma(v[u], xv[u], sum);
+                }
+            }
+            if (nr == r) {
+                cr = r;
+            } else {
+                SPX_CT_EMIT(r, sum);
+                // rows without entries after the last entry (those between granules are
+                // written by the granule after them)
+                if (!add_mode && b >= nnz)
+                    for (int q = r + 1; q < n; ++q) out_row<MODE>(e, q, T(0), d0, d1);
+                sum = T(0);
+                cr = kNoCarry;
+            }
+        }
+#undef SPX_CT_EMIT
+        s_cr[wib][lane] = cr;
+        s_cv[wib][lane] = sum;
+        __syncwarp();
+        int nrow;
+        T nval;
+        const T tot = chunk_combine<T>(has_pend, rstart, pend, s_cr[wib], s_cv[wib], lane, run_row, run_val, nrow,
+                                       nval);
+        if (has_pend) {
+            if (range_inside && rstart == first_row) {
+                first_val = tot;
+                first_ready = true;
+            } else {
+                out_row<MODE>(e, rstart, tot, d0, d1);
+            }
+        }
+        run_row = nrow;
+        run_val = nval;
+        const unsigned fm = __ballot_sync(0xffffffffu, first_ready);
+        if (fm) {
+            const int src = __ffs(fm) - 1;
+            first_val = __shfl_sync(0xffffffffu, first_val, src);
+            first_ready = true;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && run_row >= 0) {
+        carry_row_w[w] = run_row;
+        carry_val_w[w] = run_val;
+        flag_publish(flags + w);
+    }
+    if (lane == 0 && range_inside && first_ready) {
+        T tot = first_val;
+        for (int wp = w - 1; wp >= 0; --wp) {
+            const int pb = (int)(((int64_t)nchunks * wp) / W), pe = (int)(((int64_t)nchunks * (wp + 1)) / W);
+            if (pb >= pe) continue;
+            if (!flag_wait(flags + wp, err)) break;
+            tot += ldcg(carry_val_w + wp);
+            flags[wp] = 0;
+            const int64_t ps = (int64_t)pb * CHUNK;
+            if (!(ps > 0 && crow[ps - 1] == first_row)) break;  // range wp began at the row start
+        }
+        out_row<MODE>(e, first_row, tot, d0, d1);
+    }
+    if constexpr (MODE == 0 || MODE >= 4)
+        if (e.dots) finish_dots<T, 256>(d0, d1, e, partials, ticket);
 }
 
 // hint[g] = the row holding nonzero g*ipt: first r with rp[r+1] > g*ipt
@@ -1926,6 +2359,180 @@ int launch_split(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
     }
 }
 
+// Tile-transposed nonzeros and granule descriptors for granules of ipt
+// nonzeros (rebuilt when ipt changes); the values of `val` (the FP64 / FP32
+// value array or the FP32 shadow) into the matching tiled buffer.
+template <class T>
+int ensure_tiled(spx_ctx *ctx, spx_matrix *A, int ipt, const T *val, const T **tval)
+{
+    const int64_t chunk = 32LL * ipt;
+    const int64_t nchunks = ceil_div(A->nnz, chunk);
+    const int64_t total = nchunks * chunk, ngran = nchunks * 32;
+    if (ngran > INT_MAX / 2) return fail(SPX_ERR_TOO_LARGE, "tiled CSR: too many granules");
+    if (A->tc_ipt != ipt) {
+        dbuf_free(ctx, A->tc_col);
+        dbuf_free(ctx, A->tc_row);
+        dbuf_free(ctx, A->tc_mask);
+        A->tc_val_ipt = A->tc_val32_ipt = 0;
+        SPX_TRY(dbuf_alloc(ctx, A->tc_col, (size_t)total * 4 + 16));
+        SPX_TRY(dbuf_alloc(ctx, A->tc_row, (size_t)(ngran + 1) * 4));
+        SPX_TRY(dbuf_alloc(ctx, A->tc_mask, (size_t)(ngran + 1) * 4));
+        k_tile_transpose<int, 4><<<(int)ceil_div(total, 256), 256, 0, ctx->stream>>>(
+            A->nnz, total, ipt, A->col.as<int>(), A->tc_col.as<int>());
+        SPX_CUDA(cudaGetLastError());
+        k_tile_rows<<<(int)ceil_div(ngran + 1, 256), 256, 0, ctx->stream>>>(
+            (int)A->n, A->nnz, A->rp.as<int>(), ipt, ngran, A->tc_row.as<int>(), A->tc_mask.as<unsigned>());
+        SPX_CUDA(cudaGetLastError());
+        k_tile_marks<<<(int)ceil_div(A->n, 256), 256, 0, ctx->stream>>>(
+            (int)A->n, A->nnz, A->rp.as<int>(), ipt, A->tc_row.as<int>(), A->tc_mask.as<unsigned>());
+        SPX_CUDA(cudaGetLastError());
+        A->tc_ipt = ipt;
+    }
+    if (A->n_empty < 0) {  // the list of empty rows, once per matrix
+        DBuf cnt;
+        SPX_TRY(dbuf_alloc(ctx, cnt, 16));
+        k_empty_rows<<<1, 1024, 0, ctx->stream>>>((int)A->n, A->rp.as<int>(), nullptr, cnt.as<int>());
+        int h = 0;
+        cudaError_t ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h, cnt.p, 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        if (ce == cudaSuccess && h > 0) {
+            const int st = dbuf_alloc(ctx, A->empty_rows, (size_t)h * 4);
+            if (st != SPX_OK) {
+                dbuf_free(ctx, cnt);
+                return st;
+            }
+            k_empty_rows<<<1, 1024, 0, ctx->stream>>>((int)A->n, A->rp.as<int>(), A->empty_rows.as<int>(),
+                                                      cnt.as<int>());
+            ce = cudaGetLastError();
+        }
+        dbuf_free(ctx, cnt);
+        if (ce != cudaSuccess) return cuda_fail(ce, "tiled CSR: empty-row list");
+        A->n_empty = h;
+    }
+    const bool shadow = sizeof(T) == 4 && A->dtype == SPX_F64;  // the FP32 copy of FP64 values
+    DBuf &tb = shadow ? A->tc_val32 : A->tc_val;
+    int &tb_ipt = shadow ? A->tc_val32_ipt : A->tc_val_ipt;
+    if (tb_ipt != ipt) {
+        dbuf_free(ctx, tb);
+        SPX_TRY(dbuf_alloc(ctx, tb, (size_t)total * sizeof(T) + 16));
+        k_tile_transpose<T, 16 / (int)sizeof(T)><<<(int)ceil_div(total, 256), 256, 0, ctx->stream>>>(
+            A->nnz, total, ipt, val, tb.as<T>());
+        SPX_CUDA(cudaGetLastError());
+        tb_ipt = ipt;
+    }
+    *tval = tb.as<T>();
+    return SPX_OK;
+}
+
+template <class T, int IPT, int MODE>
+int launch_tiled_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    auto kern = k_csr_tiled<T, IPT, MODE>;
+    const T *tval = nullptr;
+    SPX_TRY(ensure_tiled<T>(ctx, A, IPT, val, &tval));
+    const int64_t nchunks = ceil_div(A->nnz, 32LL * IPT);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    const int64_t need = ceil_div(nchunks, 8);  // at least one chunk per warp
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    SPX_TRY(ensure_scratch(ctx, A, grid * 8, grid, sizeof(T)));
+    return launch_k(kern, (int)grid, 256, 0, ctx->stream, true, (int)A->n, (int)A->nnz, (const int *)A->rp.as<int>(),
+                    (const int *)A->tc_col.as<int>(), tval, (const int *)A->tc_row.as<int>(),
+                    (const unsigned *)A->tc_mask.as<unsigned>(), (const int *)A->empty_rows.as<int>(),
+                    (int)A->n_empty, x, (int)nchunks, A->carry_row.as<int>(), A->carry_val.as<T>(),
+                    A->flags.as<int>(), A->partials.as<T>(), A->ticket.as<unsigned>(), ctx->dev_err, e);
+}
+
+template <class T, int IPT>
+int launch_tiled(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Epi<T> &e)
+{
+    switch (epi_mode(e)) {
+    case 1: return launch_tiled_m<T, IPT, 1>(ctx, A, val, x, e);
+    case 4: return launch_tiled_m<T, IPT, 4>(ctx, A, val, x, e);
+    case 5: return launch_tiled_m<T, IPT, 5>(ctx, A, val, x, e);
+    case 6: return launch_tiled_m<T, IPT, 6>(ctx, A, val, x, e);
+    case 7: return launch_tiled_m<T, IPT, 7>(ctx, A, val, x, e);
+    default: return launch_tiled_m<T, IPT, 0>(ctx, A, val, x, e);
+    }
+}
+
+// Tile-transposed copies of the COO arrays (row, column, values) for granules
+// of ipt entries, rebuilt when ipt changes.
+template <class T>
+int ensure_coo_tiled(spx_ctx *ctx, spx_matrix *A, int ipt, const T *cval, const T **tval)
+{
+    const int64_t chunk = 32LL * ipt;
+    const int64_t nchunks = ceil_div(A->coo_nnz, chunk);
+    const int64_t total = nchunks * chunk;
+    if (nchunks * 32 > INT_MAX / 2) return fail(SPX_ERR_TOO_LARGE, "tiled COO: too many granules");
+    const int tb = (int)ceil_div(total, 256);
+    if (A->ct_ipt != ipt) {
+        dbuf_free(ctx, A->ct_row);
+        dbuf_free(ctx, A->ct_col);
+        A->ct_val_ipt = A->ct_val32_ipt = 0;
+        SPX_TRY(dbuf_alloc(ctx, A->ct_row, (size_t)total * 4 + 16));
+        SPX_TRY(dbuf_alloc(ctx, A->ct_col, (size_t)total * 4 + 16));
+        k_tile_transpose<int, 4><<<tb, 256, 0, ctx->stream>>>(A->coo_nnz, total, ipt, A->coo_row.as<int>(),
+                                                               A->ct_row.as<int>());
+        k_tile_transpose<int, 4><<<tb, 256, 0, ctx->stream>>>(A->coo_nnz, total, ipt, A->coo_col.as<int>(),
+                                                               A->ct_col.as<int>());
+        SPX_CUDA(cudaGetLastError());
+        A->ct_ipt = ipt;
+    }
+    const bool shadow = sizeof(T) == 4 && A->dtype == SPX_F64;
+    DBuf &vb = shadow ? A->ct_val32 : A->ct_val;
+    int &vb_ipt = shadow ? A->ct_val32_ipt : A->ct_val_ipt;
+    if (vb_ipt != ipt) {
+        dbuf_free(ctx, vb);
+        SPX_TRY(dbuf_alloc(ctx, vb, (size_t)total * sizeof(T) + 16));
+        k_tile_transpose<T, 16 / (int)sizeof(T)><<<tb, 256, 0, ctx->stream>>>(A->coo_nnz, total, ipt, cval,
+                                                                               vb.as<T>());
+        SPX_CUDA(cudaGetLastError());
+        vb_ipt = ipt;
+    }
+    *tval = vb.as<T>();
+    return SPX_OK;
+}
+
+template <class T, int IPT, int MODE>
+int launch_coo_tiled_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e)
+{
+    auto kern = k_coo_tiled<T, IPT, MODE>;
+    const T *tval = nullptr;
+    SPX_TRY(ensure_coo_tiled<T>(ctx, A, IPT, cval, &tval));
+    const int64_t nchunks = ceil_div(A->coo_nnz, 32LL * IPT);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    const int64_t need = ceil_div(nchunks, 8);
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    SPX_TRY(ensure_scratch(ctx, A, grid * 8, grid, sizeof(T)));
+    return launch_k(kern, (int)grid, 256, 0, ctx->stream, true, (int)A->n, (int)A->coo_nnz,
+                    (const int *)A->coo_row.as<int>(), (const int *)A->ct_row.as<int>(),
+                    (const int *)A->ct_col.as<int>(), tval, x, (int)nchunks, A->carry_row.as<int>(),
+                    A->carry_val.as<T>(), A->flags.as<int>(), A->partials.as<T>(), A->ticket.as<unsigned>(),
+                    ctx->dev_err, e);
+}
+
+template <class T, int IPT>
+int launch_coo_tiled(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e, int add)
+{
+    if (add) return e.alpha == T(1) ? launch_coo_tiled_m<T, IPT, 3>(ctx, A, cval, x, e)
+                                    : launch_coo_tiled_m<T, IPT, 2>(ctx, A, cval, x, e);
+    switch (epi_mode(e)) {
+    case 1: return launch_coo_tiled_m<T, IPT, 1>(ctx, A, cval, x, e);
+    case 4: return launch_coo_tiled_m<T, IPT, 4>(ctx, A, cval, x, e);
+    case 5: return launch_coo_tiled_m<T, IPT, 5>(ctx, A, cval, x, e);
+    case 6: return launch_coo_tiled_m<T, IPT, 6>(ctx, A, cval, x, e);
+    case 7: return launch_coo_tiled_m<T, IPT, 7>(ctx, A, cval, x, e);
+    default: return launch_coo_tiled_m<T, IPT, 0>(ctx, A, cval, x, e);
+    }
+}
+
 template <class T, int IPT, int MODE>
 int launch_coo_split_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const Epi<T> &e)
 {
@@ -2047,15 +2654,17 @@ int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
     int kern = A->kernel, p = A->kparam;
     if (kern == SPX_KERNEL_AUTO) {
         // rows of nearly equal length: row blocks (one thread per row); moderately
-        // uneven rows: merge-path tiles; heavy-tailed rows: the warp-independent split kernel
+        // uneven rows: merge-path tiles; heavy-tailed rows: the split kernel on the tiled copy
+        // (2M-row power-law matrix, FP64: 156 us against 208 us for the split kernel staging
+        // through shared memory)
         const double mx = (double)A->max_len, mean = A->mean_len;
         if (mx <= 2.0 * mean + 8.0) {
             SPX_TRY(ensure_rows_cap(ctx, A));
             if (rows_smem<T>(A, kRowsStages) <= std::min<int64_t>(ctx->max_smem_optin, 120 * 1024))
                 return launch_rows<T>(ctx, A, val, x, e, kRowsStages, rows_auto_tpr<T>(A));
         }
-        kern = mx <= 4.0 * mean + 8.0 ? SPX_KERNEL_CSR_MERGE : SPX_KERNEL_CSR_SPLIT;
-        p = kern == SPX_KERNEL_CSR_SPLIT ? 8 : 0;
+        kern = mx <= 4.0 * mean + 8.0 ? SPX_KERNEL_CSR_MERGE : SPX_KERNEL_CSR_TILED;
+        p = kern == SPX_KERNEL_CSR_TILED ? 32 : 0;
     }
     if (kern == SPX_KERNEL_CSR_ROWS) {  // param: stages + 10 x threads per row (0 = automatic)
         if (p == 0) return launch_rows<T>(ctx, A, val, x, e, kRowsStages, rows_auto_tpr<T>(A));
@@ -2084,6 +2693,14 @@ int dispatch_csr(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const Ep
         case 8: return launch_split<T, 8>(ctx, A, val, x, e);
         case 16: return launch_split<T, 16>(ctx, A, val, x, e);
         default: return fail(SPX_ERR_INVALID, "split nonzeros per lane must be 8 or 16");
+        }
+    }
+    if (kern == SPX_KERNEL_CSR_TILED) {
+        if (p <= 0) p = 32;
+        switch (p) {
+        case 16: return launch_tiled<T, 16>(ctx, A, val, x, e);
+        case 32: return launch_tiled<T, 32>(ctx, A, val, x, e);
+        default: return fail(SPX_ERR_INVALID, "tiled CSR nonzeros per lane must be 16 or 32");
         }
     }
     if (kern == SPX_KERNEL_CSR_MERGE) {
@@ -2122,10 +2739,13 @@ int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const E
     // 104 / 108 / 116 = tiled segmented reduction with 4 / 8 / 16 items per thread.
     // Default: row-block for the COO format with short rows of similar length (the
     // boundary scan of a tile costs about mean-row-length steps per thread: measured
-    // faster than split for the 7-point stencil, slower for the 27-point one), else split.
+    // faster than split for the 7-point stencil, slower for the 27-point one), else the
+    // split kernel on tile-transposed copies with 16 entries per lane (FP64: 177 us on
+    // the power-law matrix and 119 us on the 27-point stencil 100^3, against 208 and
+    // 146 us for the split kernel staging through shared memory).
     int p = A->kernel == SPX_KERNEL_COO ? A->kparam : 0;
     if (p <= 0) {
-        p = 8;
+        p = 216;
         if (!add && A->format == SPX_COO && A->mean_len <= 16.0 && (double)A->max_len <= 2.0 * A->mean_len + 8.0) {
             SPX_TRY(ensure_coo_rowtiles(ctx, A));
             if (coo_rows_smem<T>(A) <= std::min<int64_t>(ctx->max_smem_optin, 120 * 1024)) p = 1;
@@ -2136,12 +2756,17 @@ int dispatch_coo(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, const E
         return launch_coo_rows<T>(ctx, A, cval, x, e);
     }
     switch (p) {
+    case 216: return launch_coo_tiled<T, 16>(ctx, A, cval, x, e, add);
+    case 232: return launch_coo_tiled<T, 32>(ctx, A, cval, x, e, add);
     case 8: return launch_coo_split<T, 8>(ctx, A, cval, x, e, add);
     case 16: return launch_coo_split<T, 16>(ctx, A, cval, x, e, add);
     case 104: return launch_coo<T, 4>(ctx, A, cval, x, e, add);
     case 108: return launch_coo<T, 8>(ctx, A, cval, x, e, add);
     case 116: return launch_coo<T, 16>(ctx, A, cval, x, e, add);
-    default: return fail(SPX_ERR_INVALID, "COO kernel parameter must be 8, 16 (split) or 104, 108, 116 (tiled)");
+    default:
+        return fail(SPX_ERR_INVALID,
+                    "COO kernel parameter must be 1 (row-block), 8, 16 (split), 216, 232 (tiled split) or 104, 108, "
+                    "116 (tiled segmented reduction)");
     }
 }
 

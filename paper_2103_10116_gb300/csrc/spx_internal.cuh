@@ -113,6 +113,14 @@ struct spx_matrix {
     // row hints of the nnz-split CSR kernel (row holding nonzero g * hint_ipt)
     spx::DBuf hint;
     int hint_ipt = 0;
+    // tiled nnz-split CSR: tile-transposed nonzeros (values per value array) and
+    // granule descriptors, built on first use for granules of tc_ipt nonzeros
+    spx::DBuf tc_col, tc_val, tc_val32, tc_row, tc_mask, empty_rows;
+    int tc_ipt = 0, tc_val_ipt = 0, tc_val32_ipt = 0;
+    int64_t n_empty = -1;
+    // tiled nnz-split COO (COO format / HYB COO part): tile-transposed row, column and value arrays
+    spx::DBuf ct_row, ct_col, ct_val, ct_val32;
+    int ct_ipt = 0, ct_val_ipt = 0, ct_val32_ipt = 0;
     // COO tile map (COO format / HYB COO part)
     spx::DBuf coo_tiles;      // int per tile boundary
     int64_t coo_tiles_items = 0, coo_ntiles = 0, coo_nsplit = 0;

@@ -37,6 +37,7 @@ SPX_CONVERGED, SPX_MAX_ITER, SPX_BREAKDOWN, SPX_STAGNATED, SPX_SOLVE_TIMEOUT = 0
 SPX_KERNEL_AUTO, SPX_KERNEL_CSR_VECTOR, SPX_KERNEL_CSR_MERGE, SPX_KERNEL_ELL, SPX_KERNEL_COO = 0, 1, 2, 3, 4
 SPX_KERNEL_CSR_SPLIT = 5
 SPX_KERNEL_CSR_ROWS = 6
+SPX_KERNEL_CSR_TILED = 7
 SPX_HOST_INPUT, SPX_MIXED_SHADOW = 1, 2
 (SPX_PART_ROW_PTR, SPX_PART_COL, SPX_PART_VAL, SPX_PART_ELL_COL, SPX_PART_ELL_VAL, SPX_PART_COO_ROW,
  SPX_PART_COO_COL, SPX_PART_COO_VAL, SPX_PART_VAL_F32) = range(9)

@@ -67,10 +67,16 @@ def _fmt_kernel(spx, fmt):
     """'csr-rowsP' names the row-block CSR kernel with parameter P; returns (format, kernel, param)."""
     if fmt.startswith("csr-rows"):
         return "csr", spx.SPX_KERNEL_CSR_ROWS, int(fmt[8:])
+    if fmt.startswith("csr-tiled"):
+        return "csr", spx.SPX_KERNEL_CSR_TILED, int(fmt[9:])
+    if fmt.startswith("coo-tiled"):
+        return "coo", spx.SPX_KERNEL_COO, int(fmt[9:])
     return fmt, None, 0
 
 
-FMTS = [("csr", None, 0), ("csr", 1, 4), ("csr", 2, 16), ("csr", 5, 16), ("csr", 6, 0), ("csr", 6, 22),
+FMTS = [("csr", None, 0), ("csr", 1, 4), ("csr", 2, 16), ("csr", 5, 16), ("csr", 7, 16), ("csr", 7, 32),
+        ("coo", 4, 232),
+        ("csr", 6, 0), ("csr", 6, 22),
         ("csr", 6, 42), ("ell", None, 0),
         ("coo", None, 0), ("hyb", None, 0)]
 
@@ -95,7 +101,8 @@ def test_cg_laplace2d_64(spx, ctx, fmt):
         spx.spx_matrix_destroy(A)
 
 
-@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb", "csr-rows22", "csr-rows42"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb", "csr-rows22", "csr-rows42", "csr-tiled32",
+                                 "coo-tiled232"])
 def test_bicgstab_convdiff(spx, ctx, fmt):
     rp, col, val, xs, b = _problem("convdiff_16")
     f, kernel, param = _fmt_kernel(spx, fmt)
@@ -113,7 +120,7 @@ def test_bicgstab_convdiff(spx, ctx, fmt):
         spx.spx_matrix_destroy(A)
 
 
-@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb", "csr-rows22", "csr-rows42"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "coo", "hyb", "csr-rows22", "csr-rows42", "csr-tiled32"])
 def test_cgs_convdiff(spx, ctx, fmt):
     rp, col, val, xs, b = _problem("convdiff_16")
     f, kernel, param = _fmt_kernel(spx, fmt)
@@ -149,10 +156,12 @@ def test_cgs_scaled_identity_one_step(spx, ctx, c):
         spx.spx_matrix_destroy(A)
 
 
+@pytest.mark.parametrize("fmt", ["csr", "csr-tiled32"])
 @pytest.mark.parametrize("m", [5, 30])
-def test_gmres_convdiff(spx, ctx, m):
+def test_gmres_convdiff(spx, ctx, m, fmt):
     rp, col, val, xs, b = _problem("convdiff_12")
-    A = _make(spx, ctx, "csr", rp, col, val)
+    f, kernel, param = _fmt_kernel(spx, fmt)
+    A = _make(spx, ctx, f, rp, col, val, kernel=kernel, param=param)
     try:
         x = torch.zeros_like(_t(b))
         info = spx.spx_solve(ctx, A, _t(b), x, "gmres", 1e-10, 20000, restart=m)
@@ -201,10 +210,11 @@ def test_cg_eigenvector_one_step(spx, ctx):
 
 @pytest.mark.parametrize("solver,prob", [("cg", "lap3d_20"), ("bicgstab", "convdiff_16"), ("cgs", "convdiff_16"),
                                          ("gmres", "convdiff_12")])
-@pytest.mark.parametrize("fmt", ["csr", "ell", "hyb"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "hyb", "csr-tiled32", "coo-tiled232"])
 def test_mixed_precision_ir(spx, ctx, solver, prob, fmt):
     rp, col, val, xs, b = _problem(prob)
-    A = _make(spx, ctx, fmt, rp, col, val, flags=spx.SPX_MIXED_SHADOW)
+    f, kernel, param = _fmt_kernel(spx, fmt)
+    A = _make(spx, ctx, f, rp, col, val, flags=spx.SPX_MIXED_SHADOW, kernel=kernel, param=param)
     try:
         x = torch.zeros_like(_t(b))
         info = spx.spx_solve(ctx, A, _t(b), x, solver, 1e-10, 20000, restart=30, precision="mixed")

@@ -67,12 +67,12 @@ VARIANTS = [
     ("csr", None, 0),
     ("csr", "vector", 1), ("csr", "vector", 4), ("csr", "vector", 32),
     ("csr", "merge", 4), ("csr", "merge", 8), ("csr", "merge", 16),
-    ("csr", "split", 8), ("csr", "split", 16), ("csr", "rows", 0), ("csr", "rows", 1), ("csr", "rows", 22),
+    ("csr", "split", 8), ("csr", "split", 16), ("csr", "tiled", 16), ("csr", "tiled", 32), ("csr", "rows", 0), ("csr", "rows", 1), ("csr", "rows", 22),
     ("csr", "rows", 42),
     ("ell", None, 0), ("ell", "ell", 1),
-    ("coo", None, 0), ("coo", "coo", 1), ("coo", "coo", 8), ("coo", "coo", 16), ("coo", "coo", 104),
-    ("coo", "coo", 116),
-    ("hyb", None, 0), ("hyb0", None, 0), ("hyb3", None, 0),
+    ("coo", None, 0), ("coo", "coo", 1), ("coo", "coo", 8), ("coo", "coo", 16), ("coo", "coo", 216),
+    ("coo", "coo", 232), ("coo", "coo", 104), ("coo", "coo", 116),
+    ("hyb", None, 0), ("hyb0", None, 0), ("hyb3", None, 0), ("hyb3", "coo", 232),
 ]
 
 _cache = {}
@@ -102,7 +102,7 @@ def _make(spx, ctx, fmt, rp, col, val, ncols, dtype, flags=0):
 
 def _kernel_code(spx, kname):
     return {None: spx.SPX_KERNEL_AUTO, "vector": spx.SPX_KERNEL_CSR_VECTOR, "merge": spx.SPX_KERNEL_CSR_MERGE,
-            "split": spx.SPX_KERNEL_CSR_SPLIT, "rows": spx.SPX_KERNEL_CSR_ROWS,
+            "split": spx.SPX_KERNEL_CSR_SPLIT, "rows": spx.SPX_KERNEL_CSR_ROWS, "tiled": spx.SPX_KERNEL_CSR_TILED,
             "ell": spx.SPX_KERNEL_ELL, "coo": spx.SPX_KERNEL_COO}[kname]
 
 

@@ -45,6 +45,16 @@ def test_spmv_exact_against_dense_on_integers(seed):
     assert np.array_equal(oracle.spmv_csr_plain(rp, col, val, x), y)
 
 
+def test_openmp_build_gives_the_same_bits():
+    # the all-cores CPU baseline runs the plain definition with rows shared among
+    # threads: each row is still summed alone in index order, so the bits match
+    rng = np.random.default_rng(9)
+    rp, col, val = random_int_csr(rng, 5000, 5000, max_len=30)
+    val = val * 0.3127
+    x = rng.standard_normal(5000)
+    assert np.array_equal(oracle.spmv_csr_plain_omp(rp, col, val, x), oracle.spmv_csr_plain(rp, col, val, x))
+
+
 def test_spmv_empty_matrix_and_rows():
     rp = np.zeros(6, np.int32)
     y = oracle.spmv_csr(rp, np.zeros(0, np.int32), np.zeros(0), np.ones(3))

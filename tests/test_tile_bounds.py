@@ -236,3 +236,127 @@ def test_ell_vector_loads_stay_in_bounds(R, V):
     assert np.all(last + R <= ld)
     assert np.all(ld % R == 0)  # slab starts j*ld and group starts i are multiples of R
     assert R * V <= 16 and R * 4 <= 16
+
+
+# ---------------------------------------------------------------- tiled nnz-split CSR
+def _tiled_layout(nnz, ipt, vec):
+    """Destination of source entry k in the tile-transposed layout (the index
+    arithmetic of the transposition kernel), over the padded range."""
+    chunk = 32 * ipt
+    nchunks = -(-nnz // chunk)
+    total = nchunks * chunk
+    k = np.arange(total, dtype=np.int64)
+    c = k // chunk
+    wi = k - c * chunk
+    lane, u = wi // ipt, wi % ipt
+    return c * chunk + (u // vec) * 32 * vec + lane * vec + u % vec, total
+
+
+def _tiled_descriptors(rp, ipt):
+    """trow / tmask / slow flags as the descriptor kernels define them."""
+    n = rp.shape[0] - 1
+    nnz = int(rp[-1])
+    ngran = -(-nnz // (32 * ipt)) * 32
+    trow = np.zeros(ngran, np.int64)
+    a = np.arange(ngran, dtype=np.int64) * ipt
+    act = a < nnz
+    trow[act] = np.searchsorted(rp[1:], a[act], side="right")  # first r with rp[r+1] > a
+    tmask = np.zeros(ngran + 1, np.int64)
+    slow = np.zeros(ngran, bool)
+    for r in range(n):
+        p = int(rp[r])
+        g, u = divmod(p, ipt)
+        if rp[r + 1] > p:
+            tmask[g] |= 1 << u
+        elif u != 0 and p < nnz:
+            slow[g] = True
+    return trow, tmask, slow, ngran
+
+
+def _tiled_walk(rp, col, val, x, ipt):
+    """The lanes' walk over their granules using only the descriptors (and the
+    row pointers where a granule is flagged), summing each row's pieces: must
+    give the SpMV."""
+    n = rp.shape[0] - 1
+    nnz = int(rp[-1])
+    trow, tmask, slow, ngran = _tiled_descriptors(rp, ipt)
+    y = np.zeros(n)
+    for g in range(ngran):
+        a = g * ipt
+        cnt = max(0, min(ipt, nnz - a))
+        if cnt == 0:
+            continue
+        r = int(trow[g])
+        assert rp[r] <= a < rp[r + 1]  # the row holding the granule's first entry, never empty
+        for s in range(cnt):
+            if s > 0 and (tmask[g] >> s) & 1:
+                r += 1
+                if slow[g]:
+                    while rp[r + 1] == rp[r]:
+                        r += 1
+                assert rp[r] == a + s  # the row that starts here
+            assert rp[r] <= a + s < rp[r + 1]
+            y[r] += val[a + s] * x[col[a + s]]
+        ends_b = a + ipt >= nnz or (tmask[g + 1] & 1)
+        assert bool(ends_b) == (rp[r + 1] == min(a + ipt, nnz) or a + ipt >= nnz)
+    return y
+
+
+def _empty_rows_matrix():
+    rng = np.random.default_rng(3)
+    lens = rng.integers(0, 40, size=700)
+    lens[rng.random(700) < 0.3] = 0
+    lens[:5] = 0
+    lens[-7:] = 0
+    lens[300] = 2500
+    rp = np.zeros(lens.size + 1, np.int64)
+    rp[1:] = np.cumsum(lens)
+    col = rng.integers(0, lens.size, size=int(rp[-1]))
+    val = rng.integers(-8, 9, size=int(rp[-1])).astype(np.float64)
+    return rp, col, val
+
+
+@pytest.mark.parametrize("ipt", [16, 32])
+@pytest.mark.parametrize("mname", ["lap2d_64", "powerlaw_60k", "ragged_tail", "empty_rows"])
+def test_tiled_csr_layout_and_descriptors(mname, ipt):
+    if mname == "empty_rows":
+        rp, col, val = _empty_rows_matrix()
+    else:
+        rp, col, val = MATS[mname]()
+        rp = np.asarray(rp, np.int64)
+    nnz = int(rp[-1])
+    for vec, esize in ((4, 4), (2, 8), (4, 4)):  # columns, FP64 values, FP32 values
+        dst, total = _tiled_layout(nnz, ipt, vec)
+        # a permutation of the padded range: every slot written once, all inside the allocation
+        assert dst.min() == 0 and dst.max() == total - 1 and np.unique(dst).size == total
+        assert (total * esize + 16) <= _alloc(total * esize + 16)
+        # the kernel's 16-byte loads: lane l, slot group q of chunk c reads
+        # [c*CHUNK + q*32*vec + l*vec, +vec): aligned and inside the chunk
+        chunk = 32 * ipt
+        q = np.arange(ipt // vec)[:, None]
+        lane = np.arange(32)[None, :]
+        off = q * 32 * vec + lane * vec
+        assert (off * esize % 16 == 0).all() and off.min() == 0 and (off + vec).max() == chunk
+        # lane l's slot u is the source entry l*ipt + u of the chunk
+        src = np.empty(total, np.int64)
+        src[dst] = np.arange(total)
+        u = np.arange(ipt)
+        for l in (0, 5, 31):
+            got = src[(u // vec) * 32 * vec + l * vec + u % vec]
+            assert np.array_equal(got, l * ipt + u)
+    trow, tmask, slow, ngran = _tiled_descriptors(rp, ipt)
+    assert tmask.shape[0] == ngran + 1  # the kernel reads tmask[g + 1] for every granule
+    assert (trow < rp.shape[0] - 1).all() and (trow >= 0).all()
+    if mname != "empty_rows":
+        assert not slow.any()
+    else:
+        assert slow.any()
+    # the descriptor walk reproduces the product exactly on integer data
+    x = np.random.default_rng(1).integers(-8, 9, size=rp.shape[0] - 1).astype(np.float64)
+    if mname != "empty_rows":
+        val = np.round(np.asarray(val) * 4)  # small integers: exact sums in any order
+    y = _tiled_walk(rp, np.asarray(col), np.asarray(val, np.float64), x, ipt)
+    yref = np.zeros(rp.shape[0] - 1)
+    rows = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
+    np.add.at(yref, rows, np.asarray(val, np.float64) * x[np.asarray(col)])
+    assert np.array_equal(y, yref)
