@@ -385,12 +385,36 @@ int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const int32_t *row_
                       const double *values, const double *b, double *x, int solver, double tol, int64_t max_iter,
                       int restart, int precision, int64_t *req_id);
 
+/* Queue one solve A x = b on a RESIDENT operator: A is a square FP64 matrix
+ * handle (any format) on the server's device, created by the caller and
+ * borrowed until the request completes (not destroyed, and not used by the
+ * caller for spmv / solve meanwhile: a solve caches its workspace in the
+ * handle).  Nothing of A is uploaded; b[n] and x[n] are HOST buffers as in
+ * spx_server_submit.  Requests on the same handle run one at a time (later
+ * ones wait while other requests are admitted past them); requests on
+ * different handles overlap.  MIXED needs A created with SPX_MIXED_SHADOW.
+ * Always solved on a slot (the batch lanes take host operators only).
+ * This is the submit call of the solve server in its resident-matrix form
+ * (the paper's Section 5 solvers, served).  Errors: SPX_ERR_INVALID,
+ * SPX_ERR_TOO_LARGE (workspace > budget). */
+int spx_server_submit_matrix(spx_server *S, spx_matrix *A, const double *b, double *x, int solver, double tol,
+                             int64_t max_iter, int restart, int precision, int64_t *req_id);
+
 typedef struct {
     int64_t id;
     int32_t error;       /* spx_status of the request's own library calls (SPX_OK normally) */
     int32_t pad;
     spx_solve_info info; /* as filled by spx_solve */
     double submit_ms, admit_ms, done_ms;  /* host clock, milliseconds since spx_server_create */
+    /* Where the time after admission went (host clock, milliseconds).  Slot
+     * requests: upload of the operator and b, set-up (validation, statistics,
+     * the library's copy of the operator; 0 for a resident operator), the
+     * solve, the download of x.  Batched requests: the phases of the whole
+     * batch they ran in (set-up = gathering the operators into pinned staging,
+     * upload = copy and device build). */
+    double upload_ms, setup_ms, solve_ms, download_ms;
+    int32_t batched;     /* 1: solved by a batch lane */
+    int32_t pad2;
 } spx_server_result;
 
 /* Collect up to max_results completed requests into results (host array),

@@ -56,14 +56,22 @@ int dbuf_alloc(spx_ctx *ctx, DBuf &b, size_t bytes)
         return fail(SPX_ERR_OOM, "device allocation of " + std::to_string(padded) + " bytes failed");
     }
     b.bytes = bytes;
+    b.free_fn = ctx->alloc ? ctx->free : nullptr;
+    b.free_user = ctx->user;
     return SPX_OK;
 }
 
 void dbuf_free(spx_ctx *ctx, DBuf &b)
 {
-    if (b.p) dfree(ctx, b.p, round_up(b.bytes, 16) + kArrayPad);
+    if (b.p) {
+        const size_t padded = round_up(b.bytes, 16) + kArrayPad;
+        if (b.free_fn) b.free_fn(b.p, padded, ctx->stream, b.free_user);
+        else cudaFreeAsync(b.p, ctx->stream);
+    }
     b.p = nullptr;
     b.bytes = 0;
+    b.free_fn = nullptr;
+    b.free_user = nullptr;
 }
 
 // Sets the context's device for the lifetime of a call, restores the caller's.

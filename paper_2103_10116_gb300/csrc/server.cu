@@ -55,14 +55,21 @@ struct Request {
     const int32_t *rp, *col;
     const double *val, *b;
     double *x;
+    spx_matrix *A;  // resident operator (spx_server_submit_matrix), else null
     int solver, precision, restart;
     double tol;
     int64_t max_iter;
     size_t footprint;
     Clock::time_point t_submit, t_admit, t_done;
+    double upload_ms, setup_ms, solve_ms, download_ms;  // phases after admission
     spx_solve_info info;
     int error;
 };
+
+double ms_between(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
 
 }  // namespace
 
@@ -77,6 +84,7 @@ struct spx_server {
     int64_t batch_rows = 0, batch_rows_limit = 0;
     std::vector<Request *> done;
     std::vector<std::thread> workers;
+    std::vector<const spx_matrix *> busy;  // resident operators with a request running
     std::atomic<bool> stop{false};
     int64_t next_id = 1;
     int active = 0;
@@ -99,6 +107,21 @@ size_t request_footprint(int64_t n, int64_t nnz, int solver, int precision, int 
     return csr + shadow + vecs + (size_t)n * 16 /* b, x */ + (1u << 20);
 }
 
+// The request a free slot admits next: the first queued request whose resident
+// operator (if any) is not in use by a running request -- two solves on one
+// handle would share its workspace -- provided its footprint fits what the
+// budget has left (FIFO: a request that does not fit blocks the ones after it).
+// Null if none can start now.  Called with S->mu held.
+static std::deque<Request *>::iterator next_admissible(spx_server *S)
+{
+    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        const Request *R = *it;
+        if (R->A && std::find(S->busy.begin(), S->busy.end(), R->A) != S->busy.end()) continue;
+        return S->in_use + R->footprint <= S->budget ? it : S->queue.end();
+    }
+    return S->queue.end();
+}
+
 static void worker_main(spx_server *S)
 {
     cudaSetDevice(S->device);
@@ -114,45 +137,73 @@ static void worker_main(spx_server *S)
         Request *R = nullptr;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            // FIFO admission: the head request waits until its footprint fits
-            S->cv_work.wait(lk, [&] {
-                return S->stop.load() ||
-                       (!S->queue.empty() && S->in_use + S->queue.front()->footprint <= S->budget);
-            });
+            S->cv_work.wait(lk, [&] { return S->stop.load() || next_admissible(S) != S->queue.end(); });
             if (S->stop.load()) break;
-            if (S->queue.empty() || S->in_use + S->queue.front()->footprint > S->budget) continue;
-            R = S->queue.front();
-            S->queue.pop_front();
+            auto it = next_admissible(S);
+            if (it == S->queue.end()) continue;
+            R = *it;
+            S->queue.erase(it);
             S->in_use += R->footprint;
             S->active += 1;
+            if (R->A) S->busy.push_back(R->A);
             R->t_admit = Clock::now();
         }
         S->cv_work.notify_all();  // another slot may admit the next request too
         int err = SPX_OK;
-        spx_matrix *A = nullptr;
-        void *bd = nullptr, *xd = nullptr;
+        spx_matrix *A = R->A;
+        void *bd = nullptr, *xd = nullptr, *rpd = nullptr, *cold = nullptr, *vald = nullptr;
         std::memset(&R->info, 0, sizeof(R->info));
         const size_t vb = (size_t)R->n * 8;
-        err = spx_matrix_create(ctx, &A, SPX_CSR, SPX_F64, R->n, R->n, R->nnz, R->rp, R->col, R->val, SPX_F64, -1,
-                                SPX_HOST_INPUT | (R->precision == SPX_PREC_MIXED ? SPX_MIXED_SHADOW : 0u));
+        // upload: the operator (unless resident) and b
+        if (!R->A) {
+            if (cudaMallocAsync(&rpd, (size_t)(R->n + 1) * 4 + 16, st) != cudaSuccess ||
+                cudaMallocAsync(&cold, (size_t)R->nnz * 4 + 16, st) != cudaSuccess ||
+                cudaMallocAsync(&vald, (size_t)R->nnz * 8 + 16, st) != cudaSuccess)
+                err = SPX_ERR_OOM;
+            if (err == SPX_OK &&
+                (cudaMemcpyAsync(rpd, R->rp, (size_t)(R->n + 1) * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                 (R->nnz > 0 && cudaMemcpyAsync(cold, R->col, (size_t)R->nnz * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+                 (R->nnz > 0 && cudaMemcpyAsync(vald, R->val, (size_t)R->nnz * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)))
+                err = SPX_ERR_CUDA;
+        }
         if (err == SPX_OK && cudaMallocAsync(&bd, vb + 16, st) != cudaSuccess) err = SPX_ERR_OOM;
         if (err == SPX_OK && cudaMallocAsync(&xd, vb + 16, st) != cudaSuccess) err = SPX_ERR_OOM;
         if (err == SPX_OK && cudaMemcpyAsync(bd, R->b, vb, cudaMemcpyHostToDevice, st) != cudaSuccess) err = SPX_ERR_CUDA;
         if (err == SPX_OK && cudaMemsetAsync(xd, 0, vb, st) != cudaSuccess) err = SPX_ERR_CUDA;
+        cudaStreamSynchronize(st);
+        const auto t_up = Clock::now();
+        // set-up: validation, statistics and the library's own copy of the operator
+        if (err == SPX_OK && !R->A)
+            err = spx_matrix_create(ctx, &A, SPX_CSR, SPX_F64, R->n, R->n, R->nnz, (const int32_t *)rpd,
+                                    (const int32_t *)cold, vald, SPX_F64, -1,
+                                    R->precision == SPX_PREC_MIXED ? SPX_MIXED_SHADOW : 0u);
+        cudaStreamSynchronize(st);
+        if (rpd) cudaFreeAsync(rpd, st);
+        if (cold) cudaFreeAsync(cold, st);
+        if (vald) cudaFreeAsync(vald, st);
+        const auto t_setup = Clock::now();
         if (err == SPX_OK)
             err = spx_solve(ctx, A, bd, xd, R->solver, R->tol, R->max_iter, R->restart, R->precision, &R->info);
+        cudaStreamSynchronize(st);
+        const auto t_solve = Clock::now();
         if (err == SPX_OK && cudaMemcpyAsync(R->x, xd, vb, cudaMemcpyDeviceToHost, st) != cudaSuccess) err = SPX_ERR_CUDA;
         cudaStreamSynchronize(st);
-        if (A) spx_matrix_destroy(A);
+        const auto t_down = Clock::now();
+        if (A && !R->A) spx_matrix_destroy(A);
         if (bd) cudaFreeAsync(bd, st);
         if (xd) cudaFreeAsync(xd, st);
         cudaStreamSynchronize(st);
         R->error = err;
+        R->upload_ms = ms_between(R->t_admit, t_up);
+        R->setup_ms = ms_between(t_up, t_setup);
+        R->solve_ms = ms_between(t_setup, t_solve);
+        R->download_ms = ms_between(t_solve, t_down);
         R->t_done = Clock::now();
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->in_use -= R->footprint;
             S->active -= 1;
+            if (R->A) S->busy.erase(std::find(S->busy.begin(), S->busy.end(), R->A));
             S->done.push_back(R);
         }
         S->cv_work.notify_all();
@@ -205,8 +256,9 @@ struct Pinned {
 // Solve the requests rs (same solver settings) as one batch; per-request
 // errors (an invalid operator) are set in R->error, the batch's own error is
 // returned.
-static int run_batch(spx_ctx *ctx, cudaStream_t st, Pinned &stage, std::vector<Request *> &rs)
+static int run_batch(spx_ctx *ctx, cudaStream_t st, Pinned &stage, std::vector<Request *> &rs, double *phase_ms)
 {
+    const auto t_start = Clock::now();
     std::vector<Request *> ok;
     for (Request *R : rs) {
         std::memset(&R->info, 0, sizeof(R->info));
@@ -242,6 +294,7 @@ static int run_batch(spx_ctx *ctx, cudaStream_t st, Pinned &stage, std::vector<R
         nnz_off[s + 1] = nnz_off[s] + R->nnz;
     }
     const Request *h0 = ok[0];
+    const auto t_staged = Clock::now();
     spx_batch *B = nullptr;
     int err = spx_batch_create(ctx, &B, SPX_F64, ns, row_off, nnz_off, rp, col, val,
                                SPX_HOST_INPUT | (h0->precision == SPX_PREC_MIXED ? SPX_MIXED_SHADOW : 0u));
@@ -251,13 +304,23 @@ static int run_batch(spx_ctx *ctx, cudaStream_t st, Pinned &stage, std::vector<R
     if (err == SPX_OK && cudaMallocAsync(&xd, vb + 16, st) != cudaSuccess) err = fail(SPX_ERR_OOM, "batch x");
     if (err == SPX_OK && cudaMemcpyAsync(bd, b, vb, cudaMemcpyHostToDevice, st) != cudaSuccess) err = SPX_ERR_CUDA;
     if (err == SPX_OK && cudaMemsetAsync(xd, 0, vb, st) != cudaSuccess) err = SPX_ERR_CUDA;
+    cudaStreamSynchronize(st);
+    const auto t_up = Clock::now();
     std::vector<spx_solve_info> infos((size_t)ns);
     if (err == SPX_OK)
         err = batch_solve_direct(ctx, B, bd, xd, h0->solver, h0->tol, h0->max_iter, h0->precision, h0->block,
                                  infos.data());
+    const auto t_solved = Clock::now();
     // the solve has synchronised the stream: b's staging is free for x
     if (err == SPX_OK && cudaMemcpyAsync(b, xd, vb, cudaMemcpyDeviceToHost, st) != cudaSuccess) err = SPX_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess && err == SPX_OK) err = SPX_ERR_CUDA;
+    // phases of the whole batch, reported for each of its requests: gathering the
+    // operators into pinned staging (set-up), upload and device build, the solve,
+    // the download
+    phase_ms[1] = ms_between(t_start, t_staged);
+    phase_ms[0] = ms_between(t_staged, t_up);
+    phase_ms[2] = ms_between(t_up, t_solved);
+    phase_ms[3] = ms_between(t_solved, Clock::now());
     if (err == SPX_OK) {
         for (int64_t s = 0; s < ns; ++s) {
             Request *R = ok[(size_t)s];
@@ -318,10 +381,15 @@ static void lane_main(spx_server *S)
             for (Request *R : take) R->t_admit = now;
         }
         S->cv_work.notify_all();
-        const int err = run_batch(ctx, st, stage, take);
+        double ph[4] = {0, 0, 0, 0};
+        const int err = run_batch(ctx, st, stage, take, ph);
         const auto now = Clock::now();
         for (Request *R : take) {
             if (err != SPX_OK && R->error == SPX_OK) R->error = err;
+            R->upload_ms = ph[0];
+            R->setup_ms = ph[1];
+            R->solve_ms = ph[2];
+            R->download_ms = ph[3];
             R->t_done = now;
         }
         {
@@ -366,6 +434,54 @@ extern "C" int spx_server_create(spx_ctx *ctx, spx_server **out, int64_t budget_
     return SPX_OK;
 }
 
+extern "C" int spx_server_submit_matrix(spx_server *S, spx_matrix *A, const double *b, double *x, int solver,
+                                        double tol, int64_t max_iter, int restart, int precision, int64_t *req_id)
+{
+    if (!S || !A || !b || !x || !req_id) return fail(SPX_ERR_INVALID, "spx_server_submit_matrix: bad argument");
+    if (A->dtype != SPX_F64 || A->n != A->ncols || A->n <= 0)
+        return fail(SPX_ERR_INVALID, "spx_server_submit_matrix: A must be a square FP64 matrix");
+    if (A->ctx->device != S->device) return fail(SPX_ERR_INVALID, "spx_server_submit_matrix: A is on another device");
+    if (precision == SPX_PREC_MIXED && !A->val32.p && !A->ell_val32.p && !A->coo_val32.p)
+        return fail(SPX_ERR_INVALID, "spx_server_submit_matrix: MIXED needs A created with SPX_MIXED_SHADOW");
+    int base_solver = 0, bs = 0;
+    bool jacobi = false, adaptive = false;
+    if (parse_solver_code(solver, &base_solver, &jacobi, &bs, &adaptive) != SPX_OK)
+        return fail(SPX_ERR_INVALID, "spx_server_submit_matrix: bad solver");
+    Request *R = new Request();
+    R->n = A->n;
+    R->nnz = A->nnz;
+    R->rp = nullptr;
+    R->col = nullptr;
+    R->val = nullptr;
+    R->A = A;
+    R->b = b;
+    R->x = x;
+    R->solver = solver;
+    R->precision = precision;
+    R->restart = restart;
+    R->tol = tol;
+    R->max_iter = max_iter;
+    // the operator is resident (the caller's); the workspace, b and x are the request's
+    R->footprint = request_footprint(A->n, 0, base_solver, precision, restart) + (jacobi ? (size_t)A->n * 24 : 0) +
+                   (size_t)A->n * (size_t)bs * (adaptive ? 12 : 8);
+    R->error = SPX_OK;
+    R->t_submit = Clock::now();
+    R->block = 0;
+    R->batched = false;
+    if (R->footprint > S->budget) {
+        delete R;
+        return fail(SPX_ERR_TOO_LARGE, "request footprint exceeds the server's byte budget");
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        R->id = S->next_id++;
+        S->queue.push_back(R);
+    }
+    *req_id = R->id;
+    S->cv_work.notify_all();
+    return SPX_OK;
+}
+
 extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                                  const double *values, const double *b, double *x, int solver, double tol,
                                  int64_t max_iter, int restart, int precision, int64_t *req_id)
@@ -377,6 +493,7 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     if (parse_solver_code(solver, &base_solver, &jacobi, &bs, &adaptive) != SPX_OK)
         return fail(SPX_ERR_INVALID, "spx_server_submit: bad solver");
     Request *R = new Request();
+    R->A = nullptr;
     R->n = n;
     R->nnz = nnz;
     R->rp = row_ptr;
@@ -429,6 +546,12 @@ extern "C" int spx_server_poll(spx_server *S, spx_server_result *results, int ma
         out[i].submit_ms = ms(R->t_submit);
         out[i].admit_ms = ms(R->t_admit);
         out[i].done_ms = ms(R->t_done);
+        out[i].upload_ms = R->upload_ms;
+        out[i].setup_ms = R->setup_ms;
+        out[i].solve_ms = R->solve_ms;
+        out[i].download_ms = R->download_ms;
+        out[i].batched = R->batched ? 1 : 0;
+        out[i].pad2 = 0;
         delete R;
     }
     S->done.erase(S->done.begin(), S->done.begin() + k);

@@ -1254,7 +1254,8 @@ struct Timer {
 
 // Runs `body` either directly on ctx->stream or, for reuse, as a captured CUDA
 // graph keyed by `key` (captured on the private capture stream, launched on
-// ctx->stream).  The first call of a key runs eagerly so that every lazily
+// ctx->stream).  Keys include the context: a graph holds the context's error
+// word, so a matrix solved from another context captures its own graph.  The first call of a key runs eagerly so that every lazily
 // allocated scratch exists before capture.
 template <class F> int run_chunk(spx_ctx *ctx, SolverWork *w, const uint64_t key[8], bool use_graph, F &&body)
 {
@@ -1697,7 +1698,7 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
             const uint64_t key[8] = {(uint64_t)solver, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
                                      (uint64_t)use32, (uint64_t)chunk, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16) |
                                      ((uint64_t)w->bj_adapt << 24),
-                                     (uint64_t)(uintptr_t)A, 0};
+                                     (uint64_t)(uintptr_t)A, (uint64_t)(uintptr_t)ctx << 1};
             SPX_TRY(run_chunk(ctx, w, key, graphs, [&]() -> int {
                 for (int c = 0; c < chunk; ++c)
                     SPX_TRY(solver == SPX_CG ? cg_iter(R) : solver == SPX_CGS ? cgs_iter(R) : bi_iter(R));
@@ -1817,7 +1818,7 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
         const uint64_t key[8] = {(uint64_t)SPX_GMRES, (uint64_t)(uintptr_t)x, (uint64_t)(uintptr_t)b,
                                  (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16) |
                                      ((uint64_t)w->bj_adapt << 24),
-                                 (uint64_t)(uintptr_t)A, 1};
+                                 (uint64_t)(uintptr_t)A, ((uint64_t)(uintptr_t)ctx << 1) | 1u};
         SPX_TRY(run_chunk(ctx, w, key, n >= kGraphMinRows, cycle));
         SPX_TRY(read_state<T>(ctx, w, sizeof(GState<T>)));
         ++cycles;

@@ -65,10 +65,15 @@ namespace spx {
 void *dalloc(spx_ctx *ctx, size_t bytes);
 void dfree(spx_ctx *ctx, void *p, size_t bytes);
 
-// A device buffer owned by a handle, freed through the allocating context.
+// A device buffer owned by a handle.  It remembers the allocator that made it
+// (the allocating context's callback, or none: cudaMallocAsync), so any
+// context may free it: a matrix solved from several contexts (the server's
+// slots) holds buffers from each.
 struct DBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    spx_free_fn free_fn = nullptr;
+    void *free_user = nullptr;
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 int dbuf_alloc(spx_ctx *ctx, DBuf &b, size_t bytes);

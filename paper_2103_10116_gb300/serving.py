@@ -24,6 +24,13 @@ class Server:
         self.live[rid] = (rp, col, val, b, x)
         return rid
 
+    def submit_matrix(self, A: int, b, solver="cg", tol=1e-8, max_iter=100000, precision="mixed") -> int:
+        """A request on a resident matrix handle (kept alive by the caller)."""
+        x = np.zeros(b.shape[0])
+        rid = spx.spx_server_submit_matrix(self.h, A, b, x, solver, tol, max_iter, 30, precision)
+        self.live[rid] = (A, None, None, b, x)
+        return rid
+
     def poll(self, wait_ms: int = 0) -> int:
         got = spx.spx_server_poll(self.h, 1024, wait_ms)
         for r in got:

@@ -75,7 +75,9 @@ class spx_solve_info(C.Structure):
 
 class spx_server_result(C.Structure):
     _fields_ = [("id", C.c_int64), ("error", C.c_int32), ("pad", C.c_int32), ("info", spx_solve_info),
-                ("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double)]
+                ("submit_ms", C.c_double), ("admit_ms", C.c_double), ("done_ms", C.c_double),
+                ("upload_ms", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+                ("download_ms", C.c_double), ("batched", C.c_int32), ("pad2", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -108,6 +110,7 @@ SIGNATURES = {
     "spx_batch_tune": (_I, [_P, _P, _I, _I, C.POINTER(C.c_int)]),
     "spx_server_create": (_I, [_P, _PP, _I64, _I]),
     "spx_server_submit": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(C.c_int64)]),
+    "spx_server_submit_matrix": (_I, [_P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(C.c_int64)]),
     "spx_server_poll": (_I, [_P, C.POINTER(spx_server_result), _I, _I, C.POINTER(C.c_int)]),
     "spx_server_set_batching": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
     "spx_probe_gather": (_I, [_P, _I64, _P, _P, _I, _P]),
@@ -468,6 +471,21 @@ def spx_server_submit(S: int, row_ptr, col_idx, values, b, x, solver="cg", tol: 
     return rid.value
 
 
+def spx_server_submit_matrix(S: int, A: int, b, x, solver="cg", tol: float = 1e-8, max_iter: int = 100000,
+                             restart: int = 30, precision="mixed") -> int:
+    """Queue a solve on a resident matrix handle A (FP64, square) with HOST numpy b and x
+    (float64); A, b and x stay alive and untouched until the request completes."""
+    import numpy as np
+    for a in (b, x):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise TypeError("spx_server_submit_matrix takes contiguous float64 numpy b and x")
+    rid = C.c_int64()
+    _check(load().spx_server_submit_matrix(S, A, b.ctypes.data, x.ctypes.data, SOLVERS.get(solver, solver),
+                                           float(tol), int(max_iter), int(restart),
+                                           PRECISIONS.get(precision, precision), C.byref(rid)))
+    return rid.value
+
+
 def spx_server_poll(S: int, max_results: int = 256, wait_ms: int = 0) -> list[dict]:
     buf = (spx_server_result * max(1, max_results))()
     cnt = C.c_int()
@@ -476,7 +494,9 @@ def spx_server_poll(S: int, max_results: int = 256, wait_ms: int = 0) -> list[di
     for i in range(cnt.value):
         r = buf[i]
         out.append({"id": r.id, "error": r.error, "info": _info(r.info), "submit_ms": r.submit_ms,
-                    "admit_ms": r.admit_ms, "done_ms": r.done_ms})
+                    "admit_ms": r.admit_ms, "done_ms": r.done_ms, "upload_ms": r.upload_ms,
+                    "setup_ms": r.setup_ms, "solve_ms": r.solve_ms, "download_ms": r.download_ms,
+                    "batched": bool(r.batched)})
     return out
 
 

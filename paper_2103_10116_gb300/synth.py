@@ -226,6 +226,55 @@ def diagdom_random(n: int, seed: int, nnz_min: int = 8, nnz_max: int = 32):
     return _finish(n, allr[order], allc[order], allv[order])
 
 
+class DiagDomFamily:
+    """Diagonally dominant random rows for any size n <= n_max, from one master
+    draw, so that a stream of requests of continuously distributed sizes needs
+    no per-request generation beyond one pass over the column indices.
+
+    Row i has L_i ~ U{nnz_min..nnz_max} entries (at most n): the diagonal first,
+    then m = L_i - 1 off-diagonal columns, values N(0, 1) off the diagonal and
+    2 * sum |off-diagonal| on it (strictly diagonally dominant, nonsymmetric).
+    The off-diagonal columns of the size-n matrix are a stratified uniform
+    sample of [0, n) without i: with the n - 1 candidates cut into m integer
+    strata [floor(j (n-1) / m), floor((j+1) (n-1) / m)), the j-th column is
+    uniform in stratum j, moved past the diagonal; they are distinct for
+    n - 1 >= m.  Row pointers and values of the size-n matrix are prefixes of
+    the master arrays (views); only the columns depend on n."""
+
+    def __init__(self, n_max: int, seed: int, nnz_min: int = 8, nnz_max: int = 32):
+        rng = np.random.default_rng(seed)
+        L = rng.integers(nnz_min, nnz_max + 1, size=n_max).astype(np.int64)
+        self.n_max = n_max
+        self.nnz_max = nnz_max
+        self.rp = np.zeros(n_max + 1, np.int32)
+        self.rp[1:] = np.cumsum(L)
+        nnz = int(self.rp[-1])
+        self.row = np.repeat(np.arange(n_max, dtype=np.int64), L)
+        j = np.arange(nnz, dtype=np.int64) - np.repeat(self.rp[:-1].astype(np.int64), L)  # 0 = diagonal
+        self.diag = j == 0
+        self.j = np.maximum(j - 1, 0)           # stratum of an off-diagonal entry
+        self.m = np.maximum(L - 1, 1)[self.row]  # strata in its row
+        self.v = rng.random(nnz)                 # position inside the stratum
+        off = ~self.diag
+        vals = rng.standard_normal(nnz)
+        dsum = np.bincount(self.row[off], weights=np.abs(vals[off]), minlength=n_max)
+        vals[self.diag] = 2.0 * dsum
+        self.val = vals
+
+    def matrix(self, n: int):
+        """(row_ptr, col, val) of the size-n member (n - 1 >= nnz_max - 1)."""
+        if not (self.nnz_max <= n <= self.n_max):
+            raise ValueError("size outside the family")
+        nnz = int(self.rp[n])
+        row, j, m = self.row[:nnz], self.j[:nnz], self.m[:nnz]
+        lo = j * (n - 1) // m
+        w = (j + 1) * (n - 1) // m - lo
+        c = lo + np.minimum((self.v[:nnz] * w).astype(np.int64), w - 1)
+        c += c >= row
+        col = np.where(self.diag[:nnz], row, c).astype(np.int32)
+        return self.rp[: n + 1], col, self.val[:nnz]
+
+
 def uniform_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """x ~ U[lo, hi] in double."""
     return np.random.default_rng(seed).uniform(lo, hi, size=n)

@@ -161,3 +161,73 @@ def test_preconditioned_requests_alone_equal_mix(spx, ctx):
                 assert np.array_equal(srv.results[rid]["x"], ra["x"])
     finally:
         srv.close()
+
+
+def test_resident_matrix_requests(spx, ctx):
+    """Requests on resident matrix handles: nothing of the operator is uploaded
+    (set-up time 0), a handle serves several requests (one at a time, the
+    others overlapping with requests on other handles), every result meets
+    tol on the oracle-formed residual and equals the same request alone, bit
+    for bit; the phase times are reported."""
+    from paper_2103_10116_gb300.serving import Server
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+    mats = [synth.laplace3d_7pt(24), synth.laplace3d_7pt(30)]
+    handles = [spx.spx_matrix_create(ctx, "csr", t(rp), t(col), t(val), flags=spx.SPX_MIXED_SHADOW)
+               for rp, col, val in mats]
+    torch.cuda.synchronize()
+    srv = Server(ctx, 0, max_slots=4, batch_rows=0)
+    try:
+        bs = [[synth.uniform_vector(rp.shape[0] - 1, seed=400 + 10 * h + k) for k in range(3)]
+              for h, (rp, _, _) in enumerate(mats)]
+        alone = {}
+        for h in range(2):
+            for k in range(3):
+                rid = srv.submit_matrix(handles[h], bs[h][k], solver="cg", tol=1e-8)
+                srv.drain()
+                alone[(h, k)] = srv.results[rid]
+        ids = {}
+        for k in range(3):
+            for h in range(2):
+                ids[(h, k)] = srv.submit_matrix(handles[h], bs[h][k], solver="cg", tol=1e-8)
+        srv.drain()
+        for (h, k), rid in ids.items():
+            rm, ra = srv.results[rid], alone[(h, k)]
+            rp, col, val = mats[h]
+            b = bs[h][k]
+            assert rm["error"] == 0 and rm["info"].status == spx.SPX_CONVERGED, rm
+            r = b - oracle.spmv_csr(rp, col, val, rm["x"])
+            assert np.linalg.norm(r) / np.linalg.norm(b) <= residual_limit(rp, col, val, b, rm["x"], 1e-8)
+            assert np.array_equal(rm["x"], ra["x"])
+            assert rm["setup_ms"] == 0.0 or rm["setup_ms"] < 1.0  # no operator to build
+            assert rm["solve_ms"] > 0 and not rm["batched"]
+        # requests on one handle never overlapped
+        for h in range(2):
+            spans = sorted((srv.results[ids[(h, k)]]["admit_ms"], srv.results[ids[(h, k)]]["done_ms"])
+                           for k in range(3))
+            assert all(spans[i][1] <= spans[i + 1][0] for i in range(2)), spans
+    finally:
+        srv.close()
+        for A in handles:
+            spx.spx_matrix_destroy(A)
+
+
+def test_phase_times_of_uploaded_requests(spx, ctx):
+    from paper_2103_10116_gb300.serving import Server
+    srv = Server(ctx, 0, max_slots=2)
+    try:
+        rp, col, val = synth.laplace3d_7pt(34)       # a slot request
+        rps, cols, vals = synth.laplace3d_7pt(12)    # a batched request
+        b, bsm = synth.uniform_vector(34**3, seed=7), synth.uniform_vector(12**3, seed=8)
+        r1 = srv.submit(rp, col, val, b, solver="cg", tol=1e-8)
+        r2 = srv.submit(rps, cols, vals, bsm, solver="cg", tol=1e-8)
+        srv.drain()
+        big, small = srv.results[r1], srv.results[r2]
+        assert not big["batched"] and small["batched"]
+        for r in (big, small):
+            assert r["error"] == 0 and r["info"].status == spx.SPX_CONVERGED
+            phases = r["upload_ms"] + r["setup_ms"] + r["solve_ms"] + r["download_ms"]
+            assert min(r["upload_ms"], r["setup_ms"], r["solve_ms"], r["download_ms"]) >= 0
+            assert phases <= r["done_ms"] - r["admit_ms"] + 1e-6
+            assert r["solve_ms"] > 0
+    finally:
+        srv.close()
