@@ -290,7 +290,7 @@ def run_gpu(args):
     if args.batched:
         secondary["batched"] = batched_secondary(spx, ctx, stream, dev)
     if args.serve_seconds > 0:
-        secondary["serving"] = serving_secondary(spx, ctx, seconds=args.serve_seconds)
+        secondary["serving"] = serving_secondary(spx, ctx, dev, seconds=args.serve_seconds)
     # the roofline is reported for one kernel: the single-launch sweep entry
     # (HYB launches two) with the largest device time per step
     single = [i for i, e in enumerate(entries) if e["launches"] == 1] or list(range(len(entries)))
@@ -351,7 +351,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def solve_bytes_per_iter(solver: str, fmt_bytes: int, n: int, m: int = 30) -> int:
+def solve_bytes_per_iter(solver: str, fmt_bytes: int, n: int, m: int = 30, V: int = 8) -> int:
     """Algorithmic bytes of one FP64 iteration in this library's fused form:
     SpMV stream (fmt_bytes: matrix + gathered vector + result) plus the vector
     kernels.  CG: SpMV (+p re-read for p.q), x/r update (4 reads, 2 writes),
@@ -359,8 +359,7 @@ def solve_bytes_per_iter(solver: str, fmt_bytes: int, n: int, m: int = 30) -> in
     x/r updates.  GMRES(m), averaged over a cycle: SpMV + one Gram-Schmidt
     pass (the j+1 basis vectors read for the dots and again for the update, w
     read and written) + normalisation; a reorthogonalisation pass is extra
-    work, not counted."""
-    V = 8
+    work, not counted.  V: bytes per vector element (8 FP64, 4 FP32)."""
     if solver == "cg":
         return fmt_bytes + V * n + 6 * V * n + 3 * V * n
     if solver == "bicgstab":
@@ -716,18 +715,19 @@ def batched_secondary(spx, ctx, stream, dev, plain_sample=4096):
     return out
 
 
-def plain_serial_f64(spx, ctx, reqs, kinds, tol, budget_s=8.0, max_count=400):
+def plain_serial_f64(spx, ctx, make, count, tol, budget_s=8.0):
     """The plain per-system FP64 path on the first requests of the trace, one
     at a time: upload the operator (host CSR), solve in FP64, read x back."""
     import torch
     t0 = time.perf_counter()
     done = 0
-    for i, (rp, col, val, b) in enumerate(reqs[:max_count]):
+    for i in range(count):
+        _, (rp, col, val, b), solver, _ = make(i)
         A = spx.spx_matrix_create(ctx, "csr", torch.from_numpy(rp), torch.from_numpy(col), torch.from_numpy(val))
         try:
             bd = torch.from_numpy(b).cuda()
             xd = torch.zeros_like(bd)
-            spx.spx_solve(ctx, A, bd, xd, solver=kinds[i], tol=tol, max_iter=100000, precision="f64")
+            spx.spx_solve(ctx, A, bd, xd, solver=solver, tol=tol, max_iter=100000, precision="f64")
             xd.cpu()
         finally:
             spx.spx_matrix_destroy(A)
@@ -738,54 +738,180 @@ def plain_serial_f64(spx, ctx, reqs, kinds, tol, budget_s=8.0, max_count=400):
     return {"sample_requests": done, "sample_s": round(el, 2), "solves_per_s": round(done / el, 1)}
 
 
-def serving_secondary(spx, ctx, seconds: float = 10.0, rate: float = 2000.0, slots: int = 16, pool: int = 12,
+def family_columns(j, m, v, row, diag, n: int, nnz: int):
+    """The column indices of the size-n member of synth.DiagDomFamily from its
+    per-entry draws (torch tensors on any device; the same integers as
+    DiagDomFamily.matrix)."""
+    import torch
+    j, m, r = j[:nnz], m[:nnz], row[:nnz]
+    lo = torch.div(j * (n - 1), m, rounding_mode="floor")
+    w = torch.div((j + 1) * (n - 1), m, rounding_mode="floor") - lo
+    c = lo + torch.minimum((v[:nnz] * w).long(), w - 1)
+    c += (c >= r).long()
+    return torch.where(diag[:nnz], r, c).int()
+
+
+def _host_bytes_cap():
+    """Host memory the serving replay may hold in request payloads: a quarter of
+    what the machine has available, at most 24 GB."""
+    try:
+        with open("/proc/meminfo") as f:
+            avail = next(int(ln.split()[1]) * 1024 for ln in f if ln.startswith("MemAvailable:"))
+    except Exception:
+        avail = 32 << 30
+    return float(min(24 << 30, avail // 4))
+
+
+def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0, slots: int = 16,
                       batch_rows=None, plain=True):
-    """Poisson arrivals (rate req/s for `seconds`), sizes log-uniform in
-    [1e3, 1e6] rows drawn from a pool of `pool` log-spaced sizes per family,
-    50/50 3D 7-point stencils (CG) and diagonally dominant random rows with
-    8-32 nonzeros (BiCGSTAB), tolerance 1e-8, FP32 inner + FP64 refinement,
-    admission by device footprint (90% of free memory).  Small requests are
-    batched by the server's batch lanes (batch_rows: their size limit, None =
-    the server default, 0 = every request on its own slot)."""
+    """Poisson arrivals (rate req/s for `seconds`) of solve requests whose sizes
+    are drawn continuously from log-U[1e3, 1e6] rows, 50/50 from two families:
+    3D 7-point stencils (k = round(n^(1/3)), n := k^3, CG) and diagonally
+    dominant random rows with 8-32 nonzeros at exactly the drawn size
+    (BiCGSTAB; synth.DiagDomFamily); tolerance 1e-8, FP32 inner iterations +
+    FP64 refinement; admission by device footprint (90% of free memory).
+    Operators come from host memory and are uploaded per request; those of at
+    most batch_rows rows go to the batch lanes (None: the server default, 0:
+    none).  Payloads are built in arrival order by a producer thread (the
+    random family's columns and every right-hand side are formed on the GPU and
+    copied to pinned host memory) and submitted when due, with a bound on the
+    host bytes held; latency counts from each request's arrival time."""
+    import collections
+    import threading
+
+    import torch
     from paper_2103_10116_gb300 import synth
-    from paper_2103_10116_gb300.serving import Server, latency_stats, poisson_trace, replay
+    from paper_2103_10116_gb300.serving import Server, latency_stats, poisson_trace, replay_lazy
     rng = np.random.default_rng(5)
-    ks = np.unique(np.round(np.geomspace(10, 100, pool)).astype(int))       # stencil k, n = k^3
-    rs = np.unique(np.round(np.geomspace(1e3, 1e6, pool)).astype(int))     # random rows
-    stencils = {int(k): synth.laplace3d_7pt(int(k)) for k in ks}
-    randoms = {int(n): synth.diagdom_random(int(n), seed=int(n) % 1000 + 7) for n in rs}
     trace = poisson_trace(rate, seconds, seed=5)
-    reqs, kinds = [], []
-    logn = rng.uniform(np.log(1e3), np.log(1e6), size=trace.shape[0])
-    fam = rng.random(trace.shape[0]) < 0.5
-    for i in range(trace.shape[0]):
-        if fam[i]:
-            k = int(ks[np.argmin(np.abs(np.log(ks.astype(float) ** 3) - logn[i]))])
-            rp, col, val = stencils[k]
-            kinds.append("cg")
-        else:
-            n = int(rs[np.argmin(np.abs(np.log(rs.astype(float)) - logn[i]))])
-            rp, col, val = randoms[n]
-            kinds.append("bicgstab")
-        b = np.random.default_rng(i).uniform(-1, 1, rp.shape[0] - 1)
-        reqs.append((rp, col, val, b))
-    srv = Server(ctx, 0, max_slots=slots, batch_rows=batch_rows)
+    N = trace.shape[0]
+    drawn = np.rint(np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=N))).astype(np.int64)
+    stencil_fam = rng.random(N) < 0.5
+    ks = np.rint(np.cbrt(drawn)).astype(np.int64)
+    rows = np.where(stencil_fam, ks ** 3, drawn)
+    F = synth.DiagDomFamily(1_000_000, seed=7)
+    gstream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(gstream):
+        d_row = torch.from_numpy(F.row).to(dev)
+        d_j = torch.from_numpy(F.j).to(dev)
+        d_m = torch.from_numpy(F.m).to(dev)
+        d_v = torch.from_numpy(F.v).to(dev)
+        d_diag = torch.from_numpy(F.diag).to(dev)
+    stencils = {}
+
+    def build(i):
+        n = int(rows[i])
+        with torch.cuda.stream(gstream):
+            g = torch.Generator(device=dev)
+            g.manual_seed(10_000 + i)
+            bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            bh.copy_(torch.rand(n, generator=g, device=dev, dtype=torch.float64).mul_(2.0).sub_(1.0),
+                     non_blocking=True)
+            if stencil_fam[i]:
+                k = int(ks[i])
+                if k not in stencils:
+                    stencils[k] = synth.laplace3d_7pt(k)
+                rp, col, val = stencils[k]
+                nbytes = 16 * n
+            else:
+                nnz = int(F.rp[n])
+                colh = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
+                colh.copy_(family_columns(d_j, d_m, d_v, d_row, d_diag, n, nnz), non_blocking=True)
+                rp, val = F.rp[: n + 1], F.val[:nnz]
+                nbytes = 16 * n + 4 * nnz
+            gstream.synchronize()
+            col = col if stencil_fam[i] else colh.numpy()
+        # the numpy views keep the pinned buffers alive until the server is done with them
+        return ("host", (rp, col, val, bh.numpy()), "cg" if stencil_fam[i] else "bicgstab", nbytes)
+
+    cap = _host_bytes_cap()
+    ready = collections.OrderedDict()
+    cv = threading.Condition()
+    state = {"next": 0, "bytes": 0.0, "stop": False, "err": None}
+
+    def producer():  # builds payloads in arrival order, at most `cap` host bytes ahead
+        try:
+            while True:
+                with cv:
+                    cv.wait_for(lambda: state["stop"] or state["bytes"] < cap / 2)
+                    if state["stop"] or state["next"] >= N:
+                        return
+                    i = state["next"]
+                    state["next"] += 1
+                item = build(i)
+                with cv:
+                    ready[i] = item
+                    state["bytes"] += item[3]
+                    cv.notify_all()
+        except Exception as e:  # reported by make()
+            with cv:
+                state["err"] = e
+                cv.notify_all()
+
+    def make(i):
+        with cv:
+            cv.wait_for(lambda: i in ready or state["err"] is not None)
+            if state["err"] is not None:
+                raise state["err"]
+            item = ready.pop(i)
+            state["bytes"] -= item[3]
+            cv.notify_all()
+        return item
+
+    prod = threading.Thread(target=producer, daemon=True)
+    prod.start()
+    with cv:  # a head start: the first second of arrivals built before the clock starts
+        cv.wait_for(lambda: state["next"] >= min(N, int(rate)) or state["bytes"] >= cap / 2 or state["err"])
+    srv = Server(ctx, 0, max_slots=slots, batch_rows=batch_rows, keep_x=False)
     try:
         eff_rows = spx.spx_server_set_batching(srv.h, -1)
-        wall, ids = replay(srv, trace, reqs, lambda i: kinds[i], tol=1e-8, precision="mixed")
+        wall, ids, delays = replay_lazy(srv, trace, make, max_pending_bytes=cap / 2, tol=1e-8, precision="mixed")
         res = [srv.results[i] for i in ids]
     finally:
         srv.close()
-    st = latency_stats(res)
+        with cv:
+            state["stop"] = True
+            cv.notify_all()
+        prod.join()
+    st = latency_stats(res, delays)
     conv = sum(1 for r in res if r["info"].status == spx.SPX_CONVERGED and r["error"] == 0)
-    busy = sum(r["done_ms"] - r["admit_ms"] for r in res) / 1e3
+    peak, _ = _peaks()
+    # the offered load at the HBM roofline: every request's FP32 inner iterations and FP64 outer
+    # residuals at their algorithmic bytes
+    nnz_of = np.where(stencil_fam, 7 * rows - 6 * ks ** 2, F.rp[np.minimum(rows, F.n_max)])
+    roof = 0.0
+    for i, r in enumerate(res):
+        n, nnz, solver = int(rows[i]), int(nnz_of[i]), "cg" if stencil_fam[i] else "bicgstab"
+        inner = solve_bytes_per_iter(solver, algorithmic_bytes("csr", 4, n, n, nnz), n, V=4)
+        outer = algorithmic_bytes("csr", 8, n, n, nnz) + 5 * 8 * n
+        roof += (r["info"].inner_iterations * inner + max(1, r["info"].restarts) * outer) / (peak * 1e9)
+
+    def phases(sel):
+        if not sel:
+            return None
+        out = {"requests": len(sel)}
+        for ph in ("upload_ms", "setup_ms", "solve_ms", "download_ms"):
+            v = np.array([r[ph] for r in sel])
+            out[ph] = {"p50": round(float(np.percentile(v, 50)), 3), "p90": round(float(np.percentile(v, 90)), 3),
+                       "sum_s": round(float(v.sum()) / 1e3, 2)}
+        return out
+
+    slot_res = [r for r in res if not r["batched"]]
     st.update({"requests": len(res), "converged": conv, "arrival_rate_per_s": rate, "window_s": seconds,
                "wall_s": round(wall, 2), "solves_per_s": round(len(res) / wall, 1), "slots": slots,
-               "slot_busy_s": round(busy, 2), "pool_sizes_per_family": int(len(ks)), "batch_rows": int(eff_rows),
-               "batched_requests": int(sum(1 for i in range(len(reqs)) if reqs[i][0].shape[0] - 1 <= eff_rows
-                                           and kinds[i] in ("cg", "bicgstab")))})
+               "batch_rows": int(eff_rows), "batched_requests": int(sum(1 for r in res if r["batched"])),
+               "sizes": "log-uniform rows in [1e3, 1e6], exact per request (stencils: the nearest k^3)",
+               "distinct_sizes": int(np.unique(rows).size),
+               "offered_gpu_s_at_roofline": round(roof, 2),
+               "rho_at_roofline": round(roof / seconds, 3),
+               "capacity_solves_per_s_at_roofline": round(len(res) / roof, 1),
+               "achieved_frac_of_roofline_capacity": round(roof / wall, 3),
+               "client_delay_ms_p50": round(float(np.percentile(delays, 50)), 3),
+               "host_bytes_cap": int(cap),
+               "phases_slot_route": phases(slot_res),
+               "phases_batch_route": phases([r for r in res if r["batched"]])})
     if plain:
-        st["plain_per_system_f64"] = plain_serial_f64(spx, ctx, reqs, kinds, 1e-8)
+        st["plain_per_system_f64"] = plain_serial_f64(spx, ctx, build, min(400, N), 1e-8)
         st["speedup_vs_plain_f64"] = round(st["solves_per_s"] / st["plain_per_system_f64"]["solves_per_s"], 2)
     return st
 

@@ -12,7 +12,7 @@
 //     at once once the solve has stopped, so the host enqueues a chunk of
 //     iterations as one CUDA graph and reads the stop flag once per chunk;
 //   * GMRES orthogonalises with classical Gram-Schmidt, repeated once when the
-//     first pass cancels most of the vector (selective reorthogonalisation),
+//     first pass cancels nearly all of the vector (selective reorthogonalisation),
 //     which reads the Krylov basis in long coalesced streams instead of one
 //     dependent dot product per basis vector (modified Gram-Schmidt).
 // Convergence policy: recurrence residual ||r||/||b|| <= tol, then the true
@@ -813,10 +813,18 @@ __global__ void __launch_bounds__(kVB)
 // ------------------------------------------------------------------ GMRES kernels
 // Basis V[k] = base + k*ld, k = 0..m.  The Arnoldi step j forms w = A v_j in
 // V[j+1] (with ||w||^2 from the SpMV epilogue), then classical Gram-Schmidt
-// with selective reorthogonalisation (the criterion of Daniel, Gragg, Kaufman
-// and Stewart, 1976): h1 = V_j^T w; w -= V_j h1; and only if that pass
-// cancelled most of w (||w_new|| < ||w_old|| / sqrt 2) a second pass
-// h2 = V_j^T w; w -= V_j h2.  h = h1 + h2; H(j+1, j) = ||w||; v_{j+1} = w / ||w||.
+// with selective reorthogonalisation: h1 = V_j^T w; w -= V_j h1; and only if
+// that pass cancelled nearly all of w (||w_new|| < ||w_old|| / 8) a second
+// pass h2 = V_j^T w; w -= V_j h2.  h = h1 + h2; H(j+1, j) = ||w||;
+// v_{j+1} = w / ||w||.  One pass leaves w_new orthogonal to V_j up to about
+// eps ||w_old|| / ||w_new||, so the threshold bounds that loss at 8 eps per
+// step.  (The classic criterion of Daniel, Gragg, Kaufman and Stewart, 1976,
+// reorthogonalises below 1/sqrt 2: on diagonally dominant matrices such as the
+// upwind convection-diffusion operator, A v_j is mostly v_j and one pass keeps
+// 26-42% of the norm, so that criterion asks for the second pass at every step,
+// doubling the FP64 work of the orthogonalisation for an orthogonality gain
+// from about 4 eps to eps.)
+constexpr double kGmReorthKeep2 = 1.0 / 64.0;  // (||w_new|| / ||w_old||)^2 below which the second pass runs
 
 // Gram-Schmidt kernels.  Rows are processed in chunks of kGmRows (grid-stride
 // over a fixed grid).  Dots: the chunk of w sits in shared memory; warp wp
@@ -930,13 +938,14 @@ __device__ __forceinline__ void gm_rows_update(const T *__restrict__ V, int64_t 
     }
 }
 
-// First pass: h1 = V_j^T w.
+// A dots pass: h = V_j^T w.  The first pass always runs (h1); the second
+// (h2, second = true) only when the first update asked for it.
 template <class T>
 __global__ void __launch_bounds__(kVB)
     k_gm_dots(int64_t n, int64_t ld, const T *__restrict__ V, int j, const GState<T> *gs, T *hout, T *partials,
-              unsigned *ticket)
+              unsigned *ticket, bool second)
 {
-    if (gs->skip) return;
+    if (gs->skip || (second && !gs->reorth)) return;
     const T *w = V + (int64_t)(j + 1) * ld;
     __shared__ T ws[kGmRows];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -988,64 +997,49 @@ template <class T> __device__ void gm_finish_column(GState<T> *gs, GSmall<T> sm,
     }
 }
 
-// First update and second dots, fused over each chunk of rows:
-// w -= V_j h1 (written back and kept in shared memory), ||w||^2, and
-// h2 = V_j^T w from the chunk just updated (its basis rows are still in
-// L1/L2).  The last block compares ||w||^2 with ||A v_j||^2 (wa[1], from
-// the SpMV): if the first pass kept more than half of it (squared), the
-// column is finished with h2 = 0; otherwise the second update runs.
+// First update: w -= V_j h1 with ||w||^2 of the result accumulated on the way.
+// The last block compares it with ||A v_j||^2 (wa[1], from the SpMV): if the
+// pass kept more than 1/8 of the norm, the column is finished with h2 = 0;
+// otherwise the reorthogonalisation runs (second dots pass, second update).
+// The common case thus costs one dots pass and one update over the basis:
+// 2 (j+1) n FMAs per Arnoldi step.
 template <class T>
 __global__ void __launch_bounds__(kVB)
-    k_gm_upd_dots(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, const T *wa,
-                  T *partials, unsigned *ticket)
+    k_gm_upd1(int64_t n, int64_t ld, T *__restrict__ V, int j, GState<T> *gs, GSmall<T> sm, const T *wa,
+              T *partials, unsigned *ticket)
 {
     if (gs->skip) return;
     T *w = V + (int64_t)(j + 1) * ld;
     __shared__ T hs[kGmKmax];
-    __shared__ T ws[kGmRows];
     __shared__ T red[kVB / 32];
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int jn = j + 1;
     if (threadIdx.x < kGmKmax) hs[threadIdx.x] = threadIdx.x < jn ? ldcg(sm.h1 + threadIdx.x) : T(0);
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+    __syncthreads();
+    constexpr int R = 4;
     T ww = T(0);
-    for (int64_t r0 = (int64_t)blockIdx.x * kGmRows; r0 < n; r0 += (int64_t)gridDim.x * kGmRows) {
-        const int nr = (int)min((int64_t)kGmRows, n - r0);
-        __syncthreads();  // hs loaded / ws free
-        constexpr int R = kGmRows / kVB;
+    const int64_t stride = (int64_t)gridDim.x * kVB;
+    for (int64_t i = blockIdx.x * (int64_t)kVB + threadIdx.x; i < n; i += R * stride) {
         bool ok[R];
         T wr[R];
 #pragma unroll
         for (int u = 0; u < R; ++u) {
-            const int il = threadIdx.x + kVB * u;
-            ok[u] = il < nr;
-            wr[u] = ok[u] ? w[r0 + il] : T(0);
+            ok[u] = i + u * stride < n;
+            wr[u] = ok[u] ? w[i + u * stride] : T(0);
         }
-        gm_rows_update<T, R>(V, ld, r0 + threadIdx.x, kVB, ok, jn, hs, wr);
+        gm_rows_update<T, R>(V, ld, i, stride, ok, jn, hs, wr);
 #pragma unroll
         for (int u = 0; u < R; ++u) {
-            const int il = threadIdx.x + kVB * u;
-            if (ok[u]) {
-                w[r0 + il] = wr[u];
-                ws[il] = wr[u];
-            }
+            if (ok[u]) w[i + u * stride] = wr[u];
             ww = fma(wr[u], wr[u], ww);  // zero for rows past the end
         }
-        __syncthreads();
-        gm_chunk_dots<T>(V, ld, r0, nr, ws, j, lane, wp, acc);
     }
-    // ||w||^2 partial at slot [kGmKmax + 1][block]
     const T bsum = block_sum<T, kVB>(ww, red);
-    if (threadIdx.x == 0) partials[(int64_t)(kGmKmax + 1) * gridDim.x + blockIdx.x] = bsum;
-    bool last;
-    gm_store_dots<T>(acc, j, lane, wp, partials, sm.h2, ticket, last);
-    if (!last) return;
+    if (threadIdx.x == 0) partials[blockIdx.x] = bsum;
+    if (!last_block(ticket, gridDim.x)) return;
     T s = T(0);
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVB)
-        s += ldcg(partials + (int64_t)(kGmKmax + 1) * gridDim.x + b);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kVB) s += ldcg(partials + b);
     s = block_sum<T, kVB>(s, red);
-    const bool again = s < T(0.5) * ldcg(wa + 1);  // ||w_new||^2 < ||w_old||^2 / 2
-    __syncthreads();  // h2 stores of this block done
+    const bool again = s < T(kGmReorthKeep2) * ldcg(wa + 1);
     if (!again && threadIdx.x < jn) sm.h2[threadIdx.x] = T(0);
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -1798,8 +1792,9 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
             ea.want_yy = true;  // ||A v_j||^2 -> dots[1], for the reorthogonalisation test
             ea.dots = dots;
             SPX_TRY(spmv_launch<T>(ctx, A, Z ? Z : V + (int64_t)j * ld, ea, use32));  // A v_j or A M^-1 v_j
-            k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk);
-            k_gm_upd_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dots, part, tk);
+            k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h1, part, tk, false);
+            k_gm_upd1<T><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dots, part, tk);
+            k_gm_dots<T><<<gd, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm.h2, part, tk, true);
             k_gm_upd2<T><<<gu, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, part, tk);
             k_gm_scale<T><<<g, kVB, 0, ctx->stream>>>(n, ld, V, j, gs, sm, dinv, Z);
             // (when this step ended the cycle, the apply's Z is never read: the next
