@@ -149,12 +149,6 @@ int spx_ctx_set_stream(spx_ctx *ctx, void *stream);
  * themselves; asynchronous calls (spx_spmv) are checked by calling it. */
 int spx_ctx_check(spx_ctx *ctx);
 
-/* Test hook for the failure path: launch one wait that nothing will satisfy
- * (which = 0: a look-back flag; 1: an mbarrier phase), limited to about a
- * millisecond of SM clocks.  It gives up, records the error and returns, so
- * the following spx_ctx_check reports SPX_ERR_TIMEOUT.  Nothing hangs or
- * faults.  Asynchronous.  Errors: SPX_ERR_INVALID. */
-int spx_selftest_wait_timeout(spx_ctx *ctx, int which);
 
 /* ------------------------------------------------------------------ matrices */
 
@@ -274,14 +268,6 @@ int spx_spmv_csr_noalloc(void *stream, int dtype, int64_t nrows, int64_t ncols, 
                          const int32_t *row_ptr, const int32_t *col_idx, const void *values, const void *x,
                          void *y);
 
-/* A measurement aid (not part of the paper's method): stream col_idx[nnz]
- * and gather x (dtype SPX_F64 or SPX_F32) at every index, summing the
- * gathered values; nothing is stored except, practically never, out[0]
- * (device, one element).  Its time is the floor any SpMV kernel has on that
- * sparsity pattern: the gathers of x plus 4 bytes per nonzero.  Device
- * pointers; every index must lie inside x (not checked).  Asynchronous on the
- * context stream.  Errors: SPX_ERR_INVALID. */
-int spx_probe_gather(spx_ctx *ctx, int64_t nnz, const int32_t *col_idx, const void *x, int dtype, void *out);
 
 /* ------------------------------------------------------------------ BLAS-1 */
 
@@ -436,6 +422,26 @@ int spx_server_pending(spx_server *S, int64_t *queued, int64_t *running, int64_t
 /* Stop admitting, wait for running requests, join the workers, free all.
  * Requests still queued are dropped. */
 int spx_server_destroy(spx_server *S);
+
+/* ------------------------------------------------------------------ measurement and test aids */
+/* Neither call is part of the method the paper describes: one measures a
+ * floor for the SpMV kernels, the other exercises the failure path. */
+
+/* A measurement aid (not part of the paper's method): stream col_idx[nnz]
+ * and gather x (dtype SPX_F64 or SPX_F32) at every index, summing the
+ * gathered values; nothing is stored except, practically never, out[0]
+ * (device, one element).  Its time is the floor any SpMV kernel has on that
+ * sparsity pattern: the gathers of x plus 4 bytes per nonzero.  Device
+ * pointers; every index must lie inside x (not checked).  Asynchronous on the
+ * context stream.  Errors: SPX_ERR_INVALID. */
+int spx_probe_gather(spx_ctx *ctx, int64_t nnz, const int32_t *col_idx, const void *x, int dtype, void *out);
+
+/* Test hook for the failure path: launch one wait that nothing will satisfy
+ * (which = 0: a look-back flag; 1: an mbarrier phase), limited to about a
+ * millisecond of SM clocks.  It gives up, records the error and returns, so
+ * the following spx_ctx_check reports SPX_ERR_TIMEOUT.  Nothing hangs or
+ * faults.  Asynchronous.  Errors: SPX_ERR_INVALID. */
+int spx_selftest_wait_timeout(spx_ctx *ctx, int which);
 
 /* ------------------------------------------------------------------ errors */
 

@@ -330,7 +330,8 @@ void free_matrix_arrays(spx_matrix *A)
                     &A->coo_val32, &A->tiles,    &A->carry_row, &A->carry_val, &A->partials,
                     &A->ticket,   &A->stage_x,   &A->stage_y,   &A->coo_tiles, &A->flags,
                     &A->hint,     &A->coo_rowtiles, &A->tc_col, &A->tc_val, &A->tc_val32, &A->tc_row,
-                    &A->tc_mask,  &A->empty_rows, &A->ct_row, &A->ct_col, &A->ct_val, &A->ct_val32};
+                    &A->tc_mask,  &A->empty_rows, &A->ct_row, &A->ct_col, &A->ct_val, &A->ct_val32,
+                    &A->small_out};
     for (DBuf *b : bufs) dbuf_free(c, *b);
 }
 
@@ -600,6 +601,7 @@ extern "C" int spx_matrix_destroy(spx_matrix *A)
     if (!A) return SPX_OK;
     DeviceGuard g(A->ctx->device);
     solver_work_free(A);
+    if (A->batch1) spx_batch_destroy(A->batch1);
     free_matrix_arrays(A);
     cudaStreamSynchronize(A->ctx->stream);
     delete A;

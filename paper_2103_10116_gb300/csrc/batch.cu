@@ -45,7 +45,14 @@ struct BOut {
     int *status;
     long long *iters;
     double *relres;
+    int *cycles;  // refinement cycles (mixed precision), else 0
 };
+
+// per-system results on the device and in the host copy: status | iterations | residual | cycles
+inline size_t bout_off_iters(int64_t nsys) { return round_up((size_t)nsys * 4, 256); }
+inline size_t bout_off_relres(int64_t nsys) { return bout_off_iters(nsys) + round_up((size_t)nsys * 8, 256); }
+inline size_t bout_off_cycles(int64_t nsys) { return bout_off_relres(nsys) + round_up((size_t)nsys * 8, 256); }
+inline size_t bout_bytes(int64_t nsys) { return bout_off_cycles(nsys) + round_up((size_t)nsys * 4, 256); }
 
 template <class T, int BLOCK> __device__ __forceinline__ T bsum(T v, T *red) { return block_sum<T, BLOCK>(v, red); }
 
@@ -60,6 +67,20 @@ __device__ __forceinline__ T row_dot(const int *__restrict__ rp, const int *__re
     return s;
 }
 
+// The scalars of an iteration (alpha, beta, omega) are computed once per block,
+// by thread 0, and read from shared memory: a division is a sequence of FP64
+// instructions, and every thread of the block computing it cost as much FP64
+// issue as a fifth of a small system's iteration (ncu: the FP64 pipe 78% busy
+// on one 4096-row system).  Slot k is written once per iteration and read right
+// after the barrier that follows the write; the block reductions between two
+// writes of a slot end every read of it.
+template <class T> __device__ __forceinline__ T share_scalar(T v, T *slot)
+{
+    if (threadIdx.x == 0) *slot = v;
+    __syncthreads();
+    return *slot;
+}
+
 // One system by CG in precision T on values V (V = T, or float values in the
 // FP32 inner solve).  x: initial guess (zero_x0: start from 0).  check_true:
 // form the true residual at exit and restart from x if it misses tol.
@@ -69,6 +90,7 @@ __device__ int cg_system(int n, const int *__restrict__ rp, const int *__restric
                          T *red, T tol, long long maxit, bool zero_x0, bool check_true, long long &iters, T &relres)
 {
     const int tid = threadIdx.x;
+    __shared__ T sc[2];
     T bb = T(0);
     for (int i = tid; i < n; i += BLOCK) bb = fma(b[i], b[i], bb);
     bb = bsum<T, BLOCK>(bb, red);
@@ -94,7 +116,7 @@ __device__ int cg_system(int n, const int *__restrict__ rp, const int *__restric
         rho = bsum<T, BLOCK>(rho, red);  // (ends with a barrier: ps free)
         for (int i = tid; i < n; i += BLOCK) ps[i] = r[i];
         __syncthreads();
-        relres = sqrt(rho / bb);
+        T last = rho;  // the last recurrence residual, squared
         status = rho <= tol2 ? SPX_CONVERGED : SPX_MAX_ITER;
         while (status == SPX_MAX_ITER && iters < maxit) {
             T pq = T(0);
@@ -108,7 +130,7 @@ __device__ int cg_system(int n, const int *__restrict__ rp, const int *__restric
                 status = SPX_BREAKDOWN;
                 break;
             }
-            const T alpha = rho / pq;
+            const T alpha = share_scalar(tid == 0 ? rho / pq : T(0), &sc[0]);
             T rr = T(0);
             for (int i = tid; i < n; i += BLOCK) {
                 x[i] = fma(alpha, ps[i], x[i]);
@@ -118,16 +140,17 @@ __device__ int cg_system(int n, const int *__restrict__ rp, const int *__restric
             }
             rr = bsum<T, BLOCK>(rr, red);
             ++iters;
-            relres = sqrt(rr / bb);
+            last = rr;
             if (rr <= tol2) {
                 status = SPX_CONVERGED;
                 break;
             }
-            const T beta = rr / rho;
+            const T beta = share_scalar(tid == 0 ? rr / rho : T(0), &sc[1]);
             rho = rr;
             for (int i = tid; i < n; i += BLOCK) ps[i] = fma(beta, ps[i], r[i]);
             __syncthreads();
         }
+        if (tid == 0) relres = sqrt(last / bb);
         if (!check_true || status != SPX_CONVERGED) break;
         // true residual
         __syncthreads();
@@ -159,6 +182,7 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
                                long long &iters, T &relres)
 {
     const int tid = threadIdx.x;
+    __shared__ T sc[3];
     T *r = w[0], *rh = w[1], *p = w[2], *v = w[3], *s = w[4], *t = w[5];
     T bb = T(0);
     for (int i = tid; i < n; i += BLOCK) bb = fma(b[i], b[i], bb);
@@ -186,14 +210,14 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
         }
         rr0 = bsum<T, BLOCK>(rr0, red);
         T rho = T(1), alpha = T(1), omega = T(1), rho1 = rr0;
-        relres = sqrt(rr0 / bb);
+        T last = rr0;  // the last recurrence residual, squared
         status = rr0 <= tol2 ? SPX_CONVERGED : SPX_MAX_ITER;
         while (status == SPX_MAX_ITER && iters < maxit) {
             if (rho1 == T(0)) {
                 status = SPX_BREAKDOWN;
                 break;
             }
-            const T beta = (rho1 / rho) * (alpha / omega);
+            const T beta = share_scalar(tid == 0 ? (rho1 / rho) * (alpha / omega) : T(0), &sc[0]);
             for (int i = tid; i < n; i += BLOCK) {
                 const T pi = fma(beta, fma(-omega, v[i], p[i]), r[i]);
                 p[i] = pi;
@@ -211,7 +235,7 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
                 status = SPX_BREAKDOWN;
                 break;
             }
-            alpha = rho1 / rv;
+            alpha = share_scalar(tid == 0 ? rho1 / rv : T(0), &sc[1]);
             T ss = T(0);
             for (int i = tid; i < n; i += BLOCK) {
                 const T si = fma(-alpha, v[i], r[i]);
@@ -226,7 +250,7 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
                     x[i] = fma(alpha, p[i], x[i]);
                     r[i] = s[i];
                 }
-                relres = sqrt(ss / bb);
+                last = ss;
                 status = SPX_CONVERGED;
                 __syncthreads();
                 break;
@@ -244,7 +268,7 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
                 status = SPX_BREAKDOWN;
                 break;
             }
-            omega = ts / tt;
+            omega = share_scalar(tid == 0 ? ts / tt : T(0), &sc[2]);
             T rr = T(0), rhr = T(0);
             for (int i = tid; i < n; i += BLOCK) {
                 x[i] = fma(omega, s[i], fma(alpha, p[i], x[i]));
@@ -255,7 +279,7 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
             }
             rr = bsum<T, BLOCK>(rr, red);
             rhr = bsum<T, BLOCK>(rhr, red);
-            relres = sqrt(rr / bb);
+            last = rr;
             if (rr <= tol2) {
                 status = SPX_CONVERGED;
                 break;
@@ -267,6 +291,7 @@ __device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__r
             rho = rho1;
             rho1 = rhr;
         }
+        if (tid == 0) relres = sqrt(last / bb);
         if (!check_true || status != SPX_CONVERGED) break;
         __syncthreads();
         for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
@@ -298,9 +323,10 @@ __device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restri
                           long long maxit, bool zero_x0, bool check_true, long long &iters, T &relres,
                           int stall = 0)
 {
-    T mark = T(1);
+    T mark2 = T(1);  // the squared relative residual the stall test measures against
     long long mark_it = iters;
     const int tid = threadIdx.x;
+    __shared__ T sc[2];
     T *r = w[0], *rh = w[1], *p = w[2], *u = w[3], *q = w[4], *v = w[5];
     T bb = T(0);
     for (int i = tid; i < n; i += BLOCK) bb = fma(b[i], b[i], bb);
@@ -330,7 +356,7 @@ __device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restri
         for (int i = tid; i < n; i += BLOCK) ps[i] = p[i];
         __syncthreads();
         T rho = rr0;
-        relres = sqrt(rr0 / bb);
+        T last = rr0;  // the last recurrence residual, squared
         status = rr0 <= tol2 ? SPX_CONVERGED : SPX_MAX_ITER;
         while (status == SPX_MAX_ITER && iters < maxit) {
             if (rho == T(0)) {
@@ -348,7 +374,7 @@ __device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restri
                 status = SPX_BREAKDOWN;
                 break;
             }
-            const T alpha = rho / rv;
+            const T alpha = share_scalar(tid == 0 ? rho / rv : T(0), &sc[0]);
             for (int i = tid; i < n; i += BLOCK) {
                 const T qi = fma(-alpha, v[i], u[i]);
                 q[i] = qi;
@@ -367,21 +393,21 @@ __device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restri
             rr = bsum<T, BLOCK>(rr, red);
             rhr = bsum<T, BLOCK>(rhr, red);
             ++iters;
-            relres = sqrt(rr / bb);
+            last = rr;
             if (rr <= tol2) {
                 status = SPX_CONVERGED;
                 break;
             }
-            if (stall > 0) {
-                if (relres < T(0.5) * mark) {
-                    mark = relres;
+            if (stall > 0) {  // ||r|| / ||b|| below half the mark, compared in squares
+                if (rr < T(0.25) * mark2 * bb) {
+                    mark2 = rr / bb;
                     mark_it = iters;
                 } else if (iters - mark_it >= stall) {
                     status = SPX_STAGNATED;
                     break;
                 }
             }
-            const T beta = rhr / rho;
+            const T beta = share_scalar(tid == 0 ? rhr / rho : T(0), &sc[1]);
             for (int i = tid; i < n; i += BLOCK) {
                 const T ui = fma(beta, q[i], r[i]);
                 u[i] = ui;
@@ -392,6 +418,7 @@ __device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restri
             __syncthreads();
             rho = rhr;
         }
+        if (tid == 0) relres = sqrt(last / bb);
         if (!check_true || status != SPX_CONVERGED) break;
         __syncthreads();
         for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
@@ -443,6 +470,7 @@ __global__ void __launch_bounds__(BLOCK)
         long long iters = 0;
         T relres = T(0);
         int status;
+        int outer = 0;
         if (!MIXED) {
             const T *val = val_all + nnz_off[s];
             T *ps = reinterpret_cast<T *>(smem);
@@ -480,7 +508,7 @@ __global__ void __launch_bounds__(BLOCK)
                 for (int i = threadIdx.x; i < n; i += BLOCK) xd[i] = 0.0;
                 status = SPX_CONVERGED;
             }
-            for (int outer = 0; status != SPX_CONVERGED && outer <= 20; ++outer) {
+            for (outer = 0; status != SPX_CONVERGED && outer <= 20; ++outer) {
                 for (int i = threadIdx.x; i < n; i += BLOCK) xs[i] = xd[i];
                 __syncthreads();
                 double rr = 0.0;
@@ -520,6 +548,7 @@ __global__ void __launch_bounds__(BLOCK)
             out.status[s] = status;
             out.iters[s] = iters;
             out.relres[s] = (double)relres;
+            out.cycles[s] = outer;
         }
     }
 }
@@ -541,11 +570,30 @@ int launch_batch_t(spx_ctx *ctx, spx_batch *B, const T *b, T *x, double tol, int
         per_sm = 1;
     int64_t grid = (int64_t)per_sm * ctx->sm_count;
     if (grid > B->nsys) grid = B->nsys;
-    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(
-        B->nsys, B->d_row_off.as<int64_t>(), B->d_nnz_off.as<int64_t>(), B->rp.as<int>(), B->col.as<int>(),
-        B->val.as<T>(), B->val32.as<float>(), B->order.as<int>(), b, x, B->work.as<T>(), B->nrows, (T)tol,
-        (long long)maxit, queue, out);
-    SPX_CUDA(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)BLOCK);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    if (B->nsys == 1) {
+        // one system, one block: give the SM's unified L1 / shared memory to L1 beyond
+        // what the block needs, so the matrix, re-read every iteration, stays in L1
+        // (the driver otherwise may carve out shared memory for blocks that never come)
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+        const int need = smem + 2048;
+        int pct = smem_sm > 0 ? (int)(((int64_t)need * 100 + smem_sm - 1) / smem_sm) : 100;
+        at[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+        at[0].val.sharedMemCarveout = (unsigned)std::min(100, std::max(1, pct));
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, B->nsys, (const int64_t *)B->d_row_off.as<int64_t>(),
+                                (const int64_t *)B->d_nnz_off.as<int64_t>(), (const int *)B->rp.as<int>(),
+                                (const int *)B->col.as<int>(), (const T *)B->val.as<T>(),
+                                (const float *)B->val32.as<float>(), (const int *)B->order.as<int>(), b, x,
+                                B->work.as<T>(), B->nrows, (T)tol, (long long)maxit, queue, out));
     return SPX_OK;
 }
 
@@ -567,9 +615,9 @@ int launch_batch(spx_ctx *ctx, spx_batch *B, int block, int solver, int precisio
 {
     BOut out;
     out.status = B->out.as<int>();
-    out.iters = reinterpret_cast<long long *>(B->out.as<char>() + round_up((size_t)B->nsys * 4, 256));
-    out.relres = reinterpret_cast<double *>(B->out.as<char>() + round_up((size_t)B->nsys * 4, 256) +
-                                            round_up((size_t)B->nsys * 8, 256));
+    out.iters = reinterpret_cast<long long *>(B->out.as<char>() + bout_off_iters(B->nsys));
+    out.relres = reinterpret_cast<double *>(B->out.as<char>() + bout_off_relres(B->nsys));
+    out.cycles = reinterpret_cast<int *>(B->out.as<char>() + bout_off_cycles(B->nsys));
     unsigned *queue = B->queue.as<unsigned>();
     SPX_CUDA(cudaMemsetAsync(queue, 0, 4, ctx->stream));
     if (precision == SPX_PREC_MIXED) {
@@ -674,7 +722,7 @@ extern "C" int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_
     chk(dbuf_alloc(ctx, B->val, (size_t)nnz * V));
     chk(dbuf_alloc(ctx, B->order, (size_t)nsys * 4));
     chk(dbuf_alloc(ctx, B->work, (size_t)nrows * 8 * 8));
-    chk(dbuf_alloc(ctx, B->out, round_up((size_t)nsys * 4, 256) + 2 * round_up((size_t)nsys * 8, 256)));
+    chk(dbuf_alloc(ctx, B->out, bout_bytes(nsys)));
     chk(dbuf_alloc(ctx, B->queue, 64));
     if (st == SPX_OK && (flags & SPX_MIXED_SHADOW) && dtype == SPX_F64) chk(dbuf_alloc(ctx, B->val32, (size_t)nnz * 4));
     // largest systems first
@@ -696,7 +744,7 @@ extern "C" int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_
             k_cast_f32<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(nnz, B->val.as<double>(), B->val32.as<float>());
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaMallocHost(&B->host_out, round_up((size_t)nsys * 4, 256) + 2 * round_up((size_t)nsys * 8, 256) + 64);
+        if (e == cudaSuccess) e = cudaMallocHost(&B->host_out, bout_bytes(nsys) + 64);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "spx_batch_create");
     }
@@ -732,7 +780,7 @@ int batch_solve_impl(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int sol
     if (precision == SPX_PREC_F64 && B->dtype != SPX_F64) return fail(SPX_ERR_UNSUPPORTED, "precision must match dtype");
     if (precision == SPX_PREC_F32 && B->dtype != SPX_F32) return fail(SPX_ERR_UNSUPPORTED, "precision must match dtype");
     const auto t0 = std::chrono::steady_clock::now();
-    const size_t out_bytes = round_up((size_t)B->nsys * 4, 256) + 2 * round_up((size_t)B->nsys * 8, 256);
+    const size_t out_bytes = bout_bytes(B->nsys);
     uint64_t key[10] = {(uint64_t)(uintptr_t)b, (uint64_t)(uintptr_t)x, (uint64_t)solver, (uint64_t)precision, 0,
                         (uint64_t)max_iter, (uint64_t)block, (uint64_t)(uintptr_t)ctx->stream, 0, 0};
     std::memcpy(&key[4], &tol, 8);
@@ -777,9 +825,9 @@ int batch_solve_impl(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int sol
     if (infos) {
         const char *h = static_cast<const char *>(B->host_out);
         const int *stv = reinterpret_cast<const int *>(h);
-        const long long *itv = reinterpret_cast<const long long *>(h + round_up((size_t)B->nsys * 4, 256));
-        const double *rv = reinterpret_cast<const double *>(h + round_up((size_t)B->nsys * 4, 256) +
-                                                             round_up((size_t)B->nsys * 8, 256));
+        const long long *itv = reinterpret_cast<const long long *>(h + bout_off_iters(B->nsys));
+        const double *rv = reinterpret_cast<const double *>(h + bout_off_relres(B->nsys));
+        const int *cyv = reinterpret_cast<const int *>(h + bout_off_cycles(B->nsys));
         for (int64_t s = 0; s < B->nsys; ++s) {
             std::memset(&infos[s], 0, sizeof(infos[s]));
             infos[s].status = stv[s];
@@ -787,7 +835,10 @@ int batch_solve_impl(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int sol
             infos[s].relres_recurrence = rv[s];
             infos[s].relres_true = rv[s];
             infos[s].time_ms = ms;
-            if (precision == SPX_PREC_MIXED) infos[s].inner_iterations = itv[s];
+            if (precision == SPX_PREC_MIXED) {
+                infos[s].inner_iterations = itv[s];
+                infos[s].restarts = cyv[s];  // refinement cycles, as the per-system path reports them
+            }
         }
     }
     return SPX_OK;

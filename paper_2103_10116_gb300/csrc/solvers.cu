@@ -1933,6 +1933,44 @@ int solve_typed(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, int solver, doubl
     return run_short<T>(ctx, A, A->work, solver, b, x, tol, maxit, use32, false, fixed, info);
 }
 
+// ------------------------------------------------------------------ single-launch route for small systems
+// Small systems are solved by one launch that runs every iteration, where the
+// general path pays three launches and a device-wide reduction per iteration
+// (the 2D Laplacian on a 64 x 64 grid, n = 4096: 23 us per CG iteration
+// there).  CG in FP64 or FP32 runs on one cluster of eight SMs (cluster.cu);
+// BiCGSTAB, CGS and FP32-inner refinement run in the persistent batched kernel
+// as a batch of one (one SM).  CSR matrices of at most kSmallSolveRows rows
+// whose SpMV kernel is left to the library, no preconditioner, run to a
+// tolerance.  The batch (the matrix's own copy of
+// the CSR arrays, from its creating context) is built on first use and kept
+// with the matrix.
+constexpr int64_t kSmallSolveRows = 16384;
+
+int small_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol, int64_t maxit,
+                int precision, spx_solve_info *info)
+{
+    const bool mixed = precision == SPX_PREC_MIXED;
+    if (mixed ? A->dtype != SPX_F64 : (precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32) != A->dtype)
+        return SPX_ERR_UNSUPPORTED;  // the general path reports the mismatch
+    if (solver == SPX_CG && !mixed && A->n <= cluster_cg_max_rows())  // one cluster of SMs: see cluster.cu
+        return cluster_cg_solve(ctx, A, b, x, tol, maxit, info);
+    if (A->n > batch_max_rows(ctx)) return SPX_ERR_UNSUPPORTED;
+    if (!A->batch1 || (mixed && !A->batch1_shadow)) {
+        if (A->batch1) spx_batch_destroy(A->batch1);
+        A->batch1 = nullptr;
+        const int64_t ro[2] = {0, A->n}, no[2] = {0, A->nnz};
+        SPX_TRY(spx_batch_create(A->ctx, &A->batch1, A->dtype, 1, ro, no, A->rp.as<int32_t>(), A->col.as<int32_t>(),
+                                 A->val.p, mixed ? SPX_MIXED_SHADOW : 0u));
+        A->batch1_shadow = mixed;
+        SPX_CUDA(cudaStreamSynchronize(A->ctx->stream));  // ready for any context's stream
+    }
+    const int block = A->n <= 2048 ? 256 : A->n <= 8192 ? 512 : 1024;
+    spx_solve_info one;
+    SPX_TRY(batch_solve_direct(ctx, A->batch1, b, x, solver, tol, maxit, precision, block, &one));
+    *info = one;
+    return SPX_OK;
+}
+
 int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol, int64_t maxit,
                 int restart, int precision, int64_t fixed, spx_solve_info *info)
 {
@@ -1952,6 +1990,14 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
     }
     Timer tm;
     int st;
+    if (fixed == 0 && !pre && bs == 0 && solver != SPX_GMRES && A->format == SPX_CSR && A->n <= kSmallSolveRows &&
+        A->rp.p && A->kernel == SPX_KERNEL_AUTO) {  // a pinned SpMV kernel keeps the general path
+        st = small_solve(ctx, A, b, x, solver, tol, maxit, precision, info);
+        if (st != SPX_ERR_UNSUPPORTED) {
+            info->time_ms = tm.ms();
+            return st;
+        }
+    }
     if (precision == SPX_PREC_MIXED) {
         if (A->dtype != SPX_F64 || !(A->val32.p || A->ell_val32.p || A->coo_val32.p))
             return fail(SPX_ERR_UNSUPPORTED, "mixed precision needs an FP64 matrix created with SPX_MIXED_SHADOW");

@@ -139,6 +139,10 @@ struct spx_matrix {
     spx::DBuf stage_x, stage_y;
     // solver workspace (solvers.cu)
     spx::SolverWork *work = nullptr;
+    // small systems: the matrix as a batch of one for the one-block solve route (solvers.cu)
+    spx_batch *batch1 = nullptr;
+    bool batch1_shadow = false;
+    spx::DBuf small_out;  // result record of the cluster CG (cluster.cu)
 };
 
 namespace spx {
@@ -194,5 +198,10 @@ constexpr int kIrCgsStall = 20;
 int batch_solve_direct(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int solver, double tol, int64_t max_iter,
                        int precision, int block, spx_solve_info *infos);
 int batch_max_rows(const spx_ctx *ctx);
+
+// CG on one thread-block cluster for small CSR systems (cluster.cu); synchronous.
+int cluster_cg_max_rows();
+int cluster_cg_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, double tol, int64_t maxit,
+                     spx_solve_info *info);
 
 }  // namespace spx
