@@ -1937,14 +1937,16 @@ int solve_typed(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, int solver, doubl
 // Small systems are solved by one launch that runs every iteration, where the
 // general path pays three launches and a device-wide reduction per iteration
 // (the 2D Laplacian on a 64 x 64 grid, n = 4096: 23 us per CG iteration
-// there).  CG in FP64 or FP32 runs on one cluster of eight SMs (cluster.cu);
-// BiCGSTAB, CGS and FP32-inner refinement run in the persistent batched kernel
-// as a batch of one (one SM).  CSR matrices of at most kSmallSolveRows rows
-// whose SpMV kernel is left to the library, no preconditioner, run to a
-// tolerance.  The batch (the matrix's own copy of
-// the CSR arrays, from its creating context) is built on first use and kept
-// with the matrix.
-constexpr int64_t kSmallSolveRows = 16384;
+// there).  CG in FP64 or FP32 on up to kSmallSolveRows rows runs on one
+// cluster of 16 (or 8) SMs (cluster.cu); BiCGSTAB, CGS and FP32-inner
+// refinement on up to kSmallBatchRows rows run in the persistent batched
+// kernel as a batch of one (one SM, whose two FP64 lanes bound it, so larger
+// systems take the general path).  CSR matrices whose SpMV kernel is left to
+// the library, no preconditioner, run to a tolerance.  The batch (the matrix's
+// own copy of the CSR arrays, from its creating context) is built on first use
+// and kept with the matrix.
+constexpr int64_t kSmallSolveRows = 32768;   // CG on a cluster
+constexpr int64_t kSmallBatchRows = 4096;    // the other solvers on one SM
 
 int small_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol, int64_t maxit,
                 int precision, spx_solve_info *info)
@@ -1952,9 +1954,11 @@ int small_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
     const bool mixed = precision == SPX_PREC_MIXED;
     if (mixed ? A->dtype != SPX_F64 : (precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32) != A->dtype)
         return SPX_ERR_UNSUPPORTED;  // the general path reports the mismatch
-    if (solver == SPX_CG && !mixed && A->n <= cluster_cg_max_rows())  // one cluster of SMs: see cluster.cu
-        return cluster_cg_solve(ctx, A, b, x, tol, maxit, info);
-    if (A->n > batch_max_rows(ctx)) return SPX_ERR_UNSUPPORTED;
+    if (solver == SPX_CG && !mixed && A->n <= cluster_cg_max_rows()) {  // one cluster of SMs: see cluster.cu
+        const int st = cluster_cg_solve(ctx, A, b, x, tol, maxit, info);
+        if (st != SPX_ERR_UNSUPPORTED) return st;
+    }
+    if (A->n > kSmallBatchRows || A->n > batch_max_rows(ctx)) return SPX_ERR_UNSUPPORTED;
     if (!A->batch1 || (mixed && !A->batch1_shadow)) {
         if (A->batch1) spx_batch_destroy(A->batch1);
         A->batch1 = nullptr;

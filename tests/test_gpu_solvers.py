@@ -285,3 +285,33 @@ def test_cg_full_size_poisson_128(spx, ctx):
         assert _true_relres(rp, col, val, b, x.cpu().numpy()) <= residual_limit(rp, col, val, b, x.cpu().numpy(), 1e-10)
     finally:
         spx.spx_matrix_destroy(A)
+
+
+@pytest.mark.parametrize("n_side", [1, 3, 32, 64, 65, 100, 181])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_small_cg_single_launch_route(spx, ctx, n_side, dtype):
+    """Small CSR systems with the automatic kernel: CG runs in one launch on a
+    thread-block cluster (up to 32768 rows; n_side^2 rows here, from 1 row to
+    32761, with slices of the cluster's blocks left empty or ragged).  Same
+    oracle checks as the general path; FP32 to a tolerance it can reach."""
+    rp, col, val = synth.laplace2d_5pt(n_side)
+    n = rp.shape[0] - 1
+    xs = synth.uniform_vector(n, seed=3)
+    b = oracle.spmv_csr(rp, col, val, xs)
+    tol = 1e-10 if dtype == torch.float64 else 1e-5
+    A = _make(spx, ctx, "csr", rp, col, val, dtype=dtype)
+    try:
+        x = torch.zeros(n, dtype=dtype, device=DEV)
+        info = spx.spx_solve(ctx, A, _t(b).to(dtype), x, "cg", tol, 20000,
+                             precision="f64" if dtype == torch.float64 else "f32")
+        assert info.status == spx.SPX_CONVERGED, info
+        xh = x.double().cpu().numpy()
+        _, oinfo = oracle.cg(rp, col, val, b, tol=tol, maxit=20000)
+        if dtype == torch.float64:
+            assert info.relres_true <= tol
+            assert _true_relres(rp, col, val, b, xh) <= residual_limit(rp, col, val, b, xh, tol)
+            assert abs(info.iterations - oinfo.iterations) <= max(3, oinfo.iterations // 10), (info, oinfo)
+        else:  # FP32 arithmetic: the FP64 residual of the FP32 solution, with FP32 rounding slack
+            assert _true_relres(rp, col, val, b, xh) <= 3 * tol
+    finally:
+        spx.spx_matrix_destroy(A)
