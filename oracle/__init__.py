@@ -131,6 +131,8 @@ def _lib(mutant: int = 0) -> C.CDLL:
             lib.orc_ir.restype = C.c_int
             lib.orc_ir.argtypes = [i64, p, p, p, C.c_int, p, p, dbl, dbl, C.c_int, i64,
                                    C.POINTER(_Info)]
+            lib.orc_cg_reliable.restype = C.c_int
+            lib.orc_cg_reliable.argtypes = [i64, p, p, p, p, p, dbl, dbl, i64, C.POINTER(_Info)]
             lib.orc_spmv_repeat.argtypes = [i64, p, p, p, p, p, C.c_int]
             _LIBS[mutant] = lib
         return _LIBS[mutant]
@@ -347,3 +349,16 @@ def ir(rp, col, val, b, solver="cg", tol=1e-10, inner_tol=1e-4, max_outer=20,
                   C.byref(info))
     return x, SolveInfo(info.status, info.iterations, info.restarts, info.relres_recurrence,
                         info.relres_true)
+
+
+def cg_reliable(rp, col, val, b, tol=1e-10, delta=0.1, maxit=100000, x0=None, mutant=0):
+    """Mixed-precision CG with reliable updates: FP32 iterations, FP64 residual
+    replacement whenever the FP32 residual fell by delta (see the C source)."""
+    rp, col, val = _csr(rp, col, val)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = rp.shape[0] - 1
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    inf = _Info()
+    _lib(mutant).orc_cg_reliable(n, _ptr(rp), _ptr(col), _ptr(val), _ptr(b), _ptr(x), float(tol), float(delta),
+                                 int(maxit), C.byref(inf))
+    return x, SolveInfo(inf.status, inf.iterations, inf.restarts, inf.relres_recurrence, inf.relres_true)

@@ -17,7 +17,8 @@
  *     for the others; block inverses by Gauss-Jordan with partial pivoting,
  *     optionally stored in FP32 for well-conditioned blocks);
  *   - iterative refinement with an FP32 inner Krylov solve and FP64 outer
- *     residual and update.
+ *     residual and update, and CG with FP32 iterations and FP64 residual
+ *     replacement ("reliable updates": the Krylov space is kept).
  *
  * Build flags must keep IEEE semantics: -O2 -ffp-contract=off, no fast-math,
  * so that x86-64 and aarch64 hosts produce identical bits.  A second build with
@@ -1113,6 +1114,89 @@ int orc_ir(int64_t n, const int32_t *rp, const int32_t *col, const double *val, 
     info->relres_recurrence = rel;
     info->relres_true = rel;
     free(v32); free(r); free(r32); free(d32);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Mixed-precision CG with reliable updates (the residual replacement of     */
+/* Sleijpen and van der Vorst, Computing 56, 1996, applied to CG with FP32   */
+/* iterations): CG runs in FP32 on the FP32-rounded values, its iterate      */
+/* accumulated in an FP32 correction y.  When the FP32 recurrence residual   */
+/* falls below delta times its largest value since the last update, or below */
+/* tol ||b||, or the iteration budget is spent, y is added to the FP64 x, the */
+/* residual is recomputed as b - A x in FP64 with the FP64 values, and the   */
+/* FP32 residual is replaced by its rounding.  The direction p is kept (no   */
+/* restart of the Krylov space); beta is formed with the replaced residual.  */
+/* The solve ends when the FP64 residual meets tol.  restarts = updates.     */
+/* ------------------------------------------------------------------------- */
+int orc_cg_reliable(int64_t n, const int32_t *rp, const int32_t *col, const double *val,
+                    const double *b, double *x, double tol, double delta, int64_t maxit,
+                    orc_info *info)
+{
+    memset(info, 0, sizeof(*info));
+    int64_t nnz = rp[n];
+    double bnorm = nrm2(n, b);
+    if (bnorm == 0.0) {
+        memset(x, 0, (size_t)n * sizeof(double));
+        return 0;
+    }
+    float *v32 = malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+    for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)val[k];
+    double *r = malloc(sizeof(double) * (size_t)n);
+    size_t fb = sizeof(float) * (size_t)n;
+    float *r32 = malloc(fb), *p = malloc(fb), *q = malloc(fb), *y = malloc(fb);
+    /* the FP64 residual of the current x */
+    orc_spmv_csr(n, rp, col, val, x, r);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    double rel = nrm2(n, r) / bnorm;
+    int status = rel <= tol ? ORC_CONVERGED : ORC_MAX_ITER;
+    int64_t it = 0;
+    int updates = 0;
+    const float ftol = (float)(tol * bnorm);
+    for (int64_t i = 0; i < n; ++i) { r32[i] = (float)r[i]; p[i] = r32[i]; y[i] = 0.0f; }
+    float rho = dot_f32(n, r32, r32);
+    float maxr = sqrtf(rho);
+    while (status != ORC_CONVERGED && it < maxit) {
+        spmv_f32(n, rp, col, v32, p, q);
+        float pq = dot_f32(n, p, q);
+        if (pq == 0.0f) { status = ORC_BREAKDOWN; break; }
+        float alpha = rho / pq;
+        for (int64_t i = 0; i < n; ++i) { y[i] += alpha * p[i]; r32[i] -= alpha * q[i]; }
+        float rho1 = dot_f32(n, r32, r32);
+        ++it;
+        float rn32 = sqrtf(rho1);
+        if (rn32 > maxr) maxr = rn32;
+        if (rn32 <= ftol || rn32 < (float)delta * maxr || it >= maxit) {
+            /* reliable update: fold y into the FP64 x and replace the residual */
+            for (int64_t i = 0; i < n; ++i) { x[i] += (double)y[i]; y[i] = 0.0f; }
+#if ORC_MUTANT == 15
+            /* planted: the FP64 residual is never recomputed (the recurrence is trusted) */
+            for (int64_t i = 0; i < n; ++i) r[i] = (double)r32[i];
+#else
+            orc_spmv_csr(n, rp, col, val, x, r);
+            for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+#endif
+            rel = nrm2(n, r) / bnorm;
+            ++updates;
+            if (rel <= tol) { status = ORC_CONVERGED; break; }
+            for (int64_t i = 0; i < n; ++i) r32[i] = (float)r[i];
+            rho1 = dot_f32(n, r32, r32);
+            maxr = sqrtf(rho1);
+#if ORC_MUTANT == 16
+            rho = rho1;  /* planted: restart the Krylov space (beta = 0) at every update */
+            for (int64_t i = 0; i < n; ++i) p[i] = 0.0f;
+#endif
+        }
+        float beta = rho1 / rho;
+        for (int64_t i = 0; i < n; ++i) p[i] = r32[i] + beta * p[i];
+        rho = rho1;
+    }
+    info->status = status;
+    info->iterations = it;
+    info->restarts = updates;
+    info->relres_recurrence = rel;
+    info->relres_true = rel;
+    free(v32); free(r); free(r32); free(p); free(q); free(y);
     return 0;
 }
 
