@@ -34,6 +34,12 @@ template <class T> struct KState {
     T mark;
     long long mark_it;
     int stall;
+    // reliable updates (FP32 CG inside FP64 residual replacement): when
+    // ru_delta2 > 0 the iteration also stops, for an update, once r.r has
+    // fallen below ru_delta2 times its largest value since the last update
+    // (maxr2); 0 in every other solve
+    T ru_delta2;
+    T maxr2;
 };
 
 enum : int {
@@ -52,6 +58,8 @@ enum : int {
     FIN_PCG_R = 12,     // dots[0] = r.r, dots[1] = r.z -> convergence on r, beta = (r.z)' / (r.z), rho
     FIN_CG_RR = 13,     // dots[0] = r.r              -> convergence only (block-PCG: r.z comes next)
     FIN_PCG_RZ = 14,    // dots[0] = r.z (z = M^-1 r) -> beta = (r.z)' / (r.z), rho (block-PCG)
+    FIN_RU_FIRST = 15,  // dots[0] = r.r of the first FP32 residual -> rho, maxr2; iterating again
+    FIN_RU_NEXT = 16,   // dots[0] = r.r of a replaced FP32 residual -> beta with it, rho, maxr2
 };
 
 template <class T> __device__ __forceinline__ void kstop(KState<T> *s, int status)
@@ -100,8 +108,24 @@ template <class T> __device__ __forceinline__ void run_fin(int fin, void *state,
         s->relres = sqrt(rr / s->bb);
         if (rr <= s->tol2) { kstop(s, SPX_CONVERGED); break; }
         if (s->iters >= s->maxit) { kstop(s, SPX_MAX_ITER); break; }
+        if (s->ru_delta2 > T(0)) {  // due for a reliable update: the host replaces r, keeps p
+            if (rr > s->maxr2) s->maxr2 = rr;
+            if (rr < s->ru_delta2 * s->maxr2) { kstop(s, SPX_CONVERGED); break; }
+        }
         s->beta = rr / s->rho;
         s->rho = rr;
+        break;
+    }
+    case FIN_RU_FIRST:
+    case FIN_RU_NEXT: {  // r holds the rounding of the FP64 residual; p = r (first) or r + beta p
+        const T rr = dots[0];
+        s->beta = fin == FIN_RU_NEXT ? rr / s->rho : T(0);
+        s->rho = rr;
+        s->maxr2 = rr;
+        s->done = 0;
+        s->skip_t = 0;
+        s->status = SPX_MAX_ITER;
+        if (s->iters >= s->maxit) kstop(s, SPX_MAX_ITER);
         break;
     }
     case FIN_BI_RV: {

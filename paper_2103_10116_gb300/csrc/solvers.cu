@@ -1849,9 +1849,147 @@ __global__ void k_ir_update(int64_t n, double *__restrict__ x, const float *__re
         x[i] = fma(s, (double)d[i], x[i]);
 }
 
+// r32 = fl32(r64) with r32.r32 reduced (FP32, fixed order) into the state by `fin`
+// (FIN_RU_FIRST / FIN_RU_NEXT)
+__global__ void __launch_bounds__(kVB)
+    k_ru_replace(int64_t n, const double *__restrict__ r64, float *__restrict__ r32, int fin, KState<float> *st,
+                 float *partials, unsigned *ticket)
+{
+    float d0 = 0.f;
+    double rv[kU];
+    SPX_ROWS_LOOP(rv[u] = r64[i];, const float ri = (float)rv[u]; r32[i] = ri; d0 = fmaf(ri, ri, d0);)
+    grid_dots_finish<float, kVB>(d0, 0.f, (float *)nullptr, fin, st, partials, ticket);
+}
+
+// Mixed-precision CG with reliable updates (the residual replacement of
+// Sleijpen and van der Vorst, 1996): the FP32 CG iteration (the kernels of
+// the FP32 solve, on the FP32 value copy) runs with its iterate accumulated
+// in an FP32 correction d; when its recurrence residual has fallen below
+// delta = 0.1 of its largest value since the last update (or below tol ||b||,
+// or the budget is spent) the iteration stops, d is added to the FP64 x, the
+// residual b - A x is formed in FP64 with the FP64 values, and its rounding
+// replaces the FP32 residual; the direction p is kept and beta is formed with
+// the replaced residual, so the solve keeps CG's iteration count (a
+// refinement cycle that restarts the inner solve starts its Krylov space
+// again: 618 FP32 iterations against 428 for FP64 CG on the 7-point Poisson
+// matrix 128^3).  restarts reports the updates.
+constexpr double kRuDelta = 0.1;
+
+int run_cg_reliable(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, double tol, int64_t maxit,
+                    spx_solve_info *info)
+{
+    const int64_t n = A->n;
+    SolverWork *&w = A->work;
+    SPX_TRY(work_prepare<double>(ctx, w, n, SPX_CG, 0));  // FP64: the residual
+    SPX_TRY(work_prepare<float>(ctx, w->inner, n, SPX_CG, 0));
+    if (!w->ir.p) SPX_TRY(dbuf_alloc(ctx, w->ir, (size_t)n * 8 + 2 * (size_t)round_up(n, 64) * 4 + 256));
+    SolverWork *wi = w->inner;
+    double *r = w->ir.as<double>();
+    float *d32 = reinterpret_cast<float *>(w->ir.as<char>() + round_up((size_t)n * 8, 256));
+    float *r32 = vec<float>(wi, 0), *p32 = vec<float>(wi, 1);
+    KState<float> *st = wi->state.as<KState<float>>();
+    KState<float> *h = static_cast<KState<float> *>(wi->host);
+    const int g = vgrid(ctx, n);
+    double bb = 0;
+    {
+        double d[2];
+        SPX_TRY(dot_launch<double>(ctx, n, b, b, w->dots.as<double>()));
+        SPX_CUDA(cudaMemcpyAsync(d, w->dots.p, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+        bb = d[0];
+    }
+    if (bb == 0.0) {
+        SPX_CUDA(cudaMemsetAsync(x, 0, (size_t)n * 8, ctx->stream));
+        SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+        info->status = SPX_CONVERGED;
+        return SPX_OK;
+    }
+    // r = b - A x in FP64 (with ||r||^2); true if it meets tol
+    auto fp64_residual = [&](double &rel) -> int {
+        Epi<double> e;
+        e.alpha = -1.0;
+        e.beta = 1.0;
+        e.z = b;
+        e.y = r;
+        e.want_yy = true;
+        e.dots = w->dots.as<double>();
+        SPX_TRY(spmv_launch<double>(ctx, A, x, e, false));
+        double d[2];
+        SPX_TRY(read_dots<double>(ctx, w, d));
+        rel = std::sqrt(d[1] / bb);
+        return SPX_OK;
+    };
+    KState<float> hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.bb = (float)bb;
+    hs.rtol2 = (float)(tol * tol);
+    hs.tol2 = (float)(tol * tol * bb);
+    hs.maxit = maxit;
+    hs.status = SPX_MAX_ITER;
+    hs.ru_delta2 = (float)(kRuDelta * kRuDelta);
+    SPX_CUDA(cudaMemcpyAsync(st, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+    SPX_CUDA(cudaMemsetAsync(d32, 0, (size_t)n * 4, ctx->stream));
+    double rel = 0.0;
+    SPX_TRY(fp64_residual(rel));
+    int status = rel <= tol ? SPX_CONVERGED : SPX_MAX_ITER;
+    int updates = 0;
+    if (status != SPX_CONVERGED) {
+        k_ru_replace<<<g, kVB, 0, ctx->stream>>>(n, r, r32, FIN_RU_FIRST, st, wi->red.as<float>(),
+                                                 wi->ticket.as<unsigned>());
+        SPX_CUDA(cudaMemcpyAsync(p32, r32, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    KrylovRun<float> R{ctx, A, wi, nullptr, d32, true, SPX_CG};
+    const int chunk = n < 200000 ? 32 : 16;
+    const bool graphs = n >= kGraphMinRows;
+    int64_t launched = 0;
+    while (status != SPX_CONVERGED) {
+        SPX_TRY(read_state<float>(ctx, wi, sizeof(KState<float>)));
+        while (!h->done) {
+            const uint64_t key[8] = {(uint64_t)SPX_CG,   (uint64_t)(uintptr_t)d32, 0, 1, (uint64_t)chunk, 4 | (1u << 30),
+                                     (uint64_t)(uintptr_t)A, (uint64_t)(uintptr_t)ctx << 1};
+            SPX_TRY(run_chunk(ctx, wi, key, graphs, [&]() -> int {
+                for (int c = 0; c < chunk; ++c) SPX_TRY(cg_iter(R));
+                return SPX_OK;
+            }));
+            launched += chunk;
+            SPX_TRY(read_state<float>(ctx, wi, sizeof(KState<float>)));
+            if (launched > maxit + 4 * chunk) return fail(SPX_ERR_CUDA, "solver did not stop");
+        }
+        // reliable update: x += d in FP64, the residual again in FP64
+        k_ir_update<<<g, kVB, 0, ctx->stream>>>(n, x, d32, 1.0);
+        SPX_CUDA(cudaGetLastError());
+        SPX_CUDA(cudaMemsetAsync(d32, 0, (size_t)n * 4, ctx->stream));
+        SPX_TRY(fp64_residual(rel));
+        ++updates;
+        if (rel <= tol) {
+            status = SPX_CONVERGED;
+            break;
+        }
+        if (h->status != SPX_CONVERGED) {  // the budget is spent, or the iteration broke down
+            status = h->status;
+            break;
+        }
+        // the rounding of the FP64 residual replaces r; beta with it; p = r + beta p
+        k_ru_replace<<<g, kVB, 0, ctx->stream>>>(n, r, r32, FIN_RU_NEXT, st, wi->red.as<float>(),
+                                                 wi->ticket.as<unsigned>());
+        k_cg_p<float, false><<<g, kVB, 0, ctx->stream>>>(n, r32, p32, nullptr, st);
+        SPX_CUDA(cudaGetLastError());
+    }
+    SPX_TRY(check_dev_err(ctx));
+    SPX_TRY(read_state<float>(ctx, wi, sizeof(KState<float>)));
+    info->status = status;
+    info->iterations = h->iters;
+    info->inner_iterations = h->iters;
+    info->restarts = updates;
+    info->relres_recurrence = rel;
+    info->relres_true = rel;
+    return SPX_OK;
+}
+
 int run_ir(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, int solver, double tol, int64_t maxit,
            int m, bool pre, int bs, bool adapt, spx_solve_info *info)
 {
+    if (solver == SPX_CG && !pre && bs == 0) return run_cg_reliable(ctx, A, b, x, tol, maxit, info);
     const int64_t n = A->n;
     SolverWork *&w = A->work;
     SPX_TRY(work_prepare<double>(ctx, w, n, SPX_CG, 0));  // outer: r and scratch only

@@ -223,7 +223,13 @@ def test_mixed_precision_ir(spx, ctx, solver, prob, fmt):
         assert info.relres_true <= 1e-10 and _true_relres(rp, col, val, b, xh) <= residual_limit(rp, col, val, b, xh, 1e-10)
         assert info.restarts >= 2 and info.inner_iterations > 0
         assert np.linalg.norm(xh - xs) / np.linalg.norm(xs) <= 1e-7
-        if solver != "gmres":
+        if solver == "cg":
+            # CG: FP32 iterations with FP64 residual replacement (reliable updates)
+            _, oinfo = oracle.cg_reliable(rp, col, val, b, tol=1e-10)
+            assert oinfo.status == oracle.CONVERGED
+            assert abs(info.iterations - oinfo.iterations) <= max(3, oinfo.iterations // 10), (info, oinfo)
+            assert abs(info.restarts - oinfo.restarts) <= 3, (info, oinfo)
+        elif solver != "gmres":
             _, oinfo = oracle.ir(rp, col, val, b, solver=solver, tol=1e-10)
             assert oinfo.status == oracle.CONVERGED
             assert abs(info.restarts - oinfo.restarts) <= 2, (info, oinfo)
