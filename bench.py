@@ -770,9 +770,9 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
     dominant random rows with 8-32 nonzeros at exactly the drawn size
     (BiCGSTAB; synth.DiagDomFamily); tolerance 1e-8, FP32 inner iterations +
     FP64 refinement; admission by device footprint (90% of free memory).
-    Operators come from host memory and are uploaded per request; those of at
-    most batch_rows rows go to the batch lanes (None: the server default, 0:
-    none).  Payloads are built in arrival order by a producer thread (the
+    Operators come from pinned host memory and are uploaded per request; those
+    of at most batch_rows rows go to the batch lanes (None: the server default,
+    0: none).  Payloads are built in arrival order by a producer thread (the
     random family's columns and every right-hand side are formed on the GPU and
     copied to pinned host memory) and submitted when due, with a bound on the
     host bytes held; latency counts from each request's arrival time."""
@@ -790,6 +790,9 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
     ks = np.rint(np.cbrt(drawn)).astype(np.int64)
     rows = np.where(stencil_fam, ks ** 3, drawn)
     F = synth.DiagDomFamily(1_000_000, seed=7)
+    # request payloads live in pinned host memory, as a serving front end's receive buffers would
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    f_rp, f_val = pin(F.rp), pin(F.val)
     gstream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(gstream):
         d_row = torch.from_numpy(F.row).to(dev)
@@ -810,14 +813,14 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
             if stencil_fam[i]:
                 k = int(ks[i])
                 if k not in stencils:
-                    stencils[k] = synth.laplace3d_7pt(k)
+                    stencils[k] = tuple(pin(a) for a in synth.laplace3d_7pt(k))
                 rp, col, val = stencils[k]
                 nbytes = 16 * n
             else:
                 nnz = int(F.rp[n])
                 colh = torch.empty(nnz, dtype=torch.int32, pin_memory=True)
                 colh.copy_(family_columns(d_j, d_m, d_v, d_row, d_diag, n, nnz), non_blocking=True)
-                rp, val = F.rp[: n + 1], F.val[:nnz]
+                rp, val = f_rp[: n + 1], f_val[:nnz]
                 nbytes = 16 * n + 4 * nnz
             gstream.synchronize()
             col = col if stencil_fam[i] else colh.numpy()
@@ -879,12 +882,13 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
     # the offered load at the HBM roofline: every request's FP32 inner iterations and FP64 outer
     # residuals at their algorithmic bytes
     nnz_of = np.where(stencil_fam, 7 * rows - 6 * ks ** 2, F.rp[np.minimum(rows, F.n_max)])
-    roof = 0.0
+    roof_i = []
     for i, r in enumerate(res):
         n, nnz, solver = int(rows[i]), int(nnz_of[i]), "cg" if stencil_fam[i] else "bicgstab"
         inner = solve_bytes_per_iter(solver, algorithmic_bytes("csr", 4, n, n, nnz), n, V=4)
         outer = algorithmic_bytes("csr", 8, n, n, nnz) + 5 * 8 * n
-        roof += (r["info"].inner_iterations * inner + max(1, r["info"].restarts) * outer) / (peak * 1e9)
+        roof_i.append((r["info"].inner_iterations * inner + max(1, r["info"].restarts) * outer) / (peak * 1e9))
+    roof = float(sum(roof_i))
 
     def phases(sel):
         if not sel:
@@ -897,6 +901,19 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
         return out
 
     slot_res = [r for r in res if not r["batched"]]
+    # where the time goes, by size: the requests' own solve phases against their roofline time
+    buckets = {}
+    for lo, hi in ((1e3, 2.5e4), (2.5e4, 1e5), (1e5, 3e5), (3e5, 1.01e6)):
+        sel = [i for i in range(len(res)) if lo <= rows[i] < hi]
+        if not sel:
+            continue
+        roof_ms = [roof_i[i] * 1e3 for i in sel]
+        solve_ms = [res[i]["solve_ms"] for i in sel]
+        buckets[f"{int(lo)}-{int(hi)}"] = {
+            "requests": len(sel), "batched": int(sum(1 for i in sel if res[i]["batched"])),
+            "roofline_s": round(sum(roof_ms) / 1e3, 2), "solve_phase_s": round(sum(solve_ms) / 1e3, 2),
+            "upload_phase_s": round(sum(res[i]["upload_ms"] for i in sel) / 1e3, 2),
+            "setup_phase_s": round(sum(res[i]["setup_ms"] for i in sel) / 1e3, 2)}
     st.update({"requests": len(res), "converged": conv, "arrival_rate_per_s": rate, "window_s": seconds,
                "wall_s": round(wall, 2), "solves_per_s": round(len(res) / wall, 1), "slots": slots,
                "batch_rows": int(eff_rows), "batched_requests": int(sum(1 for r in res if r["batched"])),
@@ -908,6 +925,7 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
                "achieved_frac_of_roofline_capacity": round(roof / wall, 3),
                "client_delay_ms_p50": round(float(np.percentile(delays, 50)), 3),
                "host_bytes_cap": int(cap),
+               "by_size": buckets,
                "phases_slot_route": phases(slot_res),
                "phases_batch_route": phases([r for r in res if r["batched"]])})
     if plain:
