@@ -914,7 +914,12 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
             "roofline_s": round(sum(roof_ms) / 1e3, 2), "solve_phase_s": round(sum(solve_ms) / 1e3, 2),
             "upload_phase_s": round(sum(res[i]["upload_ms"] for i in sel) / 1e3, 2),
             "setup_phase_s": round(sum(res[i]["setup_ms"] for i in sel) / 1e3, 2)}
-    st.update({"requests": len(res), "converged": conv, "arrival_rate_per_s": rate, "window_s": seconds,
+    bad = [{"request": i, "rows": int(rows[i]), "family": "stencil" if stencil_fam[i] else "random",
+            "batched": bool(r["batched"]), "error": r["error"], "status": r["info"].status_name,
+            "iterations": r["info"].iterations, "restarts": r["info"].restarts, "relres": r["info"].relres_true}
+           for i, r in enumerate(res) if r["info"].status != spx.SPX_CONVERGED or r["error"] != 0]
+    st.update({"requests": len(res), "converged": conv, "not_converged": bad[:12],
+               "arrival_rate_per_s": rate, "window_s": seconds,
                "wall_s": round(wall, 2), "solves_per_s": round(len(res) / wall, 1), "slots": slots,
                "batch_rows": int(eff_rows), "batched_requests": int(sum(1 for r in res if r["batched"])),
                "sizes": "log-uniform rows in [1e3, 1e6], exact per request (stencils: the nearest k^3)",

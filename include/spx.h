@@ -348,9 +348,9 @@ int spx_batch_tune(spx_ctx *ctx, spx_batch *B, int solver, int precision, int *c
 /* A continuous-batching solve server on ctx's device.  budget_bytes caps the
  * device memory of the requests running at once (<= 0: 90% of the free
  * memory at creation); max_slots is the number of large requests that may
- * run concurrently, each on its own stream (1..64).  Small CG / BiCGSTAB / CGS
- * requests (unpreconditioned) (FP64 or MIXED, at most 24 576 rows by default, see
- * spx_server_set_batching) are instead gathered by four batch lanes: each
+ * run concurrently, each on its own stream (1..64).  Small and mid-size CG /
+ * BiCGSTAB / CGS requests (unpreconditioned) (FP64 or MIXED, at most 24 576 rows by default,
+ * see spx_server_set_batching) are instead gathered by four batch lanes: each
  * lane solves every queued small request of one kind (same solver, tol,
  * max_iter, precision and size class) in one launch of the batched kernel,
  * and the lanes run concurrently with each other and with the slots.  The
@@ -409,8 +409,9 @@ typedef struct {
 int spx_server_poll(spx_server *S, spx_server_result *results, int max_results, int wait_ms, int *count);
 
 /* Route requests of at most max_rows rows to the batch lanes from now on
- * (0: none; capped at what the batched kernel holds, about 28 000 rows;
- * negative: leave the limit unchanged, only report it).
+ * (0: none; capped at 262 144 rows; negative: leave the limit unchanged, only
+ * report it).  A batched request runs on one SM of the persistent batched
+ * kernel, batched with queued requests of its size class.
  * *effective (may be NULL) receives the limit in force.  A request's result
  * does not depend on the route of others, but the same request may differ in
  * the last bits between the two routes (different reduction trees). */

@@ -24,6 +24,9 @@ int fail(int status, const std::string &msg)
 }
 int cuda_fail(cudaError_t e, const char *what)
 {
+    // clear the runtime's record of a non-sticky error (a launch refused for its
+    // resources, an invalid argument), so the thread's next call does not report it
+    cudaGetLastError();
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SPX_ERR_OOM : SPX_ERR_CUDA;
 }

@@ -448,8 +448,11 @@ __global__ void __launch_bounds__(BLOCK)
             const int *__restrict__ rp_all, const int *__restrict__ col_all, const T *__restrict__ val_all,
             const float *__restrict__ val32_all, const int *__restrict__ order, const T *__restrict__ b_all,
             T *__restrict__ x_all, T *__restrict__ work, int64_t nrows, T tol, long long maxit, unsigned *queue,
-            BOut out)
+            BOut out, int smem_vec)
 {
+    // The vector the products gather from lives in shared memory (smem_vec) or,
+    // for systems too large for it, in the global workspace (slots 6 and 7 of
+    // the eight per row; read through L1).
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T red[BLOCK / 32];
     __shared__ float redf[BLOCK / 32];
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(BLOCK)
         int outer = 0;
         if (!MIXED) {
             const T *val = val_all + nnz_off[s];
-            T *ps = reinterpret_cast<T *>(smem);
+            T *ps = smem_vec ? reinterpret_cast<T *>(smem) : work + 6 * nrows + ro;
             if (SOLVER == SPX_CG) {
                 status = cg_system<T, T, BLOCK>(n, rp, col, val, b, x, work + ro, work + nrows + ro, ps, red, tol,
                                                 maxit, false, true, iters, relres);
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(BLOCK)
             // outer FP64 refinement
             const double *val = reinterpret_cast<const double *>(val_all) + nnz_off[s];
             const float *v32 = val32_all + nnz_off[s];
-            double *xs = reinterpret_cast<double *>(smem);
+            double *xs = smem_vec ? reinterpret_cast<double *>(smem) : reinterpret_cast<double *>(work) + 6 * nrows + ro;
             double *r64 = reinterpret_cast<double *>(work) + ro;
             float *fw = reinterpret_cast<float *>(reinterpret_cast<double *>(work) + nrows);
             float *r32 = fw + ro, *d32 = fw + nrows + ro;
@@ -528,7 +531,8 @@ __global__ void __launch_bounds__(BLOCK)
                 for (int i = threadIdx.x; i < n; i += BLOCK) r32[i] = (float)(r64[i] / rn);
                 __syncthreads();
                 float rel32 = 0.f;
-                float *ps32 = reinterpret_cast<float *>(smem);
+                float *ps32 = smem_vec ? reinterpret_cast<float *>(smem)
+                                       : reinterpret_cast<float *>(reinterpret_cast<double *>(work) + 7 * nrows) + ro;
                 // at most kIrInnerCap inner iterations per refinement cycle
                 const long long cyc_max = min(maxit, iters + (long long)kIrInnerCap);
                 if (SOLVER == SPX_CG)
@@ -560,11 +564,13 @@ int launch_batch_t(spx_ctx *ctx, spx_batch *B, const T *b, T *x, double tol, int
                    unsigned *queue)
 {
     auto kern = k_batch<T, BLOCK, SOLVER, MIXED>;
-    const int smem = (int)(B->max_n * (MIXED ? 8 : sizeof(T)));
-    if (smem > ctx->max_smem_optin - 1024)
-        return fail(SPX_ERR_TOO_LARGE, "a batched system is too large for the shared-memory tile");
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batch)");
+    int smem = (int)(B->max_n * (MIXED ? 8 : sizeof(T)));
+    const int smem_vec = smem <= ctx->max_smem_optin - 1024 ? 1 : 0;  // else the vector stays in global memory
+    if (!smem_vec) smem = 0;
+    // the opt-in only ever grows (smem_optin): the server's batch lanes launch this
+    // kernel from several threads with different sizes, and lowering the limit
+    // between another thread's opt-in and its launch got that launch refused
+    SPX_TRY(smem_optin(reinterpret_cast<const void *>(kern), smem));
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -575,25 +581,11 @@ int launch_batch_t(spx_ctx *ctx, spx_batch *B, const T *b, T *x, double tol, int
     cfg.blockDim = dim3((unsigned)BLOCK);
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = ctx->stream;
-    cudaLaunchAttribute at[1];
-    if (B->nsys == 1) {
-        // one system, one block: give the SM's unified L1 / shared memory to L1 beyond
-        // what the block needs, so the matrix, re-read every iteration, stays in L1
-        // (the driver otherwise may carve out shared memory for blocks that never come)
-        int smem_sm = 0;
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
-        const int need = smem + 2048;
-        int pct = smem_sm > 0 ? (int)(((int64_t)need * 100 + smem_sm - 1) / smem_sm) : 100;
-        at[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
-        at[0].val.sharedMemCarveout = (unsigned)std::min(100, std::max(1, pct));
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-    }
     SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, B->nsys, (const int64_t *)B->d_row_off.as<int64_t>(),
                                 (const int64_t *)B->d_nnz_off.as<int64_t>(), (const int *)B->rp.as<int>(),
                                 (const int *)B->col.as<int>(), (const T *)B->val.as<T>(),
                                 (const float *)B->val32.as<float>(), (const int *)B->order.as<int>(), b, x,
-                                B->work.as<T>(), B->nrows, (T)tol, (long long)maxit, queue, out));
+                                B->work.as<T>(), B->nrows, (T)tol, (long long)maxit, queue, out, smem_vec));
     return SPX_OK;
 }
 

@@ -43,16 +43,17 @@ def _requests(large=False):
     return reqs
 
 
-@pytest.mark.parametrize("batch_rows", [None, 0])
+@pytest.mark.parametrize("batch_rows", [None, 65536, 0])
 def test_alone_equals_mix(spx, ctx, batch_rows):
-    """batch_rows None: small requests go through the batch lanes, the large
-    one through a slot; 0: every request on a slot of its own."""
+    """batch_rows None (the default, 24576): small requests go through the
+    batch lanes, the large one (32^3 rows) through a slot; 65536: the large
+    one is batched too, its gathered vector in global memory; 0: every
+    request on a slot of its own."""
     from paper_2103_10116_gb300.serving import Server
     reqs = _requests(large=True)
     srv = Server(ctx, 0, max_slots=4, batch_rows=batch_rows)
-    assert (srv.batch_rows is None) or srv.batch_rows == 0
-    if batch_rows is None:
-        assert 20000 <= spx.spx_server_set_batching(srv.h, -1) < 32**3
+    eff = spx.spx_server_set_batching(srv.h, -1)
+    assert eff == (24576 if batch_rows is None else batch_rows)
     try:
         alone = {}
         for i, (rp, col, val, b, solver) in enumerate(reqs):
@@ -213,7 +214,7 @@ def test_resident_matrix_requests(spx, ctx):
 
 def test_phase_times_of_uploaded_requests(spx, ctx):
     from paper_2103_10116_gb300.serving import Server
-    srv = Server(ctx, 0, max_slots=2)
+    srv = Server(ctx, 0, max_slots=2, batch_rows=24576)
     try:
         rp, col, val = synth.laplace3d_7pt(34)       # a slot request
         rps, cols, vals = synth.laplace3d_7pt(12)    # a batched request
@@ -229,5 +230,57 @@ def test_phase_times_of_uploaded_requests(spx, ctx):
             assert min(r["upload_ms"], r["setup_ms"], r["solve_ms"], r["download_ms"]) >= 0
             assert phases <= r["done_ms"] - r["admit_ms"] + 1e-6
             assert r["solve_ms"] > 0
+    finally:
+        srv.close()
+
+
+@pytest.mark.parametrize("which", ["stencil29", "random4645", "stencil12"])
+def test_single_request_batches(spx, ctx, which):
+    """A batch lane solving one request alone, at sizes the trace produced when a
+    launch was once refused (a shared-memory carve-out hint that did not fit):
+    every request completes without error and meets tol."""
+    from paper_2103_10116_gb300.serving import Server
+    if which.startswith("stencil"):
+        m = int(which[7:])
+        rp, col, val = synth.laplace3d_7pt(m)
+        solver = "cg"
+    else:
+        rp, col, val = synth.diagdom_random(int(which[6:]), seed=3)
+        solver = "bicgstab"
+    b = synth.uniform_vector(rp.shape[0] - 1, seed=11)
+    srv = Server(ctx, 0, max_slots=2)
+    try:
+        for _ in range(2):
+            rid = srv.submit(rp, col, val, b, solver=solver, tol=1e-8)
+            srv.drain()
+            r = srv.results[rid]
+            assert r["error"] == 0 and r["batched"] and r["info"].status == spx.SPX_CONVERGED, r
+            res = b - oracle.spmv_csr(rp, col, val, r["x"])
+            assert np.linalg.norm(res) / np.linalg.norm(b) <= residual_limit(rp, col, val, b, r["x"], 1e-8)
+    finally:
+        srv.close()
+
+
+def test_concurrent_lanes_of_different_sizes(spx, ctx):
+    """Many small requests of every batch size class at once: the four batch
+    lanes launch the batched kernel concurrently with different shared-memory
+    sizes, and no launch may be refused (the shared-memory opt-in only grows)."""
+    from paper_2103_10116_gb300.serving import Server
+    rng = np.random.default_rng(8)
+    sizes = rng.integers(800, 24000, size=160)
+    mats = {}
+    srv = Server(ctx, 0, max_slots=2, keep_x=False)
+    try:
+        ids = []
+        for k, n in enumerate(sizes):
+            n = int(n)
+            if n not in mats:
+                mats[n] = synth.diagdom_random(n, seed=n % 97)
+            rp, col, val = mats[n]
+            ids.append(srv.submit(rp, col, val, synth.uniform_vector(n, seed=k), solver="bicgstab", tol=1e-8))
+        srv.drain()
+        for rid in ids:
+            r = srv.results[rid]
+            assert r["error"] == 0 and r["info"].status == spx.SPX_CONVERGED, r
     finally:
         srv.close()
