@@ -5,7 +5,8 @@ One step = one SpMV of every (matrix, value type, format) of the sweep:
   * 27-point 3D stencil on 100^3 (n = 1,000,000, nnz = 26,463,592);
   * power-law random matrix, n = 2,000,000, row lengths Pareto(tail 1.5) with
     mean 16 and cap 20,000, uniform columns, N(0,1) values (nnz = 32.0M);
-  x {FP64, FP32} x {CSR (merge-path), ELL, COO, HYB}, int32 indices.  ELL of
+  x {FP64, FP32} x {CSR (kernel chosen from row statistics), ELL, COO, HYB},
+int32 indices.  ELL of
 the power-law matrix does not fit (20,000 x 2M padded slots) and is reported
 as rejected, as the library does.
 
@@ -15,8 +16,8 @@ COO (V+8) nnz + 2 V n, HYB (V+4) k n + (V+8) nnz_coo + 2 V n (x read once,
 y written once).  Every matrix is larger than the 129 MB L2 and the step
 cycles through 14 matrices, so nothing stays cached between timed steps.
 
---impl reference times the CPU oracle (sequential C, FP64 compensated CSR
-SpMV) on the same workload and metric.  Multi-GPU (torchrun): independent
+--impl reference times the CPU oracle (its plain index-order FP64 CSR SpMV,
+OpenMP over rows on every host core) on the same workload and metric.  Multi-GPU (torchrun): independent
 replicas, one per GPU, no collective on the data path (weak scaling).
 """
 from __future__ import annotations
