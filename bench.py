@@ -290,14 +290,17 @@ def run_gpu(args):
         secondary["jacobi"] = jacobi_secondary(spx, ctx, stream, dev)
     if args.batched:
         secondary["batched"] = batched_secondary(spx, ctx, stream, dev)
+    floors = gather_floor(spx, ctx, stream, mats, dev)
     if args.serve_seconds > 0:
-        secondary["serving"] = serving_secondary(spx, ctx, dev, seconds=args.serve_seconds)
+        # random gathers of x per second on the power-law pattern (32 M uniform columns), FP32
+        pl = mats.get("powerlaw_2m")
+        rate = pl[1].shape[0] / (floors["powerlaw_2m/f32"] * 1e-6) if pl is not None else None
+        secondary["serving"] = serving_secondary(spx, ctx, dev, seconds=args.serve_seconds, gather_rate=rate)
     # the roofline is reported for one kernel: the single-launch sweep entry
     # (HYB launches two) with the largest device time per step
     single = [i for i, e in enumerate(entries) if e["launches"] == 1] or list(range(len(entries)))
     dom = max(single, key=lambda i: per_entry_ms[i])
     de = entries[dom]
-    floors = gather_floor(spx, ctx, stream, mats, dev)
     achieved = de["bytes"] / (per_entry_ms[dom] * 1e-3) / 1e9
     traffic = _traffic(de["name"])
     result = {
@@ -763,7 +766,7 @@ def _host_bytes_cap():
     return float(min(24 << 30, avail // 4))
 
 
-def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0, slots: int = 16,
+def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0, slots: int = 16, gather_rate=None,
                       batch_rows=None, plain=True):
     """Poisson arrivals (rate req/s for `seconds`) of solve requests whose sizes
     are drawn continuously from log-U[1e3, 1e6] rows, 50/50 from two families:
@@ -869,6 +872,7 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
     srv = Server(ctx, 0, max_slots=slots, batch_rows=batch_rows, keep_x=False)
     try:
         eff_rows = spx.spx_server_set_batching(srv.h, -1)
+        cl_rows = spx.spx_server_set_cluster_rows(srv.h, -1)
         wall, ids, delays = replay_lazy(srv, trace, make, max_pending_bytes=cap / 2, tol=1e-8, precision="mixed")
         res = [srv.results[i] for i in ids]
     finally:
@@ -883,13 +887,20 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
     # the offered load at the HBM roofline: every request's FP32 inner iterations and FP64 outer
     # residuals at their algorithmic bytes
     nnz_of = np.where(stencil_fam, 7 * rows - 6 * ks ** 2, F.rp[np.minimum(rows, F.n_max)])
-    roof_i = []
+    # and the same with each request's random gathers of x at the rate the gather probe measures
+    # (one L2 request each: the random family's columns are uniform over the matrix)
+    roof_i, floor_i = [], []
     for i, r in enumerate(res):
         n, nnz, solver = int(rows[i]), int(nnz_of[i]), "cg" if stencil_fam[i] else "bicgstab"
         inner = solve_bytes_per_iter(solver, algorithmic_bytes("csr", 4, n, n, nnz), n, V=4)
         outer = algorithmic_bytes("csr", 8, n, n, nnz) + 5 * 8 * n
-        roof_i.append((r["info"].inner_iterations * inner + max(1, r["info"].restarts) * outer) / (peak * 1e9))
+        t_hbm = (r["info"].inner_iterations * inner + max(1, r["info"].restarts) * outer) / (peak * 1e9)
+        roof_i.append(t_hbm)
+        products = r["info"].inner_iterations * (1 if solver == "cg" else 2) + max(1, r["info"].restarts)
+        t_gather = products * nnz / gather_rate if (gather_rate and not stencil_fam[i]) else 0.0
+        floor_i.append(max(t_hbm, t_gather))
     roof = float(sum(roof_i))
+    floor = float(sum(floor_i))
 
     def phases(sel):
         if not sel:
@@ -912,7 +923,9 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
         solve_ms = [res[i]["solve_ms"] for i in sel]
         buckets[f"{int(lo)}-{int(hi)}"] = {
             "requests": len(sel), "batched": int(sum(1 for i in sel if res[i]["batched"])),
-            "roofline_s": round(sum(roof_ms) / 1e3, 2), "solve_phase_s": round(sum(solve_ms) / 1e3, 2),
+            "one_cluster": int(sum(1 for i in sel if res[i]["route"] == "cluster")),
+            "roofline_s": round(sum(roof_ms) / 1e3, 2),
+            "floor_s": round(sum(floor_i[i] for i in sel), 2), "solve_phase_s": round(sum(solve_ms) / 1e3, 2),
             "upload_phase_s": round(sum(res[i]["upload_ms"] for i in sel) / 1e3, 2),
             "setup_phase_s": round(sum(res[i]["setup_ms"] for i in sel) / 1e3, 2)}
     bad = [{"request": i, "rows": int(rows[i]), "family": "stencil" if stencil_fam[i] else "random",
@@ -929,10 +942,17 @@ def serving_secondary(spx, ctx, dev, seconds: float = 10.0, rate: float = 2000.0
                "rho_at_roofline": round(roof / seconds, 3),
                "capacity_solves_per_s_at_roofline": round(len(res) / roof, 1),
                "achieved_frac_of_roofline_capacity": round(roof / wall, 3),
+               "offered_gpu_s_at_floor": round(floor, 2),
+               "floor": "per request the larger of its HBM roofline time and its random gathers of x at the "
+                        "gather probe's rate on the power-law pattern (random family only)",
+               "achieved_frac_of_floor_capacity": round(floor / wall, 3),
+               "cluster_rows": int(cl_rows),
+               "one_cluster_requests": int(sum(1 for r in res if r["route"] == "cluster")),
                "client_delay_ms_p50": round(float(np.percentile(delays, 50)), 3),
                "host_bytes_cap": int(cap),
                "by_size": buckets,
-               "phases_slot_route": phases(slot_res),
+               "phases_slot_route": phases([r for r in slot_res if r["route"] == "slot"]),
+               "phases_cluster_route": phases([r for r in slot_res if r["route"] == "cluster"]),
                "phases_batch_route": phases([r for r in res if r["batched"]])})
     if plain:
         st["plain_per_system_f64"] = plain_serial_f64(spx, ctx, build, min(400, N), 1e-8)

@@ -74,14 +74,39 @@ typedef enum { SPX_CG = 0, SPX_BICGSTAB = 1, SPX_GMRES = 2, SPX_CGS = 3 } spx_so
  * FP32 copy of its inverse (half the bytes), the others from FP64; the
  * arithmetic stays FP64.  Ignored by FP32 solves, which store FP32 inverses. */
 #define SPX_PRECOND_BLOCK_ADAPTIVE 0x400
+/* OR into the solver argument of spx_solve (or a request of spx_server_submit /
+ * spx_server_submit_matrix): run the whole solve in ONE kernel launch on one
+ * thread-block cluster (16 SMs, or 8 where the device runs no cluster of 16 or
+ * the system has fewer than 65 536 rows).  Block k of the cluster owns a slice
+ * of rows; the Krylov vectors live in a device workspace of 64 bytes per row
+ * cached in the matrix handle; the dot products are summed over the cluster in
+ * a fixed order, so the result does not depend on timing.  The iterations are
+ * the textbook recurrences of Section 5 (CG, BiCGSTAB, CGS; the true residual
+ * at exit with at most 3 restarts, as spx_solve); SPX_PREC_MIXED as
+ * spx_precision describes it.  For callers that run many mid-size solves (tens of thousands
+ * to about a million rows) at once on separate streams, such as the request
+ * server: each solve then occupies its own SMs and pays no launch per
+ * iteration.  A lone solve of a large system is faster without the flag (the
+ * general path spreads each iteration over the whole GPU).  CSR matrices of at
+ * most 2^30 rows, no preconditioner, not spx_solve_fixed, not GMRES; otherwise
+ * SPX_ERR_UNSUPPORTED (also when no such cluster fits the device). */
+#define SPX_SOLVE_ONE_CLUSTER 0x800
 
 /* Arithmetic of a solve: all FP64; all FP32 (values, vectors, dots and
- * scalars in float); or FP64 iterative refinement around an FP32 inner solve
- * (outer residual r = b - A x and update x += d in double on the FP64 values;
- * inner Krylov iterations in float on an FP32 copy of the values).  An inner
- * cycle solves A d = r / ||r|| to 1e-4 relative in at most 500 iterations, at
- * most 20 cycles; an inner CGS cycle also ends once its recurrence residual
- * has gone 20 iterations without halving. */
+ * scalars in float); or MIXED, Krylov iterations in float on an FP32 copy of
+ * the values with FP64 corrections on the FP64 values:
+ *   - CG: reliable updates (residual replacement, Sleijpen and van der Vorst):
+ *     the FP32 iterate is accumulated in a correction that is added to the
+ *     FP64 x whenever the FP32 recurrence residual has fallen below 0.1 of its
+ *     largest value since the last update (or to tol ||b||, or the budget is
+ *     spent); then b - A x is formed in FP64 and its rounding replaces the
+ *     FP32 residual, the search direction kept.  info->restarts counts the
+ *     updates.
+ *   - BiCGSTAB, CGS, GMRES: FP64 iterative refinement (outer residual
+ *     r = b - A x and update x += d in double); an inner cycle solves
+ *     A d = r / ||r|| to 1e-4 relative in at most 500 iterations, at most 20
+ *     cycles; an inner CGS cycle also ends once its recurrence residual has
+ *     gone 20 iterations without halving.  info->restarts counts the cycles. */
 typedef enum { SPX_PREC_F64 = 0, SPX_PREC_F32 = 1, SPX_PREC_MIXED = 2 } spx_precision;
 
 typedef enum {
@@ -333,8 +358,8 @@ int spx_batch_destroy(spx_batch *B);
 /* Solve all systems of B in one persistent kernel launch (CG, BiCGSTAB or CGS),
  * b and x concatenated by row_off (device, dtype of the batch; x is the
  * initial guess on entry).  infos: HOST array of nsys entries, or NULL.
- * precision SPX_PREC_MIXED runs FP32 batched inner solves inside FP64
- * refinement.  Synchronous. */
+ * precision SPX_PREC_MIXED as spx_precision describes it (CG with reliable
+ * updates, BiCGSTAB and CGS with refinement cycles).  Synchronous. */
 int spx_batch_solve(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int solver, double tol,
                     int64_t max_iter, int precision, spx_solve_info *infos);
 
@@ -379,7 +404,8 @@ int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const int32_t *row_
  * spx_server_submit.  Requests on the same handle run one at a time (later
  * ones wait while other requests are admitted past them); requests on
  * different handles overlap.  MIXED needs A created with SPX_MIXED_SHADOW.
- * Always solved on a slot (the batch lanes take host operators only).
+ * Always solved on a slot (the batch lanes take host operators only), with the
+ * one-cluster solve when spx_server_set_cluster_rows's rule selects it.
  * This is the submit call of the solve server in its resident-matrix form
  * (the paper's Section 5 solvers, served).  Errors: SPX_ERR_INVALID,
  * SPX_ERR_TOO_LARGE (workspace > budget). */
@@ -399,7 +425,7 @@ typedef struct {
      * batch they ran in (set-up = gathering the operators into pinned staging,
      * upload = copy and device build). */
     double upload_ms, setup_ms, solve_ms, download_ms;
-    int32_t batched;     /* 1: solved by a batch lane */
+    int32_t batched;     /* route: 1 a batch lane, 2 a slot with the one-cluster solve, 0 a slot */
     int32_t pad2;
 } spx_server_result;
 
@@ -416,6 +442,22 @@ int spx_server_poll(spx_server *S, spx_server_result *results, int max_results, 
  * does not depend on the route of others, but the same request may differ in
  * the last bits between the two routes (different reduction trees). */
 int spx_server_set_batching(spx_server *S, int64_t max_rows, int64_t *effective);
+
+/* Solve the slot requests of at most max_rows rows that are CG / BiCGSTAB /
+ * CGS without preconditioner on a CSR operator whose rows hold at most 8
+ * entries on average with SPX_SOLVE_ONE_CLUSTER (one launch on one
+ * thread-block cluster per request) from now on; 0: none; capped at 2^30;
+ * negative: leave the limit unchanged, only report it.  The default is 65 536
+ * rows (measured: sixteen concurrent mixed CG solves of a 27 000-row 7-point
+ * stencil completed 1.7x as many solves per second on clusters, 97 000 rows
+ * broke even, longer rows with random columns were slower on clusters).  The
+ * decision uses only the request's own matrix.  A request submitted with
+ * SPX_SOLVE_ONE_CLUSTER
+ * in its solver code takes that route whatever its size.  *effective (may be
+ * NULL) receives the limit in force.  As with the batch lanes, a request's
+ * result does not depend on other requests; the routes may differ in the last
+ * bits. */
+int spx_server_set_cluster_rows(spx_server *S, int64_t max_rows, int64_t *effective);
 
 /* Requests waiting for admission, running, and the device bytes reserved. */
 int spx_server_pending(spx_server *S, int64_t *queued, int64_t *running, int64_t *bytes_in_use);

@@ -334,7 +334,7 @@ void free_matrix_arrays(spx_matrix *A)
                     &A->ticket,   &A->stage_x,   &A->stage_y,   &A->coo_tiles, &A->flags,
                     &A->hint,     &A->coo_rowtiles, &A->tc_col, &A->tc_val, &A->tc_val32, &A->tc_row,
                     &A->tc_mask,  &A->empty_rows, &A->ct_row, &A->ct_col, &A->ct_val, &A->ct_val32,
-                    &A->small_out};
+                    &A->small_out, &A->cl_work};
     for (DBuf *b : bufs) dbuf_free(c, *b);
 }
 

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "dev_common.cuh"
+#include "krylov_rows.cuh"
 #include "spx_internal.cuh"
 
 struct spx_batch {
@@ -39,8 +40,6 @@ struct spx_batch {
 
 namespace spx {
 
-constexpr int kBatchMaxRestarts = 3;
-
 struct BOut {
     int *status;
     long long *iters;
@@ -54,405 +53,21 @@ inline size_t bout_off_relres(int64_t nsys) { return bout_off_iters(nsys) + roun
 inline size_t bout_off_cycles(int64_t nsys) { return bout_off_relres(nsys) + round_up((size_t)nsys * 8, 256); }
 inline size_t bout_bytes(int64_t nsys) { return bout_off_cycles(nsys) + round_up((size_t)nsys * 4, 256); }
 
-template <class T, int BLOCK> __device__ __forceinline__ T bsum(T v, T *red) { return block_sum<T, BLOCK>(v, red); }
-
-// y_i = (A x)_i for the rows this thread owns, x in shared memory
-template <class T, class V>
-__device__ __forceinline__ T row_dot(const int *__restrict__ rp, const int *__restrict__ col,
-                                     const V *__restrict__ val, const T *xs, int i)
-{
-    T s = T(0);
-    const int a = rp[i], b = rp[i + 1];
-    for (int k = a; k < b; ++k) s = fma((T)val[k], xs[col[k]], s);
-    return s;
-}
-
-// The scalars of an iteration (alpha, beta, omega) are computed once per block,
-// by thread 0, and read from shared memory: a division is a sequence of FP64
-// instructions, and every thread of the block computing it cost as much FP64
-// issue as a fifth of a small system's iteration (ncu: the FP64 pipe 78% busy
-// on one 4096-row system).  Slot k is written once per iteration and read right
-// after the barrier that follows the write; the block reductions between two
-// writes of a slot end every read of it.
-template <class T> __device__ __forceinline__ T share_scalar(T v, T *slot)
-{
-    if (threadIdx.x == 0) *slot = v;
-    __syncthreads();
-    return *slot;
-}
-
-// One system by CG in precision T on values V (V = T, or float values in the
-// FP32 inner solve).  x: initial guess (zero_x0: start from 0).  check_true:
-// form the true residual at exit and restart from x if it misses tol.
-template <class T, class V, int BLOCK>
-__device__ int cg_system(int n, const int *__restrict__ rp, const int *__restrict__ col, const V *__restrict__ val,
-                         const T *__restrict__ b, T *__restrict__ x, T *__restrict__ r, T *__restrict__ q, T *ps,
-                         T *red, T tol, long long maxit, bool zero_x0, bool check_true, long long &iters, T &relres)
-{
-    const int tid = threadIdx.x;
-    __shared__ T sc[2];
-    T bb = T(0);
-    for (int i = tid; i < n; i += BLOCK) bb = fma(b[i], b[i], bb);
-    bb = bsum<T, BLOCK>(bb, red);
-    if (bb == T(0)) {
-        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
-        relres = T(0);
-        return SPX_CONVERGED;
-    }
-    const T tol2 = tol * tol * bb;
-    if (zero_x0)
-        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
-    int status = SPX_MAX_ITER;
-    for (int restart = 0;; ++restart) {
-        // r = b - A x ; p = r ; rho = r.r
-        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
-        __syncthreads();
-        T rho = T(0);
-        for (int i = tid; i < n; i += BLOCK) {
-            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
-            r[i] = ri;
-            rho = fma(ri, ri, rho);
-        }
-        rho = bsum<T, BLOCK>(rho, red);  // (ends with a barrier: ps free)
-        for (int i = tid; i < n; i += BLOCK) ps[i] = r[i];
-        __syncthreads();
-        T last = rho;  // the last recurrence residual, squared
-        status = rho <= tol2 ? SPX_CONVERGED : SPX_MAX_ITER;
-        while (status == SPX_MAX_ITER && iters < maxit) {
-            T pq = T(0);
-            for (int i = tid; i < n; i += BLOCK) {
-                const T qi = row_dot<T, V>(rp, col, val, ps, i);
-                q[i] = qi;
-                pq = fma(ps[i], qi, pq);
-            }
-            pq = bsum<T, BLOCK>(pq, red);
-            if (pq == T(0)) {
-                status = SPX_BREAKDOWN;
-                break;
-            }
-            const T alpha = share_scalar(tid == 0 ? rho / pq : T(0), &sc[0]);
-            T rr = T(0);
-            for (int i = tid; i < n; i += BLOCK) {
-                x[i] = fma(alpha, ps[i], x[i]);
-                const T ri = fma(-alpha, q[i], r[i]);
-                r[i] = ri;
-                rr = fma(ri, ri, rr);
-            }
-            rr = bsum<T, BLOCK>(rr, red);
-            ++iters;
-            last = rr;
-            if (rr <= tol2) {
-                status = SPX_CONVERGED;
-                break;
-            }
-            const T beta = share_scalar(tid == 0 ? rr / rho : T(0), &sc[1]);
-            rho = rr;
-            for (int i = tid; i < n; i += BLOCK) ps[i] = fma(beta, ps[i], r[i]);
-            __syncthreads();
-        }
-        if (tid == 0) relres = sqrt(last / bb);
-        if (!check_true || status != SPX_CONVERGED) break;
-        // true residual
-        __syncthreads();
-        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
-        __syncthreads();
-        T rt = T(0);
-        for (int i = tid; i < n; i += BLOCK) {
-            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
-            rt = fma(ri, ri, rt);
-        }
-        rt = bsum<T, BLOCK>(rt, red);
-        relres = sqrt(rt / bb);
-        if (rt <= tol2) break;
-        if (restart == kBatchMaxRestarts) {
-            status = SPX_STAGNATED;
-            break;
-        }
-    }
-    __syncthreads();
-    return status;
-}
-
-// One system by BiCGSTAB (r^ = r0), vectors r, rh, p, v, s, t in global
-// workspace w[0..5]; the vector an SpMV gathers from is staged in ps.
-template <class T, class V, int BLOCK>
-__device__ int bicgstab_system(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                               const V *__restrict__ val, const T *__restrict__ b, T *__restrict__ x, T *const *w,
-                               T *ps, T *red, T tol, long long maxit, bool zero_x0, bool check_true,
-                               long long &iters, T &relres)
-{
-    const int tid = threadIdx.x;
-    __shared__ T sc[3];
-    T *r = w[0], *rh = w[1], *p = w[2], *v = w[3], *s = w[4], *t = w[5];
-    T bb = T(0);
-    for (int i = tid; i < n; i += BLOCK) bb = fma(b[i], b[i], bb);
-    bb = bsum<T, BLOCK>(bb, red);
-    if (bb == T(0)) {
-        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
-        relres = T(0);
-        return SPX_CONVERGED;
-    }
-    const T tol2 = tol * tol * bb;
-    if (zero_x0)
-        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
-    int status = SPX_MAX_ITER;
-    for (int restart = 0;; ++restart) {
-        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
-        __syncthreads();
-        T rr0 = T(0);
-        for (int i = tid; i < n; i += BLOCK) {
-            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
-            r[i] = ri;
-            rh[i] = ri;
-            p[i] = T(0);
-            v[i] = T(0);
-            rr0 = fma(ri, ri, rr0);
-        }
-        rr0 = bsum<T, BLOCK>(rr0, red);
-        T rho = T(1), alpha = T(1), omega = T(1), rho1 = rr0;
-        T last = rr0;  // the last recurrence residual, squared
-        status = rr0 <= tol2 ? SPX_CONVERGED : SPX_MAX_ITER;
-        while (status == SPX_MAX_ITER && iters < maxit) {
-            if (rho1 == T(0)) {
-                status = SPX_BREAKDOWN;
-                break;
-            }
-            const T beta = share_scalar(tid == 0 ? (rho1 / rho) * (alpha / omega) : T(0), &sc[0]);
-            for (int i = tid; i < n; i += BLOCK) {
-                const T pi = fma(beta, fma(-omega, v[i], p[i]), r[i]);
-                p[i] = pi;
-                ps[i] = pi;
-            }
-            __syncthreads();
-            T rv = T(0);
-            for (int i = tid; i < n; i += BLOCK) {
-                const T vi = row_dot<T, V>(rp, col, val, ps, i);
-                v[i] = vi;
-                rv = fma(rh[i], vi, rv);
-            }
-            rv = bsum<T, BLOCK>(rv, red);
-            if (rv == T(0)) {
-                status = SPX_BREAKDOWN;
-                break;
-            }
-            alpha = share_scalar(tid == 0 ? rho1 / rv : T(0), &sc[1]);
-            T ss = T(0);
-            for (int i = tid; i < n; i += BLOCK) {
-                const T si = fma(-alpha, v[i], r[i]);
-                s[i] = si;
-                ps[i] = si;
-                ss = fma(si, si, ss);
-            }
-            ss = bsum<T, BLOCK>(ss, red);
-            ++iters;
-            if (ss <= tol2) {
-                for (int i = tid; i < n; i += BLOCK) {
-                    x[i] = fma(alpha, p[i], x[i]);
-                    r[i] = s[i];
-                }
-                last = ss;
-                status = SPX_CONVERGED;
-                __syncthreads();
-                break;
-            }
-            T ts = T(0), tt = T(0);
-            for (int i = tid; i < n; i += BLOCK) {
-                const T ti = row_dot<T, V>(rp, col, val, ps, i);
-                t[i] = ti;
-                ts = fma(ti, s[i], ts);
-                tt = fma(ti, ti, tt);
-            }
-            ts = bsum<T, BLOCK>(ts, red);
-            tt = bsum<T, BLOCK>(tt, red);
-            if (tt == T(0)) {
-                status = SPX_BREAKDOWN;
-                break;
-            }
-            omega = share_scalar(tid == 0 ? ts / tt : T(0), &sc[2]);
-            T rr = T(0), rhr = T(0);
-            for (int i = tid; i < n; i += BLOCK) {
-                x[i] = fma(omega, s[i], fma(alpha, p[i], x[i]));
-                const T ri = fma(-omega, t[i], s[i]);
-                r[i] = ri;
-                rr = fma(ri, ri, rr);
-                rhr = fma(rh[i], ri, rhr);
-            }
-            rr = bsum<T, BLOCK>(rr, red);
-            rhr = bsum<T, BLOCK>(rhr, red);
-            last = rr;
-            if (rr <= tol2) {
-                status = SPX_CONVERGED;
-                break;
-            }
-            if (omega == T(0)) {
-                status = SPX_BREAKDOWN;
-                break;
-            }
-            rho = rho1;
-            rho1 = rhr;
-        }
-        if (tid == 0) relres = sqrt(last / bb);
-        if (!check_true || status != SPX_CONVERGED) break;
-        __syncthreads();
-        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
-        __syncthreads();
-        T rt = T(0);
-        for (int i = tid; i < n; i += BLOCK) {
-            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
-            rt = fma(ri, ri, rt);
-        }
-        rt = bsum<T, BLOCK>(rt, red);
-        relres = sqrt(rt / bb);
-        if (rt <= tol2) break;
-        if (restart == kBatchMaxRestarts) {
-            status = SPX_STAGNATED;
-            break;
-        }
-    }
-    __syncthreads();
-    return status;
-}
-
-// One system by CGS (Sonneveld; shadow residual r^ = r0).  The SpMV operands
-// (p, then u + q) are staged in turn through the shared-memory vector ps.
-// stall > 0 (inner cycle of refinement, x0 = 0): also stop once the recurrence
-// residual has gone `stall` iterations without halving.
-template <class T, class V, int BLOCK>
-__device__ int cgs_system(int n, const int *__restrict__ rp, const int *__restrict__ col, const V *__restrict__ val,
-                          const T *__restrict__ b, T *__restrict__ x, T *const *w, T *ps, T *red, T tol,
-                          long long maxit, bool zero_x0, bool check_true, long long &iters, T &relres,
-                          int stall = 0)
-{
-    T mark2 = T(1);  // the squared relative residual the stall test measures against
-    long long mark_it = iters;
-    const int tid = threadIdx.x;
-    __shared__ T sc[2];
-    T *r = w[0], *rh = w[1], *p = w[2], *u = w[3], *q = w[4], *v = w[5];
-    T bb = T(0);
-    for (int i = tid; i < n; i += BLOCK) bb = fma(b[i], b[i], bb);
-    bb = bsum<T, BLOCK>(bb, red);
-    if (bb == T(0)) {
-        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
-        relres = T(0);
-        return SPX_CONVERGED;
-    }
-    const T tol2 = tol * tol * bb;
-    if (zero_x0)
-        for (int i = tid; i < n; i += BLOCK) x[i] = T(0);
-    int status = SPX_MAX_ITER;
-    for (int restart = 0;; ++restart) {
-        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
-        __syncthreads();
-        T rr0 = T(0);
-        for (int i = tid; i < n; i += BLOCK) {
-            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
-            r[i] = ri;
-            rh[i] = ri;
-            p[i] = ri;
-            u[i] = ri;
-            rr0 = fma(ri, ri, rr0);
-        }
-        rr0 = bsum<T, BLOCK>(rr0, red);  // (its barrier also ends every read of ps)
-        for (int i = tid; i < n; i += BLOCK) ps[i] = p[i];
-        __syncthreads();
-        T rho = rr0;
-        T last = rr0;  // the last recurrence residual, squared
-        status = rr0 <= tol2 ? SPX_CONVERGED : SPX_MAX_ITER;
-        while (status == SPX_MAX_ITER && iters < maxit) {
-            if (rho == T(0)) {
-                status = SPX_BREAKDOWN;
-                break;
-            }
-            T rv = T(0);
-            for (int i = tid; i < n; i += BLOCK) {  // v = A p
-                const T vi = row_dot<T, V>(rp, col, val, ps, i);
-                v[i] = vi;
-                rv = fma(rh[i], vi, rv);
-            }
-            rv = bsum<T, BLOCK>(rv, red);
-            if (rv == T(0)) {
-                status = SPX_BREAKDOWN;
-                break;
-            }
-            const T alpha = share_scalar(tid == 0 ? rho / rv : T(0), &sc[0]);
-            for (int i = tid; i < n; i += BLOCK) {
-                const T qi = fma(-alpha, v[i], u[i]);
-                q[i] = qi;
-                const T wi = u[i] + qi;
-                x[i] = fma(alpha, wi, x[i]);
-                ps[i] = wi;
-            }
-            __syncthreads();
-            T rr = T(0), rhr = T(0);
-            for (int i = tid; i < n; i += BLOCK) {  // r -= alpha A (u + q)
-                const T ri = fma(-alpha, row_dot<T, V>(rp, col, val, ps, i), r[i]);
-                r[i] = ri;
-                rr = fma(ri, ri, rr);
-                rhr = fma(rh[i], ri, rhr);
-            }
-            rr = bsum<T, BLOCK>(rr, red);
-            rhr = bsum<T, BLOCK>(rhr, red);
-            ++iters;
-            last = rr;
-            if (rr <= tol2) {
-                status = SPX_CONVERGED;
-                break;
-            }
-            if (stall > 0) {  // ||r|| / ||b|| below half the mark, compared in squares
-                if (rr < T(0.25) * mark2 * bb) {
-                    mark2 = rr / bb;
-                    mark_it = iters;
-                } else if (iters - mark_it >= stall) {
-                    status = SPX_STAGNATED;
-                    break;
-                }
-            }
-            const T beta = share_scalar(tid == 0 ? rhr / rho : T(0), &sc[1]);
-            for (int i = tid; i < n; i += BLOCK) {
-                const T ui = fma(beta, q[i], r[i]);
-                u[i] = ui;
-                const T pi = fma(beta, fma(beta, p[i], q[i]), ui);
-                p[i] = pi;
-                ps[i] = pi;
-            }
-            __syncthreads();
-            rho = rhr;
-        }
-        if (tid == 0) relres = sqrt(last / bb);
-        if (!check_true || status != SPX_CONVERGED) break;
-        __syncthreads();
-        for (int i = tid; i < n; i += BLOCK) ps[i] = x[i];
-        __syncthreads();
-        T rt = T(0);
-        for (int i = tid; i < n; i += BLOCK) {
-            const T ri = b[i] - row_dot<T, V>(rp, col, val, ps, i);
-            rt = fma(ri, ri, rt);
-        }
-        rt = bsum<T, BLOCK>(rt, red);
-        relres = sqrt(rt / bb);
-        if (rt <= tol2) break;
-        if (restart == kBatchMaxRestarts) {
-            status = SPX_STAGNATED;
-            break;
-        }
-    }
-    __syncthreads();
-    return status;
-}
-
-// The persistent kernel.  MIXED: FP64 refinement (r = b - A64 x, x += ||r|| d)
-// around an FP32 inner solve of A32 d = r / ||r|| to 1e-4 on float values.
+// The persistent kernel: each block takes the next system from the queue and
+// solves it alone (krylov_rows.cuh, one block owning all rows).  The vector
+// the products gather from lives in shared memory (smem_vec) or, for systems
+// too large for it, in the global workspace (slots 6 and 7 of the eight per
+// row; read through L1, the block being the only reader).  Launch bounds of
+// 1024 threads per SM hold every variant at 64 registers without spills
+// (without the bound, ptxas gave some variants 32 registers and spilled).
 template <class T, int BLOCK, int SOLVER, bool MIXED>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
     k_batch(int64_t nsys, const int64_t *__restrict__ row_off, const int64_t *__restrict__ nnz_off,
             const int *__restrict__ rp_all, const int *__restrict__ col_all, const T *__restrict__ val_all,
             const float *__restrict__ val32_all, const int *__restrict__ order, const T *__restrict__ b_all,
             T *__restrict__ x_all, T *__restrict__ work, int64_t nrows, T tol, long long maxit, unsigned *queue,
             BOut out, int smem_vec)
 {
-    // The vector the products gather from lives in shared memory (smem_vec) or,
-    // for systems too large for it, in the global workspace (slots 6 and 7 of
-    // the eight per row; read through L1).
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T red[BLOCK / 32];
     __shared__ float redf[BLOCK / 32];
@@ -465,94 +80,15 @@ __global__ void __launch_bounds__(BLOCK)
         if (q >= nsys) break;
         const int s = order[q];
         const int64_t ro = row_off[s];
-        const int n = (int)(row_off[s + 1] - ro);
-        const int *rp = rp_all + ro + s;
-        const int *col = col_all + nnz_off[s];
-        const T *b = b_all + ro;
-        T *x = x_all + ro;
-        long long iters = 0;
-        T relres = T(0);
-        int status;
-        int outer = 0;
-        if (!MIXED) {
-            const T *val = val_all + nnz_off[s];
-            T *ps = smem_vec ? reinterpret_cast<T *>(smem) : work + 6 * nrows + ro;
-            if (SOLVER == SPX_CG) {
-                status = cg_system<T, T, BLOCK>(n, rp, col, val, b, x, work + ro, work + nrows + ro, ps, red, tol,
-                                                maxit, false, true, iters, relres);
-            } else if (SOLVER == SPX_CGS) {
-                T *w[6];
-                for (int k = 0; k < 6; ++k) w[k] = work + (int64_t)k * nrows + ro;
-                status = cgs_system<T, T, BLOCK>(n, rp, col, val, b, x, w, ps, red, tol, maxit, false, true, iters,
-                                                 relres);
-            } else {
-                T *w[6];
-                for (int k = 0; k < 6; ++k) w[k] = work + (int64_t)k * nrows + ro;
-                status = bicgstab_system<T, T, BLOCK>(n, rp, col, val, b, x, w, ps, red, tol, maxit, false, true,
-                                                      iters, relres);
-            }
-        } else {
-            // outer FP64 refinement
-            const double *val = reinterpret_cast<const double *>(val_all) + nnz_off[s];
-            const float *v32 = val32_all + nnz_off[s];
-            double *xs = smem_vec ? reinterpret_cast<double *>(smem) : reinterpret_cast<double *>(work) + 6 * nrows + ro;
-            double *r64 = reinterpret_cast<double *>(work) + ro;
-            float *fw = reinterpret_cast<float *>(reinterpret_cast<double *>(work) + nrows);
-            float *r32 = fw + ro, *d32 = fw + nrows + ro;
-            float *fv[6];
-            for (int k = 0; k < 6; ++k) fv[k] = fw + (int64_t)(2 + k) * nrows + ro;
-            const double *bd = reinterpret_cast<const double *>(b);
-            double *xd = reinterpret_cast<double *>(x);
-            double bb = 0.0;
-            for (int i = threadIdx.x; i < n; i += BLOCK) bb = fma(bd[i], bd[i], bb);
-            bb = bsum<double, BLOCK>(bb, reinterpret_cast<double *>(red));
-            status = SPX_MAX_ITER;
-            if (bb == 0.0) {
-                for (int i = threadIdx.x; i < n; i += BLOCK) xd[i] = 0.0;
-                status = SPX_CONVERGED;
-            }
-            for (outer = 0; status != SPX_CONVERGED && outer <= 20; ++outer) {
-                for (int i = threadIdx.x; i < n; i += BLOCK) xs[i] = xd[i];
-                __syncthreads();
-                double rr = 0.0;
-                for (int i = threadIdx.x; i < n; i += BLOCK) {
-                    const double ri = bd[i] - row_dot<double, double>(rp, col, val, xs, i);
-                    r64[i] = ri;
-                    rr = fma(ri, ri, rr);
-                }
-                rr = bsum<double, BLOCK>(rr, reinterpret_cast<double *>(red));
-                relres = (T)sqrt(rr / bb);
-                if (rr <= (double)tol * (double)tol * bb) {
-                    status = SPX_CONVERGED;
-                    break;
-                }
-                if (outer == 20 || iters >= maxit) break;
-                const double rn = sqrt(rr);
-                for (int i = threadIdx.x; i < n; i += BLOCK) r32[i] = (float)(r64[i] / rn);
-                __syncthreads();
-                float rel32 = 0.f;
-                float *ps32 = smem_vec ? reinterpret_cast<float *>(smem)
-                                       : reinterpret_cast<float *>(reinterpret_cast<double *>(work) + 7 * nrows) + ro;
-                // at most kIrInnerCap inner iterations per refinement cycle
-                const long long cyc_max = min(maxit, iters + (long long)kIrInnerCap);
-                if (SOLVER == SPX_CG)
-                    cg_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv[0], fv[1], ps32, redf, 1e-4f,
-                                                   cyc_max, true, false, iters, rel32);
-                else if (SOLVER == SPX_CGS)
-                    cgs_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, cyc_max, true,
-                                                    false, iters, rel32, kIrCgsStall);
-                else
-                    bicgstab_system<float, float, BLOCK>(n, rp, col, v32, r32, d32, fv, ps32, redf, 1e-4f, cyc_max,
-                                                         true, false, iters, rel32);
-                for (int i = threadIdx.x; i < n; i += BLOCK) xd[i] = fma(rn, (double)d32[i], xd[i]);
-                __syncthreads();
-            }
-        }
+        BlockRows<BLOCK> g((int)(row_off[s + 1] - ro));
+        const SysOut o = solve_rows<T, BLOCK, SOLVER, MIXED>(
+            g, rp_all + ro + s, col_all + nnz_off[s], val_all + nnz_off[s], MIXED ? val32_all + nnz_off[s] : nullptr,
+            b_all + ro, x_all + ro, work, nrows, ro, smem_vec ? smem : nullptr, red, redf, tol, maxit);
         if (threadIdx.x == 0) {
-            out.status[s] = status;
-            out.iters[s] = iters;
-            out.relres[s] = (double)relres;
-            out.cycles[s] = outer;
+            out.status[s] = o.status;
+            out.iters[s] = o.iters;
+            out.relres[s] = o.relres;
+            out.cycles[s] = o.cycles;
         }
     }
 }

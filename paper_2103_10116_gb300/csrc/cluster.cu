@@ -20,7 +20,11 @@
 // (23 us per iteration).
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+
 #include "dev_common.cuh"
+#include "krylov_rows.cuh"
 #include "spx_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -29,6 +33,7 @@ namespace spx {
 namespace {
 
 constexpr int kClMaxRowsPerBlock = 4096;
+constexpr size_t kOutBytes = 64;  // the result record of either cluster solve
 
 struct ClOut {
     int status;
@@ -72,7 +77,7 @@ __device__ __forceinline__ T dist_row_dot(cg::cluster_group &cl, const int *__re
 }
 
 template <class T, int CL, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, 1)  // one block per SM: no register cap, no spills
     k_cluster_cg(int n, int lg, const int *__restrict__ rp, const int *__restrict__ col, const T *__restrict__ val,
                  const T *__restrict__ b, T *__restrict__ x, T tol, long long maxit, ClOut *out)
 {
@@ -198,9 +203,22 @@ namespace {
 
 // The largest cluster (16 blocks, a non-portable size, else the portable 8)
 // this device can run for the kernel's shared memory; 0 if none.
+// Asked once per (device, shared-memory size).
 template <class T, int CL, int BLOCK> int cluster_fits(int smem)
 {
     auto kern = k_cluster_cg<T, CL, BLOCK>;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> known;  // (device, smem) -> clusters
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = known.find({dev, smem});
+    if (it != known.end()) return it->second;
+    int &nc = known[{dev, smem}];
+    nc = 0;
     if (smem_optin(reinterpret_cast<const void *>(kern), smem) != SPX_OK) return 0;
     if (CL > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
@@ -217,10 +235,9 @@ template <class T, int CL, int BLOCK> int cluster_fits(int smem)
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    int nc = 0;
     if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        return 0;
+        nc = 0;
     }
     return nc;
 }
@@ -272,7 +289,7 @@ int cluster_cg_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, double
                      spx_solve_info *info)
 {
     if (A->format != SPX_CSR || !A->rp.p || A->n < 1 || A->n > cluster_cg_max_rows()) return SPX_ERR_UNSUPPORTED;
-    if (!A->small_out.p) SPX_TRY(dbuf_alloc(A->ctx, A->small_out, sizeof(ClOut)));
+    if (!A->small_out.p) SPX_TRY(dbuf_alloc(A->ctx, A->small_out, kOutBytes));
     ClOut *out = A->small_out.as<ClOut>();
     const int st = A->dtype == SPX_F64
                        ? cluster_cg_typed<double>(ctx, A, static_cast<const double *>(b), static_cast<double *>(x),
@@ -288,6 +305,171 @@ int cluster_cg_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, double
     info->restarts = h.restarts;
     info->relres_recurrence = h.relres;
     info->relres_true = h.relres;
+    return SPX_OK;
+}
+
+// ------------------------------------------------------------------ one system per cluster, any size
+// The solve of a mid-size system (tens of thousands to about a million rows)
+// on the general path is a chain of hundreds of launches of kernels with a
+// few microseconds of work each: launch and drain latency, not memory, bound
+// it (a 97 336-row 7-point stencil: 20.6 us per FP32 CG iteration for about
+// 1.5 us of HBM traffic).  Here one cluster of CL blocks runs the whole solve
+// in one launch (krylov_rows.cuh with the cluster group): block k owns rows
+// [k R, (k+1) R), the vectors live in a global workspace of 8 doubles per row
+// that stays in L2 for such sizes, the gathered vector is read through L2
+// after a cluster barrier, and the group sums go through distributed shared
+// memory.  One cluster uses 16 (or 8) SMs, so a lone large solve is faster on
+// the general path; many such solves on separate streams (the request server)
+// run side by side on disjoint SMs with no launch between iterations.
+template <class T, int CL, int BLOCK, int SOLVER, bool MIXED>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
+    k_cluster_solve(int n, const int *__restrict__ rp, const int *__restrict__ col, const T *__restrict__ val,
+                    const float *__restrict__ val32, const T *__restrict__ b, T *__restrict__ x, T *__restrict__ work,
+                    T tol, long long maxit, SysOut *out)
+{
+    __shared__ T red[BLOCK / 32];
+    __shared__ float redf[BLOCK / 32];
+    __shared__ double part[8];
+    __shared__ double bc[2];
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int R = ((n + CL - 1) / CL + 31) & ~31;  // n <= 2^30: no overflow
+    ClusterRows<CL, BLOCK> g;
+    g.lo = min(n, rank * R);
+    g.hi = min(n, g.lo + R);
+    g.part = part;
+    g.bc = bc;
+    const SysOut o = solve_rows<T, BLOCK, SOLVER, MIXED>(g, rp, col, val, val32, b, x, work, n, 0, nullptr, red,
+                                                         redf, tol, maxit);
+    if (rank == 0 && threadIdx.x == 0) *out = o;
+    cg::this_cluster().sync();  // no block exits while another may still read its shared memory
+}
+
+namespace {
+
+constexpr int kClSolveBlock = 512;
+
+template <class T, int CL, int SOLVER, bool MIXED> cudaLaunchConfig_t cl_cfg(cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(kClSolveBlock);
+    cfg.dynamicSmemBytes = 0;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// Clusters of CL blocks of this kernel the device can hold at once (0: none),
+// asked once per (kernel, device): the query takes driver locks, and the
+// request server's slots launch this kernel from many threads at once.
+template <class T, int CL, int SOLVER, bool MIXED> int cl_solve_fits()
+{
+    auto kern = k_cluster_solve<T, CL, kClSolveBlock, SOLVER, MIXED>;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    static std::mutex mu;
+    static std::map<int, int> known;  // device -> clusters
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = known.find(dev);
+    if (it != known.end()) return it->second;
+    int nc = 0;
+    if (CL > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+    } else {
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = cl_cfg<T, CL, SOLVER, MIXED>(at);
+        if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            nc = 0;
+        }
+    }
+    known[dev] = nc;
+    return nc;
+}
+
+template <class T, int CL, int SOLVER, bool MIXED>
+int cl_solve_launch(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, double tol, int64_t maxit, SysOut *out)
+{
+    auto kern = k_cluster_solve<T, CL, kClSolveBlock, SOLVER, MIXED>;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cl_cfg<T, CL, SOLVER, MIXED>(at);
+    cfg.stream = ctx->stream;
+    const float *v32 = MIXED ? A->val32.as<float>() : nullptr;
+    SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, (int)A->n, (const int *)A->rp.as<int>(), (const int *)A->col.as<int>(),
+                                (const T *)A->val.as<T>(), v32, b, x, A->cl_work.as<T>(), (T)tol, (long long)maxit,
+                                out));
+    return SPX_OK;
+}
+
+// Clusters of 16 blocks for systems of at least 65 536 rows (8 rows per thread),
+// where the device runs such clusters; else 8 blocks.
+constexpr int64_t kClSolve16Rows = 65536;
+
+template <class T, int SOLVER, bool MIXED>
+int cl_solve_typed(spx_ctx *ctx, spx_matrix *A, const T *b, T *x, double tol, int64_t maxit, SysOut *out)
+{
+    if (A->n >= kClSolve16Rows && cl_solve_fits<T, 16, SOLVER, MIXED>() > 0)
+        return cl_solve_launch<T, 16, SOLVER, MIXED>(ctx, A, b, x, tol, maxit, out);
+    if (cl_solve_fits<T, 8, SOLVER, MIXED>() > 0) return cl_solve_launch<T, 8, SOLVER, MIXED>(ctx, A, b, x, tol, maxit, out);
+    return SPX_ERR_UNSUPPORTED;
+}
+
+template <class T, bool MIXED>
+int cl_solve_solver(spx_ctx *ctx, spx_matrix *A, int solver, const T *b, T *x, double tol, int64_t maxit, SysOut *out)
+{
+    if (solver == SPX_CG) return cl_solve_typed<T, SPX_CG, MIXED>(ctx, A, b, x, tol, maxit, out);
+    if (solver == SPX_CGS) return cl_solve_typed<T, SPX_CGS, MIXED>(ctx, A, b, x, tol, maxit, out);
+    return cl_solve_typed<T, SPX_BICGSTAB, MIXED>(ctx, A, b, x, tol, maxit, out);
+}
+
+}  // namespace
+
+int cluster_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol, int64_t maxit,
+                  int precision, spx_solve_info *info)
+{
+    if (A->format != SPX_CSR || !A->rp.p)
+        return fail(SPX_ERR_UNSUPPORTED, "the one-cluster solve runs on CSR matrices");
+    if (solver != SPX_CG && solver != SPX_BICGSTAB && solver != SPX_CGS)
+        return fail(SPX_ERR_UNSUPPORTED, "the one-cluster solve runs CG, BiCGSTAB or CGS");
+    const bool mixed = precision == SPX_PREC_MIXED;
+    if (mixed && (A->dtype != SPX_F64 || !A->val32.p))
+        return fail(SPX_ERR_UNSUPPORTED, "mixed precision needs an FP64 matrix created with SPX_MIXED_SHADOW");
+    if (!mixed && (precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32) != A->dtype)
+        return fail(SPX_ERR_UNSUPPORTED, "precision must match the matrix dtype (or use MIXED)");
+    if (A->n > (int64_t)1 << 30) return fail(SPX_ERR_TOO_LARGE, "the one-cluster solve takes at most 2^30 rows");
+    if (!A->small_out.p) SPX_TRY(dbuf_alloc(A->ctx, A->small_out, kOutBytes));
+    if (!A->cl_work.p) SPX_TRY(dbuf_alloc(A->ctx, A->cl_work, (size_t)A->n * 64));
+    SysOut *out = reinterpret_cast<SysOut *>(A->small_out.p);
+    int st;
+    if (mixed)
+        st = cl_solve_solver<double, true>(ctx, A, solver, static_cast<const double *>(b), static_cast<double *>(x),
+                                           tol, maxit, out);
+    else if (A->dtype == SPX_F64)
+        st = cl_solve_solver<double, false>(ctx, A, solver, static_cast<const double *>(b), static_cast<double *>(x),
+                                            tol, maxit, out);
+    else
+        st = cl_solve_solver<float, false>(ctx, A, solver, static_cast<const float *>(b), static_cast<float *>(x), tol,
+                                           maxit, out);
+    if (st == SPX_ERR_UNSUPPORTED) return fail(st, "no thread-block cluster of 8 or 16 blocks fits this device");
+    if (st != SPX_OK) return st;
+    SysOut h;
+    SPX_CUDA(cudaMemcpyAsync(&h, out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    SPX_CUDA(cudaStreamSynchronize(ctx->stream));
+    info->status = h.status;
+    info->iterations = h.iters;
+    info->relres_recurrence = h.relres;
+    info->relres_true = h.relres;
+    if (mixed) {
+        info->inner_iterations = h.iters;
+        info->restarts = h.cycles;
+    }
     return SPX_OK;
 }
 

@@ -2122,7 +2122,8 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
     if (A->n != A->ncols) return fail(SPX_ERR_INVALID, "spx_solve: the matrix must be square");
     bool pre = false, adapt = false;
     int bs = 0;
-    SPX_TRY(parse_solver_code(solver, &solver, &pre, &bs, &adapt));
+    const bool one_cluster = (solver & SPX_SOLVE_ONE_CLUSTER) != 0;
+    SPX_TRY(parse_solver_code(solver & ~SPX_SOLVE_ONE_CLUSTER, &solver, &pre, &bs, &adapt));
     if (!(tol >= 0.0) || maxit < 0) return fail(SPX_ERR_INVALID, "spx_solve: bad tol or max_iter");
     if (solver == SPX_GMRES && (restart < 1 || restart > kGmKmax - 1))
         return fail(SPX_ERR_UNSUPPORTED, "GMRES restart length must be in [1, 31]");
@@ -2132,6 +2133,14 @@ int solve_entry(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver,
     }
     Timer tm;
     int st;
+    if (one_cluster) {
+        if (fixed != 0 || pre || bs != 0 || solver == SPX_GMRES)
+            return fail(SPX_ERR_UNSUPPORTED, "the one-cluster solve runs CG, BiCGSTAB or CGS to a tolerance, "
+                                             "without preconditioner");
+        st = cluster_solve(ctx, A, b, x, solver, tol, maxit, precision, info);
+        info->time_ms = tm.ms();
+        return st;
+    }
     if (fixed == 0 && !pre && bs == 0 && solver != SPX_GMRES && A->format == SPX_CSR && A->n <= kSmallSolveRows &&
         A->rp.p && A->kernel == SPX_KERNEL_AUTO) {  // a pinned SpMV kernel keeps the general path
         st = small_solve(ctx, A, b, x, solver, tol, maxit, precision, info);

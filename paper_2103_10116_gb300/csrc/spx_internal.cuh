@@ -142,7 +142,8 @@ struct spx_matrix {
     // small systems: the matrix as a batch of one for the one-block solve route (solvers.cu)
     spx_batch *batch1 = nullptr;
     bool batch1_shadow = false;
-    spx::DBuf small_out;  // result record of the cluster CG (cluster.cu)
+    spx::DBuf small_out;  // result record of the cluster solves (cluster.cu)
+    spx::DBuf cl_work;    // workspace of the one-cluster solve of a mid-size system (cluster.cu)
 };
 
 namespace spx {
@@ -203,5 +204,10 @@ int batch_max_rows(const spx_ctx *ctx);
 int cluster_cg_max_rows();
 int cluster_cg_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, double tol, int64_t maxit,
                      spx_solve_info *info);
+// A whole solve (CG, BiCGSTAB or CGS; F64, F32 or MIXED) of a CSR system in one
+// launch on one thread-block cluster, vectors in global memory (cluster.cu);
+// synchronous.  SPX_ERR_UNSUPPORTED when no cluster fits the device.
+int cluster_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, double tol, int64_t maxit,
+                  int precision, spx_solve_info *info);
 
 }  // namespace spx

@@ -27,6 +27,7 @@ SPX_PRECOND_JACOBI = 0x100
 SPX_PRECOND_BLOCK_JACOBI = 0x200
 SPX_PRECOND_BLOCK_SHIFT = 16
 SPX_PRECOND_BLOCK_ADAPTIVE = 0x400
+SPX_SOLVE_ONE_CLUSTER = 0x800
 
 
 def SPX_PRECOND_BLOCK(bs: int) -> int:
@@ -113,6 +114,7 @@ SIGNATURES = {
     "spx_server_submit_matrix": (_I, [_P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(C.c_int64)]),
     "spx_server_poll": (_I, [_P, C.POINTER(spx_server_result), _I, _I, C.POINTER(C.c_int)]),
     "spx_server_set_batching": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
+    "spx_server_set_cluster_rows": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
     "spx_probe_gather": (_I, [_P, _I64, _P, _P, _I, _P]),
     "spx_ctx_check": (_I, [_P]),
     "spx_selftest_wait_timeout": (_I, [_P, _I]),
@@ -400,10 +402,12 @@ def _solver_code(solver, precond, block_size=8):
 
 def spx_solve(ctx: int, A: int, b: torch.Tensor, x: torch.Tensor, solver="cg", tol: float = 1e-10,
               max_iter: int = 10000, restart: int = 30, precision="f64", precond=None,
-              block_size: int = 8) -> SolveInfo:
+              block_size: int = 8, one_cluster: bool = False) -> SolveInfo:
+    """one_cluster: the whole solve in one launch on one thread-block cluster (SPX_SOLVE_ONE_CLUSTER)."""
     info = spx_solve_info()
-    _check(load().spx_solve(ctx, A, _ptr(b), _ptr(x), _solver_code(solver, precond, block_size), float(tol),
-                            int(max_iter), int(restart), PRECISIONS.get(precision, precision), C.byref(info)))
+    code = _solver_code(solver, precond, block_size) | (SPX_SOLVE_ONE_CLUSTER if one_cluster else 0)
+    _check(load().spx_solve(ctx, A, _ptr(b), _ptr(x), code, float(tol), int(max_iter), int(restart),
+                            PRECISIONS.get(precision, precision), C.byref(info)))
     return _info(info)
 
 
@@ -496,7 +500,7 @@ def spx_server_poll(S: int, max_results: int = 256, wait_ms: int = 0) -> list[di
         out.append({"id": r.id, "error": r.error, "info": _info(r.info), "submit_ms": r.submit_ms,
                     "admit_ms": r.admit_ms, "done_ms": r.done_ms, "upload_ms": r.upload_ms,
                     "setup_ms": r.setup_ms, "solve_ms": r.solve_ms, "download_ms": r.download_ms,
-                    "batched": bool(r.batched)})
+                    "batched": r.batched == 1, "route": ("slot", "batch", "cluster")[r.batched]})
     return out
 
 
@@ -517,6 +521,14 @@ def spx_probe_gather(ctx: int, col_idx: torch.Tensor, x: torch.Tensor, out: torc
 def spx_server_set_batching(S: int, max_rows: int) -> int:
     eff = C.c_int64(0)
     _check(load().spx_server_set_batching(S, int(max_rows), C.byref(eff)))
+    return eff.value
+
+
+def spx_server_set_cluster_rows(S: int, max_rows: int) -> int:
+    """Route slot requests of at most max_rows rows to the one-cluster solve (0: none;
+    negative: report only); returns the limit in force."""
+    eff = C.c_int64()
+    _check(load().spx_server_set_cluster_rows(S, int(max_rows), C.byref(eff)))
     return eff.value
 
 

@@ -61,3 +61,20 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert "NULL" in spx.spx_last_error()
     out = C.c_void_p()
     assert lib.spx_matrix_create(None, C.byref(out), 0, 0, 1, 1, 0, None, None, None, 0, -1, 0) == spx.SPX_ERR_INVALID
+
+
+def test_header_constants_match_binding():
+    """Every integer #define and enum constant of include/spx.h that the binding
+    also names has the same value there."""
+    src = open(os.path.join(ROOT, "include", "spx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"^#define\s+(SPX_\w+)\s+(0x[0-9a-fA-F]+|\d+)u?\s*$",
+                                                                   src, flags=re.M)}
+    for body in re.findall(r"typedef\s+enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"(SPX_\w+)\s*=\s*(-?\d+)", body):
+            consts[name] = int(val)
+    assert "SPX_SOLVE_ONE_CLUSTER" in consts and "SPX_CG" in consts
+    checked = [n for n in consts if hasattr(spx, n)]
+    assert len(checked) >= 20
+    bad = {n: (consts[n], getattr(spx, n)) for n in checked if getattr(spx, n) != consts[n]}
+    assert not bad, bad

@@ -59,7 +59,7 @@ def _check(ro, xs, b, systems, x, tol, err_tol, infos=None, oracle_solver=None):
             assert not xb.any()
             continue
         rr = b[r0:r1] - oracle.spmv_csr(lrp, lcol, lval, xb)
-        assert np.linalg.norm(rr) / np.linalg.norm(b[r0:r1]) <= tol * 1.05, s
+        assert np.linalg.norm(rr) / np.linalg.norm(b[r0:r1]) <= residual_limit(lrp, lcol, lval, b[r0:r1], xb, tol), s
         assert np.linalg.norm(xb - xs[r0:r1]) / np.linalg.norm(xs[r0:r1]) <= err_tol, s
         if infos is not None and oracle_solver is not None:
             _, oi = oracle_solver(lrp, lcol, lval, b[r0:r1], tol=tol, maxit=20000)
@@ -114,6 +114,18 @@ def test_batch_mixed(spx, ctx, batch, solver):
         infos = spx.spx_batch_solve(ctx, B, _t(b), x, len(systems), solver, 1e-10, 20000, precision="mixed")
         assert all(i.status == spx.SPX_CONVERGED for i in infos), [i.status for i in infos]
         _check(ro, xs, b, systems, x.cpu().numpy(), 1e-10, 1e-7)
+        # CG: reliable updates (FP32 iterations, FP64 residual replacement); the others: refinement cycles
+        for s_, (lrp, lcol, lval) in enumerate(systems[:12]):
+            bs = b[int(ro[s_]): int(ro[s_ + 1])]
+            if not bs.any():
+                continue
+            if solver == "cg":
+                _, oi = oracle.cg_reliable(lrp, lcol, lval, bs, tol=1e-10)
+                assert abs(infos[s_].iterations - oi.iterations) <= max(3, oi.iterations // 10), (s_, infos[s_], oi)
+                assert abs(infos[s_].restarts - oi.restarts) <= 3, (s_, infos[s_], oi)
+            else:
+                _, oi = oracle.ir(lrp, lcol, lval, bs, solver=solver, tol=1e-10)
+                assert abs(infos[s_].restarts - oi.restarts) <= 2, (s_, infos[s_], oi)
     finally:
         spx.spx_batch_destroy(B)
 

@@ -67,6 +67,13 @@ def test_alone_equals_mix(spx, ctx, batch_rows):
             rp, col, val, b, solver = reqs[i]
             mix_ids.setdefault(i, []).append(srv.submit(rp, col, val, b, solver=solver, tol=1e-8))
         srv.drain()
+        # routes: batch lanes up to the batch limit; above it (or with the lanes off)
+        # short-row operators of at most 65536 rows solve on one cluster, the rest on the general path
+        for i, (rp, col, val, b, solver) in enumerate(reqs):
+            n = rp.shape[0] - 1
+            short = col.shape[0] <= 8 * n
+            want = "batch" if n <= eff else ("cluster" if short and n <= 65536 else "slot")
+            assert alone[i]["route"] == want, (i, n, alone[i]["route"])
         for i, (rp, col, val, b, solver) in enumerate(reqs):
             ra = alone[i]
             assert ra["error"] == 0 and ra["info"].status == spx.SPX_CONVERGED, ra
@@ -282,5 +289,37 @@ def test_concurrent_lanes_of_different_sizes(spx, ctx):
         for rid in ids:
             r = srv.results[rid]
             assert r["error"] == 0 and r["info"].status == spx.SPX_CONVERGED, r
+    finally:
+        srv.close()
+
+
+def test_cluster_route_setting_and_flag(spx, ctx):
+    """spx_server_set_cluster_rows(0) keeps short-row slot requests on the
+    general path; SPX_SOLVE_ONE_CLUSTER in a request's solver code sends it to
+    the cluster route whatever its rows; both routes meet tol."""
+    from paper_2103_10116_gb300.serving import Server
+    rp, col, val = synth.laplace3d_7pt(32)
+    b = synth.uniform_vector(32**3, seed=5)
+    rpd, cold, vald = synth.diagdom_random(30000, seed=6)
+    bd = synth.uniform_vector(30000, seed=7)
+    srv = Server(ctx, 0, max_slots=2)
+    try:
+        assert spx.spx_server_set_cluster_rows(srv.h, -1) == 65536
+        a = srv.submit(rp, col, val, b, solver="cg", tol=1e-8)
+        d = srv.submit(rpd, cold, vald, bd, solver="bicgstab", tol=1e-8)
+        f = srv.submit(rpd, cold, vald, bd, solver=spx.SPX_BICGSTAB | spx.SPX_SOLVE_ONE_CLUSTER, tol=1e-8)
+        srv.drain()
+        assert spx.spx_server_set_cluster_rows(srv.h, 0) == 0
+        g = srv.submit(rp, col, val, b, solver="cg", tol=1e-8)
+        srv.drain()
+        routes = [srv.results[i]["route"] for i in (a, d, f, g)]
+        assert routes == ["cluster", "slot", "cluster", "slot"], routes
+        for i, (rp_, col_, val_, b_) in ((a, (rp, col, val, b)), (d, (rpd, cold, vald, bd)),
+                                         (f, (rpd, cold, vald, bd)), (g, (rp, col, val, b))):
+            r = srv.results[i]
+            assert r["error"] == 0 and r["info"].status == spx.SPX_CONVERGED, r
+            x = r["x"]
+            rel = np.linalg.norm(b_ - oracle.spmv_csr(rp_, col_, val_, x)) / np.linalg.norm(b_)
+            assert rel <= residual_limit(rp_, col_, val_, b_, x, 1e-8), (i, rel)
     finally:
         srv.close()

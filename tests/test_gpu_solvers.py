@@ -321,3 +321,30 @@ def test_small_cg_single_launch_route(spx, ctx, n_side, dtype):
             assert _true_relres(rp, col, val, b, xh) <= 3 * tol
     finally:
         spx.spx_matrix_destroy(A)
+
+
+@pytest.mark.parametrize("solver", ["cg", "bicgstab", "cgs"])
+def test_small_mixed_single_launch_route(spx, ctx, solver):
+    """Mixed precision on a system of at most 4096 rows runs as a batch of one
+    in the persistent batched kernel: CG with reliable updates, BiCGSTAB and
+    CGS with refinement cycles, each against its oracle."""
+    rp, col, val = synth.laplace2d_5pt(40) if solver == "cg" else synth.convdiff3d_upwind(12)
+    n = rp.shape[0] - 1
+    xs = synth.uniform_vector(n, seed=3)
+    b = oracle.spmv_csr(rp, col, val, xs)
+    A = _make(spx, ctx, "csr", rp, col, val, flags=spx.SPX_MIXED_SHADOW)
+    try:
+        x = torch.zeros(n, dtype=torch.float64, device=DEV)
+        info = spx.spx_solve(ctx, A, _t(b), x, solver, 1e-10, 20000, precision="mixed")
+        assert info.status == spx.SPX_CONVERGED, info
+        xh = x.cpu().numpy()
+        assert _true_relres(rp, col, val, b, xh) <= residual_limit(rp, col, val, b, xh, 1e-10)
+        if solver == "cg":
+            _, oi = oracle.cg_reliable(rp, col, val, b, tol=1e-10)
+            assert abs(info.iterations - oi.iterations) <= max(3, oi.iterations // 10), (info, oi)
+            assert abs(info.restarts - oi.restarts) <= 3, (info, oi)
+        else:
+            _, oi = oracle.ir(rp, col, val, b, solver=solver, tol=1e-10)
+            assert abs(info.restarts - oi.restarts) <= 2, (info, oi)
+    finally:
+        spx.spx_matrix_destroy(A)
