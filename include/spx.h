@@ -122,7 +122,7 @@ typedef enum {
     SPX_KERNEL_AUTO = 0,        /* format default, chosen from row-length statistics */
     SPX_KERNEL_CSR_VECTOR = 1,  /* CSR: one sub-warp of `param` lanes (1..32, power of 2) per row */
     SPX_KERNEL_CSR_MERGE = 2,   /* CSR: merge-path split of rows + nonzeros, TMA-staged tiles */
-    SPX_KERNEL_ELL = 3,         /* ELL / HYB ELL part: one thread per `param` rows (1, 2 or 4) */
+    SPX_KERNEL_ELL = 3,         /* ELL / HYB ELL part: one thread per `param` rows (1, 2, or 4 in FP32; default 2) */
     SPX_KERNEL_COO = 4,         /* COO / HYB COO part: 1 = row-block (COO format; the default for short rows
                                    of similar length), 8/16 = warp-independent split,
                                    216/232 = the split on tile-transposed copies of the COO arrays with 16/32

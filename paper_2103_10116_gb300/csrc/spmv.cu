@@ -642,8 +642,14 @@ __global__ void __launch_bounds__(ROWS * TPR)
         if (live) {
             const int a0 = s_rp[q] - j0;
             const int len = (j1 > j0 ? s_rp[q + 1] - j0 : a0) - a0;
-            // this lane's entries: a0 + sub + TPR*u for u < cnt
-            const int cnt = TPR == 1 ? len : (len - sub + TPR - 1) / TPR;
+            // this lane's entries: a0 + sub + TPR*u for u < mine.  Every lane of a row
+            // steps through cnt = ceil(len / TPR) slots, a lane's slots past its own
+            // entries adding 0 * 0: the FMA sequence is then the same in every lane of
+            // the row (with a per-lane count, rows whose length is not a multiple of
+            // TPR ran both tail branches in one warp, one FP64 instruction more per row
+            // pair on the 27-point stencil)
+            const int cnt = TPR == 1 ? len : (len + TPR - 1) / TPR;
+            const int mine = TPR == 1 ? len : (len - sub + TPR - 1) / TPR;
             const int *pc = s_col + a0 + sub;
             const T *pv = s_val + a0 + sub;
             int a = 0;
@@ -651,19 +657,21 @@ __global__ void __launch_bounds__(ROWS * TPR)
                 T v[CH], xv[CH];
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
-                    v[u] = pv[(a + u) * TPR];
-                    xv[u] = __ldg(x + pc[(a + u) * TPR]);
+                    const bool real = TPR == 1 || a + u < mine;
+                    v[u] = real ? pv[(a + u) * TPR] : T(0);
+                    xv[u] = real ? __ldg(x + pc[(a + u) * TPR]) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < CH; ++u) sum = fma(v[u], xv[u], sum);
             }
-            const int rem = cnt - a;  // 0 .. CH-1: gathers issued together, FMAs only for real entries
+            const int rem = cnt - a;  // 0 .. CH-1: gathers issued together, FMAs only for the row's slots
             if (rem > 0) {
                 T v[CH - 1], xv[CH - 1];
 #pragma unroll
                 for (int u = 0; u < CH - 1; ++u) {
-                    v[u] = u < rem ? pv[(a + u) * TPR] : T(0);
-                    xv[u] = u < rem ? __ldg(x + pc[(a + u) * TPR]) : T(0);
+                    const bool real = u < rem && (TPR == 1 || a + u < mine);
+                    v[u] = real ? pv[(a + u) * TPR] : T(0);
+                    xv[u] = real ? __ldg(x + pc[(a + u) * TPR]) : T(0);
                 }
                 if (rem & 4) {
 #pragma unroll
@@ -2741,7 +2749,7 @@ template <class T>
 int dispatch_ell(spx_ctx *ctx, spx_matrix *A, const T *eval, const T *x, const Epi<T> &e)
 {
     int p = A->kernel == SPX_KERNEL_ELL ? A->kparam : 0;
-    if (p <= 0) p = (int)(16 / sizeof(T));
+    if (p <= 0) p = 2;  // two rows per thread (FP32 with four: 58.0 against 54.0 us on the 27-point stencil)
     if constexpr (sizeof(T) == 8) {
         if (p == 1) return launch_ell<T, 1>(ctx, A, eval, x, e);
         if (p == 2) return launch_ell<T, 2>(ctx, A, eval, x, e);
