@@ -262,6 +262,7 @@ extern "C" int spx_ctx_create(spx_ctx **out, int device, void *stream, spx_alloc
         return cuda_fail(e, "cudaGetDeviceProperties");
     }
     c->sm_count = prop.multiProcessorCount;
+    c->grid_sms = c->sm_count;
     c->max_smem_optin = (int)prop.sharedMemPerBlockOptin;
     c->l2_bytes = prop.l2CacheSize;
     c->red_grid = c->sm_count * 4;
@@ -285,6 +286,14 @@ extern "C" int spx_ctx_create(spx_ctx **out, int device, void *stream, spx_alloc
         return cuda_fail(e, "spx_ctx_create");
     }
     *out = c;
+    return SPX_OK;
+}
+
+extern "C" int spx_ctx_set_grid_sms(spx_ctx *ctx, int sms, int *effective)
+{
+    if (!ctx) return fail(SPX_ERR_INVALID, "spx_ctx_set_grid_sms: NULL context");
+    ctx->grid_sms = sms <= 0 ? ctx->sm_count : std::min(sms, ctx->sm_count);
+    if (effective) *effective = ctx->grid_sms;
     return SPX_OK;
 }
 
@@ -341,7 +350,7 @@ void free_matrix_arrays(spx_matrix *A)
 int grid1d(spx_ctx *ctx, int64_t work, int block = 256)
 {
     int64_t g = ceil_div(work, block);
-    const int64_t cap = (int64_t)ctx->sm_count * 16;
+    const int64_t cap = (int64_t)ctx->grid_sms * 16;
     if (g > cap) g = cap;
     return (int)(g < 1 ? 1 : g);
 }

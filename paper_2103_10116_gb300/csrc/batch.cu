@@ -110,7 +110,7 @@ int launch_batch_t(spx_ctx *ctx, spx_batch *B, const T *b, T *x, double tol, int
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
-    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    int64_t grid = (int64_t)per_sm * ctx->grid_sms;
     if (grid > B->nsys) grid = B->nsys;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -269,7 +269,7 @@ extern "C" int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_
         if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(B->val.p, values, (size_t)nnz * V, kind, ctx->stream);
         if (e == cudaSuccess && nsys > 0) e = cudaMemcpyAsync(B->order.p, order.data(), (size_t)nsys * 4, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess && B->val32.p && nnz > 0) {
-            k_cast_f32<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(nnz, B->val.as<double>(), B->val32.as<float>());
+            k_cast_f32<<<ctx->grid_sms * 8, 256, 0, ctx->stream>>>(nnz, B->val.as<double>(), B->val32.as<float>());
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaMallocHost(&B->host_out, bout_bytes(nsys) + 64);
@@ -310,7 +310,8 @@ int batch_solve_impl(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int sol
     const auto t0 = std::chrono::steady_clock::now();
     const size_t out_bytes = bout_bytes(B->nsys);
     uint64_t key[10] = {(uint64_t)(uintptr_t)b, (uint64_t)(uintptr_t)x, (uint64_t)solver, (uint64_t)precision, 0,
-                        (uint64_t)max_iter, (uint64_t)block, (uint64_t)(uintptr_t)ctx->stream, 0, 0};
+                        (uint64_t)max_iter, (uint64_t)block, (uint64_t)(uintptr_t)ctx->stream,
+                        (uint64_t)ctx->grid_sms, 0};
     std::memcpy(&key[4], &tol, 8);
     bool same = use_graph && B->gexec;
     for (int i = 0; i < 10 && same; ++i) same = B->gkey[i] == key[i];

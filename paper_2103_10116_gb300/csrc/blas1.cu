@@ -43,6 +43,7 @@ template <class T> int dot_launch(spx_ctx *ctx, int64_t n, const T *x, const T *
 {
     int64_t g = ceil_div(n, kDotBlock * 4);
     if (g > ctx->red_grid) g = ctx->red_grid;
+    if (g > (int64_t)ctx->grid_sms * 4) g = (int64_t)ctx->grid_sms * 4;
     if (g < 1) g = 1;
     T *partials = static_cast<T *>(ctx->red);
     unsigned *ticket = reinterpret_cast<unsigned *>(static_cast<char *>(ctx->red) +
@@ -56,7 +57,7 @@ template <class T> int axpby_launch(spx_ctx *ctx, int64_t n, T alpha, const T *x
 {
     if (n == 0) return SPX_OK;
     int64_t g = ceil_div(n, 256);
-    if (g > (int64_t)ctx->sm_count * 8) g = (int64_t)ctx->sm_count * 8;
+    if (g > (int64_t)ctx->grid_sms * 8) g = (int64_t)ctx->grid_sms * 8;
     k_axpby<T><<<(int)g, 256, 0, ctx->stream>>>(n, alpha, x, beta, y);
     SPX_CUDA(cudaGetLastError());
     return SPX_OK;

@@ -61,6 +61,18 @@ constexpr int64_t kServeBatchRowsMax = 262144; // the largest limit spx_server_s
 constexpr int64_t kServeClusterRows = 65536;    // default size limit of one-cluster requests
 constexpr int64_t kServeClusterRowsMax = 1 << 30;
 constexpr double kServeClusterMeanLen = 8.0;    // ... and their largest mean row length
+// Slot grids are sized for a share of the device's SMs, so that the kernels of
+// concurrent slots run side by side (spx_ctx_set_grid_sms).  Sixteen concurrent
+// mixed solves to 1e-8 of one matrix (solves per second at whole-device / half /
+// quarter / eighth grids): 7-point stencils of 250 000 rows 534 / 750 / 839 /
+// 743, of 512 000 rows 292 / 376 / 391 / 353, of 10^6 rows 154 / 175 / 179 /
+// 166; rows of 20 random columns, 10^5 rows 1092 / 1277 / 1233 / 1039,
+// 3 x 10^5 rows 506 / 521 / 490 / 414.  The rule (-1) takes a quarter for short
+// rows and a half for long ones.  On the mixed serving trace no setting beat
+// whole-device grids beyond run-to-run variation (whole device 397-403 solves
+// per second, the rule 382, a half 414, a quarter 374), so the default is 0.
+constexpr int kServeShortRowShare = 4;
+constexpr int kServeLongRowShare = 2;
 constexpr size_t kMaxBatchSystems = 4096;
 constexpr int64_t kMaxBatchRows = 16 << 20;
 
@@ -102,6 +114,8 @@ struct spx_server {
     std::deque<Request *> bqueue;  // requests for the batch lanes
     int64_t batch_rows = 0, batch_rows_limit = 0;
     int64_t cluster_rows = 0;
+    int slot_sms = 0;  // grid share of the slots' contexts (spx_ctx_set_grid_sms; 0: the whole device;
+                       // -1: by the request's mean row length, kServeShortRowShare / kServeLongRowShare)
     std::vector<Request *> done;
     std::vector<std::thread> workers;
     std::vector<const spx_matrix *> busy;  // resident operators with a request running
@@ -189,6 +203,7 @@ static void worker_main(spx_server *S)
     }
     for (;;) {
         Request *R = nullptr;
+        int sms = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop.load() || next_admissible(S) != S->queue.end(); });
@@ -201,6 +216,7 @@ static void worker_main(spx_server *S)
             S->active += 1;
             if (R->A) S->busy.push_back(R->A);
             R->t_admit = Clock::now();
+            sms = S->slot_sms;
         }
         S->cv_work.notify_all();  // another slot may admit the next request too
         int err = SPX_OK;
@@ -237,6 +253,11 @@ static void worker_main(spx_server *S)
         if (vald) cudaFreeAsync(vald, st);
         const auto t_setup = Clock::now();
         if (err == SPX_OK && R->cluster_auto) R->one_cluster = A->mean_len <= kServeClusterMeanLen;
+        if (err == SPX_OK) {  // the grid share: the server's setting, else by the operator's row length
+            const bool short_rows = A->mean_len <= kServeClusterMeanLen;
+            spx_ctx_set_grid_sms(ctx, sms >= 0 ? sms : ctx->sm_count / (short_rows ? kServeShortRowShare : kServeLongRowShare),
+                                 nullptr);
+        }
         if (err == SPX_OK)
             err = spx_solve(ctx, A, bd, xd, R->solver | (R->one_cluster ? SPX_SOLVE_ONE_CLUSTER : 0), R->tol,
                             R->max_iter, R->restart, R->precision, &R->info);
@@ -496,6 +517,7 @@ extern "C" int spx_server_create(spx_ctx *ctx, spx_server **out, int64_t budget_
     S->batch_rows_limit = kServeBatchRowsMax;
     S->batch_rows = std::min<int64_t>(kServeBatchRows, S->batch_rows_limit);
     S->cluster_rows = kServeClusterRows;
+    S->slot_sms = 0;
     for (int i = 0; i < max_slots; ++i) S->workers.emplace_back(worker_main, S);
     for (int i = 0; i < kBatchLanes; ++i) S->workers.emplace_back(lane_main, S);
     *out = S;
@@ -668,5 +690,14 @@ extern "C" int spx_server_set_cluster_rows(spx_server *S, int64_t max_rows, int6
     std::lock_guard<std::mutex> lk(S->mu);
     if (max_rows >= 0) S->cluster_rows = std::min<int64_t>(max_rows, kServeClusterRowsMax);
     if (effective) *effective = S->cluster_rows;
+    return SPX_OK;
+}
+
+extern "C" int spx_server_set_slot_sms(spx_server *S, int sms, int *effective)
+{
+    if (!S) return fail(SPX_ERR_INVALID, "spx_server_set_slot_sms: NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (sms >= -1) S->slot_sms = sms;
+    if (effective) *effective = S->slot_sms;
     return SPX_OK;
 }

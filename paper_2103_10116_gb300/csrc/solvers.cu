@@ -1231,7 +1231,7 @@ template <class T> T *vec(SolverWork *w, int k) { return w->vecs.as<T>() + (int6
 int vgrid(spx_ctx *ctx, int64_t n, int cap_per_sm = 3)
 {
     int64_t g = ceil_div(n, kVB);
-    const int64_t cap = (int64_t)ctx->sm_count * cap_per_sm;
+    const int64_t cap = (int64_t)ctx->grid_sms * cap_per_sm;
     if (g > cap) g = cap;
     return (int)(g < 1 ? 1 : g);
 }
@@ -1251,8 +1251,13 @@ struct Timer {
 // ctx->stream).  Keys include the context: a graph holds the context's error
 // word, so a matrix solved from another context captures its own graph.  The first call of a key runs eagerly so that every lazily
 // allocated scratch exists before capture.
-template <class F> int run_chunk(spx_ctx *ctx, SolverWork *w, const uint64_t key[8], bool use_graph, F &&body)
+template <class F> int run_chunk(spx_ctx *ctx, SolverWork *w, const uint64_t key_in[8], bool use_graph, F &&body)
 {
+    // the grids a capture records depend on the context's grid share: part of the key
+    // (bits 52 and up of the context slot; context addresses stay below 2^48)
+    uint64_t key[8];
+    std::memcpy(key, key_in, sizeof(key));
+    key[7] ^= (uint64_t)ctx->grid_sms << 52;
     bool same = w->gexec != nullptr;
     for (int i = 0; i < 8 && same; ++i) same = w->gkey[i] == key[i];
     if (same) {
@@ -1531,7 +1536,7 @@ template <class T> int ensure_dinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
     if (!w->pre || w->bs || w->dinv.p) return SPX_OK;
     const int64_t n = A->n;
     SPX_TRY(dbuf_alloc(ctx, w->dinv, (size_t)(n > 0 ? n : 1) * sizeof(T)));
-    const int g = (int)std::min<int64_t>(ceil_div(n > 0 ? n : 1, 256), (int64_t)ctx->sm_count * 16);
+    const int g = (int)std::min<int64_t>(ceil_div(n > 0 ? n : 1, 256), (int64_t)ctx->grid_sms * 16);
     const bool csr = A->format == SPX_CSR;
     const int64_t ew = (A->format == SPX_ELL || A->format == SPX_HYB) ? A->ell_w : 0;
     const int64_t cn = (A->format == SPX_COO || A->format == SPX_HYB) ? A->coo_nnz : 0;
@@ -1553,7 +1558,7 @@ template <class V, class T>
 int bj_build_small(spx_ctx *ctx, spx_matrix *A, SolverWork *w, float *m32)
 {
     const int64_t n = A->n, nb = ceil_div(n > 0 ? n : 1, (int64_t)w->bs);
-    const int g = (int)std::min<int64_t>(ceil_div(nb, kBjTpb), (int64_t)ctx->sm_count * 16);
+    const int g = (int)std::min<int64_t>(ceil_div(nb, kBjTpb), (int64_t)ctx->grid_sms * 16);
     const bool csr = A->format == SPX_CSR;
     const int64_t ew = (A->format == SPX_ELL || A->format == SPX_HYB) ? A->ell_w : 0;
     const int64_t cn = (A->format == SPX_COO || A->format == SPX_HYB) ? A->coo_nnz : 0;
@@ -1584,7 +1589,7 @@ template <class T> int ensure_bjinv(spx_ctx *ctx, spx_matrix *A, SolverWork *w)
     if (w->bj_adapt) SPX_TRY(dbuf_alloc(ctx, w->bjinv32, (size_t)(nb * bs * bs) * sizeof(float)));
     float *m32 = w->bj_adapt ? w->bjinv32.as<float>() : nullptr;
     if (bs <= 8) return A->dtype == SPX_F64 ? bj_build_small<double, T>(ctx, A, w, m32) : bj_build_small<float, T>(ctx, A, w, m32);
-    const int g = (int)std::min<int64_t>(ceil_div(nb, kBjWarps), (int64_t)ctx->sm_count * 32);
+    const int g = (int)std::min<int64_t>(ceil_div(nb, kBjWarps), (int64_t)ctx->grid_sms * 32);
     const int smem = kBjWarps * (int)(bs * 2 * bs + bs) * 8;
     const bool csr = A->format == SPX_CSR;
     const int64_t ew = (A->format == SPX_ELL || A->format == SPX_HYB) ? A->ell_w : 0;
@@ -1770,7 +1775,7 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
     SPX_CUDA(cudaMemcpyAsync(gs, &hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
     const int g = vgrid(ctx, n, 2);
     int gd = (int)ceil_div(n, kGmRows);  // dots passes: persistent grid, at most 4 blocks per SM
-    if (gd > 4 * ctx->sm_count) gd = 4 * ctx->sm_count;
+    if (gd > 4 * ctx->grid_sms) gd = 4 * ctx->grid_sms;
     if (gd < 1) gd = 1;
     const int gu = vgrid(ctx, n, 8);
     auto cycle = [&]() -> int {

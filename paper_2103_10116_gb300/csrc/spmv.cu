@@ -2050,7 +2050,7 @@ template <class K> int grid_for(spx_ctx *ctx, K kernel, int block, int smem, int
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    int64_t g = (int64_t)per_sm * ctx->sm_count;
+    int64_t g = (int64_t)per_sm * ctx->grid_sms;
     if (g > work_blocks) g = work_blocks;
     return (int)(g < 1 ? 1 : g);
 }
@@ -2220,7 +2220,7 @@ int ensure_rows_cap(spx_ctx *ctx, spx_matrix *A)
     int cap = 0;
     cudaError_t e = cudaMemsetAsync(m.p, 0, 4, ctx->stream);
     if (e == cudaSuccess && ntiles > 0) {
-        const int g = (int)std::min<int64_t>(ceil_div(ntiles, 256), (int64_t)ctx->sm_count * 8);
+        const int g = (int)std::min<int64_t>(ceil_div(ntiles, 256), (int64_t)ctx->grid_sms * 8);
         k_tile_max_nnz<<<g, 256, 0, ctx->stream>>>((int)A->n, A->rp.as<int>(), kRowsTile, (int)ntiles, m.as<int>());
         e = cudaGetLastError();
     }
@@ -2365,7 +2365,7 @@ int launch_split_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const 
     const int64_t nchunks = ceil_div(ceil_div(A->nnz, IPT), 32);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    int64_t grid = (int64_t)per_sm * ctx->grid_sms;
     const int64_t need = ceil_div(nchunks, 8);  // at least one chunk per warp
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
@@ -2464,7 +2464,7 @@ int launch_tiled_m(spx_ctx *ctx, spx_matrix *A, const T *val, const T *x, const 
     const int64_t nchunks = ceil_div(A->nnz, 32LL * IPT);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    int64_t grid = (int64_t)per_sm * ctx->grid_sms;
     const int64_t need = ceil_div(nchunks, 8);  // at least one chunk per warp
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
@@ -2536,7 +2536,7 @@ int launch_coo_tiled_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, c
     const int64_t nchunks = ceil_div(A->coo_nnz, 32LL * IPT);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    int64_t grid = (int64_t)per_sm * ctx->grid_sms;
     const int64_t need = ceil_div(nchunks, 8);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
@@ -2572,7 +2572,7 @@ int launch_coo_split_m(spx_ctx *ctx, spx_matrix *A, const T *cval, const T *x, c
     const int64_t nchunks = ceil_div(ceil_div(A->coo_nnz, IPT), 32);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * ctx->sm_count;
+    int64_t grid = (int64_t)per_sm * ctx->grid_sms;
     const int64_t need = ceil_div(nchunks, 8);
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
@@ -3035,7 +3035,7 @@ extern "C" int spx_probe_gather(spx_ctx *ctx, int64_t nnz, const int32_t *col_id
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
-    const int grid = ctx->sm_count * 8;
+    const int grid = ctx->grid_sms * 8;
     if (dtype == SPX_F64)
         k_gather_probe<double><<<grid, 256, 0, ctx->stream>>>(nnz, col_idx, static_cast<const double *>(x),
                                                              static_cast<double *>(out));

@@ -48,7 +48,8 @@ struct spx_ctx {
     spx_alloc_fn alloc = nullptr;
     spx_free_fn free = nullptr;
     void *user = nullptr;
-    int sm_count = 0;
+    int sm_count = 0;  // the device's SMs: every scratch buffer is sized for grids over all of them
+    int grid_sms = 0;  // SMs the context's launch grids are sized for (<= sm_count; spx_ctx_set_grid_sms)
     int max_smem_optin = 0;
     int64_t l2_bytes = 0;
     // small always-resident device scratch: reduction tickets, flags

@@ -114,6 +114,8 @@ SIGNATURES = {
     "spx_server_submit_matrix": (_I, [_P, _P, _P, _P, _I, _D, _I64, _I, _I, C.POINTER(C.c_int64)]),
     "spx_server_poll": (_I, [_P, C.POINTER(spx_server_result), _I, _I, C.POINTER(C.c_int)]),
     "spx_server_set_batching": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
+    "spx_ctx_set_grid_sms": (_I, [_P, _I, C.POINTER(C.c_int)]),
+    "spx_server_set_slot_sms": (_I, [_P, _I, C.POINTER(C.c_int)]),
     "spx_server_set_cluster_rows": (_I, [_P, _I64, C.POINTER(C.c_int64)]),
     "spx_probe_gather": (_I, [_P, _I64, _P, _P, _I, _P]),
     "spx_ctx_check": (_I, [_P]),
@@ -211,6 +213,13 @@ def spx_ctx_create(device: int = 0, stream=None, allocator: str = "torch") -> in
 
 def spx_ctx_destroy(ctx: int):
     _check(load().spx_ctx_destroy(ctx))
+
+
+def spx_ctx_set_grid_sms(ctx: int, sms: int) -> int:
+    """Size the context's launch grids for `sms` SMs (<= 0: the whole device); returns the value in force."""
+    eff = C.c_int()
+    _check(load().spx_ctx_set_grid_sms(ctx, int(sms), C.byref(eff)))
+    return eff.value
 
 
 def spx_ctx_set_stream(ctx: int, stream):
@@ -521,6 +530,14 @@ def spx_probe_gather(ctx: int, col_idx: torch.Tensor, x: torch.Tensor, out: torc
 def spx_server_set_batching(S: int, max_rows: int) -> int:
     eff = C.c_int64(0)
     _check(load().spx_server_set_batching(S, int(max_rows), C.byref(eff)))
+    return eff.value
+
+
+def spx_server_set_slot_sms(S: int, sms: int) -> int:
+    """Grid share of the server's slots (0: whole device, the default; -1: by row length; below -1: report
+    only); returns the setting in force."""
+    eff = C.c_int()
+    _check(load().spx_server_set_slot_sms(S, int(sms), C.byref(eff)))
     return eff.value
 
 

@@ -58,6 +58,9 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     # argument validation happens before any CUDA call
     assert lib.spx_matrix_get_info(None, None) == spx.SPX_ERR_INVALID
     assert lib.spx_spmv(None, None, None, None) == spx.SPX_ERR_INVALID
+    assert lib.spx_ctx_set_grid_sms(None, 0, None) == spx.SPX_ERR_INVALID
+    assert lib.spx_server_set_slot_sms(None, 0, None) == spx.SPX_ERR_INVALID
+    assert lib.spx_server_set_cluster_rows(None, 0, None) == spx.SPX_ERR_INVALID
     assert "NULL" in spx.spx_last_error()
     out = C.c_void_p()
     assert lib.spx_matrix_create(None, C.byref(out), 0, 0, 1, 1, 0, None, None, None, 0, -1, 0) == spx.SPX_ERR_INVALID

@@ -305,6 +305,8 @@ def test_cluster_route_setting_and_flag(spx, ctx):
     srv = Server(ctx, 0, max_slots=2)
     try:
         assert spx.spx_server_set_cluster_rows(srv.h, -1) == 65536
+        assert spx.spx_server_set_slot_sms(srv.h, -2) == 0  # the default: whole-device grids
+        assert spx.spx_server_set_slot_sms(srv.h, -1) == -1  # grid share by row length from here on
         a = srv.submit(rp, col, val, b, solver="cg", tol=1e-8)
         d = srv.submit(rpd, cold, vald, bd, solver="bicgstab", tol=1e-8)
         f = srv.submit(rpd, cold, vald, bd, solver=spx.SPX_BICGSTAB | spx.SPX_SOLVE_ONE_CLUSTER, tol=1e-8)
