@@ -1,4 +1,6 @@
-// cluster.cu -- CG on one thread-block cluster for small systems.
+// cluster.cu -- whole solves in one launch on one thread-block cluster: CG for
+// small systems with its vectors in shared memory (this part), and CG, BiCGSTAB
+// or CGS of any size with its vectors in global memory (k_cluster_solve, below).
 //
 // A system of at most 16 * 4096 rows is solved by one cluster of 16 thread
 // blocks on 16 SMs (8 where the device runs no cluster of 16), launched once
@@ -7,7 +9,7 @@
 // its shared memory; the product A p reads the entries of p it needs from
 // the other blocks' shared memory through the cluster's distributed shared
 // memory, and the dot products are summed by every block from the block
-// partials in rank order, so all blocks take the same decisions and the
+// partials in one fixed order, so all blocks take the same decisions and the
 // result does not depend on timing.  An iteration costs three cluster
 // barriers and no kernel launch.  The textbook CG recurrences (Hestenes and
 // Stiefel, the form the Krylov solvers of Section 5 follow), then the true
@@ -42,20 +44,27 @@ struct ClOut {
     double relres;
 };
 
-// Sum of v over the cluster: block sums, then every block adds the CL
-// block partials in rank order (the same bits in every block).  `slot`
-// alternates between the reductions of an iteration; see the barrier
-// argument in k_cluster_cg.
+// Sum of v over the cluster: block sums, then in every block warp 0 adds the CL
+// block partials in one fixed shuffle order (the same bits in every block) and
+// shares the total through shared memory.  (Every thread reading all CL remote
+// partials took CL distributed-shared-memory loads per thread per sum.)  `slot`
+// alternates between the reductions of an iteration; see the barrier argument
+// in k_cluster_cg.  bc is rewritten by the next sum only after its block
+// barriers, which every thread reaches after reading it.
 template <class T, int CL, int BLOCK>
 __device__ __forceinline__ T cluster_sum(cg::cluster_group &cl, T v, T *red, T *part, int slot)
 {
+    __shared__ T bc;
     v = block_sum<T, BLOCK>(v, red);
     if (threadIdx.x == 0) part[slot] = v;
     cl.sync();
-    T s = T(0);
-#pragma unroll
-    for (int k = 0; k < CL; ++k) s += *cl.map_shared_rank(part + slot, k);
-    return s;
+    if (threadIdx.x < 32) {
+        T p = threadIdx.x < CL ? *cl.map_shared_rank(part + slot, (unsigned)threadIdx.x) : T(0);
+        p = warp_sum(p);
+        if (threadIdx.x == 0) bc = p;
+    }
+    __syncthreads();
+    return bc;
 }
 
 // (A v)_i for the local row i (global row g) with v distributed over the
