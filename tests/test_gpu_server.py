@@ -43,17 +43,22 @@ def _requests(large=False):
     return reqs
 
 
-@pytest.mark.parametrize("batch_rows", [None, 65536, 0])
-def test_alone_equals_mix(spx, ctx, batch_rows):
+@pytest.mark.parametrize("batch_rows,cluster_rows", [(None, None), (65536, None), (0, None), (0, 65536)])
+def test_alone_equals_mix(spx, ctx, batch_rows, cluster_rows):
     """batch_rows None (the default, 24576): small requests go through the
     batch lanes, the large one (32^3 rows) through a slot; 65536: the large
     one is batched too, its gathered vector in global memory; 0: every
-    request on a slot of its own."""
+    request on a slot of its own; with cluster_rows 65536 the short-row ones
+    as one-cluster solves."""
     from paper_2103_10116_gb300.serving import Server
     reqs = _requests(large=True)
     srv = Server(ctx, 0, max_slots=4, batch_rows=batch_rows)
     eff = spx.spx_server_set_batching(srv.h, -1)
     assert eff == (24576 if batch_rows is None else batch_rows)
+    if cluster_rows is not None:
+        spx.spx_server_set_cluster_rows(srv.h, cluster_rows)
+    cl_rows = spx.spx_server_set_cluster_rows(srv.h, -1)
+    assert cl_rows == (0 if cluster_rows is None else cluster_rows)
     try:
         alone = {}
         for i, (rp, col, val, b, solver) in enumerate(reqs):
@@ -68,11 +73,11 @@ def test_alone_equals_mix(spx, ctx, batch_rows):
             mix_ids.setdefault(i, []).append(srv.submit(rp, col, val, b, solver=solver, tol=1e-8))
         srv.drain()
         # routes: batch lanes up to the batch limit; above it (or with the lanes off)
-        # short-row operators of at most 65536 rows solve on one cluster, the rest on the general path
+        # short-row operators of at most cl_rows rows solve on one cluster, the rest on the general path
         for i, (rp, col, val, b, solver) in enumerate(reqs):
             n = rp.shape[0] - 1
             short = col.shape[0] <= 8 * n
-            want = "batch" if n <= eff else ("cluster" if short and n <= 65536 else "slot")
+            want = "batch" if n <= eff else ("cluster" if short and n <= cl_rows else "slot")
             assert alone[i]["route"] == want, (i, n, alone[i]["route"])
         for i, (rp, col, val, b, solver) in enumerate(reqs):
             ra = alone[i]
@@ -304,7 +309,8 @@ def test_cluster_route_setting_and_flag(spx, ctx):
     bd = synth.uniform_vector(30000, seed=7)
     srv = Server(ctx, 0, max_slots=2)
     try:
-        assert spx.spx_server_set_cluster_rows(srv.h, -1) == 65536
+        assert spx.spx_server_set_cluster_rows(srv.h, -1) == 0  # the default: no cluster route
+        assert spx.spx_server_set_cluster_rows(srv.h, 65536) == 65536
         assert spx.spx_server_set_slot_sms(srv.h, -2) == 0  # the default: whole-device grids
         assert spx.spx_server_set_slot_sms(srv.h, -1) == -1  # grid share by row length from here on
         a = srv.submit(rp, col, val, b, solver="cg", tol=1e-8)
