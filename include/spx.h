@@ -457,14 +457,13 @@ int spx_server_set_batching(spx_server *S, int64_t max_rows, int64_t *effective)
 /* Solve the slot requests of at most max_rows rows that are CG / BiCGSTAB /
  * CGS without preconditioner on a CSR operator whose rows hold at most 8
  * entries on average with SPX_SOLVE_ONE_CLUSTER (one launch on one
- * thread-block cluster per request) from now on; 0: none (the default);
- * capped at 2^30; negative: leave the limit unchanged, only report it.
- * Measured with sixteen concurrent mixed CG solves of a 27 000-row 7-point
- * stencil: 1.5-1.7x the solves per second of the general path launching its
- * kernels directly, slightly fewer than the general path replaying CUDA
- * graphs (which it does from 8192 rows on); longer rows with random columns
- * were slower on clusters at every size.  The decision uses only the request's
- * own matrix.  A request submitted with
+ * thread-block cluster per request) from now on; 0: none; capped at 2^30;
+ * negative: leave the limit unchanged, only report it.  The default is 65 536
+ * rows (measured: sixteen concurrent mixed CG solves of a 27 000-row 7-point
+ * stencil completed 1.5-1.7x as many solves per second on clusters as on the
+ * general path, whose one solve per matrix launches its kernels directly below
+ * 50 000 rows; 97 000 rows broke even; longer rows with random columns were
+ * slower on clusters).  The decision uses only the request's own matrix.  A request submitted with
  * SPX_SOLVE_ONE_CLUSTER
  * in its solver code takes that route whatever its size.  *effective (may be
  * NULL) receives the limit in force.  As with the batch lanes, a request's

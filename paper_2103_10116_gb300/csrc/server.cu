@@ -25,15 +25,18 @@
 // Slot requests of CG / BiCGSTAB / CGS (unpreconditioned) on CSR operators of
 // at most cluster_rows rows whose rows hold at most 8 entries on average (the
 // 7-point stencil's class) may run the whole solve in one launch on one
-// thread-block cluster (SPX_SOLVE_ONE_CLUSTER; off by default,
-// spx_server_set_cluster_rows turns it on).  Sixteen concurrent solves of a
-// 27 000-row 7-point stencil (mixed CG to 1e-8) completed 1.5-1.7x as many
-// solves per second on clusters as on the general path launching its kernels
-// directly, but slightly fewer (1535-1662 against 1735) once the general path
-// replayed CUDA graphs at that size; for longer rows with random columns the
-// cluster route was slower at every size measured.  The decision reads the row
-// statistics of the request's own matrix, so it does not depend on other
-// requests.
+// thread-block cluster (SPX_SOLVE_ONE_CLUSTER): on the general path such a
+// solve is hundreds of dependent launches of kernels with a few microseconds
+// of work each (and a request solves its matrix once, too few times to repay
+// capturing CUDA graphs).  Sixteen concurrent solves of a 27 000-row 7-point
+// stencil (mixed CG to 1e-8) completed 1.5-1.7x as many solves per second on
+// clusters as on the general path launching its kernels directly; on the
+// serving trace the solve phases of the 25 000 - 100 000-row requests summed to
+// 128 s with the route and 187 s without.  At 97 000 rows the two broke even,
+// and for longer rows with random columns the cluster route was slower at every
+// size measured, so the rule takes short rows of at most 65 536 rows.  The
+// decision reads the row statistics of the request's own matrix, so it does not
+// depend on other requests.
 //
 // Results do not depend on what else runs: every kernel of a solve uses only
 // its own matrix's and slot's scratch, with fixed-order reductions; a
@@ -58,7 +61,7 @@ using Clock = std::chrono::steady_clock;
 constexpr int kBatchLanes = 4;
 constexpr int64_t kServeBatchRows = 24576;     // default size limit of batched requests
 constexpr int64_t kServeBatchRowsMax = 262144; // the largest limit spx_server_set_batching accepts
-constexpr int64_t kServeClusterRows = 0;        // default size limit of one-cluster requests (none)
+constexpr int64_t kServeClusterRows = 65536;    // default size limit of one-cluster requests
 constexpr int64_t kServeClusterRowsMax = 1 << 30;
 constexpr double kServeClusterMeanLen = 8.0;    // ... and their largest mean row length
 // Slot grids are sized for a share of the device's SMs, so that the kernels of

@@ -33,12 +33,21 @@ namespace spx {
 constexpr int kVB = 256;        // block of the vector kernels
 constexpr int kGmKmax = 32;     // largest GMRES restart length (basis held in registers per row)
 constexpr int kMaxRestarts = 3;
-// Solves of at least kGraphMinRows rows replay their iterations as CUDA graphs;
-// smaller ones launch directly.  Mixed CG to 1e-8 on a 27 000-row 7-point
-// stencil: 4.48 ms launched directly, 2.37 ms with graphs (the first solve,
-// which captures them, 2.0 against 2.4 ms); BiCGSTAB on 30 000 rows of 20 random
-// columns 2.02 against 1.18 ms.
+// When a solve replays its iterations as CUDA graphs: systems of at least
+// kGraphFirstSolveRows rows from their first solve on (capturing costs about a
+// millisecond, which one solve of such a system repays), systems of at least
+// kGraphMinRows rows from their second solve on the same matrix.  Mixed CG to
+// 1e-8 on a 27 000-row 7-point stencil took 4.48 ms launched directly and 2.37 ms
+// replaying graphs (BiCGSTAB on 30 000 rows of 20 random columns: 2.02 against
+// 1.18 ms); but a request server that solves every matrix once lost throughput
+// capturing a graph per request (sixteen slots capturing at once: the solve
+// phases of its 25 000 - 100 000-row requests summed to 206 s against 187 s).
 constexpr int64_t kGraphMinRows = 8192;
+constexpr int64_t kGraphFirstSolveRows = 50000;
+bool graphs_for(const spx_matrix *A)
+{
+    return A->n >= kGraphFirstSolveRows || (A->n >= kGraphMinRows && A->solves > 0);
+}
 
 // ------------------------------------------------------------------ GMRES state
 template <class T> struct GState {
@@ -1683,9 +1692,7 @@ int run_short(spx_ctx *ctx, spx_matrix *A, SolverWork *w, int solver, const T *b
     KState<T> *h = static_cast<KState<T> *>(w->host);
     int restarts = 0;
     const int chunk = fixed > 0 ? 64 : (n < 200000 ? 32 : 16);
-    // capturing a graph costs about a millisecond: worth it when a large system
-    // replays the chunk many times, not for small one-off solves
-    const bool graphs = n >= kGraphMinRows;
+    const bool graphs = graphs_for(A);
     for (;;) {
         SPX_TRY(krylov_init(R));
         SPX_TRY(read_state<T>(ctx, w, sizeof(KState<T>)));
@@ -1824,7 +1831,7 @@ int run_gmres(spx_ctx *ctx, spx_matrix *A, SolverWork *w, const T *b, T *x, doub
                                  (uint64_t)use32, (uint64_t)m, (uint64_t)sizeof(T) | ((uint64_t)w->pre << 8) | ((uint64_t)w->bs << 16) |
                                      ((uint64_t)w->bj_adapt << 24),
                                  (uint64_t)(uintptr_t)A, ((uint64_t)(uintptr_t)ctx << 1) | 1u};
-        SPX_TRY(run_chunk(ctx, w, key, n >= kGraphMinRows, cycle));
+        SPX_TRY(run_chunk(ctx, w, key, graphs_for(A), cycle));
         SPX_TRY(read_state<T>(ctx, w, sizeof(GState<T>)));
         ++cycles;
         if (h->done) break;
@@ -1950,7 +1957,7 @@ int run_cg_reliable(spx_ctx *ctx, spx_matrix *A, const double *b, double *x, dou
     }
     KrylovRun<float> R{ctx, A, wi, nullptr, d32, true, SPX_CG};
     const int chunk = n < 200000 ? 32 : 16;
-    const bool graphs = n >= kGraphMinRows;
+    const bool graphs = graphs_for(A);
     int64_t launched = 0;
     while (status != SPX_CONVERGED) {
         SPX_TRY(read_state<float>(ctx, wi, sizeof(KState<float>)));
@@ -2205,7 +2212,9 @@ extern "C" int spx_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, in
 {
     if (!ctx) return fail(SPX_ERR_INVALID, "spx_solve: ctx is NULL");
     DevGuard g(ctx->device);
-    return solve_entry(ctx, A, b, x, solver, tol, max_iter, restart, precision, 0, info);
+    const int st = solve_entry(ctx, A, b, x, solver, tol, max_iter, restart, precision, 0, info);
+    if (A) ++A->solves;
+    return st;
 }
 
 extern "C" int spx_solve_fixed(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solver, int64_t iterations,
@@ -2214,5 +2223,7 @@ extern "C" int spx_solve_fixed(spx_ctx *ctx, spx_matrix *A, const void *b, void 
     if (!ctx) return fail(SPX_ERR_INVALID, "spx_solve_fixed: ctx is NULL");
     if (iterations < 1) return fail(SPX_ERR_INVALID, "spx_solve_fixed: iterations must be >= 1");
     DevGuard g(ctx->device);
-    return solve_entry(ctx, A, b, x, solver, 0.0, iterations, restart, precision, iterations, info);
+    const int st = solve_entry(ctx, A, b, x, solver, 0.0, iterations, restart, precision, iterations, info);
+    if (A) ++A->solves;
+    return st;
 }

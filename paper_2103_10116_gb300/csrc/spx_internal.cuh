@@ -145,6 +145,7 @@ struct spx_matrix {
     bool batch1_shadow = false;
     spx::DBuf small_out;  // result record of the cluster solves (cluster.cu)
     spx::DBuf cl_work;    // workspace of the one-cluster solve of a mid-size system (cluster.cu)
+    int64_t solves = 0;   // spx_solve calls made on this matrix (solvers.cu: when to capture graphs)
 };
 
 namespace spx {

@@ -43,13 +43,13 @@ def _requests(large=False):
     return reqs
 
 
-@pytest.mark.parametrize("batch_rows,cluster_rows", [(None, None), (65536, None), (0, None), (0, 65536)])
+@pytest.mark.parametrize("batch_rows,cluster_rows", [(None, None), (65536, None), (0, None), (0, 0)])
 def test_alone_equals_mix(spx, ctx, batch_rows, cluster_rows):
     """batch_rows None (the default, 24576): small requests go through the
     batch lanes, the large one (32^3 rows) through a slot; 65536: the large
     one is batched too, its gathered vector in global memory; 0: every
-    request on a slot of its own; with cluster_rows 65536 the short-row ones
-    as one-cluster solves."""
+    request on a slot of its own (the short-row ones up to 65536 rows as
+    one-cluster solves, the default; with cluster_rows 0 on the general path)."""
     from paper_2103_10116_gb300.serving import Server
     reqs = _requests(large=True)
     srv = Server(ctx, 0, max_slots=4, batch_rows=batch_rows)
@@ -58,7 +58,7 @@ def test_alone_equals_mix(spx, ctx, batch_rows, cluster_rows):
     if cluster_rows is not None:
         spx.spx_server_set_cluster_rows(srv.h, cluster_rows)
     cl_rows = spx.spx_server_set_cluster_rows(srv.h, -1)
-    assert cl_rows == (0 if cluster_rows is None else cluster_rows)
+    assert cl_rows == (65536 if cluster_rows is None else cluster_rows)
     try:
         alone = {}
         for i, (rp, col, val, b, solver) in enumerate(reqs):
@@ -309,8 +309,7 @@ def test_cluster_route_setting_and_flag(spx, ctx):
     bd = synth.uniform_vector(30000, seed=7)
     srv = Server(ctx, 0, max_slots=2)
     try:
-        assert spx.spx_server_set_cluster_rows(srv.h, -1) == 0  # the default: no cluster route
-        assert spx.spx_server_set_cluster_rows(srv.h, 65536) == 65536
+        assert spx.spx_server_set_cluster_rows(srv.h, -1) == 65536  # the default
         assert spx.spx_server_set_slot_sms(srv.h, -2) == 0  # the default: whole-device grids
         assert spx.spx_server_set_slot_sms(srv.h, -1) == -1  # grid share by row length from here on
         a = srv.submit(rp, col, val, b, solver="cg", tol=1e-8)
