@@ -329,7 +329,11 @@ int cluster_cg_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, double
 // after a cluster barrier, and the group sums go through distributed shared
 // memory.  One cluster uses 16 (or 8) SMs, so a lone large solve is faster on
 // the general path; many such solves on separate streams (the request server)
-// run side by side on disjoint SMs with no launch between iterations.
+// run side by side with no launch between iterations, though sixteen at once
+// completed only three to four times the solves per second of one, and each
+// thread walking its own row makes rows of many random columns costly (one
+// warp's column and value loads touch up to 32 lines).  Measured faster than
+// the general path for short rows up to a few tens of thousands of rows.
 template <class T, int CL, int BLOCK, int SOLVER, bool MIXED>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK)
     k_cluster_solve(int n, const int *__restrict__ rp, const int *__restrict__ col, const T *__restrict__ val,
