@@ -360,3 +360,51 @@ def test_tiled_csr_layout_and_descriptors(mname, ipt):
     rows = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
     np.add.at(yref, rows, np.asarray(val, np.float64) * x[np.asarray(col)])
     assert np.array_equal(y, yref)
+
+
+# ------------------------------------------------------------------ cluster solves
+# The two cluster kernels split a system's rows over the blocks of one cluster:
+# the small-system CG gives block k the slice [k R, (k+1) R) of R = 2^lg rows,
+# lg the least with CL << lg >= n, and keeps it in shared memory (4 vectors of R
+# values, R at most 4096); the one-cluster solve of any size gives block k
+# [min(n, k R), min(n, k R + R)) with R = ceil(n / CL) rounded up to 32.  Every
+# row must belong to exactly one block, a block's slice must start on a multiple
+# of 32 rows (its threads' rows then fall in whole warps' sectors), and the small
+# CG's slices must fit the shared memory it asks for.
+
+
+def _cluster_small_slices(n, cl):
+    lg = 0
+    while (cl << lg) < n:
+        lg += 1
+    r = 1 << lg
+    return r, [(min(n, k * r), min(n, (k + 1) * r)) for k in range(cl)]
+
+
+def _cluster_solve_slices(n, cl):
+    r = ((n + cl - 1) // cl + 31) & ~31
+    return r, [(min(n, k * r), min(n, k * r + r)) for k in range(cl)]
+
+
+@pytest.mark.parametrize("cl", [8, 16])
+def test_cluster_row_slices_partition_the_rows(cl):
+    sizes = [1, 2, 5, 31, 32, 33, 4095, 4096, 4097, 8000, 32761, 65535, 65536, 68921, 10**6, 2**30]
+    for n in sizes:
+        for slices_of, small in ((_cluster_solve_slices, False), (_cluster_small_slices, True)):
+            if small and n > cl * 4096:
+                continue  # the small CG takes at most 4096 rows per block
+            r, sl = slices_of(n, cl)
+            covered = 0
+            for k, (lo, hi) in enumerate(sl):
+                assert 0 <= lo <= hi <= n
+                assert hi - lo <= r
+                if hi > lo:
+                    assert lo == covered, (n, cl, k)  # contiguous, in rank order, no overlap
+                    covered = hi
+                if not small:
+                    assert lo % 32 == 0 or lo == n
+            assert covered == n, (n, cl)
+            if small:
+                assert r <= 4096 and 4 * r * 8 <= SMEM_OPTIN  # four FP64 slices in shared memory
+            else:
+                assert r % 32 == 0 and r * cl >= n
