@@ -34,20 +34,15 @@ constexpr int kVB = 256;        // block of the vector kernels
 constexpr int kGmKmax = 32;     // largest GMRES restart length (basis held in registers per row)
 constexpr int kMaxRestarts = 3;
 // When a solve replays its iterations as CUDA graphs: systems of at least
-// kGraphFirstSolveRows rows from their first solve on (capturing costs about a
-// millisecond, which one solve of such a system repays), systems of at least
-// kGraphMinRows rows from their second solve on the same matrix.  Mixed CG to
-// 1e-8 on a 27 000-row 7-point stencil took 4.48 ms launched directly and 2.37 ms
-// replaying graphs (BiCGSTAB on 30 000 rows of 20 random columns: 2.02 against
-// 1.18 ms); but a request server that solves every matrix once lost throughput
-// capturing a graph per request (sixteen slots capturing at once: the solve
-// phases of its 25 000 - 100 000-row requests summed to 206 s against 187 s).
+// kGraphMinRows rows, from their second solve on the same matrix (the first
+// launches directly).  Mixed CG to 1e-8 on a 27 000-row 7-point stencil took
+// 4.48 ms launched directly and 2.37 ms replaying graphs (BiCGSTAB on 30 000
+// rows of 20 random columns: 2.02 against 1.18 ms); but a request server that
+// solves every matrix once lost throughput capturing a graph per request
+// (sixteen slots capturing at once: the solve phases of its 25 000 - 100 000-row
+// requests summed to 206 s against 187 s).
 constexpr int64_t kGraphMinRows = 8192;
-constexpr int64_t kGraphFirstSolveRows = 50000;
-bool graphs_for(const spx_matrix *A)
-{
-    return A->n >= kGraphFirstSolveRows || (A->n >= kGraphMinRows && A->solves > 0);
-}
+bool graphs_for(const spx_matrix *A) { return A->n >= kGraphMinRows && A->solves > 0; }
 
 // ------------------------------------------------------------------ GMRES state
 template <class T> struct GState {
