@@ -472,8 +472,8 @@ def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
     number 10 (Peclet 10 * 129), unscaled, where the constant diagonal leaves
     Jacobi nothing to do and the blocks hold the strong upwind couplings along
     x.  b = A x*, tol 1e-10, FP64, CSR.  solve_ms: the median of up to three
-    solves after one that builds the preconditioner and captures the graphs
-    (first_solve_ms)."""
+    solves after one that builds the preconditioner (first_solve_ms); solves
+    from a matrix's second on replay CUDA graphs."""
     import torch
     from paper_2103_10116_gb300 import synth
     rng = np.random.default_rng(21)
@@ -505,7 +505,7 @@ def jacobi_secondary(spx, ctx, stream, dev, max_iter: int = 20000):
                                 ("adaptive_block_jacobi", "_block8_adaptive")):
                     x = torch.zeros(n, dtype=torch.float64, device=dev)
                     first = spx.spx_solve(ctx, A, b, x, solver, 1e-10, max_iter, restart=30, precond=pc,
-                                          block_size=8)  # builds M^-1 and captures the graphs
+                                          block_size=8)  # builds M^-1
                     times = []
                     for _ in range(3 if first.time_ms < 1000 else 1):  # median of up to three timed solves
                         x.zero_()
