@@ -32,7 +32,8 @@ struct spx_batch {
     spx::DBuf work;      // 4 vectors of nrows doubles
     spx::DBuf out;       // per system: status (int), iters (long long), relres (double)
     spx::DBuf queue;     // work-queue counter
-    void *host_out = nullptr;
+    void *host_out = nullptr;          // pinned copy of `out` for the captured graph (made on first use)
+    std::vector<char> host_out_pageable;  // the same for one-shot solves, which copy synchronously
     int block = 0;       // chosen threads per system (0 = not tuned: heuristic)
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[10] = {0};
@@ -272,7 +273,6 @@ extern "C" int spx_batch_create(spx_ctx *ctx, spx_batch **out, int dtype, int64_
             k_cast_f32<<<ctx->grid_sms * 8, 256, 0, ctx->stream>>>(nnz, B->val.as<double>(), B->val32.as<float>());
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaMallocHost(&B->host_out, bout_bytes(nsys) + 64);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "spx_batch_create");
     }
@@ -315,9 +315,15 @@ int batch_solve_impl(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int sol
     std::memcpy(&key[4], &tol, 8);
     bool same = use_graph && B->gexec;
     for (int i = 0; i < 10 && same; ++i) same = B->gkey[i] == key[i];
+    // the result read-back: into pinned memory when it is part of a captured graph;
+    // a one-shot batch (the request server builds one per launch) copies into
+    // pageable memory and spares a pinned allocation per batch
+    if (use_graph && !B->host_out) SPX_CUDA(cudaMallocHost(&B->host_out, out_bytes + 64));
+    if (!use_graph) B->host_out_pageable.resize(out_bytes + 64);
+    void *hout = use_graph ? B->host_out : static_cast<void *>(B->host_out_pageable.data());
     auto body = [&]() -> int {
         SPX_TRY(launch_batch(ctx, B, block, solver, precision, b, x, tol, max_iter));
-        SPX_CUDA(cudaMemcpyAsync(B->host_out, B->out.p, out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        SPX_CUDA(cudaMemcpyAsync(hout, B->out.p, out_bytes, cudaMemcpyDeviceToHost, ctx->stream));
         return SPX_OK;
     };
     if (same) {
@@ -352,7 +358,7 @@ int batch_solve_impl(spx_ctx *ctx, spx_batch *B, const void *b, void *x, int sol
     SPX_CUDA(cudaStreamSynchronize(ctx->stream));
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (infos) {
-        const char *h = static_cast<const char *>(B->host_out);
+        const char *h = static_cast<const char *>(hout);
         const int *stv = reinterpret_cast<const int *>(h);
         const long long *itv = reinterpret_cast<const long long *>(h + bout_off_iters(B->nsys));
         const double *rv = reinterpret_cast<const double *>(h + bout_off_relres(B->nsys));
