@@ -2,8 +2,9 @@
 //
 // Requests (a CSR operator in host memory, a right-hand side, an output
 // buffer, solver settings) enter a FIFO queue.  A request is admitted to a
-// free slot as soon as its device footprint (matrix arrays, FP32 shadow,
-// solver workspace, b and x) fits in what the byte budget has left; while it
+// free slot as soon as its device footprint (matrix arrays, FP32 shadow, the
+// tiled copy of heavy-tailed rows, solver workspace, b and x) fits in what the
+// byte budget has left; while it
 // runs, later requests keep being admitted into the other slots, so solves
 // of different sizes overlap on the GPU.  Each slot is a worker thread with
 // its own context and CUDA stream: the operator is uploaded, solved on the
@@ -93,6 +94,7 @@ struct Request {
     int solver, precision, restart;
     double tol;
     int64_t max_iter;
+    size_t tiled;  // the general path's tile-transposed copy of the nonzeros (heavy-tailed rows), else 0
     size_t footprint;
     Clock::time_point t_submit, t_admit, t_done;
     double upload_ms, setup_ms, solve_ms, download_ms;  // phases after admission
@@ -144,6 +146,27 @@ size_t request_footprint(int64_t n, int64_t nnz, int solver, int precision, int 
     return csr + shadow + vecs + (size_t)n * 16 /* b, x */ + (1u << 20);
 }
 
+// Device bytes of the tile-transposed copy of the nonzeros that the SpMV of a
+// CSR matrix with heavy-tailed rows builds on first use (the automatic kernel
+// choice takes the tiled nnz-split kernel when the longest row exceeds four
+// times the mean plus 8): column indices and FP64 values, the FP32 values as
+// well in mixed precision, padded to whole chunks of 32 x 32 nonzeros, plus the
+// granule descriptors and the list of empty rows.  0 for other matrices, whose
+// kernels read the CSR arrays in place.  row_ptr: the request's n + 1 host row
+// offsets (read only here, before the request is queued).
+size_t tiled_copy_bytes(int64_t n, int64_t nnz, const int32_t *row_ptr, int precision)
+{
+    if (n <= 0 || nnz <= 0) return 0;
+    int64_t mx = 0;
+    for (int64_t i = 0; i < n; ++i) mx = std::max<int64_t>(mx, (int64_t)row_ptr[i + 1] - (int64_t)row_ptr[i]);
+    const double mean = (double)nnz / (double)n;
+    if ((double)mx <= 4.0 * mean + 8.0) return 0;
+    constexpr int64_t kChunk = 32 * 32;
+    const size_t total = (size_t)((nnz + kChunk - 1) / kChunk * kChunk);
+    const size_t per_nz = 4 + 8 + (precision == SPX_PREC_MIXED ? 4 : 0);
+    return total * per_nz + (total / 32 + 1) * 8 + (size_t)n * 4 + 64;
+}
+
 // the same for a request solved on one cluster: its workspace is 64 bytes per row
 size_t cluster_footprint(int64_t n, int64_t nnz, int precision)
 {
@@ -171,6 +194,7 @@ size_t routed_footprint(const Request *R, int base_solver, bool jacobi, int bs, 
 {
     const int64_t nnz = resident ? 0 : R->nnz;
     const size_t general = request_footprint(R->n, nnz, base_solver, R->precision, R->restart) +
+                           (resident ? 0 : R->tiled) +
                            (jacobi ? (size_t)R->n * 24 : 0) +                     // M^-1 and the preconditioned vectors
                            (size_t)R->n * (size_t)bs * (adaptive ? 12 : 8);       // block-Jacobi inverses
     if (!R->one_cluster) return general;
@@ -557,6 +581,7 @@ extern "C" int spx_server_submit_matrix(spx_server *S, spx_matrix *A, const doub
     R->tol = tol;
     R->max_iter = max_iter;
     R->block = 0;
+    R->tiled = 0;  // a resident matrix's own buffers are the caller's
     route_request(S, R, solver, asked, A->format == SPX_CSR && A->rp.p != nullptr);
     // the operator is resident (the caller's); the workspace, b and x are the request's
     R->footprint = routed_footprint(R, base_solver, jacobi, bs, adaptive, true);
@@ -603,6 +628,7 @@ extern "C" int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const in
     R->tol = tol;
     R->max_iter = max_iter;
     route_request(S, R, solver, asked, true);
+    R->tiled = R->batched || (R->one_cluster && !R->cluster_auto) ? 0 : tiled_copy_bytes(n, nnz, row_ptr, precision);
     R->footprint = routed_footprint(R, base_solver, jacobi, bs, adaptive, false);
     R->error = SPX_OK;
     R->t_submit = Clock::now();
