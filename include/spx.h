@@ -401,8 +401,11 @@ int spx_server_create(spx_ctx *ctx, spx_server **out, int64_t budget_bytes, int 
  * admitted (FIFO, as soon as its device footprint fits in the budget) and
  * freed when it completes.  x receives the solution (initial guess 0).
  * solver / tol / max_iter / restart / precision as in spx_solve (MIXED keeps
- * an FP32 copy of the values).  *req_id receives the request id.  Returns at
- * once.  Errors: SPX_ERR_INVALID, SPX_ERR_TOO_LARGE (footprint > budget). */
+ * an FP32 copy of the values).  The footprint counts a second, tile-transposed
+ * copy of the nonzeros when the rows are heavy-tailed (longest row above four
+ * times the mean plus 8), found by reading row_ptr during this call.  *req_id
+ * receives the request id.  Returns at once.  Errors: SPX_ERR_INVALID,
+ * SPX_ERR_TOO_LARGE (footprint > budget). */
 int spx_server_submit(spx_server *S, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                       const double *values, const double *b, double *x, int solver, double tol, int64_t max_iter,
                       int restart, int precision, int64_t *req_id);
