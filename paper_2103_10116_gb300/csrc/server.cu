@@ -2,9 +2,9 @@
 //
 // Requests (a CSR operator in host memory, a right-hand side, an output
 // buffer, solver settings) enter a FIFO queue.  A request is admitted to a
-// free slot as soon as its device footprint (matrix arrays, FP32 shadow, the
-// tiled copy of heavy-tailed rows, solver workspace, b and x) fits in what the
-// byte budget has left; while it
+// free slot as soon as its device footprint (the uploaded matrix arrays and
+// the library's copy, FP32 shadow, the tiled copy of heavy-tailed rows, solver
+// workspace, b and x) fits in what the byte budget has left; while it
 // runs, later requests keep being admitted into the other slots, so solves
 // of different sizes overlap on the GPU.  Each slot is a worker thread with
 // its own context and CUDA stream: the operator is uploaded, solved on the
@@ -133,11 +133,16 @@ struct spx_server {
 
 namespace spx {
 
-// device bytes a request needs while it runs (upper estimate)
-size_t request_footprint(int64_t n, int64_t nnz, int solver, int precision, int restart)
+// Device bytes a request needs while it runs (upper estimate).  An uploaded
+// operator counts twice: the worker's upload buffers and the library's own
+// copy of the matrix coexist while the matrix is built (the upload buffers are
+// freed before the solve allocates its workspace; counting both at once keeps
+// the estimate an upper bound).  A resident operator (uploaded = false) is the
+// caller's and counts nothing.
+size_t request_footprint(int64_t n, int64_t nnz, bool uploaded, int solver, int precision, int restart)
 {
-    const size_t csr = (size_t)nnz * 12 + (size_t)(n + 1) * 4;
-    const size_t shadow = precision == SPX_PREC_MIXED ? (size_t)nnz * 4 : 0;
+    const size_t csr = uploaded ? 2 * ((size_t)nnz * 12 + (size_t)(n + 1) * 4) : 0;
+    const size_t shadow = uploaded && precision == SPX_PREC_MIXED ? (size_t)nnz * 4 : 0;
     size_t vecs;
     const size_t V = precision == SPX_PREC_F32 ? 4 : 8;
     const int nv = solver == SPX_CG ? 4 : solver == SPX_BICGSTAB ? 7 : solver == SPX_CGS ? 8 : restart + 2;
@@ -168,10 +173,10 @@ size_t tiled_copy_bytes(int64_t n, int64_t nnz, const int32_t *row_ptr, int prec
 }
 
 // the same for a request solved on one cluster: its workspace is 64 bytes per row
-size_t cluster_footprint(int64_t n, int64_t nnz, int precision)
+size_t cluster_footprint(int64_t n, int64_t nnz, bool uploaded, int precision)
 {
-    const size_t csr = (size_t)nnz * 12 + (size_t)(n + 1) * 4;
-    const size_t shadow = precision == SPX_PREC_MIXED ? (size_t)nnz * 4 : 0;
+    const size_t csr = uploaded ? 2 * ((size_t)nnz * 12 + (size_t)(n + 1) * 4) : 0;
+    const size_t shadow = uploaded && precision == SPX_PREC_MIXED ? (size_t)nnz * 4 : 0;
     return csr + shadow + (size_t)n * 64 + (size_t)n * 16 + (1u << 20);
 }
 
@@ -192,13 +197,12 @@ void route_request(spx_server *S, Request *R, int code, bool asked, bool csr)
 // route waits for its row statistics reserves the larger of the two.
 size_t routed_footprint(const Request *R, int base_solver, bool jacobi, int bs, bool adaptive, bool resident)
 {
-    const int64_t nnz = resident ? 0 : R->nnz;
-    const size_t general = request_footprint(R->n, nnz, base_solver, R->precision, R->restart) +
+    const size_t general = request_footprint(R->n, R->nnz, !resident, base_solver, R->precision, R->restart) +
                            (resident ? 0 : R->tiled) +
                            (jacobi ? (size_t)R->n * 24 : 0) +                     // M^-1 and the preconditioned vectors
                            (size_t)R->n * (size_t)bs * (adaptive ? 12 : 8);       // block-Jacobi inverses
     if (!R->one_cluster) return general;
-    const size_t cl = cluster_footprint(R->n, nnz, R->precision);
+    const size_t cl = cluster_footprint(R->n, R->nnz, !resident, R->precision);
     return R->cluster_auto ? std::max(cl, general) : cl;
 }
 
