@@ -202,7 +202,9 @@ int spx_ctx_check(spx_ctx *ctx);
 int spx_matrix_create(spx_ctx *ctx, spx_matrix **out, int format, int dtype, int64_t nrows,
                       int64_t ncols, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                       const void *values, int values_dtype, int64_t hyb_width, unsigned flags);
-/* Free a matrix and all its device arrays (ordered on the creating context's stream). */
+/* Free a matrix and all its device arrays (ordered on the creating context's
+ * stream).  Work on A issued on another context's stream must have completed
+ * first (synchronise that stream). */
 int spx_matrix_destroy(spx_matrix *A);
 
 typedef struct {

@@ -298,7 +298,7 @@ int cluster_cg_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, double
                      spx_solve_info *info)
 {
     if (A->format != SPX_CSR || !A->rp.p || A->n < 1 || A->n > cluster_cg_max_rows()) return SPX_ERR_UNSUPPORTED;
-    if (!A->small_out.p) SPX_TRY(dbuf_alloc(A->ctx, A->small_out, kOutBytes));
+    if (!A->small_out.p) SPX_TRY(dbuf_alloc(ctx, A->small_out, kOutBytes));  // stream-ordered with its use
     ClOut *out = A->small_out.as<ClOut>();
     const int st = A->dtype == SPX_F64
                        ? cluster_cg_typed<double>(ctx, A, static_cast<const double *>(b), static_cast<double *>(x),
@@ -457,8 +457,8 @@ int cluster_solve(spx_ctx *ctx, spx_matrix *A, const void *b, void *x, int solve
     if (!mixed && (precision == SPX_PREC_F64 ? SPX_F64 : SPX_F32) != A->dtype)
         return fail(SPX_ERR_UNSUPPORTED, "precision must match the matrix dtype (or use MIXED)");
     if (A->n > (int64_t)1 << 30) return fail(SPX_ERR_TOO_LARGE, "the one-cluster solve takes at most 2^30 rows");
-    if (!A->small_out.p) SPX_TRY(dbuf_alloc(A->ctx, A->small_out, kOutBytes));
-    if (!A->cl_work.p) SPX_TRY(dbuf_alloc(A->ctx, A->cl_work, (size_t)A->n * 64));
+    if (!A->small_out.p) SPX_TRY(dbuf_alloc(ctx, A->small_out, kOutBytes));  // stream-ordered with its use
+    if (!A->cl_work.p) SPX_TRY(dbuf_alloc(ctx, A->cl_work, (size_t)A->n * 64));
     SysOut *out = reinterpret_cast<SysOut *>(A->small_out.p);
     int st;
     if (mixed)
